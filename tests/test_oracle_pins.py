@@ -1,0 +1,482 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a published
+known-answer vector, the paper's worked example, a closed-form solution, a
+conservation law, a textbook average or brute force on tiny inputs.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_09642_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+QE, ME, EPS0, KB = 1.602176634e-19, 9.1093837015e-31, 8.8541878128e-12, 1.380649e-23
+MAR = 39.948 * 1.66053906660e-27
+
+
+def _quiet(**kw):
+    """A discharge with no drive and no space charge (W = 0): E = 0 exactly."""
+    base = dict(weight=0.0, harmonics=((0.0, 0.0),), n_grid=101, capacity=1 << 17)
+    base.update(kw)
+    return wl.Discharge(**base)
+
+
+def _tables(n=200_000, de=1e-3, **kw):
+    return wl.constant_cross_sections(n, de, **kw)
+
+
+# ------------------------------------------------------------------ RNG
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        out = oracle.philox4x32_10(v[0:4], v[4:6])
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_uniform_ranges():
+    assert oracle.u53(0, 0) == 0.0
+    assert oracle.u53(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    assert oracle.u53(0x80000000, 0) == 0.5
+    assert oracle.u24(0) == 0.0
+    assert oracle.u24(0xFFFFFFFF) == np.float32(1.0 - 2.0 ** -24)
+    assert oracle.u24(0x80000000) == 0.5
+
+
+# ------------------------------------------------------------------ derived quantities (Table 1/2)
+def test_reference_discharge_derived():
+    d = wl.reference_discharge()
+    se, si = _tables(1000)
+    s = oracle.Sim(d, se, si, 1e-3)
+    dv = s.derived()
+    assert dv["dx"] == pytest.approx(0.025 / 399, rel=1e-15)
+    assert dv["dt_e"] == pytest.approx(1.0 / (13.56e6 * 4000), rel=1e-15)
+    assert dv["dt_i"] == pytest.approx(20.0 / (13.56e6 * 4000), rel=1e-15)
+    assert dv["n_gas"] == pytest.approx(10.0 / (KB * 350.0), rel=1e-15)
+    # printed magnitudes: dx = 6.266e-5 m, dt_e = 1.8437e-11 s, n = 2.069e21 m^-3
+    assert abs(dv["dx"] - 6.266e-5) < 1e-8
+    assert abs(dv["dt_e"] - 1.8437e-11) < 1e-15
+    assert abs(dv["n_gas"] - 2.069e21) < 1e18
+
+
+# ------------------------------------------------------------------ deposition (Sec. 2.1.1, Alg. 2)
+def test_weight_density_worked_example():
+    g = {}
+    for l in open(os.path.join(GOLDEN, "weight_density_example.txt")):
+        if l.strip() and l[0] != "#":
+            k, v = l.split()
+            g[k] = float(v)
+    n, L, A, W = int(g["n_particles"]), g["gap_m"], g["area_m2"], g["weight"]
+    ng = 251
+    dx = L / (ng - 1)
+    x = (np.arange(n) + 0.5) * (L / n)
+    dens = oracle.deposit_paper(x, ng, 1.0 / dx, W / (A * dx))
+    vol = np.full(ng, A * dx)
+    vol[0] = vol[-1] = A * dx / 2
+    mean = (dens * vol).sum() / (A * L)
+    assert mean == pytest.approx(g["mean_density_m3"], rel=1e-12)
+
+
+def test_deposit_single_particle_brute_force():
+    ng, L = 11, 1.0
+    dx = L / (ng - 1)
+    for x in (0.0, 0.05, 0.37, 0.5, 0.999, 1.0):
+        dens = oracle.deposit_paper([x], ng, 1.0 / dx, 1.0)
+        p = min(int(x / dx), ng - 2)
+        w1 = (p + 1) - x / dx
+        expect = np.zeros(ng)
+        expect[p] += w1
+        expect[p + 1] += 1 - w1
+        expect[0] *= 2
+        expect[-1] *= 2
+        assert np.allclose(dens, expect, atol=1e-15), x
+
+
+def test_deposit_total_weight_and_fixed_point():
+    rng = np.random.default_rng(3)
+    ng, L, W, A = 400, 0.025, 7e4, 1e-4
+    dx = L / (ng - 1)
+    x = rng.uniform(0, L, 20_000)
+    x[:3] = [0.0, L, L * 0.5]
+    fw = W / (A * dx)
+    dens = oracle.deposit_paper(x, ng, 1.0 / dx, fw)
+    vol = np.full(ng, A * dx)
+    vol[0] = vol[-1] = A * dx / 2
+    assert (dens * vol).sum() == pytest.approx(W * x.size, rel=1e-12)
+    q = oracle.deposit_fixed(x, ng, 1.0 / dx)
+    assert int(q.sum()) == x.size * 2 ** 32          # exact: each particle is 2^32 units
+    assert (q >= 0).all()
+    dens_q = oracle.density_from_fixed(q, fw)
+    # fixed-point rounding is at most 1/2 unit of 2^-32 per particle and point
+    cnt = np.bincount(np.minimum((x / dx).astype(int), ng - 2), minlength=ng)
+    per_point = cnt + np.concatenate([[0], cnt[:-1]])
+    bound = fw * (per_point + 1) * 2.0 ** -33 * 2 + 1e-6
+    assert (np.abs(dens_q - dens) <= bound).all()
+
+
+def test_deposit_fixed_f32_matches_f64_on_exact_positions():
+    ng, L = 64, 1.0
+    dx = L / (ng - 1)
+    x = (np.arange(1, 500) / 512.0).astype(np.float32)  # exactly representable
+    q32 = oracle.deposit_fixed_f32(x, ng, np.float32(1.0 / dx))
+    assert int(q32.sum()) == x.size * 2 ** 32
+    q64 = oracle.deposit_fixed(x.astype(np.float64), ng, 1.0 / dx)
+    # the same cell for every particle, splits within FP32 rounding
+    assert np.abs(q32 - q64).max() < 2 ** 32 * 1e-5 * 8
+
+
+# ------------------------------------------------------------------ Poisson (Sec. 2.1.2, Alg. 3)
+@pytest.mark.parametrize("ng", [3, 7, 400, 801])
+def test_poisson_uniform_charge_parabola(ng):
+    L, V, rho0 = 0.025, 250.0, 3e-4
+    dx = L / (ng - 1)
+    x = np.arange(ng) * dx
+    phi, ef = oracle.poisson(np.full(ng, rho0), dx, V)
+    exact = V * (1 - x / L) + rho0 * x * (L - x) / (2 * EPS0)
+    scale = np.abs(exact).max()
+    assert np.abs(phi - exact).max() <= 1e-12 * scale
+    e_exact = V / L - rho0 * (L - 2 * x) / (2 * EPS0)   # E = -dphi/dx, exact also at the electrodes
+    assert np.abs(ef - e_exact).max() <= 1e-10 * np.abs(e_exact).max()
+
+
+def test_poisson_satisfies_discrete_equation():
+    rng = np.random.default_rng(5)
+    ng, L, V = 400, 0.025, -117.0
+    dx = L / (ng - 1)
+    rho = rng.normal(0, 1e-4, ng)
+    phi, ef = oracle.poisson(rho, dx, V)
+    assert phi[0] == V and phi[-1] == 0.0
+    lhs = (-phi[:-2] + 2 * phi[1:-1] - phi[2:]) / dx ** 2
+    assert np.abs(lhs - rho[1:-1] / EPS0).max() <= 1e-9 * np.abs(rho / EPS0).max()
+    assert np.allclose(ef[1:-1], (phi[:-2] - phi[2:]) / (2 * dx), rtol=0, atol=1e-12 * np.abs(ef).max())
+    assert ef[0] == pytest.approx((phi[0] - phi[1]) / dx - rho[0] * dx / (2 * EPS0), rel=1e-14)
+
+
+# ------------------------------------------------------------------ leapfrog (Sec. 2.1.4, Alg. 4)
+def test_leapfrog_uniform_field_closed_form():
+    V = 0.02  # E = 0.8 V/m: electrons move ~2 mm in 1e4 steps
+    d = _quiet(harmonics=((0.0, V),), gap_m=0.025)
+    se, si = _tables(1000, sigma_e=(0, 0, 0), sigma_i=(0, 0))
+    rng = np.random.default_rng(7)
+    n = 64
+    x0 = rng.uniform(0.010, 0.015, n)
+    v0 = rng.uniform(-2e3, 2e3, n)
+    e = wl.Particles(x0.copy(), v0.copy(), np.zeros(n), np.zeros(n))
+    i = wl.Particles(x0.copy(), (v0 / 50).copy(), np.zeros(n), np.zeros(n))
+    s = oracle.Sim(d, se, si, 1e-3, e, i)
+    dv = s.derived()
+    nsteps = 10_000
+    s.step(nsteps)
+    E = V / d.gap_m
+    a_e = -QE * E / ME
+    dt = dv["dt_e"]
+    x, vx, _, _ = s.particles(0)
+    k = nsteps
+    xe = x0 + k * v0 * dt + a_e * dt * dt * k * (k + 1) / 2
+    ve = v0 + k * a_e * dt
+    assert s.count(0) == n
+    assert np.abs(x - xe).max() <= 1e-12 * np.abs(xe).max()
+    assert np.abs(vx - ve).max() <= 1e-12 * np.abs(ve).max()
+    # ions: pushed every N_SUB-th step with dt_i
+    a_i = QE * E / MAR
+    dti = dv["dt_i"]
+    ki = nsteps // d.ion_subcycle
+    xi, vxi, _, _ = s.particles(1)
+    xie = x0 + ki * (v0 / 50) * dti + a_i * dti * dti * ki * (ki + 1) / 2
+    assert np.abs(xi - xie).max() <= 1e-12 * np.abs(xie).max()
+    vie = (v0 / 50) + ki * a_i * dti
+    assert np.abs(vxi - vie).max() <= 1e-12 * np.abs(vie).max()
+
+
+# ------------------------------------------------------------------ boundaries (Sec. 2.1.5, Alg. 5)
+def test_absorption_and_canonical_compaction():
+    d = _quiet(gap_m=1.0, n_grid=11)
+    se, si = _tables(1000, sigma_e=(0, 0, 0), sigma_i=(0, 0))
+    s = oracle.Sim(d, se, si, 1e-3)
+    dt = s.derived()["dt_e"]
+    n = 10
+    x = np.full(n, 0.5)
+    vx = np.zeros(n)
+    # slots 1 and 8 leave through x < 0 and x > L; slot 9 (tail) also leaves
+    x[1], vx[1] = 1e-9, -1e3 / dt * 1e-6
+    x[8], vx[8] = 1 - 1e-9, 1e3 / dt * 1e-6
+    x[9], vx[9] = 1 - 1e-9, 1e3 / dt * 1e-6
+    x += np.arange(n) * 1e-3 * (vx == 0)
+    s.load(0, wl.Particles(x, vx, np.arange(n, dtype=float), np.zeros(n)))
+    s.load(1, wl.Particles.empty())
+    s.step(1)
+    c = s.counters()
+    assert c["abs_e_pow"] == 1 and c["abs_e_gnd"] == 2
+    xs, _, vy, _ = s.particles(0)
+    # N' = 7: hole 1 is filled by the first tail survivor (slot 7)
+    assert list(vy) == [0, 7, 2, 3, 4, 5, 6]
+
+
+# ------------------------------------------------------------------ collisions (Sec. 2.1.6, Alg. 6)
+def _unit_sim(se=None, si=None, n=200_000, de=1e-3):
+    d = wl.reference_discharge()
+    if se is None:
+        se, si = wl.standin_cross_sections(n, de)
+    return oracle.Sim(d, se, si, de)
+
+
+def _com_parts(v1, v2, m1, m2):
+    w = (m1 * v1 + m2 * v2) / (m1 + m2)
+    return w, v1 - v2
+
+
+def test_process_selection_partition():
+    se, si = wl.standin_cross_sections(100_000, 1e-3)
+    s = _unit_sim(se, si)
+    k = 50_000  # 50 eV: all three processes open
+    u = (np.arange(100_000) + 0.5) / 100_000
+    picks = np.array([s.select_process(0, k, float(x)) for x in u])
+    frac = np.bincount(picks, minlength=3) / u.size
+    assert np.allclose(frac, se[:, k] / se[:, k].sum(), atol=2e-5)
+    picks_i = np.array([s.select_process(1, 3000, float(x)) for x in u])
+    assert np.allclose(np.bincount(picks_i, minlength=2) / u.size, si[:, 3000] / si[:, 3000].sum(), atol=2e-5)
+
+
+def test_elastic_electron_conservation_and_angle():
+    se, si = _tables(100_000, sigma_e=(1e-19, 0, 0))
+    s = _unit_sim(se, si)
+    rng = np.random.default_rng(11)
+    mu = ME * MAR / (ME + MAR)
+    loss = []
+    for _ in range(4000):
+        v = rng.normal(0, 6e5, 3)
+        uc, ue = rng.random(), rng.random()
+        proc, v1, _ = s.collide_electron(100, v, 0.3, uc, ue, 0.5)
+        assert proc == 0
+        v2p = (ME * v - ME * v1) / MAR                   # atom recoil from momentum conservation
+        ke0 = 0.5 * ME * v @ v
+        ke1 = 0.5 * ME * v1 @ v1 + 0.5 * MAR * v2p @ v2p
+        assert ke1 == pytest.approx(ke0, rel=1e-10)
+        w, g = _com_parts(v, np.zeros(3), ME, MAR)
+        gp = (v1 - w) * (ME + MAR) / MAR
+        assert np.linalg.norm(gp) == pytest.approx(np.linalg.norm(g), rel=1e-12)
+        cos_chi = gp @ g / (np.linalg.norm(gp) * np.linalg.norm(g))
+        assert cos_chi == pytest.approx(1 - 2 * uc, abs=1e-10)
+        loss.append((ke0 - 0.5 * ME * v1 @ v1) / ke0)
+    # textbook: mean fractional energy loss for isotropic scattering on a
+    # target at rest is 2 m M / (m + M)^2
+    expect = 2 * ME * MAR / (ME + MAR) ** 2
+    assert np.mean(loss) == pytest.approx(expect, rel=0.06)
+    assert mu > 0
+
+
+def test_isotropy_of_deflection():
+    se, si = _tables(100_000, sigma_e=(1e-19, 0, 0))
+    s = _unit_sim(se, si)
+    rng = np.random.default_rng(12)
+    v = np.array([3e5, -2e5, 4e5])
+    dirs = []
+    for _ in range(3000):
+        _, v1, _ = s.collide_electron(100, v, 0.1, rng.random(), rng.random(), 0.5)
+        w = ME * v / (ME + MAR)
+        dirs.append((v1 - w) / np.linalg.norm(v1 - w))
+    dirs = np.array(dirs)
+    # isotropic unit vectors: each Cartesian component is uniform on [-1, 1]
+    from scipy import stats
+    for c in range(3):
+        assert stats.kstest(dirs[:, c], "uniform", args=(-1, 2)).pvalue > 1e-3
+
+
+def test_excitation_energy_loss():
+    se, si = _tables(100_000, sigma_e=(0, 1e-19, 0))
+    s = _unit_sim(se, si)
+    rng = np.random.default_rng(13)
+    mu = ME * MAR / (ME + MAR)
+    for _ in range(500):
+        v = rng.normal(0, 1.6e6, 3)
+        eps_c = 0.5 * mu * (v @ v) / QE
+        proc, v1, _ = s.collide_electron(100, v, 0.5, rng.random(), rng.random(), 0.5)
+        w, g = _com_parts(v, np.zeros(3), ME, MAR)
+        gp = (v1 - w) * (ME + MAR) / MAR
+        if eps_c > 11.5:
+            assert proc == 1
+            assert 0.5 * mu * (gp @ gp) / QE == pytest.approx(eps_c - 11.5, rel=1e-9, abs=1e-9)
+        else:  # below threshold: executed as elastic
+            assert proc == 0
+            assert np.linalg.norm(gp) == pytest.approx(np.linalg.norm(g), rel=1e-12)
+
+
+def test_ionization_energy_sharing():
+    se, si = _tables(100_000, sigma_e=(0, 0, 1e-19))
+    s = _unit_sim(se, si)
+    rng = np.random.default_rng(14)
+    mu = ME * MAR / (ME + MAR)
+    eps0 = 60.0
+    vmag = math.sqrt(2 * eps0 * QE / mu)
+    ee = []
+    for _ in range(3000):
+        d = rng.normal(size=3)
+        v = vmag * d / np.linalg.norm(d)
+        uo = rng.random()
+        proc, v1, vej = s.collide_electron(100, v, 0.5, 0.3, rng.random(), uo)
+        assert proc == 2
+        w, g = _com_parts(v, np.zeros(3), ME, MAR)
+        gp = (v1 - w) * (ME + MAR) / MAR
+        e_s = 0.5 * mu * (gp @ gp) / QE
+        e_e = 0.5 * ME * (vej @ vej) / QE
+        avail = 0.5 * mu * (v @ v) / QE - 15.8
+        assert e_s + e_e == pytest.approx(avail, rel=1e-10)
+        # angles: cos(chi) = sqrt(eps / (eps - eps_ion)) for both electrons
+        gh = g / np.linalg.norm(g)
+        assert gp @ gh / np.linalg.norm(gp) == pytest.approx(math.sqrt(e_s / avail), abs=1e-9)
+        assert vej @ gh / np.linalg.norm(vej) == pytest.approx(math.sqrt(e_e / avail), abs=1e-9)
+        # azimuths differ by pi: the perpendicular parts are antiparallel
+        ps = gp - (gp @ gh) * gh
+        pe = vej - (vej @ gh) * gh
+        if np.linalg.norm(ps) > 1e-6 * np.linalg.norm(gp) and np.linalg.norm(pe) > 1e-6 * np.linalg.norm(vej):
+            assert ps @ pe / (np.linalg.norm(ps) * np.linalg.norm(pe)) == pytest.approx(-1.0, abs=1e-9)
+        ee.append(e_e)
+    # Opal distribution: F(e) = atan(e / w) / atan(avail / (2 w)) on [0, avail / 2]
+    from scipy import stats
+    avail = 0.5 * mu * vmag ** 2 / QE - 15.8
+    cdf = lambda e: np.arctan(np.asarray(e) / 10.0) / math.atan(avail / 20.0)
+    assert max(ee) <= avail / 2 + 1e-9
+    assert stats.kstest(ee, cdf).pvalue > 1e-3
+
+
+def test_ion_backward_gives_partner_velocity_and_isotropic_conserves():
+    se, si = _tables(100_000, sigma_i=(0.0, 1e-19))
+    s = _unit_sim(se, si)
+    rng = np.random.default_rng(15)
+    for _ in range(200):
+        v = rng.normal(0, 3e3, 3)
+        va = rng.normal(0, 300, 3)
+        proc, v1 = s.collide_ion(10, v, va, 0.5, rng.random(), rng.random())
+        assert proc == 1
+        assert np.abs(v1 - va).max() <= 1e-12 * np.abs(v).max()
+    se, si = _tables(100_000, sigma_i=(1e-19, 0.0))
+    s = _unit_sim(se, si)
+    for _ in range(200):
+        v = rng.normal(0, 3e3, 3)
+        va = rng.normal(0, 300, 3)
+        proc, v1 = s.collide_ion(10, v, va, 0.5, rng.random(), rng.random())
+        assert proc == 0
+        v2p = v + va - v1                                  # equal masses: momentum
+        assert v1 @ v1 + v2p @ v2p == pytest.approx(v @ v + va @ va, rel=1e-10)
+
+
+def test_electron_collision_rate_constant_nu():
+    # constant sigma, field off, mono-energetic: P = 1 - exp(-n sigma v dt) per step
+    n, steps = 40_000, 4
+    d = _quiet(gap_m=0.025, n_grid=51, capacity=1 << 17)
+    sig = 2e-18
+    se, si = _tables(100_000, sigma_e=(sig, 0, 0), sigma_i=(0, 0))
+    s = oracle.Sim(d, se, si, 1e-3)
+    rng = np.random.default_rng(16)
+    eps = 1.0
+    v = math.sqrt(2 * eps * QE / ME)
+    dirs = rng.normal(size=(3, n))
+    dirs /= np.linalg.norm(dirs, axis=0)
+    e = wl.Particles(rng.uniform(0.010, 0.015, n), v * dirs[0], v * dirs[1], v * dirs[2])
+    s.load(0, e)
+    s.load(1, wl.Particles.empty())
+    s.step(steps)
+    hits = s.counters()["coll_e_ela"]
+    dv = s.derived()
+    p = 1 - math.exp(-dv["n_gas"] * sig * v * dv["dt_e"])
+    mean, sd = n * steps * p, math.sqrt(n * steps * p * (1 - p))
+    assert abs(hits - mean) < 4.5 * sd
+
+
+def test_electron_collision_rate_sigma_inverse_velocity():
+    # sigma ~ 1/v gives a velocity-independent collision frequency
+    nent, de = 100_000, 1e-3
+    energies = np.arange(nent) * de
+    energies[0] = de / 2
+    c = 1e-18 * math.sqrt(2 * 1.0 * QE / ME)
+    sig = c / np.sqrt(2 * energies * QE / ME)
+    se = np.stack([sig, 0 * sig, 0 * sig])
+    si = np.zeros((2, nent))
+    d = _quiet(gap_m=0.025, n_grid=51, capacity=1 << 17)
+    rates = []
+    for eps in (0.5, 4.0, 20.0):
+        s = oracle.Sim(d, se, si, de)
+        rng = np.random.default_rng(int(eps * 10))
+        n = 30_000
+        v = math.sqrt(2 * eps * QE / ME)
+        dirs = rng.normal(size=(3, n))
+        dirs /= np.linalg.norm(dirs, axis=0)
+        s.load(0, wl.Particles(rng.uniform(0.012, 0.013, n), v * dirs[0], v * dirs[1], v * dirs[2]))
+        s.load(1, wl.Particles.empty())
+        s.step(2)
+        rates.append(s.counters()["coll_e_ela"] / (2 * n))
+    assert max(rates) - min(rates) < 5 * math.sqrt(rates[0] / 60_000)
+
+
+def test_ion_thermalisation():
+    # Ar+ in Ar at E = 0 relaxes to <M v^2 / 2> = 3/2 k T_g
+    d = _quiet(gap_m=0.05, n_grid=51, ion_subcycle=1, steps_per_cycle=40)
+    se, si = _tables(100_000, sigma_e=(0, 0, 0), sigma_i=(4e-17, 4e-17))
+    s = oracle.Sim(d, se, si, 1e-3)
+    n = 6000
+    rng = np.random.default_rng(17)
+    s.load(0, wl.Particles.empty())
+    s.load(1, wl.Particles(rng.uniform(0.02, 0.03, n), np.full(n, 2000.0), np.zeros(n), np.zeros(n)))
+    s.step(400)
+    _, vx, vy, vz = s.particles(1)
+    mean_e = 0.5 * MAR * np.mean(vx ** 2 + vy ** 2 + vz ** 2)
+    assert s.counters()["coll_i_iso"] > 20 * n
+    assert mean_e == pytest.approx(1.5 * KB * d.gas_temp_k, rel=0.05)
+
+
+# ------------------------------------------------------------------ bookkeeping and diagnostics
+def test_particle_bookkeeping_reference_start():
+    d, e, i = wl.reference_start(seed=2, n0=1500)
+    se, si = wl.standin_cross_sections(300_000)
+    s = oracle.Sim(d, se, si, wl.CS_DE_EV, e, i)
+    ne0, ni0 = s.count(0), s.count(1)
+    s.step(400)
+    c = s.counters()
+    assert s.count(0) == ne0 - c["abs_e_pow"] - c["abs_e_gnd"] + c["created"]
+    assert s.count(1) == ni0 - c["abs_i_pow"] - c["abs_i_gnd"] + c["created"]
+    assert c["coll_e_ela"] > 0 and c["abs_e_pow"] + c["abs_e_gnd"] > 0
+
+
+def test_eepf_normalisation_and_maxwellian_slope():
+    d = _quiet(gap_m=0.025, n_grid=51, capacity=1 << 18, eepf_bins=400, eepf_de_ev=0.05)
+    se, si = _tables(100_000, sigma_e=(0, 0, 0), sigma_i=(0, 0))
+    s = oracle.Sim(d, se, si, 1e-3)
+    rng = np.random.default_rng(18)
+    kt = 2.0
+    n = 200_000
+    e = wl.maxwellian(n, d.gap_m, kt * QE, ME, rng, x=rng.uniform(0.46 * d.gap_m, 0.54 * d.gap_m, n))
+    s.load(0, e)
+    s.load(1, wl.Particles.empty())
+    s.step(1, measure=True)
+    h = s.diagnostics()["eepf_counts"]
+    assert h.sum() == n - (0.5 * ME * (e.vx ** 2 + e.vy ** 2 + e.vz ** 2) / QE >= 20.0).sum()
+    en, f = oracle.eepf_normalise(h, d.eepf_de_ev)
+    assert (f * np.sqrt(en) * d.eepf_de_ev).sum() == pytest.approx(1.0, rel=1e-12)
+    m = (en > 0.5) & (en < 8.0)
+    slope = np.polyfit(en[m], np.log(f[m]), 1, w=np.sqrt(h[m]))[0]
+    assert slope == pytest.approx(-1.0 / kt, rel=0.04)
+
+
+def test_ifed_normalisation_and_energy():
+    d = _quiet(gap_m=0.025, n_grid=51, ion_subcycle=1, ifed_bins=200, ifed_de_ev=1.0)
+    se, si = _tables(1000, sigma_e=(0, 0, 0), sigma_i=(0, 0))
+    s = oracle.Sim(d, se, si, 1e-3)
+    dt = s.derived()["dt_i"]
+    n = 300
+    e_ev = np.linspace(0.2, 150.0, n)
+    v = np.sqrt(2 * e_ev * QE / MAR)
+    x = np.full(n, 1e-12)
+    s.load(0, wl.Particles.empty())
+    s.load(1, wl.Particles(x, -v, np.zeros(n), np.zeros(n)))
+    s.step(1, measure=True)
+    hp = s.diagnostics()["ifed_pow_counts"]
+    assert s.counters()["abs_i_pow"] == n
+    assert (hp == np.bincount(np.floor(e_ev).astype(int), minlength=200)).all()
+    en, F = oracle.ifed_normalise(hp, 1.0)
+    assert (F * 1.0).sum() == pytest.approx(1.0, rel=1e-12)
+    assert dt > 0

@@ -1,0 +1,211 @@
+/*
+ * edupic.h -- C ABI of the GB300 (sm_103a) PIC/MCC particle-loop library.
+ *
+ * The library steps one or more independent 1D3V electrostatic PIC/MCC
+ * simulations of argon capacitively coupled plasmas (Donko et al., arXiv
+ * 2103.09642): leapfrog push (Sec. 2.1.4, Algorithm 4), linear-weighting
+ * deposition (Sec. 2.1.1, Algorithm 2), electrode absorption with compaction
+ * (Sec. 2.1.5, Algorithm 5), e- + Ar and Ar+ + Ar Monte Carlo collisions
+ * (Sec. 2.1.6, Algorithm 6) with ion subcycling (Sec. 2.1), around a 1D
+ * Poisson solve (Sec. 2.1.2, Algorithm 3).  Every step runs in hand-written
+ * CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *  - Return EDUPIC_OK (0) on success or a negative EDUPIC_E* status.
+ *  - Pointers documented as "host" are host memory owned by the caller and
+ *    only read/written during the call.  Pointers documented as "device" are
+ *    CUDA device memory owned by the caller.
+ *  - Work is enqueued on the stream given at creation.  Calls that return
+ *    host data synchronise that stream first; edupic_step / edupic_run_cycles
+ *    only enqueue.  Errors found on the device (capacity overflow, non-finite
+ *    particle data) are reported by the next synchronising call.
+ *  - A simulation object is not thread-safe.  Distinct objects may be used
+ *    from distinct threads on distinct streams.
+ */
+#ifndef EDUPIC_H
+#define EDUPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define EDUPIC_OK 0
+#define EDUPIC_EINVAL (-1)    /* invalid argument or parameter set */
+#define EDUPIC_ENOMEM (-2)    /* arena too small / HBM budget exceeded */
+#define EDUPIC_ECAPACITY (-3) /* particle, hole or product capacity exceeded */
+#define EDUPIC_ECUDA (-4)     /* a CUDA runtime call failed */
+#define EDUPIC_ESTATE (-5)    /* call not valid in the current state */
+#define EDUPIC_ENAN (-6)      /* non-finite particle position found */
+#define EDUPIC_EIO (-7)       /* checkpoint file could not be read/written */
+#define EDUPIC_ETIMEOUT (-8)  /* bounded wait expired */
+
+/* ---------------------------------------------------------------- enums */
+#define EDUPIC_FP64 0 /* particles, push and collisions in FP64 */
+#define EDUPIC_FP32 1 /* particles, push and collisions in FP32; field and diagnostics FP64 */
+
+#define EDUPIC_ELECTRONS 0
+#define EDUPIC_IONS 1
+
+#define EDUPIC_MAX_HARMONICS 4
+#define EDUPIC_MAX_GRID 2048       /* largest N_G */
+#define EDUPIC_MAX_EEPF_BINS 2048
+#define EDUPIC_MAX_IFED_BINS 4096
+#define EDUPIC_MAX_DISCHARGES 1024 /* discharges per simulation object */
+#define EDUPIC_STEP_EVENTS 8192    /* absorbed particles (per species) and ionisations per step and discharge */
+#define EDUPIC_N_COUNTERS 16
+
+/* counter indices for edupic_get_counters */
+#define EDUPIC_C_ABS_E_POW 0    /* electrons absorbed at the powered electrode (x < 0) */
+#define EDUPIC_C_ABS_E_GND 1    /* electrons absorbed at the grounded electrode (x > L) */
+#define EDUPIC_C_ABS_I_POW 2
+#define EDUPIC_C_ABS_I_GND 3
+#define EDUPIC_C_COLL_E_ELA 4   /* e- + Ar elastic */
+#define EDUPIC_C_COLL_E_EXC 5   /* e- + Ar excitation */
+#define EDUPIC_C_COLL_E_ION 6   /* e- + Ar ionisation */
+#define EDUPIC_C_COLL_I_ISO 7   /* Ar+ + Ar isotropic */
+#define EDUPIC_C_COLL_I_BACK 8  /* Ar+ + Ar backward */
+#define EDUPIC_C_SUBTHRESHOLD 9 /* inelastic picks below threshold, executed as elastic */
+#define EDUPIC_C_CREATED 10     /* e-/Ar+ pairs created by ionisation */
+#define EDUPIC_C_DROPPED 11     /* created pairs dropped at capacity */
+
+/* ---------------------------------------------------------------- parameters */
+/* One discharge (Table 1 / Table 2 quantities of the paper).  SI units except
+ * the energy resolutions, which are in eV (Sec. 3.1). */
+typedef struct {
+    double gap_m;            /* electrode gap L */
+    double pressure_pa;      /* gas pressure */
+    double gas_temp_k;       /* gas temperature T_g */
+    double area_m2;          /* electrode area A linking weight and density (1e-4 in the paper) */
+    double weight;           /* superparticle weight W (>= 0) */
+    int32_t n_grid;          /* grid points N_G, 3..EDUPIC_MAX_GRID */
+    int32_t steps_per_cycle; /* N_T, a multiple of ion_subcycle */
+    int32_t ion_subcycle;    /* N_SUB >= 1 */
+    int32_t n_harmonics;     /* drive terms, 1..EDUPIC_MAX_HARMONICS */
+    double cycle_freq_hz;    /* the RF cycle is one period of this frequency; dt_e = 1/(f N_T) */
+    double harm_freq_hz[EDUPIC_MAX_HARMONICS]; /* V(t) = sum V_k cos(2 pi f_k t); each f_k an integer
+                                                  multiple of cycle_freq_hz (0 = DC) */
+    double harm_volt_v[EDUPIC_MAX_HARMONICS];
+    uint64_t seed;           /* key of the counter-based random numbers */
+    int32_t eepf_bins;       /* N_EEPF (2000 in the paper) */
+    int32_t ifed_bins;       /* N_IFED (200) */
+    double eepf_de_ev;       /* DE_EEPF (0.05 eV) */
+    double ifed_de_ev;       /* DE_IFED (1 eV) */
+    int64_t capacity_e;      /* particle capacity per species (MAX_N_P analogue, Sec. 3.1) */
+    int64_t capacity_i;
+    double e_exc_ev;         /* lumped excitation threshold (11.5 eV for Ar) */
+    double e_ion_ev;         /* ionisation threshold (15.8 eV for Ar) */
+    int32_t cs_entries;      /* capacity of the cross-section tables (CS_RANGES), shared by the object */
+    int32_t reserved;
+} edupic_params;
+
+typedef struct edupic_sim edupic_sim;
+
+/* ---------------------------------------------------------------- lifecycle */
+
+/* Bytes of device memory a simulation of n discharges needs (Sec. 3.1
+ * static arrays, here sized from capacities).  params: host array of n
+ * parameter sets.  precision: EDUPIC_FP64 or EDUPIC_FP32.  Writes *bytes. */
+int edupic_arena_bytes(int n_discharges, const edupic_params *params, int precision, size_t *bytes);
+
+/* Create a simulation of n discharges that are stepped together by one set of
+ * kernel launches per time step.  device_arena: caller-owned device memory of
+ * at least edupic_arena_bytes bytes, 256-byte aligned; it must stay allocated
+ * until edupic_destroy.  cuda_stream: a cudaStream_t (NULL = legacy default
+ * stream).  All discharges must share ion_subcycle and cs_entries.  The
+ * particle arrays start empty; the cross sections must be set before the
+ * first step.  On success *out owns host-side state only. */
+int edupic_create(int n_discharges, const edupic_params *params, int precision, void *device_arena,
+                  size_t arena_bytes, void *cuda_stream, edupic_sim **out);
+
+/* Release the host-side state (and CUDA graphs).  The arena is not freed. */
+int edupic_destroy(edupic_sim *sim);
+
+/* Cross sections (Sec. 3.2), shared by every discharge of the object.
+ * species: EDUPIC_ELECTRONS (n_proc 3: elastic, excitation, ionisation, by
+ * LAB energy) or EDUPIC_IONS (n_proc 2: isotropic, backward, by COM energy).
+ * sigma_m2: host, [n_proc][n_entries] row-major, in m^2, at energies k*de_ev.
+ * n_entries <= cs_entries.  Energies beyond the table use the last entry. */
+int edupic_set_cross_sections(edupic_sim *sim, int species, int n_proc, int n_entries, double de_ev,
+                              const double *sigma_m2);
+
+/* Replace the particles of one species of discharge d (host FP64 arrays of n
+ * entries; stored as FP32 in EDUPIC_FP32 mode).  The densities of that species
+ * and the field of the current step are recomputed (Algorithms 2-3), as the
+ * paper does after seeding or loading particles (Algorithm 1). */
+int edupic_load_particles(edupic_sim *sim, int d, int species, int64_t n, const double *x, const double *vx,
+                          const double *vy, const double *vz);
+
+/* ---------------------------------------------------------------- stepping */
+
+/* Enqueue n_steps PIC/MCC time steps (Sec. 2.1, Fig. 2) of every discharge.
+ * Ions are pushed and collide on steps whose index within the RF cycle is a
+ * multiple of N_SUB (ion subcycling).  measure != 0 accumulates the
+ * diagnostics of Sec. 3.5 (time-averaged densities and potential, EEPF in the
+ * central 10% of the gap, IFEDF at both electrodes). */
+int edupic_step(edupic_sim *sim, int64_t n_steps, int measure);
+
+/* Enqueue n_cycles RF cycles (n_cycles * N_T steps), as do_one_cycle() is
+ * repeated by the paper's main() (Algorithm 1).  Requires all discharges to
+ * share steps_per_cycle. */
+int edupic_run_cycles(edupic_sim *sim, int n_cycles, int measure);
+
+/* Wait for the stream and return the first device-side error (or OK). */
+int edupic_synchronize(edupic_sim *sim);
+
+/* Use (1, default) or bypass (0) the CUDA graph that replays one ion
+ * subcycle of kernel launches.  Results are identical either way. */
+int edupic_set_graphs(edupic_sim *sim, int enable);
+
+/* ---------------------------------------------------------------- read-back (synchronising) */
+
+/* Live particle counts and the global step index of discharge d. */
+int edupic_get_counts(edupic_sim *sim, int d, int64_t *n_e, int64_t *n_i, int64_t *step);
+
+/* Copy up to cap particles of one species into host arrays (FP64).  Writes
+ * *n_out with the live count; slots follow the canonical compaction order. */
+int edupic_get_particles(edupic_sim *sim, int d, int species, int64_t cap, double *x, double *vx, double *vy,
+                         double *vz, int64_t *n_out);
+
+/* Fields that the next step uses (Algorithms 2-3): densities n_e, n_i
+ * (m^-3), potential phi (V), field E (V/m), and the fixed-point deposition
+ * sums q_e, q_i (2^32 units per particle).  Any pointer may be NULL; each
+ * non-NULL array holds n_grid entries. */
+int edupic_get_fields(edupic_sim *sim, int d, double *n_e, double *n_i, double *phi, double *efield, int64_t *q_e,
+                      int64_t *q_i);
+
+/* Time-averaged densities and potential over the measured steps, and the raw
+ * EEPF / IFEDF histograms (Sec. 3.5).  Any pointer may be NULL. */
+int edupic_get_diagnostics(edupic_sim *sim, int d, double *ne_avg, double *ni_avg, double *phi_avg,
+                           int64_t *eepf_counts, int64_t *ifed_pow_counts, int64_t *ifed_gnd_counts,
+                           int64_t *measured_steps);
+
+/* Normalised EEPF f(eps) (sum f sqrt(eps) dE = 1) and IFEDFs F(eps)
+ * (sum F dE = 1) at bin centres (Sec. 3.5).  Any output may be NULL. */
+int edupic_get_eepf(edupic_sim *sim, int d, double *energy_ev, double *f);
+int edupic_get_ifed(edupic_sim *sim, int d, double *energy_ev, double *f_pow, double *f_gnd);
+
+/* Event counters (EDUPIC_C_* indices), accumulated since creation. */
+int edupic_get_counters(edupic_sim *sim, int d, int64_t out[EDUPIC_N_COUNTERS]);
+
+/* Clear the measured diagnostics of discharge d. */
+int edupic_reset_diagnostics(edupic_sim *sim, int d);
+
+/* ---------------------------------------------------------------- checkpoint */
+
+/* Save / restore the state of discharge d (counts, step index, particle
+ * coordinates), the analogue of picdata.bin (Algorithm 1).  The file has a
+ * versioned header; a restore recomputes the densities and field. */
+int edupic_save_state(edupic_sim *sim, int d, const char *path);
+int edupic_load_state(edupic_sim *sim, int d, const char *path);
+
+/* Text for a status code. */
+const char *edupic_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EDUPIC_H */

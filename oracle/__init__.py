@@ -86,6 +86,7 @@ def lib():
             L.orc_count.restype = ctypes.c_int64
             L.orc_get_particles.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, _D, _D, _D]
             L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
+            L.orc_prepare_fields.argtypes = [ctypes.c_void_p]
             L.orc_get_step.argtypes = [ctypes.c_void_p]
             L.orc_get_step.restype = ctypes.c_int64
             L.orc_set_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
@@ -266,6 +267,11 @@ class Sim:
     @step_index.setter
     def step_index(self, s: int):
         lib().orc_set_step(self._h, s)
+
+    def prepare_fields(self):
+        """Densities and field of the current step, without advancing it."""
+        lib().orc_prepare_fields(self._h)
+        return self.fields()
 
     def fields(self):
         ng = self.d.n_grid

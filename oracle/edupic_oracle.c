@@ -577,7 +577,24 @@ int orc_load_particles(orc_sim *s, int species, int64_t n, const double *x, cons
     memcpy(sp->vx, vx, sizeof(double) * (size_t)n);
     memcpy(sp->vy, vy, sizeof(double) * (size_t)n);
     memcpy(sp->vz, vz, sizeof(double) * (size_t)n);
+    /* Reading (Algorithms 1-2): a loaded species replaces its deposited
+     * density at once, also between ion steps when the ion density is held. */
+    orc_deposit_fixed(sp->x, n, s->p.n_grid, s->inv_dx, species == 0 ? s->q_e : s->q_i);
     return 0;
+}
+
+/* Steps (1)-(2) of the current step without advancing it: the densities and
+ * the field that the next call of one_step() will use. */
+void orc_prepare_fields(orc_sim *s)
+{
+    const int ng = s->p.n_grid;
+    const int64_t t = s->step % s->p.steps_per_cycle;
+    orc_deposit_fixed(s->sp[ORC_SPECIES_E].x, s->sp[ORC_SPECIES_E].n, ng, s->inv_dx, s->q_e);
+    if ((t % s->p.ion_subcycle) == 0) orc_deposit_fixed(s->sp[ORC_SPECIES_I].x, s->sp[ORC_SPECIES_I].n, ng, s->inv_dx, s->q_i);
+    orc_density_from_fixed(s->q_e, ng, s->factor_w, s->n_e);
+    orc_density_from_fixed(s->q_i, ng, s->factor_w, s->n_i);
+    for (int k = 0; k < ng; ++k) s->rho[k] = ORC_E_CHARGE * (s->n_i[k] - s->n_e[k]);
+    orc_poisson(s->rho, ng, s->dx, drive_voltage(s, t), s->phi, s->efield);
 }
 
 int64_t orc_count(const orc_sim *s, int species) { return s->sp[species].n; }

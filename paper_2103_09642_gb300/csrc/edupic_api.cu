@@ -1,0 +1,844 @@
+// Host side of the C ABI declared in include/edupic.h: parameter checks,
+// arena layout, descriptor upload, step scheduling (with one CUDA graph per
+// ion subcycle), read-back and checkpoints.  No particle arithmetic runs here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "edupic_internal.h"
+
+using namespace edupic;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kTileAlign = 1024;  // particle arrays padded to whole tiles
+constexpr double kQE = 1.602176634e-19;
+constexpr double kME = 9.1093837015e-31;
+constexpr double kEPS0 = 8.8541878128e-12;
+constexpr double kKB = 1.380649e-23;
+constexpr double kAMU = 1.66053906660e-27;
+constexpr double kArMassU = 39.948;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+long long padded(long long cap) { return (cap + kTileAlign - 1) / kTileAlign * kTileAlign; }
+
+// Byte layout of one discharge inside the arena (offsets from its base).
+struct Layout {
+    size_t x[2], vx[2], vy[2], vz[2];
+    size_t q_e, q_i, acc_e, acc_i, n_e, n_i, phi, ef, ef_t, sum_ne, sum_ni, sum_phi;
+    size_t eepf, ifed_pow, ifed_gnd, ctrl, holes[2], prod_parent, prod_x, prod_ve[3], prod_vi[3];
+    size_t bytes;
+};
+
+Layout layout_of(const edupic_params &p, size_t elem)
+{
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t n) {
+        const size_t at = o;
+        o = align_up(o + n, kAlign);
+        return at;
+    };
+    const long long cap[2] = {padded(p.capacity_e), padded(p.capacity_i)};
+    for (int s = 0; s < 2; ++s) {
+        L.x[s] = take(cap[s] * elem);
+        L.vx[s] = take(cap[s] * elem);
+        L.vy[s] = take(cap[s] * elem);
+        L.vz[s] = take(cap[s] * elem);
+    }
+    const size_t ng = (size_t)p.n_grid;
+    L.q_e = take(ng * 8);
+    L.q_i = take(ng * 8);
+    L.acc_e = take(ng * 8);
+    L.acc_i = take(ng * 8);
+    L.n_e = take(ng * 8);
+    L.n_i = take(ng * 8);
+    L.phi = take(ng * 8);
+    L.ef = take(ng * 8);
+    L.ef_t = take(ng * elem);
+    L.sum_ne = take(ng * 8);
+    L.sum_ni = take(ng * 8);
+    L.sum_phi = take(ng * 8);
+    L.eepf = take((size_t)p.eepf_bins * 8);
+    L.ifed_pow = take((size_t)p.ifed_bins * 8);
+    L.ifed_gnd = take((size_t)p.ifed_bins * 8);
+    L.ctrl = take(sizeof(Ctrl));
+    L.holes[0] = take((size_t)kEvents * 4);
+    L.holes[1] = take((size_t)kEvents * 4);
+    L.prod_parent = take((size_t)kEvents * 4);
+    L.prod_x = take((size_t)kEvents * elem);
+    for (int c = 0; c < 3; ++c) L.prod_ve[c] = take((size_t)kEvents * elem);
+    for (int c = 0; c < 3; ++c) L.prod_vi[c] = take((size_t)kEvents * elem);
+    L.bytes = o;
+    return L;
+}
+
+bool is_multiple(double f, double base)
+{
+    if (f == 0.0) return true;
+    const double r = f / base;
+    return r >= 0.5 && std::fabs(r - std::nearbyint(r)) <= 1e-9 * r;
+}
+
+int check_params(int nd, const edupic_params *ps, int precision)
+{
+    if (nd < 1 || nd > EDUPIC_MAX_DISCHARGES || !ps) return EDUPIC_EINVAL;
+    if (precision != EDUPIC_FP64 && precision != EDUPIC_FP32) return EDUPIC_EINVAL;
+    for (int d = 0; d < nd; ++d) {
+        const edupic_params &p = ps[d];
+        if (!(p.gap_m > 0) || !(p.pressure_pa >= 0) || !(p.gas_temp_k > 0) || !(p.area_m2 > 0) || !(p.weight >= 0))
+            return EDUPIC_EINVAL;
+        if (p.n_grid < 3 || p.n_grid > EDUPIC_MAX_GRID) return EDUPIC_EINVAL;
+        if (p.steps_per_cycle < 1 || p.ion_subcycle < 1 || p.steps_per_cycle % p.ion_subcycle) return EDUPIC_EINVAL;
+        if (p.ion_subcycle != ps[0].ion_subcycle || p.cs_entries != ps[0].cs_entries) return EDUPIC_EINVAL;
+        if (p.n_harmonics < 0 || p.n_harmonics > EDUPIC_MAX_HARMONICS || !(p.cycle_freq_hz > 0)) return EDUPIC_EINVAL;
+        for (int k = 0; k < p.n_harmonics; ++k)
+            if (!(p.harm_freq_hz[k] >= 0) || !is_multiple(p.harm_freq_hz[k], p.cycle_freq_hz)) return EDUPIC_EINVAL;
+        if (p.eepf_bins < 1 || p.eepf_bins > EDUPIC_MAX_EEPF_BINS || !(p.eepf_de_ev > 0)) return EDUPIC_EINVAL;
+        if (p.ifed_bins < 1 || p.ifed_bins > EDUPIC_MAX_IFED_BINS || !(p.ifed_de_ev > 0)) return EDUPIC_EINVAL;
+        if (p.capacity_e < 1 || p.capacity_i < 1 || p.capacity_e > (1ll << 31) - 2 * kTileAlign ||
+            p.capacity_i > (1ll << 31) - 2 * kTileAlign)
+            return EDUPIC_EINVAL;
+        if (p.cs_entries < 1) return EDUPIC_EINVAL;
+        if (!(p.e_exc_ev >= 0) || !(p.e_ion_ev > 0)) return EDUPIC_EINVAL;
+    }
+    return EDUPIC_OK;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? EDUPIC_OK : EDUPIC_ECUDA; }
+
+}  // namespace
+
+struct edupic_sim {
+    int nd = 0, precision = 0;
+    size_t elem = 8;
+    std::vector<edupic_params> params;
+    std::vector<Layout> layouts;
+    std::vector<size_t> base;  // arena offset of each discharge
+    std::vector<DischargeDev> desc;
+    unsigned char *arena = nullptr;
+    size_t arena_bytes = 0;
+    DischargeDev *d_desc = nullptr;
+    void *cs_tab[2] = {nullptr, nullptr};
+    bool cs_set[2] = {false, false};
+    cudaStream_t stream = nullptr;
+    int ng_max = 0, eepf_max = 0, nsub = 1, nt_common = -1;
+    int phase = 0;  // common step index modulo N_SUB
+    int grid[2] = {0, 0};
+    bool graphs = true;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+
+    ~edupic_sim()
+    {
+        for (auto &g : graph)
+            if (g) cudaGraphExecDestroy(g);
+    }
+    void drop_graphs()
+    {
+        for (auto &g : graph)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    }
+    Ctrl *ctrl(int d) const { return desc[d].ctrl; }
+};
+
+namespace {
+
+size_t shared_bytes(int nd, size_t elem, int cs_entries)
+{
+    size_t o = align_up(sizeof(DischargeDev) * nd, kAlign);
+    o += 2 * align_up((size_t)cs_entries * 4 * elem, kAlign);
+    return o;
+}
+
+void fill_desc(edupic_sim *S, int d)
+{
+    const edupic_params &p = S->params[d];
+    const Layout &L = S->layouts[d];
+    unsigned char *b = S->arena + S->base[d];
+    DischargeDev D{};
+    // Section 3.1 / Table 1 derived quantities, in the paper's expression order.
+    const double ar_mass = kArMassU * kAMU;
+    D.L = p.gap_m;
+    D.dx = p.gap_m / (p.n_grid - 1);
+    D.inv_dx = 1.0 / D.dx;
+    D.dt_e = 1.0 / (p.cycle_freq_hz * p.steps_per_cycle);
+    D.dt_i = p.ion_subcycle * D.dt_e;
+    D.factor_w = p.weight / (p.area_m2 * D.dx);
+    D.factor_e = D.dt_e / kME * kQE;
+    D.factor_i = D.dt_i / ar_mass * kQE;
+    D.n_gas = p.pressure_pa / (kKB * p.gas_temp_k);
+    D.sig_th = std::sqrt(kKB * p.gas_temp_k / ar_mass);
+    D.ar_mass = ar_mass;
+    D.mu_e = kME * ar_mass / (kME + ar_mass);
+    const double mu_arar = ar_mass / 2.0;
+    D.half_me = 0.5 * kME;
+    D.half_mar = 0.5 * ar_mass;
+    D.half_mu_e = 0.5 * D.mu_e;
+    D.half_mu_arar = 0.5 * mu_arar;
+    D.e_exc = p.e_exc_ev;
+    D.e_ion = p.e_ion_ev;
+    D.eepf_lo = 0.45 * p.gap_m;
+    D.eepf_hi = 0.55 * p.gap_m;
+    D.eepf_de = p.eepf_de_ev;
+    D.ifed_de = p.ifed_de_ev;
+    D.cs_de_e = S->desc.size() > (size_t)d ? S->desc[d].cs_de_e : 1.0;
+    D.cs_de_i = S->desc.size() > (size_t)d ? S->desc[d].cs_de_i : 1.0;
+    D.poisson_c = D.dx * D.dx * kQE * D.factor_w / (kEPS0 * 4294967296.0);
+    D.rho_c = kQE * D.factor_w / 4294967296.0;
+    for (int k = 0; k < EDUPIC_MAX_HARMONICS; ++k) {
+        D.harm_freq[k] = k < p.n_harmonics ? p.harm_freq_hz[k] : 0.0;
+        D.harm_volt[k] = k < p.n_harmonics ? p.harm_volt_v[k] : 0.0;
+    }
+    D.Lf = (float)D.L;
+    D.inv_dxf = (float)D.inv_dx;
+    D.dt_ef = (float)D.dt_e;
+    D.dt_if = (float)D.dt_i;
+    D.factor_ef = (float)D.factor_e;
+    D.factor_if = (float)D.factor_i;
+    D.n_gasf = (float)D.n_gas;
+    D.sig_thf = (float)D.sig_th;
+    D.e_of_v2_ef = (float)(0.5 * kME / kQE);
+    D.e_of_v2_if = (float)(0.5 * ar_mass / kQE);
+    D.e_of_g2_if = (float)(0.5 * mu_arar / kQE);
+    D.mu_ef = (float)D.mu_e;
+    D.e_excf = (float)p.e_exc_ev;
+    D.e_ionf = (float)p.e_ion_ev;
+    D.eepf_lof = (float)D.eepf_lo;
+    D.eepf_hif = (float)D.eepf_hi;
+    D.inv_eepf_def = (float)(1.0 / p.eepf_de_ev);
+    D.inv_ifed_def = (float)(1.0 / p.ifed_de_ev);
+    D.inv_cs_de_ef = (float)(1.0 / D.cs_de_e);
+    D.inv_cs_de_if = (float)(1.0 / D.cs_de_i);
+    D.vscale_mu_ef = (float)std::sqrt(2.0 * kQE / D.mu_e);
+    D.vscale_ef = (float)std::sqrt(2.0 * kQE / kME);
+    D.mass_ratio_ef = (float)(kME / (kME + ar_mass));
+    D.mass_ratio2_ef = (float)(ar_mass / (kME + ar_mass));
+    D.ng = p.n_grid;
+    D.nt = p.steps_per_cycle;
+    D.nsub = p.ion_subcycle;
+    D.n_harm = p.n_harmonics;
+    D.eepf_bins = p.eepf_bins;
+    D.ifed_bins = p.ifed_bins;
+    D.cs_n_e = S->desc.size() > (size_t)d ? S->desc[d].cs_n_e : 1;
+    D.cs_n_i = S->desc.size() > (size_t)d ? S->desc[d].cs_n_i : 1;
+    D.active = 1;
+    D.cap[0] = p.capacity_e;
+    D.cap[1] = p.capacity_i;
+    D.seed = p.seed;
+    for (int s = 0; s < 2; ++s) {
+        D.x[s] = b + L.x[s];
+        D.vx[s] = b + L.vx[s];
+        D.vy[s] = b + L.vy[s];
+        D.vz[s] = b + L.vz[s];
+        D.holes[s] = reinterpret_cast<int *>(b + L.holes[s]);
+    }
+    D.q_e = reinterpret_cast<long long *>(b + L.q_e);
+    D.q_i = reinterpret_cast<long long *>(b + L.q_i);
+    D.acc_e = reinterpret_cast<long long *>(b + L.acc_e);
+    D.acc_i = reinterpret_cast<long long *>(b + L.acc_i);
+    D.n_e = reinterpret_cast<double *>(b + L.n_e);
+    D.n_i = reinterpret_cast<double *>(b + L.n_i);
+    D.phi = reinterpret_cast<double *>(b + L.phi);
+    D.ef = reinterpret_cast<double *>(b + L.ef);
+    D.ef_t = b + L.ef_t;
+    D.sum_ne = reinterpret_cast<double *>(b + L.sum_ne);
+    D.sum_ni = reinterpret_cast<double *>(b + L.sum_ni);
+    D.sum_phi = reinterpret_cast<double *>(b + L.sum_phi);
+    D.eepf = reinterpret_cast<unsigned long long *>(b + L.eepf);
+    D.ifed_pow = reinterpret_cast<unsigned long long *>(b + L.ifed_pow);
+    D.ifed_gnd = reinterpret_cast<unsigned long long *>(b + L.ifed_gnd);
+    D.ctrl = reinterpret_cast<Ctrl *>(b + L.ctrl);
+    D.prod_parent = reinterpret_cast<int *>(b + L.prod_parent);
+    D.prod_x = b + L.prod_x;
+    for (int c = 0; c < 3; ++c) {
+        D.prod_ve[c] = b + L.prod_ve[c];
+        D.prod_vi[c] = b + L.prod_vi[c];
+    }
+    D.cs_e = S->cs_tab[0];
+    D.cs_i = S->cs_tab[1];
+    if (S->desc.size() <= (size_t)d) S->desc.resize(d + 1);
+    S->desc[d] = D;
+}
+
+int upload_desc(edupic_sim *S)
+{
+    cudaError_t e = cudaMemcpyAsync(S->d_desc, S->desc.data(), sizeof(DischargeDev) * S->nd, cudaMemcpyHostToDevice,
+                                    S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    return cuda_status(e);
+}
+
+template <typename T>
+int launch_step(edupic_sim *S, bool ion, int measure)
+{
+    cudaError_t e = Launch<T>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max, S->stream);
+    if (e == cudaSuccess && ion)
+        e = Launch<T>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max, S->stream);
+    if (e == cudaSuccess) e = Launch<T>::finalize(S->d_desc, S->nd, ion ? 1 : 0, measure, S->stream);
+    return cuda_status(e);
+}
+
+int launch_one(edupic_sim *S, bool ion, int measure)
+{
+    return S->precision == EDUPIC_FP32 ? launch_step<float>(S, ion, measure) : launch_step<double>(S, ion, measure);
+}
+
+// One ion subcycle (N_SUB steps starting at phase 0) as a CUDA graph.
+int build_graph(edupic_sim *S, int measure)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return EDUPIC_ECUDA;
+    int rc = EDUPIC_OK;
+    for (int k = 0; k < S->nsub && rc == EDUPIC_OK; ++k) rc = launch_one(S, k == 0, measure);
+    e = cudaStreamEndCapture(S->stream, &g);
+    if (rc != EDUPIC_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return EDUPIC_ECUDA;
+    }
+    e = cudaGraphInstantiate(&S->graph[measure], g, 0);
+    cudaGraphDestroy(g);
+    return cuda_status(e);
+}
+
+int read_ctrl(edupic_sim *S, int d, Ctrl *c)
+{
+    cudaError_t e = cudaStreamSynchronize(S->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(c, S->ctrl(d), sizeof(Ctrl), cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}
+
+int error_of(const Ctrl &c)
+{
+    if (c.error & kErrNan) return EDUPIC_ENAN;
+    if (c.error) return EDUPIC_ECAPACITY;
+    return EDUPIC_OK;
+}
+
+template <typename T>
+int upload_tables(edupic_sim *S, int species, int n_proc, int n_entries, const double *sig)
+{
+    std::vector<CsEntry<T>> tab((size_t)n_entries);
+    for (int k = 0; k < n_entries; ++k) {
+        const double s0 = sig[k], s1 = sig[(size_t)n_entries + k];
+        const double s2 = n_proc == 3 ? sig[2 * (size_t)n_entries + k] : 0.0;
+        // sum in the order calc_total_cross_sections() adds the processes
+        const double stot = n_proc == 3 ? s0 + s1 + s2 : s0 + s1;
+        CsEntry<T> c;
+        c.sigsum = (T)stot;
+        c.thr1 = (T)(s0 / stot);
+        c.thr2 = (T)(n_proc == 3 ? (s0 + s1) / stot : 1.0);
+        c.pad = (T)0;
+        tab[k] = c;
+    }
+    cudaError_t e = cudaMemcpyAsync(S->cs_tab[species], tab.data(), sizeof(CsEntry<T>) * tab.size(),
+                                    cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    return cuda_status(e);
+}
+
+template <typename T>
+int upload_particles(edupic_sim *S, int d, int sp, int64_t n, const double *const src[4])
+{
+    void *dst[4] = {S->desc[d].x[sp], S->desc[d].vx[sp], S->desc[d].vy[sp], S->desc[d].vz[sp]};
+    std::vector<T> tmp((size_t)n);
+    for (int c = 0; c < 4; ++c) {
+        for (int64_t j = 0; j < n; ++j) tmp[j] = (T)src[c][j];
+        cudaError_t e = cudaMemcpyAsync(dst[c], tmp.data(), sizeof(T) * (size_t)n, cudaMemcpyHostToDevice, S->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+        if (e != cudaSuccess) return EDUPIC_ECUDA;
+    }
+    return EDUPIC_OK;
+}
+
+template <typename T>
+int download_particles(edupic_sim *S, int d, int sp, int64_t n, double *const dst[4])
+{
+    const void *src[4] = {S->desc[d].x[sp], S->desc[d].vx[sp], S->desc[d].vy[sp], S->desc[d].vz[sp]};
+    std::vector<T> tmp((size_t)n);
+    for (int c = 0; c < 4; ++c) {
+        if (!dst[c]) continue;
+        cudaError_t e = cudaMemcpy(tmp.data(), src[c], sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return EDUPIC_ECUDA;
+        for (int64_t j = 0; j < n; ++j) dst[c][j] = (double)tmp[j];
+    }
+    return EDUPIC_OK;
+}
+
+// Recompute the densities of one species and the field of the current step.
+int refresh_species(edupic_sim *S, int d, int sp)
+{
+    const DischargeDev &D = S->desc[d];
+    const size_t ng = (size_t)S->params[d].n_grid;
+    cudaError_t e = cudaMemsetAsync(sp == 0 ? D.q_e : D.q_i, 0, ng * 8, S->stream);
+    if (e == cudaSuccess && sp == 1) e = cudaMemsetAsync(D.acc_i, 0, ng * 8, S->stream);
+    if (e != cudaSuccess) return EDUPIC_ECUDA;
+    const int also_acc = (sp == 1 && S->phase != 0) ? 1 : 0;
+    if (S->precision == EDUPIC_FP32) {
+        e = Launch<float>::deposit(S->d_desc, S->nd, d, sp, also_acc, S->stream);
+        if (e == cudaSuccess) e = Launch<float>::fields(S->d_desc, S->nd, d, S->stream);
+    } else {
+        e = Launch<double>::deposit(S->d_desc, S->nd, d, sp, also_acc, S->stream);
+        if (e == cudaSuccess) e = Launch<double>::fields(S->d_desc, S->nd, d, S->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    return cuda_status(e);
+}
+
+bool valid_d(const edupic_sim *S, int d) { return S && d >= 0 && d < S->nd; }
+
+}  // namespace
+
+extern "C" {
+
+int edupic_arena_bytes(int nd, const edupic_params *params, int precision, size_t *bytes)
+{
+    int rc = check_params(nd, params, precision);
+    if (rc) return rc;
+    if (!bytes) return EDUPIC_EINVAL;
+    const size_t elem = precision == EDUPIC_FP32 ? 4 : 8;
+    size_t tot = shared_bytes(nd, elem, params[0].cs_entries);
+    for (int d = 0; d < nd; ++d) tot += layout_of(params[d], elem).bytes;
+    *bytes = tot;
+    return EDUPIC_OK;
+}
+
+int edupic_create(int nd, const edupic_params *params, int precision, void *device_arena, size_t arena_bytes,
+                  void *cuda_stream, edupic_sim **out)
+{
+    if (!out) return EDUPIC_EINVAL;
+    *out = nullptr;
+    size_t need = 0;
+    int rc = edupic_arena_bytes(nd, params, precision, &need);
+    if (rc) return rc;
+    if (!device_arena || ((uintptr_t)device_arena % kAlign)) return EDUPIC_EINVAL;
+    if (arena_bytes < need) return EDUPIC_ENOMEM;
+    edupic_sim *S = new (std::nothrow) edupic_sim();
+    if (!S) return EDUPIC_ENOMEM;
+    S->nd = nd;
+    S->precision = precision;
+    S->elem = precision == EDUPIC_FP32 ? 4 : 8;
+    S->params.assign(params, params + nd);
+    S->arena = static_cast<unsigned char *>(device_arena);
+    S->arena_bytes = arena_bytes;
+    S->stream = static_cast<cudaStream_t>(cuda_stream);
+    S->nsub = params[0].ion_subcycle;
+    S->nt_common = params[0].steps_per_cycle;
+    for (int d = 0; d < nd; ++d) {
+        S->ng_max = std::max(S->ng_max, params[d].n_grid);
+        S->eepf_max = std::max(S->eepf_max, params[d].eepf_bins);
+        if (params[d].steps_per_cycle != S->nt_common) S->nt_common = -1;
+    }
+    // shared region: descriptors, then the two cross-section tables
+    size_t o = 0;
+    S->d_desc = reinterpret_cast<DischargeDev *>(S->arena);
+    o = align_up(sizeof(DischargeDev) * nd, kAlign);
+    const size_t tab_bytes = align_up((size_t)params[0].cs_entries * 4 * S->elem, kAlign);
+    S->cs_tab[0] = S->arena + o;
+    o += tab_bytes;
+    S->cs_tab[1] = S->arena + o;
+    o += tab_bytes;
+    for (int d = 0; d < nd; ++d) {
+        S->layouts.push_back(layout_of(params[d], S->elem));
+        S->base.push_back(o);
+        o += S->layouts.back().bytes;
+    }
+    for (int d = 0; d < nd; ++d) fill_desc(S, d);
+    cudaError_t e = cudaMemsetAsync(S->arena, 0, need, S->stream);
+    if (e != cudaSuccess) {
+        delete S;
+        return EDUPIC_ECUDA;
+    }
+    rc = upload_desc(S);
+    if (rc) {
+        delete S;
+        return rc;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int sp = 0; sp < 2; ++sp) {
+        const int eb = sp == 0 ? S->eepf_max : 0;
+        const size_t smem = precision == EDUPIC_FP32 ? Launch<float>::push_smem(nd, S->ng_max, eb)
+                                                     : Launch<double>::push_smem(nd, S->ng_max, eb);
+        int nb = precision == EDUPIC_FP32 ? Launch<float>::push_blocks_per_sm(sp, smem)
+                                          : Launch<double>::push_blocks_per_sm(sp, smem);
+        if (nb < 1) {
+            delete S;
+            return EDUPIC_ECUDA;
+        }
+        S->grid[sp] = nb * std::max(sms, 1);
+    }
+    // the field of step 0 (empty discharge: the vacuum field of V(0))
+    for (int d = 0; d < nd && rc == EDUPIC_OK; ++d) {
+        e = precision == EDUPIC_FP32 ? Launch<float>::fields(S->d_desc, nd, d, S->stream)
+                                     : Launch<double>::fields(S->d_desc, nd, d, S->stream);
+        rc = cuda_status(e);
+    }
+    if (rc == EDUPIC_OK) rc = cuda_status(cudaStreamSynchronize(S->stream));
+    if (rc) {
+        delete S;
+        return rc;
+    }
+    *out = S;
+    return EDUPIC_OK;
+}
+
+int edupic_destroy(edupic_sim *S)
+{
+    if (!S) return EDUPIC_EINVAL;
+    if (S->stream) cudaStreamSynchronize(S->stream);
+    delete S;
+    return EDUPIC_OK;
+}
+
+int edupic_set_cross_sections(edupic_sim *S, int species, int n_proc, int n_entries, double de_ev,
+                              const double *sigma_m2)
+{
+    if (!S || !sigma_m2 || (species != 0 && species != 1) || !(de_ev > 0)) return EDUPIC_EINVAL;
+    if ((species == 0 && n_proc != 3) || (species == 1 && n_proc != 2)) return EDUPIC_EINVAL;
+    if (n_entries < 1 || n_entries > S->params[0].cs_entries) return EDUPIC_EINVAL;
+    for (size_t k = 0; k < (size_t)n_proc * n_entries; ++k)
+        if (!(sigma_m2[k] >= 0) || !std::isfinite(sigma_m2[k])) return EDUPIC_EINVAL;
+    int rc = S->precision == EDUPIC_FP32 ? upload_tables<float>(S, species, n_proc, n_entries, sigma_m2)
+                                         : upload_tables<double>(S, species, n_proc, n_entries, sigma_m2);
+    if (rc) return rc;
+    for (int d = 0; d < S->nd; ++d) {
+        if (species == 0) {
+            S->desc[d].cs_n_e = n_entries;
+            S->desc[d].cs_de_e = de_ev;
+            S->desc[d].inv_cs_de_ef = (float)(1.0 / de_ev);
+        } else {
+            S->desc[d].cs_n_i = n_entries;
+            S->desc[d].cs_de_i = de_ev;
+            S->desc[d].inv_cs_de_if = (float)(1.0 / de_ev);
+        }
+    }
+    S->cs_set[species] = true;
+    return upload_desc(S);
+}
+
+int edupic_load_particles(edupic_sim *S, int d, int species, int64_t n, const double *x, const double *vx,
+                          const double *vy, const double *vz)
+{
+    if (!valid_d(S, d) || (species != 0 && species != 1) || n < 0) return EDUPIC_EINVAL;
+    if (n > (species == 0 ? S->params[d].capacity_e : S->params[d].capacity_i)) return EDUPIC_ECAPACITY;
+    if (n > 0 && (!x || !vx || !vy || !vz)) return EDUPIC_EINVAL;
+    const double L = S->params[d].gap_m;
+    for (int64_t j = 0; j < n; ++j)
+        if (!(x[j] >= 0.0 && x[j] <= L) || !std::isfinite(vx[j]) || !std::isfinite(vy[j]) || !std::isfinite(vz[j]))
+            return EDUPIC_EINVAL;
+    const double *src[4] = {x, vx, vy, vz};
+    int rc = n == 0 ? EDUPIC_OK
+                    : (S->precision == EDUPIC_FP32 ? upload_particles<float>(S, d, species, n, src)
+                                                   : upload_particles<double>(S, d, species, n, src));
+    if (rc) return rc;
+    long long nn = n;
+    cudaError_t e = cudaMemcpyAsync(&S->ctrl(d)->n[species], &nn, sizeof(nn), cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    if (e != cudaSuccess) return EDUPIC_ECUDA;
+    return refresh_species(S, d, species);
+}
+
+int edupic_step(edupic_sim *S, int64_t n_steps, int measure)
+{
+    if (!S || n_steps < 0) return EDUPIC_EINVAL;
+    if (!S->cs_set[0] || !S->cs_set[1]) return EDUPIC_ESTATE;
+    measure = measure ? 1 : 0;
+    const bool can_graph = S->graphs && S->stream != nullptr;
+    int64_t i = 0;
+    while (i < n_steps) {
+        if (can_graph && S->phase == 0 && n_steps - i >= S->nsub) {
+            if (!S->graph[measure]) {
+                int rc = build_graph(S, measure);
+                if (rc) return rc;
+            }
+            cudaError_t e = cudaGraphLaunch(S->graph[measure], S->stream);
+            if (e != cudaSuccess) return EDUPIC_ECUDA;
+            i += S->nsub;
+            continue;
+        }
+        int rc = launch_one(S, S->phase == 0, measure);
+        if (rc) return rc;
+        S->phase = (S->phase + 1) % S->nsub;
+        ++i;
+    }
+    return EDUPIC_OK;
+}
+
+int edupic_run_cycles(edupic_sim *S, int n_cycles, int measure)
+{
+    if (!S || n_cycles < 0) return EDUPIC_EINVAL;
+    if (S->nt_common < 0) return EDUPIC_EINVAL;
+    return edupic_step(S, (int64_t)n_cycles * S->nt_common, measure);
+}
+
+int edupic_synchronize(edupic_sim *S)
+{
+    if (!S) return EDUPIC_EINVAL;
+    if (cudaStreamSynchronize(S->stream) != cudaSuccess) return EDUPIC_ECUDA;
+    for (int d = 0; d < S->nd; ++d) {
+        Ctrl c;
+        int rc = read_ctrl(S, d, &c);
+        if (rc) return rc;
+        rc = error_of(c);
+        if (rc) return rc;
+    }
+    return EDUPIC_OK;
+}
+
+int edupic_set_graphs(edupic_sim *S, int enable)
+{
+    if (!S) return EDUPIC_EINVAL;
+    S->graphs = enable != 0;
+    if (!S->graphs) S->drop_graphs();
+    return EDUPIC_OK;
+}
+
+int edupic_get_counts(edupic_sim *S, int d, int64_t *n_e, int64_t *n_i, int64_t *step)
+{
+    if (!valid_d(S, d)) return EDUPIC_EINVAL;
+    Ctrl c;
+    int rc = read_ctrl(S, d, &c);
+    if (rc) return rc;
+    if (n_e) *n_e = c.n[0];
+    if (n_i) *n_i = c.n[1];
+    if (step) *step = c.step;
+    return error_of(c);
+}
+
+int edupic_get_particles(edupic_sim *S, int d, int species, int64_t cap, double *x, double *vx, double *vy,
+                         double *vz, int64_t *n_out)
+{
+    if (!valid_d(S, d) || (species != 0 && species != 1) || cap < 0) return EDUPIC_EINVAL;
+    Ctrl c;
+    int rc = read_ctrl(S, d, &c);
+    if (rc) return rc;
+    const int64_t n = c.n[species];
+    if (n_out) *n_out = n;
+    const int64_t m = std::min<int64_t>(n, cap);
+    double *dst[4] = {x, vx, vy, vz};
+    rc = S->precision == EDUPIC_FP32 ? download_particles<float>(S, d, species, m, dst)
+                                     : download_particles<double>(S, d, species, m, dst);
+    if (rc) return rc;
+    return error_of(c);
+}
+
+int edupic_get_fields(edupic_sim *S, int d, double *n_e, double *n_i, double *phi, double *efield, int64_t *q_e,
+                      int64_t *q_i)
+{
+    if (!valid_d(S, d)) return EDUPIC_EINVAL;
+    if (cudaStreamSynchronize(S->stream) != cudaSuccess) return EDUPIC_ECUDA;
+    const DischargeDev &D = S->desc[d];
+    const size_t ng = (size_t)S->params[d].n_grid;
+    struct {
+        void *dst;
+        const void *src;
+    } cp[6] = {{n_e, D.n_e}, {n_i, D.n_i}, {phi, D.phi}, {efield, D.ef}, {q_e, D.q_e}, {q_i, D.q_i}};
+    for (auto &c : cp)
+        if (c.dst && cudaMemcpy(c.dst, c.src, ng * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return EDUPIC_ECUDA;
+    return EDUPIC_OK;
+}
+
+int edupic_get_diagnostics(edupic_sim *S, int d, double *ne_avg, double *ni_avg, double *phi_avg,
+                           int64_t *eepf_counts, int64_t *ifed_pow_counts, int64_t *ifed_gnd_counts,
+                           int64_t *measured_steps)
+{
+    if (!valid_d(S, d)) return EDUPIC_EINVAL;
+    Ctrl c;
+    int rc = read_ctrl(S, d, &c);
+    if (rc) return rc;
+    const DischargeDev &D = S->desc[d];
+    const edupic_params &p = S->params[d];
+    const size_t ng = (size_t)p.n_grid;
+    const double m = c.measured > 0 ? (double)c.measured : 1.0;
+    double *outs[3] = {ne_avg, ni_avg, phi_avg};
+    const double *srcs[3] = {D.sum_ne, D.sum_ni, D.sum_phi};
+    for (int k = 0; k < 3; ++k) {
+        if (!outs[k]) continue;
+        if (cudaMemcpy(outs[k], srcs[k], ng * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return EDUPIC_ECUDA;
+        for (size_t j = 0; j < ng; ++j) outs[k][j] /= m;
+    }
+    if (eepf_counts && cudaMemcpy(eepf_counts, D.eepf, (size_t)p.eepf_bins * 8, cudaMemcpyDeviceToHost))
+        return EDUPIC_ECUDA;
+    if (ifed_pow_counts && cudaMemcpy(ifed_pow_counts, D.ifed_pow, (size_t)p.ifed_bins * 8, cudaMemcpyDeviceToHost))
+        return EDUPIC_ECUDA;
+    if (ifed_gnd_counts && cudaMemcpy(ifed_gnd_counts, D.ifed_gnd, (size_t)p.ifed_bins * 8, cudaMemcpyDeviceToHost))
+        return EDUPIC_ECUDA;
+    if (measured_steps) *measured_steps = c.measured;
+    return error_of(c);
+}
+
+int edupic_get_eepf(edupic_sim *S, int d, double *energy_ev, double *f)
+{
+    if (!valid_d(S, d)) return EDUPIC_EINVAL;
+    const edupic_params &p = S->params[d];
+    std::vector<int64_t> h((size_t)p.eepf_bins);
+    int rc = edupic_get_diagnostics(S, d, nullptr, nullptr, nullptr, h.data(), nullptr, nullptr, nullptr);
+    if (rc) return rc;
+    double tot = 0.0;
+    for (int64_t v : h) tot += (double)v;
+    for (int k = 0; k < p.eepf_bins; ++k) {
+        const double e = (k + 0.5) * p.eepf_de_ev;
+        if (energy_ev) energy_ev[k] = e;
+        if (f) f[k] = tot > 0 ? (double)h[k] / (tot * p.eepf_de_ev * std::sqrt(e)) : 0.0;
+    }
+    return EDUPIC_OK;
+}
+
+int edupic_get_ifed(edupic_sim *S, int d, double *energy_ev, double *f_pow, double *f_gnd)
+{
+    if (!valid_d(S, d)) return EDUPIC_EINVAL;
+    const edupic_params &p = S->params[d];
+    std::vector<int64_t> hp((size_t)p.ifed_bins), hg((size_t)p.ifed_bins);
+    int rc = edupic_get_diagnostics(S, d, nullptr, nullptr, nullptr, nullptr, hp.data(), hg.data(), nullptr);
+    if (rc) return rc;
+    double tp = 0.0, tg = 0.0;
+    for (int k = 0; k < p.ifed_bins; ++k) {
+        tp += (double)hp[k];
+        tg += (double)hg[k];
+    }
+    for (int k = 0; k < p.ifed_bins; ++k) {
+        if (energy_ev) energy_ev[k] = (k + 0.5) * p.ifed_de_ev;
+        if (f_pow) f_pow[k] = tp > 0 ? (double)hp[k] / (tp * p.ifed_de_ev) : 0.0;
+        if (f_gnd) f_gnd[k] = tg > 0 ? (double)hg[k] / (tg * p.ifed_de_ev) : 0.0;
+    }
+    return EDUPIC_OK;
+}
+
+int edupic_get_counters(edupic_sim *S, int d, int64_t out[EDUPIC_N_COUNTERS])
+{
+    if (!valid_d(S, d) || !out) return EDUPIC_EINVAL;
+    Ctrl c;
+    int rc = read_ctrl(S, d, &c);
+    if (rc) return rc;
+    for (int k = 0; k < EDUPIC_N_COUNTERS; ++k) out[k] = (int64_t)c.counters[k];
+    return error_of(c);
+}
+
+int edupic_reset_diagnostics(edupic_sim *S, int d)
+{
+    if (!valid_d(S, d)) return EDUPIC_EINVAL;
+    const DischargeDev &D = S->desc[d];
+    const edupic_params &p = S->params[d];
+    const size_t ng = (size_t)p.n_grid;
+    cudaError_t e = cudaMemsetAsync(D.sum_ne, 0, ng * 8, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.sum_ni, 0, ng * 8, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.sum_phi, 0, ng * 8, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.eepf, 0, (size_t)p.eepf_bins * 8, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.ifed_pow, 0, (size_t)p.ifed_bins * 8, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.ifed_gnd, 0, (size_t)p.ifed_bins * 8, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&D.ctrl->measured, 0, sizeof(long long), S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    return cuda_status(e);
+}
+
+// Checkpoint file: magic, version, step, counts, then x, vx, vy, vz of the
+// electrons and of the ions as FP64.
+static const char kMagic[8] = {'E', 'D', 'U', 'P', 'I', 'C', 'C', 'K'};
+static const int32_t kVersion = 1;
+
+int edupic_save_state(edupic_sim *S, int d, const char *path)
+{
+    if (!valid_d(S, d) || !path) return EDUPIC_EINVAL;
+    Ctrl c;
+    int rc = read_ctrl(S, d, &c);
+    if (rc) return rc;
+    rc = error_of(c);
+    if (rc) return rc;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return EDUPIC_EIO;
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8;
+    const int32_t hdr[2] = {kVersion, S->params[d].n_grid};
+    const int64_t vals[3] = {c.step, c.n[0], c.n[1]};
+    ok = ok && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 && std::fwrite(vals, sizeof(vals), 1, f) == 1;
+    for (int sp = 0; sp < 2 && ok; ++sp) {
+        const int64_t n = c.n[sp];
+        std::vector<double> a[4];
+        double *dst[4];
+        for (int k = 0; k < 4; ++k) {
+            a[k].resize((size_t)n);
+            dst[k] = a[k].data();
+        }
+        rc = S->precision == EDUPIC_FP32 ? download_particles<float>(S, d, sp, n, dst)
+                                         : download_particles<double>(S, d, sp, n, dst);
+        if (rc) {
+            std::fclose(f);
+            return rc;
+        }
+        for (int k = 0; k < 4 && ok; ++k) ok = std::fwrite(a[k].data(), 8, (size_t)n, f) == (size_t)n;
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? EDUPIC_OK : EDUPIC_EIO;
+}
+
+int edupic_load_state(edupic_sim *S, int d, const char *path)
+{
+    if (!valid_d(S, d) || !path) return EDUPIC_EINVAL;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return EDUPIC_EIO;
+    char magic[8];
+    int32_t hdr[2];
+    int64_t vals[3];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+              std::fread(hdr, sizeof(hdr), 1, f) == 1 && std::fread(vals, sizeof(vals), 1, f) == 1;
+    ok = ok && hdr[0] == kVersion && hdr[1] == S->params[d].n_grid && vals[0] >= 0 && vals[1] >= 0 && vals[2] >= 0;
+    if (!ok) {
+        std::fclose(f);
+        return EDUPIC_EIO;
+    }
+    if (vals[1] > S->params[d].capacity_e || vals[2] > S->params[d].capacity_i) {
+        std::fclose(f);
+        return EDUPIC_ECAPACITY;
+    }
+    // every discharge of an object steps on a common ion-subcycle phase
+    if (vals[0] % S->nsub != S->phase) {
+        std::fclose(f);
+        return EDUPIC_ESTATE;
+    }
+    std::vector<double> a[2][4];
+    for (int sp = 0; sp < 2 && ok; ++sp)
+        for (int k = 0; k < 4 && ok; ++k) {
+            a[sp][k].resize((size_t)vals[1 + sp]);
+            ok = std::fread(a[sp][k].data(), 8, a[sp][k].size(), f) == a[sp][k].size();
+        }
+    std::fclose(f);
+    if (!ok) return EDUPIC_EIO;
+    long long step = vals[0];
+    if (cudaMemcpy(&S->ctrl(d)->step, &step, sizeof(step), cudaMemcpyHostToDevice) != cudaSuccess)
+        return EDUPIC_ECUDA;
+    for (int sp = 0; sp < 2; ++sp) {
+        int rc = edupic_load_particles(S, d, sp, vals[1 + sp], a[sp][0].data(), a[sp][1].data(), a[sp][2].data(),
+                                       a[sp][3].data());
+        if (rc) return rc;
+    }
+    return EDUPIC_OK;
+}
+
+const char *edupic_strerror(int status)
+{
+    switch (status) {
+    case EDUPIC_OK: return "ok";
+    case EDUPIC_EINVAL: return "invalid argument";
+    case EDUPIC_ENOMEM: return "not enough device memory (arena or budget)";
+    case EDUPIC_ECAPACITY: return "particle, hole or product capacity exceeded";
+    case EDUPIC_ECUDA: return "CUDA runtime error";
+    case EDUPIC_ESTATE: return "call not valid in the current state";
+    case EDUPIC_ENAN: return "non-finite particle position";
+    case EDUPIC_EIO: return "checkpoint file error";
+    case EDUPIC_ETIMEOUT: return "bounded wait expired";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

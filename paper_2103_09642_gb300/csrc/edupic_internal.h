@@ -1,0 +1,90 @@
+// Internal structures shared by the host orchestration and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/edupic.h"
+
+namespace edupic {
+
+constexpr int kThreads = 256;          // particle-kernel block size
+constexpr int kFinalizeThreads = 512;  // one CTA per discharge for compaction + field solve
+constexpr int kEvents = EDUPIC_STEP_EVENTS;
+
+// Device error bits (ctrl->error).
+enum : int {
+    kErrHoles = 1,     // more absorbed particles in a step than kEvents
+    kErrProducts = 2,  // more ionisations in a step than kEvents
+    kErrCapacity = 4,  // created pairs dropped at particle capacity
+    kErrNan = 8,       // non-finite position
+};
+
+// Per-discharge counters and counts, written by the kernels.
+struct Ctrl {
+    long long n[2];         // live particles per species
+    long long step;         // global step index s
+    long long measured;     // steps accumulated into the diagnostics
+    int holes[2];           // absorbed particles of the current step, per species
+    int products;           // ionisations of the current step
+    int error;              // kErr* bits
+    unsigned long long counters[EDUPIC_N_COUNTERS];
+};
+
+// One cross-section table entry: n*sigma_tot is formed in the kernel as
+// sigsum * n_gas; thr1, thr2 are the cumulative process fractions.
+template <typename T>
+struct alignas(4 * sizeof(T)) CsEntry {
+    T sigsum, thr1, thr2, pad;
+};
+
+// Everything a kernel needs about one discharge (in device memory).
+struct DischargeDev {
+    // constants (FP64 values; FP32 copies below)
+    double L, dx, inv_dx, dt_e, dt_i, factor_w, factor_e, factor_i, n_gas, sig_th;
+    double half_me, half_mar, half_mu_e, half_mu_arar, mu_e, ar_mass, e_exc, e_ion;
+    double eepf_lo, eepf_hi, eepf_de, ifed_de, cs_de_e, cs_de_i;
+    double poisson_c;   // dx^2 e FACTOR_W / (eps0 2^32): f_p = c (Q_i - Q_e)
+    double rho_c;       // e FACTOR_W / 2^32
+    double harm_freq[EDUPIC_MAX_HARMONICS];
+    double harm_volt[EDUPIC_MAX_HARMONICS];
+    float Lf, inv_dxf, dt_ef, dt_if, factor_ef, factor_if, n_gasf, sig_thf;
+    float e_of_v2_ef, e_of_v2_if, e_of_g2_if, mu_ef, e_excf, e_ionf;
+    float eepf_lof, eepf_hif, inv_eepf_def, inv_ifed_def, inv_cs_de_ef, inv_cs_de_if;
+    float vscale_mu_ef;   // sqrt(2 e / mu_e)
+    float vscale_ef;      // sqrt(2 e / m_e)
+    float mass_ratio_ef;  // m_e / (m_e + M)
+    float mass_ratio2_ef; // M / (m_e + M)
+    int ng, nt, nsub, n_harm, eepf_bins, ifed_bins, cs_n_e, cs_n_i;
+    int active;
+    int pad0;
+    long long cap[2];
+    unsigned long long seed;
+    // particle SoA (T = float or double)
+    void *x[2], *vx[2], *vy[2], *vz[2];
+    // grid (FP64 unless noted)
+    long long *q_e, *q_i;      // deposition sums used by the current step
+    long long *acc_e, *acc_i;  // deposition of the next step (ions: next ion step)
+    double *n_e, *n_i, *phi, *ef;
+    void *ef_t;                // field in particle precision
+    double *sum_ne, *sum_ni, *sum_phi;
+    unsigned long long *eepf, *ifed_pow, *ifed_gnd;
+    Ctrl *ctrl;
+    int *holes[2];
+    int *prod_parent;
+    void *prod_x, *prod_ve[3], *prod_vi[3];
+    const void *cs_e, *cs_i;   // CsEntry<T> tables
+};
+
+// Launchers implemented per precision (kernels_f32.cu / kernels_f64.cu).
+template <typename T>
+struct Launch {
+    static cudaError_t deposit(const DischargeDev *dd, int nd, int d, int species, int also_acc, cudaStream_t st);
+    static cudaError_t fields(const DischargeDev *dd, int nd, int d, cudaStream_t st);
+    static cudaError_t push(const DischargeDev *dd, int nd, int species, int measure, int grid, int ng_max,
+                            int eepf_max, cudaStream_t st);
+    static cudaError_t finalize(const DischargeDev *dd, int nd, int ion_step, int measure, cudaStream_t st);
+    static size_t push_smem(int nd, int ng_max, int eepf_max);
+    static int push_blocks_per_sm(int species, size_t smem);
+};
+
+}  // namespace edupic

@@ -1,0 +1,277 @@
+"""Thin Python binding of the C ABI in ``include/edupic.h``.
+
+Argument marshalling only: device memory (one arena per simulation) and the
+stream come from PyTorch; every step of the particle loop runs in the CUDA
+library ``_build/libedupic_gb300.so``.  There is no CPU fallback: if the
+library is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, List, Optional, Sequence
+
+import numpy as np
+
+from .workloads import Discharge, Particles
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libedupic_gb300.so")
+
+FP64, FP32 = 0, 1
+ELECTRONS, IONS = 0, 1
+MAX_HARMONICS = 4
+N_COUNTERS = 16
+STEP_EVENTS = 8192
+COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela", "coll_e_exc",
+                 "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped")
+STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECAPACITY", -4: "ECUDA", -5: "ESTATE", -6: "ENAN",
+          -7: "EIO", -8: "ETIMEOUT"}
+
+
+class EdupicError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("gap_m", ctypes.c_double), ("pressure_pa", ctypes.c_double), ("gas_temp_k", ctypes.c_double),
+        ("area_m2", ctypes.c_double), ("weight", ctypes.c_double),
+        ("n_grid", ctypes.c_int32), ("steps_per_cycle", ctypes.c_int32), ("ion_subcycle", ctypes.c_int32),
+        ("n_harmonics", ctypes.c_int32), ("cycle_freq_hz", ctypes.c_double),
+        ("harm_freq_hz", ctypes.c_double * MAX_HARMONICS), ("harm_volt_v", ctypes.c_double * MAX_HARMONICS),
+        ("seed", ctypes.c_uint64), ("eepf_bins", ctypes.c_int32), ("ifed_bins", ctypes.c_int32),
+        ("eepf_de_ev", ctypes.c_double), ("ifed_de_ev", ctypes.c_double),
+        ("capacity_e", ctypes.c_int64), ("capacity_i", ctypes.c_int64),
+        ("e_exc_ev", ctypes.c_double), ("e_ion_ev", ctypes.c_double),
+        ("cs_entries", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+def to_params(d: Discharge, cs_entries: int) -> Params:
+    p = Params()
+    p.gap_m, p.pressure_pa, p.gas_temp_k, p.area_m2, p.weight = (d.gap_m, d.pressure_pa, d.gas_temp_k,
+                                                                  d.area_m2, d.weight)
+    p.n_grid, p.steps_per_cycle, p.ion_subcycle = d.n_grid, d.steps_per_cycle, d.ion_subcycle
+    p.n_harmonics = len(d.harmonics)
+    p.cycle_freq_hz = d.cycle_freq_hz
+    for k, (f, v) in enumerate(d.harmonics):
+        p.harm_freq_hz[k] = f
+        p.harm_volt_v[k] = v
+    p.seed = d.seed
+    p.eepf_bins, p.ifed_bins, p.eepf_de_ev, p.ifed_de_ev = d.eepf_bins, d.ifed_bins, d.eepf_de_ev, d.ifed_de_ev
+    p.capacity_e = p.capacity_i = d.capacity
+    p.e_exc_ev, p.e_ion_ev = d.e_exc_ev, d.e_ion_ev
+    p.cs_entries = cs_entries
+    return p
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+_Q = ctypes.POINTER(ctypes.c_int64)
+_VP = ctypes.c_void_p
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA extension not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER(Params)
+    sig = {
+        "edupic_arena_bytes": ([ctypes.c_int, P, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+        "edupic_create": ([ctypes.c_int, P, ctypes.c_int, _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+        "edupic_destroy": ([_VP]),
+        "edupic_set_cross_sections": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]),
+        "edupic_load_particles": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _D, _D, _D, _D]),
+        "edupic_step": ([_VP, ctypes.c_int64, ctypes.c_int]),
+        "edupic_run_cycles": ([_VP, ctypes.c_int, ctypes.c_int]),
+        "edupic_synchronize": ([_VP]),
+        "edupic_set_graphs": ([_VP, ctypes.c_int]),
+        "edupic_get_counts": ([_VP, ctypes.c_int, _Q, _Q, _Q]),
+        "edupic_get_particles": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _D, _D, _D, _D, _Q]),
+        "edupic_get_fields": ([_VP, ctypes.c_int, _D, _D, _D, _D, _Q, _Q]),
+        "edupic_get_diagnostics": ([_VP, ctypes.c_int, _D, _D, _D, _Q, _Q, _Q, _Q]),
+        "edupic_get_eepf": ([_VP, ctypes.c_int, _D, _D]),
+        "edupic_get_ifed": ([_VP, ctypes.c_int, _D, _D, _D]),
+        "edupic_get_counters": ([_VP, ctypes.c_int, _Q]),
+        "edupic_reset_diagnostics": ([_VP, ctypes.c_int]),
+        "edupic_save_state": ([_VP, ctypes.c_int, ctypes.c_char_p]),
+        "edupic_load_state": ([_VP, ctypes.c_int, ctypes.c_char_p]),
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.edupic_strerror.argtypes = [ctypes.c_int]
+    L.edupic_strerror.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _ck(rc: int, what: str):
+    if rc != 0:
+        raise EdupicError(rc, what)
+
+
+def _ptr(a: np.ndarray, ct=ctypes.c_double):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+class Simulation:
+    """n discharges stepped together on one CUDA stream.
+
+    ``precision`` is FP64 or FP32 (particles, push and collisions; the field
+    solve and diagnostics stay FP64).  Device memory is a single torch uint8
+    tensor (the arena); ``stream`` is a ``torch.cuda.Stream`` (default: a new
+    stream on the current device).
+    """
+
+    def __init__(self, discharges: Sequence[Discharge], precision: int = FP64, stream=None,
+                 cs_entries: int = 1_000_000, device: Optional[str] = None):
+        import torch
+
+        self._torch = torch
+        self.L = load_library()
+        self.discharges = list(discharges)
+        self.nd = len(self.discharges)
+        self.precision = precision
+        arr = (Params * self.nd)(*[to_params(d, cs_entries) for d in self.discharges])
+        self._params = arr
+        nbytes = ctypes.c_size_t(0)
+        _ck(self.L.edupic_arena_bytes(self.nd, arr, precision, ctypes.byref(nbytes)), "arena_bytes")
+        self.arena_bytes = int(nbytes.value)
+        dev = torch.device(device) if device else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self.arena = torch.empty(self.arena_bytes, dtype=torch.uint8, device=dev)
+        h = _VP()
+        with torch.cuda.device(dev):
+            _ck(self.L.edupic_create(self.nd, arr, precision, ctypes.c_void_p(self.arena.data_ptr()),
+                                     self.arena_bytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+                "create")
+        self._h = h
+
+    # ------------------------------------------------------------- lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            self.L.edupic_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------- set-up
+    def set_cross_sections(self, species: int, sigma: np.ndarray, de_ev: float):
+        s = np.ascontiguousarray(sigma, dtype=np.float64)
+        _ck(self.L.edupic_set_cross_sections(self._h, species, s.shape[0], s.shape[1], de_ev, _ptr(s)),
+            "set_cross_sections")
+
+    def load(self, d: int, species: int, parts: Particles):
+        a = [np.ascontiguousarray(getattr(parts, k), dtype=np.float64) for k in ("x", "vx", "vy", "vz")]
+        _ck(self.L.edupic_load_particles(self._h, d, species, a[0].size, *[_ptr(v) for v in a]), "load_particles")
+
+    # ------------------------------------------------------------- stepping
+    def step(self, n: int, measure: bool = False):
+        _ck(self.L.edupic_step(self._h, int(n), 1 if measure else 0), "step")
+
+    def run_cycles(self, n: int, measure: bool = False):
+        _ck(self.L.edupic_run_cycles(self._h, int(n), 1 if measure else 0), "run_cycles")
+
+    def synchronize(self):
+        _ck(self.L.edupic_synchronize(self._h), "synchronize")
+
+    def set_graphs(self, enable: bool):
+        _ck(self.L.edupic_set_graphs(self._h, 1 if enable else 0), "set_graphs")
+
+    # ------------------------------------------------------------- read-back
+    def counts(self, d: int = 0):
+        ne, ni, st = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _ck(self.L.edupic_get_counts(self._h, d, ctypes.byref(ne), ctypes.byref(ni), ctypes.byref(st)), "counts")
+        return ne.value, ni.value, st.value
+
+    def particles(self, d: int, species: int) -> List[np.ndarray]:
+        n = self.counts(d)[species]
+        a = [np.zeros(n) for _ in range(4)]
+        out = ctypes.c_int64()
+        _ck(self.L.edupic_get_particles(self._h, d, species, n, *[_ptr(v) for v in a], ctypes.byref(out)),
+            "get_particles")
+        return a
+
+    def fields(self, d: int = 0) -> dict:
+        ng = self.discharges[d].n_grid
+        f = [np.zeros(ng) for _ in range(4)]
+        q = [np.zeros(ng, dtype=np.int64) for _ in range(2)]
+        _ck(self.L.edupic_get_fields(self._h, d, *[_ptr(v) for v in f], *[_ptr(v, ctypes.c_int64) for v in q]),
+            "get_fields")
+        return dict(zip(("n_e", "n_i", "phi", "efield", "q_e", "q_i"), f + q))
+
+    def diagnostics(self, d: int = 0) -> dict:
+        dd = self.discharges[d]
+        ng = dd.n_grid
+        avg = [np.zeros(ng) for _ in range(3)]
+        e = np.zeros(dd.eepf_bins, dtype=np.int64)
+        ip = np.zeros(dd.ifed_bins, dtype=np.int64)
+        ig = np.zeros(dd.ifed_bins, dtype=np.int64)
+        m = ctypes.c_int64()
+        _ck(self.L.edupic_get_diagnostics(self._h, d, *[_ptr(v) for v in avg],
+                                          *[_ptr(v, ctypes.c_int64) for v in (e, ip, ig)], ctypes.byref(m)),
+            "get_diagnostics")
+        return dict(measured_steps=m.value, n_e=avg[0], n_i=avg[1], phi=avg[2], eepf_counts=e,
+                    ifed_pow_counts=ip, ifed_gnd_counts=ig)
+
+    def eepf(self, d: int = 0):
+        n = self.discharges[d].eepf_bins
+        e, f = np.zeros(n), np.zeros(n)
+        _ck(self.L.edupic_get_eepf(self._h, d, _ptr(e), _ptr(f)), "get_eepf")
+        return e, f
+
+    def ifed(self, d: int = 0):
+        n = self.discharges[d].ifed_bins
+        e, fp, fg = np.zeros(n), np.zeros(n), np.zeros(n)
+        _ck(self.L.edupic_get_ifed(self._h, d, _ptr(e), _ptr(fp), _ptr(fg)), "get_ifed")
+        return e, fp, fg
+
+    def counters(self, d: int = 0) -> dict:
+        c = np.zeros(N_COUNTERS, dtype=np.int64)
+        _ck(self.L.edupic_get_counters(self._h, d, _ptr(c, ctypes.c_int64)), "get_counters")
+        return {k: int(c[i]) for i, k in enumerate(COUNTER_NAMES)}
+
+    def reset_diagnostics(self, d: int = 0):
+        _ck(self.L.edupic_reset_diagnostics(self._h, d), "reset_diagnostics")
+
+    def save_state(self, d: int, path: str):
+        _ck(self.L.edupic_save_state(self._h, d, path.encode()), "save_state")
+
+    def load_state(self, d: int, path: str):
+        _ck(self.L.edupic_load_state(self._h, d, path.encode()), "load_state")
+
+
+def simulation_for(discharges: Iterable, precision: int = FP64, sigma=None, de_ev: float = 1e-3,
+                   particles=None, **kw) -> Simulation:
+    """Create a simulation, set cross sections and load (e, i) particle pairs."""
+    ds = list(discharges)
+    n_entries = sigma[0].shape[1] if sigma is not None else 1
+    sim = Simulation(ds, precision=precision, cs_entries=max(n_entries, 1), **kw)
+    if sigma is not None:
+        sim.set_cross_sections(ELECTRONS, sigma[0], de_ev)
+        sim.set_cross_sections(IONS, sigma[1], de_ev)
+    if particles is not None:
+        for d, (e, i) in enumerate(particles):
+            sim.load(d, ELECTRONS, e)
+            sim.load(d, IONS, i)
+    return sim

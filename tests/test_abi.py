@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads without a GPU, and exports every entry
+point that include/edupic.h declares; parameter checks run on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2103_09642_gb300 import build_ext
+from paper_2103_09642_gb300 import edupic as ed
+from paper_2103_09642_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(edupic_[a-z0-9_]+)\s*\(", txt,
+                                flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_ext.build()
+    return ed.load_library()
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ("edupic_create", "edupic_step", "edupic_get_fields", "edupic_save_state"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_host_side_checks(lib):
+    assert lib.edupic_strerror(0) == b"ok"
+    assert lib.edupic_strerror(-3).startswith(b"particle")
+    d = wl.reference_discharge()
+    good = ed.to_params(d, 1000)
+    out = ctypes.c_size_t(0)
+    arr = (ed.Params * 1)(good)
+    assert lib.edupic_arena_bytes(1, arr, ed.FP32, ctypes.byref(out)) == 0
+    b32 = out.value
+    assert lib.edupic_arena_bytes(1, arr, ed.FP64, ctypes.byref(out)) == 0
+    assert out.value > b32 > 0
+    for field, bad in (("n_grid", 2), ("n_grid", 5000), ("ion_subcycle", 7), ("capacity_e", 0),
+                       ("eepf_bins", 4096), ("weight", -1.0), ("gap_m", 0.0)):
+        p = ed.to_params(d, 1000)
+        setattr(p, field, bad)
+        assert lib.edupic_arena_bytes(1, (ed.Params * 1)(p), ed.FP32, ctypes.byref(out)) == -1, field
+    p = ed.to_params(d.replace(harmonics=((13.56e6 * 1.5, 100.0),)), 1000)   # not a multiple
+    assert lib.edupic_arena_bytes(1, (ed.Params * 1)(p), ed.FP32, ctypes.byref(out)) == -1
+    assert lib.edupic_arena_bytes(0, arr, ed.FP32, ctypes.byref(out)) == -1
+    assert lib.edupic_arena_bytes(1, arr, 7, ctypes.byref(out)) == -1
+
+
+def test_create_rejects_small_or_misaligned_arena(lib):
+    d = wl.reference_discharge()
+    arr = (ed.Params * 1)(ed.to_params(d, 1000))
+    out = ctypes.c_size_t(0)
+    assert lib.edupic_arena_bytes(1, arr, ed.FP32, ctypes.byref(out)) == 0
+    h = ctypes.c_void_p()
+    # never dereferenced: both are rejected before any device call
+    assert lib.edupic_create(1, arr, ed.FP32, ctypes.c_void_p(256), out.value - 1, None, ctypes.byref(h)) == -2
+    assert lib.edupic_create(1, arr, ed.FP32, ctypes.c_void_p(257), out.value, None, ctypes.byref(h)) == -1

@@ -1,0 +1,238 @@
+"""Parity of the CUDA particle loop with the CPU oracle, through the C ABI.
+
+Tolerances (derived in the design notes):
+* integer work (cell indices, fixed-point deposition, collision counts,
+  particle counts, histograms) is compared exactly;
+* the field solve: the GPU sums the exact integer form of the tridiagonal
+  system, the oracle runs the Thomas algorithm in FP64, so phi agrees to
+  1e-12 of max|phi| and E to 1e-9 of max|E|;
+* FP64 particle states after k steps: |dx| <= 1e-12 L, |dv| <= 1e-10 v_scale
+  (the field difference above plus last-bit differences of libm functions
+  in colliding particles).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_09642_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2103_09642_gb300 import build_ext  # noqa: E402
+from paper_2103_09642_gb300 import edupic as ed  # noqa: E402
+
+build_ext.build()
+
+SE, SI = wl.standin_cross_sections(300_000)
+DE = wl.CS_DE_EV
+
+
+def _pair(d, e, i, precision=ed.FP64, sigma=(SE, SI)):
+    sim = ed.simulation_for([d], precision, sigma=sigma, de_ev=DE, particles=[(e, i)])
+    ref = oracle.Sim(d, sigma[0], sigma[1], DE, e, i)
+    return sim, ref
+
+
+def _vscale(v):
+    return max(float(np.sqrt(np.mean(v * v))) if v.size else 1.0, 1.0)
+
+
+def _compare_states(sim, ref, d, tol_x=1e-12, tol_v=1e-10):
+    for sp in (0, 1):
+        g = sim.particles(0, sp)
+        o = ref.particles(sp)
+        assert g[0].size == o[0].size, f"species {sp}: count {g[0].size} vs {o[0].size}"
+        if not o[0].size:
+            continue
+        assert np.abs(g[0] - o[0]).max() <= tol_x * d.gap_m, f"species {sp}: positions"
+        for c in (1, 2, 3):
+            vs = _vscale(o[c])
+            err = np.abs(g[c] - o[c]).max()
+            assert err <= tol_v * vs, f"species {sp} component {c}: {err} vs scale {vs}"
+
+
+# --------------------------------------------------------------- deposition
+@pytest.mark.parametrize("precision", [ed.FP64, ed.FP32])
+def test_deposit_bit_exact(precision):
+    d, e, i = wl.reference_start(seed=5, n0=3000)
+    rng = np.random.default_rng(1)
+    e.x[:4] = [0.0, d.gap_m, d.gap_m * 0.5, d.gap_m * (1 - 1e-17)]
+    i.x = rng.uniform(0, d.gap_m, i.n)
+    sim = ed.simulation_for([d], precision, sigma=(SE, SI), de_ev=DE, particles=[(e, i)])
+    f = sim.fields(0)
+    ref = oracle.Sim(d, SE, SI, DE)
+    inv_dx = ref.derived()["inv_dx"]
+    if precision == ed.FP64:
+        qe = oracle.deposit_fixed(e.x, d.n_grid, inv_dx)
+        qi = oracle.deposit_fixed(i.x, d.n_grid, inv_dx)
+    else:
+        qe = oracle.deposit_fixed_f32(e.x.astype(np.float32), d.n_grid, np.float32(inv_dx))
+        qi = oracle.deposit_fixed_f32(i.x.astype(np.float32), d.n_grid, np.float32(inv_dx))
+    assert (f["q_e"] == qe).all() and (f["q_i"] == qi).all()
+    assert int(f["q_e"].sum()) == e.n * 2 ** 32
+
+
+def test_field_solve_matches_thomas():
+    d, e, i = wl.reference_steady(seed=2, n=20_000)
+    sim, ref = _pair(d, e, i)
+    g = sim.fields(0)
+    o = ref.prepare_fields()
+    assert (g["q_e"] == o["q_e"]).all() and (g["q_i"] == o["q_i"]).all()
+    assert np.array_equal(g["n_e"], o["n_e"]) and np.array_equal(g["n_i"], o["n_i"])
+    assert np.abs(g["phi"] - o["phi"]).max() <= 1e-12 * np.abs(o["phi"]).max()
+    assert np.abs(g["efield"] - o["efield"]).max() <= 1e-9 * np.abs(o["efield"]).max()
+
+
+@pytest.mark.parametrize("ng", [3, 4, 129, 400, 801, 2048])
+def test_field_solve_sizes(ng):
+    d = wl.reference_discharge(n_grid=ng, capacity=1 << 14)
+    rng = np.random.default_rng(ng)
+    n = 5000
+    e = wl.maxwellian(n, d.gap_m, 1.6e-19, 9.1e-31, rng)
+    i = wl.maxwellian(n // 2, d.gap_m, 1e-21, 6.6e-26, rng)
+    sim, ref = _pair(d, e, i)
+    g = sim.fields(0)
+    o = ref.prepare_fields()
+    assert np.abs(g["phi"] - o["phi"]).max() <= 1e-12 * np.abs(o["phi"]).max()
+    assert np.abs(g["efield"] - o["efield"]).max() <= 1e-9 * np.abs(o["efield"]).max()
+
+
+# --------------------------------------------------------------- one step, zero field
+def _quiet(**kw):
+    base = dict(weight=0.0, harmonics=((0.0, 0.0),), n_grid=101, capacity=1 << 16)
+    base.update(kw)
+    return wl.Discharge(**base)
+
+
+def test_zero_field_collisions_bit_exact_selection():
+    d = _quiet(gap_m=0.025)
+    rng = np.random.default_rng(4)
+    n = 20_000
+    e = wl.maxwellian(n, d.gap_m, 8.0 * 1.602176634e-19, 9.1093837015e-31, rng,
+                      x=rng.uniform(0.005, 0.02, n))
+    i = wl.maxwellian(n, d.gap_m, 1.380649e-23 * 3000, 6.6335e-26, rng, x=rng.uniform(0.005, 0.02, n))
+    sim, ref = _pair(d, e, i)
+    for k in range(3):
+        sim.step(1)
+        ref.step(1)
+        assert sim.counters(0) == ref.counters(), f"step {k}"
+        # positions are bit-identical until a collider's velocity (libm
+        # functions) differs in its last bit
+        _compare_states(sim, ref, d, tol_x=0.0 if k == 0 else 1e-14, tol_v=1e-12)
+
+
+def test_absorption_compaction_order():
+    d = _quiet(gap_m=1e-3, n_grid=11)
+    rng = np.random.default_rng(7)
+    n = 6000
+    e = wl.maxwellian(n, d.gap_m, 50 * 1.602176634e-19, 9.1093837015e-31, rng)
+    i = wl.maxwellian(n, d.gap_m, 1.380649e-23 * 3e6, 6.6335e-26, rng)
+    sim, ref = _pair(d, e, i, sigma=wl.constant_cross_sections(1000, DE, (0, 0, 0), (0, 0)))
+    for k in range(4):
+        sim.step(1)
+        ref.step(1)
+        assert sim.counters(0) == ref.counters()
+        _compare_states(sim, ref, d, tol_x=0.0, tol_v=0.0)
+    c = ref.counters()
+    assert c["abs_e_pow"] > 100 and c["abs_e_gnd"] > 100 and c["abs_i_pow"] > 10
+
+
+# --------------------------------------------------------------- multi-step FP64 parity
+@pytest.mark.parametrize("seed", [1, 2])
+def test_reference_start_fp64_per_step(seed):
+    d, e, i = wl.reference_start(seed=seed, n0=1000)
+    sim, ref = _pair(d, e, i)
+    for chunk in (1, 19, 20, 60, 100):
+        sim.step(chunk)
+        ref.step(chunk)
+        assert sim.counts(0)[2] == ref.step_index
+        assert sim.counters(0) == ref.counters()
+        _compare_states(sim, ref, d)
+        g = sim.fields(0)
+        o = ref.prepare_fields()
+        # the field solves differ in the last bits, so a particle's 2^-32 split
+        # may round the other way: at most one unit per particle
+        n_e, n_i = sim.counts(0)[:2]
+        assert int(np.abs(g["q_e"] - o["q_e"]).sum()) <= 2 * n_e
+        assert int(np.abs(g["q_i"] - o["q_i"]).sum()) <= 2 * n_i
+        assert g["q_e"].sum() == o["q_e"].sum() == n_e * 2 ** 32
+
+
+def test_steady_shape_fp64_with_ionisation():
+    d, e, i = wl.reference_steady(seed=4, n=30_000)
+    d = d.replace(harmonics=((13.56e6, 400.0),))
+    sim, ref = _pair(d, e, i)
+    sim.step(120, measure=True)
+    ref.step(120, measure=True)
+    c = ref.counters()
+    assert c["coll_e_ion"] > 0 and c["created"] > 0 and c["coll_i_back"] > 0
+    assert sim.counters(0) == c
+    _compare_states(sim, ref, d)
+    gd, od = sim.diagnostics(0), ref.diagnostics()
+    assert gd["measured_steps"] == od["measured_steps"] == 120
+    for k in ("eepf_counts", "ifed_pow_counts", "ifed_gnd_counts"):
+        assert (gd[k] == od[k]).all(), k
+    for k in ("n_e", "n_i"):
+        assert np.abs(gd[k] - od[k]).max() <= 1e-9 * np.abs(od[k]).max(), k
+    assert np.abs(gd["phi"] - od["phi"]).max() <= 1e-12 * np.abs(od["phi"]).max()
+
+
+# --------------------------------------------------------------- graph, batch, checkpoint
+def _run(ds, parts, precision, steps, graphs=True, measure=False):
+    sim = ed.simulation_for(ds, precision, sigma=(SE, SI), de_ev=DE, particles=parts)
+    sim.set_graphs(graphs)
+    sim.step(steps, measure=measure)
+    out = [[sim.particles(k, sp) for sp in (0, 1)] for k in range(len(ds))]
+    diag = [sim.diagnostics(k) for k in range(len(ds))]
+    cnt = [sim.counters(k) for k in range(len(ds))]
+    sim.close()
+    return out, diag, cnt
+
+
+@pytest.mark.parametrize("precision", [ed.FP64, ed.FP32])
+def test_graph_replay_identical(precision):
+    d, e, i = wl.reference_steady(seed=6, n=20_000)
+    a = _run([d], [(e, i)], precision, 47, graphs=True, measure=True)
+    b = _run([d], [(e, i)], precision, 47, graphs=False, measure=True)
+    for sp in (0, 1):
+        for c in range(4):
+            assert np.array_equal(a[0][0][sp][c], b[0][0][sp][c])
+    assert a[2] == b[2]
+    assert np.array_equal(a[1][0]["eepf_counts"], b[1][0]["eepf_counts"])
+
+
+@pytest.mark.parametrize("precision", [ed.FP64, ed.FP32])
+def test_batched_equals_alone(precision):
+    mix = wl.batch_mix(n_discharges=4, seed0=77, scale=0.01)
+    ds = [m[0] for m in mix]
+    parts = [(m[1], m[2]) for m in mix]
+    together = _run(ds, parts, precision, 41, measure=True)
+    for k in range(len(ds)):
+        alone = _run([ds[k]], [parts[k]], precision, 41, measure=True)
+        assert together[2][k] == alone[2][0]
+        for sp in (0, 1):
+            for c in range(4):
+                assert np.array_equal(together[0][k][sp][c], alone[0][0][sp][c])
+        assert np.array_equal(together[1][k]["n_e"], alone[1][0]["n_e"])
+
+
+def test_checkpoint_resume_is_exact(tmp_path):
+    d, e, i = wl.reference_start(seed=9, n0=2000)
+    full = _run([d], [(e, i)], ed.FP64, 80)
+    sim = ed.simulation_for([d], ed.FP64, sigma=(SE, SI), de_ev=DE, particles=[(e, i)])
+    sim.step(40)
+    path = str(tmp_path / "state.bin")
+    sim.save_state(0, path)
+    sim.close()
+    sim2 = ed.simulation_for([d], ed.FP64, sigma=(SE, SI), de_ev=DE)
+    sim2.load_state(0, path)
+    assert sim2.counts(0)[2] == 40
+    sim2.step(40)
+    for sp in (0, 1):
+        got = sim2.particles(0, sp)
+        for c in range(4):
+            assert np.array_equal(got[c], full[0][0][sp][c])

@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 PIC/MCC particle loop.
+
+One bench step = one RF cycle (N_T = 4000 time steps, ions every N_SUB = 20)
+of the reference argon discharge (250 V, 13.56 MHz, 25 mm, 10 Pa, 350 K,
+N_G = 400) in a synthetic steady-shape state of ~5e5 electrons + 5e5 Ar+
+(weight 1.4e4), FP32 particles, FP64 field solve, diagnostics on.  The
+metric is particle-steps/s (electron pushes every step + ion pushes on ion
+steps).  With --gpus N under torchrun every rank runs its own replica
+(independent discharges: no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (single thread, FP64) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s and % HBM roofline; batched/served vs plain at ≤2% profile error"
+UNIT = "particle-steps/s"
+HBM_PEAK_FALLBACK = 6754.5   # GB/s, STREAM-style copy measured on this machine's GB300
+BYTES_PER_PUSH_FP32 = 24     # read x, vx, vy, vz (16 B) + write x, vx (8 B)
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the electron
+# particle kernel from one ncu capture (profiles/k_push_electron_reference_steady.md),
+# valid for the kernel source whose hash is given; null otherwise.
+TRAFFIC = {"sha": None, "bytes_per_launch": None}
+N_STEADY = 500_000
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_PEAK_FALLBACK, "measured (earlier copy of the same pool figure)"
+
+
+def _kernel_sha():
+    h = hashlib.sha256()
+    for f in ("edupic_kernels.cuh", "edupic_launch.cuh", "kernels_f32.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2103_09642_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu_index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _workload(rank: int):
+    from paper_2103_09642_gb300 import workloads as wl
+
+    d, e, i = wl.reference_steady(seed=1 + rank, n=N_STEADY, capacity=2 * N_STEADY)
+    return d, e, i
+
+
+def cpu_baseline(d, e, i, steps: int = 200) -> dict:
+    """The oracle (FP64, one thread) on the first `steps` time steps of the
+    same state: a bounded sample of the workload."""
+    import oracle
+    from paper_2103_09642_gb300 import workloads as wl
+
+    se, si = wl.standin_cross_sections()
+    ref = oracle.Sim(d, se, si, wl.CS_DE_EV, e, i)
+    t0 = time.perf_counter()
+    ref.step(steps, measure=True)
+    dt = time.perf_counter() - t0
+    c = ref.counters()
+    ps = c["push_e"] + c["push_i"]
+    return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} time steps of the same {e.n}+{i.n}-particle state, FP64, one host thread "
+                      f"({ps} particle-steps in {dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2103_09642_gb300 import workloads as wl
+
+    d, e, i = _workload(0)
+    se, si = wl.standin_cross_sections()
+    ref = oracle.Sim(d, se, si, wl.CS_DE_EV, e, i)
+    sample = 20  # time steps per bench step (one ion subcycle)
+    for _ in range(args.warmup):
+        ref.step(sample, measure=True)
+    c0 = ref.counters()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ref.step(sample, measure=True)
+    dt = time.perf_counter() - t0
+    c1 = ref.counters()
+    ps = (c1["push_e"] - c0["push_e"]) + (c1["push_i"] - c0["push_i"])
+    v = ps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "reference discharge, steady-shape 5e5 e- + 5e5 Ar+, bounded sample",
+                       "time_steps_per_bench_step": sample, "n_grid": d.n_grid},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{sample} time steps per bench step of the {e.n}+{i.n}-particle state"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2103_09642_gb300 import edupic as ed
+    from paper_2103_09642_gb300 import workloads as wl
+
+    ed.load_library()
+    d, e, i = _workload(rank)
+    se, si = wl.standin_cross_sections()
+    sim = ed.simulation_for([d], ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(e, i)])
+    stream = sim.stream
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        sim.run_cycles(1, measure=True)
+    sim.synchronize()
+    c0 = sim.counters(0)
+    clocks = Clocks(local)
+    barrier()
+    ms_total = 0.0
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)          # L2 flush between timed steps (outside the events)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.run_cycles(1, measure=True)
+        b.record(stream)
+        b.synchronize()
+        ms_total += a.elapsed_time(b)
+    barrier()
+    clk = clocks.stop()
+    sim.synchronize()
+    c1 = sim.counters(0)
+    ps = (c1["push_e"] - c0["push_e"]) + (c1["push_i"] - c0["push_i"])
+    if ws > 1:
+        t = torch.tensor([ms_total, float(ps)], dtype=torch.float64, device="cuda")
+        tm = t.clone()
+        torch.distributed.all_reduce(tm[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        ms_max, ps_all = float(tm[0]), float(t[1])
+    else:
+        ms_max, ps_all = ms_total, float(ps)
+    value = ps_all / (ms_max / 1000.0)
+    n_e, n_i, _ = sim.counts(0)
+
+    # roofline of the electron particle kernel, timed live with CUDA events
+    cp0 = sim.counters(0)
+    prof_steps = 400
+    ms_k, launches = sim.profile_steps(prof_steps, measure=True)
+    cp1 = sim.counters(0)
+    push_e_per_launch = (cp1["push_e"] - cp0["push_e"]) / max(launches[0], 1)
+    dur_s = ms_k[0] / max(launches[0], 1) / 1000.0
+    achieved = BYTES_PER_PUSH_FP32 * push_e_per_launch / dur_s / 1e9
+    peak, peak_kind = _peak_hbm()
+    sha = _kernel_sha()
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sha"] == sha else None
+    share = {k: float(v) / max(float(ms_k.sum()), 1e-12) for k, v in zip(("push_e", "push_i", "finalize"), ms_k)}
+
+    # end to end through the public API: host buffers in, diagnostics out
+    e2e = None
+    if not args.no_e2e:
+        sim2 = ed.simulation_for([d], ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV)
+        reps = max(2, min(args.steps, 5))
+        h2d = 4 * 4 * (e.n + i.n)  # x, vx, vy, vz of both species, copied as FP32
+        d2h = 0
+        tot_ps, tot_t = 0, 0.0
+        for r in range(reps + 1):
+            t0 = time.perf_counter()
+            sim2.load(0, ed.ELECTRONS, e)
+            sim2.load(0, ed.IONS, i)
+            ca = sim2.counters(0)
+            sim2.run_cycles(1, measure=True)
+            diag = sim2.diagnostics(0)
+            cb = sim2.counters(0)
+            sim2.reset_diagnostics(0)
+            t1 = time.perf_counter()
+            d2h = 8 * (3 * d.n_grid + d.eepf_bins + 2 * d.ifed_bins)
+            if r > 0:  # first repetition warms the graph
+                tot_t += t1 - t0
+                tot_ps += (cb["push_e"] - ca["push_e"]) + (cb["push_i"] - ca["push_i"])
+            assert diag["measured_steps"] > 0
+        sim2.close()
+        e2e = {"value": tot_ps / tot_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "steps": reps, "note": "load particles from host FP64 arrays + 1 RF cycle + diagnostics read-back"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(d, e, i)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "reference argon discharge (250 V, 13.56 MHz, 25 mm, 10 Pa, 350 K, N_G=400, "
+                                   "N_T=4000, N_SUB=20) in a steady-shape state, ~5e5 e- + 5e5 Ar+ per GPU, "
+                                   "1 RF cycle per step, FP32 particles, FP64 field and diagnostics",
+                       "particles_e": int(n_e), "particles_i": int(n_i), "weight": d.weight,
+                       "l2": "256 MB buffer written between timed steps (outside the timed events)",
+                       "parallelism": f"replicas x{ws}", "cross_sections": "stand-in set"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_push<float, electrons>",
+                         "bytes_per_particle_step": BYTES_PER_PUSH_FP32,
+                         "particles_per_launch": push_e_per_launch, "avg_launch_us": dur_s * 1e6,
+                         "peak_kind": peak_kind, "kernel_time_share": share, "kernel_src": sha},
+            "gpu_launches": int(args.steps * (2 * d.steps_per_cycle + d.steps_per_cycle // d.ion_subcycle)),
+            "clocks": clk,
+        }
+        if e2e:
+            line["e2e"] = e2e
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -71,6 +71,8 @@ extern "C" {
 #define EDUPIC_C_SUBTHRESHOLD 9 /* inelastic picks below threshold, executed as elastic */
 #define EDUPIC_C_CREATED 10     /* e-/Ar+ pairs created by ionisation */
 #define EDUPIC_C_DROPPED 11     /* created pairs dropped at capacity */
+#define EDUPIC_C_PUSH_E 12      /* electron pushes (particle-steps) */
+#define EDUPIC_C_PUSH_I 13      /* ion pushes (particle-steps, ion steps only) */
 
 /* ---------------------------------------------------------------- parameters */
 /* One discharge (Table 1 / Table 2 quantities of the paper).  SI units except
@@ -155,6 +157,14 @@ int edupic_run_cycles(edupic_sim *sim, int n_cycles, int measure);
 
 /* Wait for the stream and return the first device-side error (or OK). */
 int edupic_synchronize(edupic_sim *sim);
+
+/* Run n_steps exactly as edupic_step does, but launch by launch (no graph)
+ * with a CUDA event pair on the object's stream around every kernel, and
+ * synchronise after each step.  out_ms[0..2] receive the summed device time
+ * (ms) of the electron particle kernel, the ion particle kernel and the
+ * per-discharge finalize kernel (compaction, append, field solve);
+ * launches[0..2] their launch counts.  Both arrays are host memory. */
+int edupic_profile_steps(edupic_sim *sim, int64_t n_steps, int measure, double out_ms[3], int64_t launches[3]);
 
 /* Use (1, default) or bypass (0) the CUDA graph that replays one ion
  * subcycle of kernel launches.  Results are identical either way. */

@@ -27,7 +27,8 @@ _lib = None
 MAX_HARM = 4
 N_COUNTERS = 16
 COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela", "coll_e_exc",
-                 "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped")
+                 "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped",
+                 "push_e", "push_i")
 
 
 def build(force: bool = False) -> str:

@@ -185,7 +185,9 @@ enum {
     ORC_C_COLL_I_BACK,
     ORC_C_SUBTHRESHOLD,
     ORC_C_CREATED,
-    ORC_C_DROPPED
+    ORC_C_DROPPED,
+    ORC_C_PUSH_E,
+    ORC_C_PUSH_I
 };
 
 /* ------------------------------------------------------------------------ */
@@ -657,6 +659,8 @@ static void one_step(orc_sim *s, int measure)
      * EEPF sampled in the centre 10% of the gap with the time-centred velocity
      * (Sec. 3.5).  Reading: the sample uses x(t) and v(t) = (v(t-dt/2) +
      * v(t+dt/2))/2. */
+    s->counters[ORC_C_PUSH_E] += E->n;
+    if (ion_step) s->counters[ORC_C_PUSH_I] += I->n;
     for (int64_t k = 0; k < E->n; ++k) {
         int c;
         double c0;

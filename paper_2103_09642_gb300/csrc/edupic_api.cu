@@ -597,6 +597,61 @@ int edupic_synchronize(edupic_sim *S)
     return EDUPIC_OK;
 }
 
+int edupic_profile_steps(edupic_sim *S, int64_t n_steps, int measure, double out_ms[3], int64_t launches[3])
+{
+    if (!S || n_steps < 0 || !out_ms || !launches) return EDUPIC_EINVAL;
+    if (!S->cs_set[0] || !S->cs_set[1]) return EDUPIC_ESTATE;
+    measure = measure ? 1 : 0;
+    cudaEvent_t ev[4];
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return EDUPIC_ECUDA;
+    for (int k = 0; k < 3; ++k) {
+        out_ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    int rc = EDUPIC_OK;
+    for (int64_t i = 0; i < n_steps && rc == EDUPIC_OK; ++i) {
+        const bool ion = S->phase == 0;
+        cudaError_t e = cudaEventRecord(ev[0], S->stream);
+        if (S->precision == EDUPIC_FP32) {
+            if (e == cudaSuccess)
+                e = Launch<float>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max, S->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1], S->stream);
+            if (e == cudaSuccess && ion)
+                e = Launch<float>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max, S->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2], S->stream);
+            if (e == cudaSuccess) e = Launch<float>::finalize(S->d_desc, S->nd, ion ? 1 : 0, measure, S->stream);
+        } else {
+            if (e == cudaSuccess)
+                e = Launch<double>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max, S->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1], S->stream);
+            if (e == cudaSuccess && ion)
+                e = Launch<double>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max, S->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2], S->stream);
+            if (e == cudaSuccess) e = Launch<double>::finalize(S->d_desc, S->nd, ion ? 1 : 0, measure, S->stream);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3], S->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+        float ms[3] = {0, 0, 0};
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
+        if (e == cudaSuccess && ion) e = cudaEventElapsedTime(&ms[1], ev[1], ev[2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[2], ev[2], ev[3]);
+        if (e != cudaSuccess) {
+            rc = EDUPIC_ECUDA;
+            break;
+        }
+        out_ms[0] += ms[0];
+        out_ms[1] += ms[1];
+        out_ms[2] += ms[2];
+        launches[0] += 1;
+        launches[1] += ion ? 1 : 0;
+        launches[2] += 1;
+        S->phase = (S->phase + 1) % S->nsub;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    return rc;
+}
+
 int edupic_set_graphs(edupic_sim *S, int enable)
 {
     if (!S) return EDUPIC_EINVAL;

@@ -501,6 +501,10 @@ __global__ void __launch_bounds__(kThreads) k_push(const DischargeDev *__restric
         }
         const long long base = (t - sPre[cur]) * (long long)TILE + (long long)tid * VEC;
         if (base >= n) continue;
+        {
+            const long long live = n - base < VEC ? n - base : VEC;
+            atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_PUSH_E : EDUPIC_C_PUSH_I), (unsigned int)live);
+        }
 
         T *X = reinterpret_cast<T *>(D->x[SP]);
         T *VX = reinterpret_cast<T *>(D->vx[SP]);

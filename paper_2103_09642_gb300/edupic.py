@@ -24,7 +24,8 @@ MAX_HARMONICS = 4
 N_COUNTERS = 16
 STEP_EVENTS = 8192
 COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela", "coll_e_exc",
-                 "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped")
+                 "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped",
+                 "push_e", "push_i")
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECAPACITY", -4: "ECUDA", -5: "ESTATE", -6: "ENAN",
           -7: "EIO", -8: "ETIMEOUT"}
 
@@ -93,6 +94,7 @@ def load_library(path: str = LIB_PATH):
         "edupic_run_cycles": ([_VP, ctypes.c_int, ctypes.c_int]),
         "edupic_synchronize": ([_VP]),
         "edupic_set_graphs": ([_VP, ctypes.c_int]),
+        "edupic_profile_steps": ([_VP, ctypes.c_int64, ctypes.c_int, _D, _Q]),
         "edupic_get_counts": ([_VP, ctypes.c_int, _Q, _Q, _Q]),
         "edupic_get_particles": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _D, _D, _D, _D, _Q]),
         "edupic_get_fields": ([_VP, ctypes.c_int, _D, _D, _D, _D, _Q, _Q]),
@@ -194,6 +196,15 @@ class Simulation:
 
     def synchronize(self):
         _ck(self.L.edupic_synchronize(self._h), "synchronize")
+
+    def profile_steps(self, n: int, measure: bool = False):
+        """Per-kernel device time (ms) and launch counts over n steps:
+        (electron push, ion push, finalize)."""
+        ms = np.zeros(3)
+        cnt = np.zeros(3, dtype=np.int64)
+        _ck(self.L.edupic_profile_steps(self._h, int(n), 1 if measure else 0, _ptr(ms), _ptr(cnt, ctypes.c_int64)),
+            "profile_steps")
+        return ms, cnt
 
     def set_graphs(self, enable: bool):
         _ck(self.L.edupic_set_graphs(self._h, 1 if enable else 0), "set_graphs")

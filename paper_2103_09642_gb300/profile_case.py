@@ -1,0 +1,52 @@
+"""A short, fixed run of the particle loop for profiler captures.
+
+  python -m paper_2103_09642_gb300.profile_case --n 5000000 --steps 3 [--fp64] [--discharges K]
+
+Runs the reference discharge in a steady-shape state with n particles per
+species (split over K independent discharges), `warmup` + `steps` time
+steps launched one by one, then prints the counters.  Sizes above ~3e6 per
+species put the FP32 particle state (16 B per particle) above the 126 MB L2.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=5_000_000)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--discharges", type=int, default=1)
+    ap.add_argument("--measure", action="store_true")
+    a = ap.parse_args()
+
+    import torch
+
+    from . import edupic as ed
+    from . import workloads as wl
+
+    torch.cuda.set_device(0)
+    per = a.n // a.discharges
+    ds, parts = [], []
+    for k in range(a.discharges):
+        d, e, i = wl.reference_steady(seed=1 + k, n=per, capacity=2 * per)
+        ds.append(d)
+        parts.append((e, i))
+    se, si = wl.standin_cross_sections()
+    sim = ed.simulation_for(ds, ed.FP64 if a.fp64 else ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV,
+                            particles=parts)
+    sim.set_graphs(False)
+    sim.step(a.warmup, measure=a.measure)
+    sim.synchronize()
+    sim.step(a.steps, measure=a.measure)
+    sim.synchronize()
+    print(json.dumps({"discharges": a.discharges, "n_per_species": a.n, "counters": sim.counters(0),
+                      "counts": sim.counts(0)}))
+    sim.close()
+
+
+if __name__ == "__main__":
+    main()

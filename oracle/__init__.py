@@ -103,6 +103,8 @@ def lib():
             L.orc_unit_collide_ion.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, _D, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_double]
             L.orc_select_process.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+            L.orc_test_uniform_f32.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
+            L.orc_test_uniform_f32.restype = ctypes.c_float
             L.orc_select_process_f32.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_float]
             _lib = L
     return _lib
@@ -131,6 +133,11 @@ def u53(a: int, b: int) -> float:
 
 def u24(a: int) -> float:
     return lib().orc_u24(a)
+
+
+def test_uniform_f32(seed: int, slot: int, step: int, species: int) -> float:
+    """Collision-test uniform of the FP32 particle mode."""
+    return lib().orc_test_uniform_f32(seed, slot, step, species)
 
 
 def deposit_paper(x, n_grid: int, inv_dx: float, factor_w: float) -> np.ndarray:

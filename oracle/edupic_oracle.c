@@ -86,7 +86,42 @@ double orc_u53(uint32_t a, uint32_t b)
 /* Uniform on [0,1) with 24 random bits from one word (FP32 particle mode). */
 float orc_u24(uint32_t a) { return (float)(a >> 8) * (1.0f / 16777216.0f); }
 
-/* One Philox block for (slot, global step, species, block index). */
+/* Random-number layout (the paper draws R01 from one sequential MT19937
+ * stream, Sec. 3.3; any assignment of independent uniforms is equivalent).
+ * Block 0 of counter word c0 = slot / 2 holds the collision-test uniforms of
+ * the two slots 2k (words 0,1) and 2k+1 (words 2,3).  Blocks b >= 1 of
+ * counter word c0 = slot hold the per-particle draws:
+ *   e-:  1 (process, chi)  2 (eta, Opal)  3, 4 Box-Muller pairs of the new Ar+
+ *   Ar+: 1, 2 Box-Muller pairs of the thermal partner  3 (process, chi)  4 (eta, -) */
+static void philox_words(uint64_t seed, uint32_t c0, int64_t step, int species, int block, uint32_t w[4])
+{
+    uint32_t ctr[4], key[2];
+    ctr[0] = c0;
+    ctr[1] = (uint32_t)(uint64_t)step;
+    ctr[2] = (uint32_t)((uint64_t)step >> 32);
+    ctr[3] = ((uint32_t)species << 8) | (uint32_t)block;
+    key[0] = (uint32_t)seed;
+    key[1] = (uint32_t)(seed >> 32);
+    orc_philox4x32_10(ctr, key, w);
+}
+
+/* Collision-test uniform of one slot (block 0, shared by slot pairs). */
+static double test_uniform(uint64_t seed, int64_t slot, int64_t step, int species)
+{
+    uint32_t w[4];
+    philox_words(seed, (uint32_t)((uint64_t)slot >> 1), step, species, 0, w);
+    return (slot & 1) ? orc_u53(w[2], w[3]) : orc_u53(w[0], w[1]);
+}
+
+/* FP32 particle mode: the same words, 24 bits each (words 0 and 2). */
+float orc_test_uniform_f32(uint64_t seed, int64_t slot, int64_t step, int species)
+{
+    uint32_t w[4];
+    philox_words(seed, (uint32_t)((uint64_t)slot >> 1), step, species, 0, w);
+    return (slot & 1) ? orc_u24(w[2]) : orc_u24(w[0]);
+}
+
+/* One per-particle Philox block (b >= 1) for (slot, global step, species). */
 static void draw_block(uint64_t seed, int64_t slot, int64_t step, int species, int block, double u[2])
 {
     uint32_t ctr[4], key[2], w[4];
@@ -720,15 +755,13 @@ static void one_step(orc_sim *s, int measure)
         int ei = energy_index(energy, s->cs_de[0], s->cs_n[0]);
         double nu = s->sigma_tot[0][ei] * velocity;
         double p_coll = 1.0 - exp(-nu * s->dt_e);
-        double u01[2];
-        draw_block(p->seed, k, s->step, ORC_SPECIES_E, 0, u01);
         /* Reading: a collision happens when R01 < P_coll (Algorithm 6) */
-        if (u01[0] < p_coll) {
+        if (test_uniform(p->seed, k, s->step, ORC_SPECIES_E) < p_coll) {
             double ua[2], ub[2], vej[3];
             int sub;
             draw_block(p->seed, k, s->step, ORC_SPECIES_E, 1, ua);
             draw_block(p->seed, k, s->step, ORC_SPECIES_E, 2, ub);
-            int proc = orc_collide_electron(s, ei, &E->vx[k], &E->vy[k], &E->vz[k], u01[1], ua[0], ua[1], ub[0], vej,
+            int proc = orc_collide_electron(s, ei, &E->vx[k], &E->vy[k], &E->vz[k], ua[0], ua[1], ub[0], ub[1], vej,
                                             &sub);
             s->counters[ORC_C_COLL_E_ELA + proc]++;
             s->counters[ORC_C_SUBTHRESHOLD] += sub;
@@ -783,8 +816,8 @@ static void one_step(orc_sim *s, int measure)
         for (int64_t k = 0; k < I->n; ++k) {
             if (s->absorbed[k]) continue;
             double ua[2], ub[2], za[2], zb[2], uc[2], ud[2];
-            draw_block(p->seed, k, s->step, ORC_SPECIES_I, 0, ua);
-            draw_block(p->seed, k, s->step, ORC_SPECIES_I, 1, ub);
+            draw_block(p->seed, k, s->step, ORC_SPECIES_I, 1, ua);
+            draw_block(p->seed, k, s->step, ORC_SPECIES_I, 2, ub);
             box_muller(ua, za);
             box_muller(ub, zb);
             double vx_a = s->sigma_th_ar * za[0], vy_a = s->sigma_th_ar * za[1], vz_a = s->sigma_th_ar * zb[0];
@@ -795,11 +828,11 @@ static void one_step(orc_sim *s, int measure)
             int ei = energy_index(energy, s->cs_de[1], s->cs_n[1]);
             double nu = s->sigma_tot[1][ei] * g;
             double p_coll = 1.0 - exp(-nu * s->dt_i);
-            draw_block(p->seed, k, s->step, ORC_SPECIES_I, 2, uc);
-            if (uc[0] < p_coll) {
-                draw_block(p->seed, k, s->step, ORC_SPECIES_I, 3, ud);
-                int proc = orc_collide_ion(s, ei, &I->vx[k], &I->vy[k], &I->vz[k], vx_a, vy_a, vz_a, uc[1], ud[0],
-                                           ud[1]);
+            if (test_uniform(p->seed, k, s->step, ORC_SPECIES_I) < p_coll) {
+                draw_block(p->seed, k, s->step, ORC_SPECIES_I, 3, uc);
+                draw_block(p->seed, k, s->step, ORC_SPECIES_I, 4, ud);
+                int proc = orc_collide_ion(s, ei, &I->vx[k], &I->vy[k], &I->vz[k], vx_a, vy_a, vz_a, uc[0], uc[1],
+                                           ud[0]);
                 s->counters[ORC_C_COLL_I_ISO + proc]++;
             }
         }

@@ -33,7 +33,7 @@ long long padded(long long cap) { return (cap + kTileAlign - 1) / kTileAlign * k
 struct Layout {
     size_t x[2], vx[2], vy[2], vz[2];
     size_t q_e, q_i, acc_e, acc_i, n_e, n_i, phi, ef, ef_t, sum_ne, sum_ni, sum_phi;
-    size_t eepf, ifed_pow, ifed_gnd, ctrl, holes[2], prod_parent, prod_x, prod_ve[3], prod_vi[3];
+    size_t eepf, ifed_pow, ifed_gnd, ctrl, holes[2], prod_parent, prod_x, prod_ve[3], prod_vi[3], vdrive;
     size_t bytes;
 };
 
@@ -76,6 +76,7 @@ Layout layout_of(const edupic_params &p, size_t elem)
     L.prod_x = take((size_t)kEvents * elem);
     for (int c = 0; c < 3; ++c) L.prod_ve[c] = take((size_t)kEvents * elem);
     for (int c = 0; c < 3; ++c) L.prod_vi[c] = take((size_t)kEvents * elem);
+    L.vdrive = take((size_t)p.steps_per_cycle * 8);
     L.bytes = o;
     return L;
 }
@@ -126,7 +127,8 @@ struct edupic_sim {
     unsigned char *arena = nullptr;
     size_t arena_bytes = 0;
     DischargeDev *d_desc = nullptr;
-    void *cs_tab[2] = {nullptr, nullptr};
+    void *cs_sig[2] = {nullptr, nullptr};
+    void *cs_thr[2] = {nullptr, nullptr};
     bool cs_set[2] = {false, false};
     cudaStream_t stream = nullptr;
     int ng_max = 0, eepf_max = 0, nsub = 1, nt_common = -1;
@@ -156,7 +158,8 @@ namespace {
 size_t shared_bytes(int nd, size_t elem, int cs_entries)
 {
     size_t o = align_up(sizeof(DischargeDev) * nd, kAlign);
-    o += 2 * align_up((size_t)cs_entries * 4 * elem, kAlign);
+    o += 2 * align_up((size_t)cs_entries * elem, kAlign);      // sigsum
+    o += 2 * align_up((size_t)cs_entries * 2 * elem, kAlign);  // thr1, thr2
     return o;
 }
 
@@ -219,10 +222,11 @@ void fill_desc(edupic_sim *S, int d)
     D.inv_ifed_def = (float)(1.0 / p.ifed_de_ev);
     D.inv_cs_de_ef = (float)(1.0 / D.cs_de_e);
     D.inv_cs_de_if = (float)(1.0 / D.cs_de_i);
-    D.vscale_mu_ef = (float)std::sqrt(2.0 * kQE / D.mu_e);
-    D.vscale_ef = (float)std::sqrt(2.0 * kQE / kME);
-    D.mass_ratio_ef = (float)(kME / (kME + ar_mass));
-    D.mass_ratio2_ef = (float)(ar_mass / (kME + ar_mass));
+    D.ndt_ef = (float)(D.n_gas * D.dt_e);
+    D.ndt_if = (float)(D.n_gas * D.dt_i);
+    D.e_idx_ef = (float)(0.5 * kME / kQE / D.cs_de_e);
+    D.g_idx_if = (float)(0.5 * mu_arar / kQE / D.cs_de_i);
+    D.inv_2dx = 1.0 / (2.0 * D.dx);
     D.ng = p.n_grid;
     D.nt = p.steps_per_cycle;
     D.nsub = p.ion_subcycle;
@@ -264,8 +268,11 @@ void fill_desc(edupic_sim *S, int d)
         D.prod_ve[c] = b + L.prod_ve[c];
         D.prod_vi[c] = b + L.prod_vi[c];
     }
-    D.cs_e = S->cs_tab[0];
-    D.cs_i = S->cs_tab[1];
+    for (int sp = 0; sp < 2; ++sp) {
+        D.cs_sig[sp] = S->cs_sig[sp];
+        D.cs_thr[sp] = S->cs_thr[sp];
+    }
+    D.vdrive = reinterpret_cast<const double *>(b + L.vdrive);
     if (S->desc.size() <= (size_t)d) S->desc.resize(d + 1);
     S->desc[d] = D;
 }
@@ -328,20 +335,40 @@ int error_of(const Ctrl &c)
 template <typename T>
 int upload_tables(edupic_sim *S, int species, int n_proc, int n_entries, const double *sig)
 {
-    std::vector<CsEntry<T>> tab((size_t)n_entries);
+    std::vector<T> sum((size_t)n_entries);
+    std::vector<T> thr(2 * (size_t)n_entries);
     for (int k = 0; k < n_entries; ++k) {
         const double s0 = sig[k], s1 = sig[(size_t)n_entries + k];
         const double s2 = n_proc == 3 ? sig[2 * (size_t)n_entries + k] : 0.0;
-        // sum in the order calc_total_cross_sections() adds the processes
+        // processes summed in order, as calc_total_cross_sections() does
         const double stot = n_proc == 3 ? s0 + s1 + s2 : s0 + s1;
-        CsEntry<T> c;
-        c.sigsum = (T)stot;
-        c.thr1 = (T)(s0 / stot);
-        c.thr2 = (T)(n_proc == 3 ? (s0 + s1) / stot : 1.0);
-        c.pad = (T)0;
-        tab[k] = c;
+        sum[k] = (T)stot;
+        thr[2 * (size_t)k] = (T)(s0 / stot);
+        thr[2 * (size_t)k + 1] = (T)(n_proc == 3 ? (s0 + s1) / stot : 1.0);
     }
-    cudaError_t e = cudaMemcpyAsync(S->cs_tab[species], tab.data(), sizeof(CsEntry<T>) * tab.size(),
+    cudaError_t e = cudaMemcpyAsync(S->cs_sig[species], sum.data(), sizeof(T) * sum.size(), cudaMemcpyHostToDevice,
+                                    S->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->cs_thr[species], thr.data(), sizeof(T) * thr.size(), cudaMemcpyHostToDevice,
+                            S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    return cuda_status(e);
+}
+
+// Drive voltage at the N_T steps of one RF cycle, V(t) = sum V_k cos(2 pi f_k t)
+// with t = step * dt_e (the waveform input of the field solve).
+int upload_drive(edupic_sim *S, int d)
+{
+    const edupic_params &p = S->params[d];
+    const double dt_e = S->desc[d].dt_e, pi = 3.14159265358979323846;
+    std::vector<double> v((size_t)p.steps_per_cycle);
+    for (int tc = 0; tc < p.steps_per_cycle; ++tc) {
+        const double t = (double)tc * dt_e;
+        double a = 0.0;
+        for (int h = 0; h < p.n_harmonics; ++h) a += p.harm_volt_v[h] * std::cos(2.0 * pi * p.harm_freq_hz[h] * t);
+        v[tc] = a;
+    }
+    cudaError_t e = cudaMemcpyAsync(const_cast<double *>(S->desc[d].vdrive), v.data(), sizeof(double) * v.size(),
                                     cudaMemcpyHostToDevice, S->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
     return cuda_status(e);
@@ -443,11 +470,14 @@ int edupic_create(int nd, const edupic_params *params, int precision, void *devi
     size_t o = 0;
     S->d_desc = reinterpret_cast<DischargeDev *>(S->arena);
     o = align_up(sizeof(DischargeDev) * nd, kAlign);
-    const size_t tab_bytes = align_up((size_t)params[0].cs_entries * 4 * S->elem, kAlign);
-    S->cs_tab[0] = S->arena + o;
-    o += tab_bytes;
-    S->cs_tab[1] = S->arena + o;
-    o += tab_bytes;
+    for (int sp = 0; sp < 2; ++sp) {
+        S->cs_sig[sp] = S->arena + o;
+        o += align_up((size_t)params[0].cs_entries * S->elem, kAlign);
+    }
+    for (int sp = 0; sp < 2; ++sp) {
+        S->cs_thr[sp] = S->arena + o;
+        o += align_up((size_t)params[0].cs_entries * 2 * S->elem, kAlign);
+    }
     for (int d = 0; d < nd; ++d) {
         S->layouts.push_back(layout_of(params[d], S->elem));
         S->base.push_back(o);
@@ -460,6 +490,7 @@ int edupic_create(int nd, const edupic_params *params, int precision, void *devi
         return EDUPIC_ECUDA;
     }
     rc = upload_desc(S);
+    for (int d = 0; d < nd && rc == EDUPIC_OK; ++d) rc = upload_drive(S, d);
     if (rc) {
         delete S;
         return rc;
@@ -518,10 +549,12 @@ int edupic_set_cross_sections(edupic_sim *S, int species, int n_proc, int n_entr
             S->desc[d].cs_n_e = n_entries;
             S->desc[d].cs_de_e = de_ev;
             S->desc[d].inv_cs_de_ef = (float)(1.0 / de_ev);
+            S->desc[d].e_idx_ef = (float)(0.5 * kME / kQE / de_ev);
         } else {
             S->desc[d].cs_n_i = n_entries;
             S->desc[d].cs_de_i = de_ev;
             S->desc[d].inv_cs_de_if = (float)(1.0 / de_ev);
+            S->desc[d].g_idx_if = (float)(0.5 * (kArMassU * kAMU / 2.0) / kQE / de_ev);
         }
     }
     S->cs_set[species] = true;

@@ -9,6 +9,8 @@ namespace edupic {
 
 constexpr int kThreads = 256;          // particle-kernel block size
 constexpr int kFinalizeThreads = 512;  // one CTA per discharge for compaction + field solve
+constexpr int kGroupA = 128;           // finalize threads doing compaction and append
+constexpr int kGroupB = kFinalizeThreads - kGroupA;  // finalize threads doing the field solve
 constexpr int kEvents = EDUPIC_STEP_EVENTS;
 
 // Device error bits (ctrl->error).
@@ -30,13 +32,9 @@ struct Ctrl {
     unsigned long long counters[EDUPIC_N_COUNTERS];
 };
 
-// One cross-section table entry: n*sigma_tot is formed in the kernel as
-// sigsum * n_gas; thr1, thr2 are the cumulative process fractions.
-template <typename T>
-struct alignas(4 * sizeof(T)) CsEntry {
-    T sigsum, thr1, thr2, pad;
-};
-
+// Cross-section tables in particle precision T: sigsum[k] = sum of the
+// process cross sections (n*sigma_tot is formed in the kernel as
+// sigsum * n_gas), thr[k] = cumulative process fractions (thr1, thr2).
 // Everything a kernel needs about one discharge (in device memory).
 struct DischargeDev {
     // constants (FP64 values; FP32 copies below)
@@ -50,10 +48,10 @@ struct DischargeDev {
     float Lf, inv_dxf, dt_ef, dt_if, factor_ef, factor_if, n_gasf, sig_thf;
     float e_of_v2_ef, e_of_v2_if, e_of_g2_if, mu_ef, e_excf, e_ionf;
     float eepf_lof, eepf_hif, inv_eepf_def, inv_ifed_def, inv_cs_de_ef, inv_cs_de_if;
-    float vscale_mu_ef;   // sqrt(2 e / mu_e)
-    float vscale_ef;      // sqrt(2 e / m_e)
-    float mass_ratio_ef;  // m_e / (m_e + M)
-    float mass_ratio2_ef; // M / (m_e + M)
+    float ndt_ef, ndt_if;  // n_gas * dt (electrons, ions)
+    float e_idx_ef;        // (m_e / 2e) / DE_CS: table index of v^2
+    float g_idx_if;        // (mu / 2e) / DE_CS: table index of g^2
+    double inv_2dx;
     int ng, nt, nsub, n_harm, eepf_bins, ifed_bins, cs_n_e, cs_n_i;
     int active;
     int pad0;
@@ -72,7 +70,9 @@ struct DischargeDev {
     int *holes[2];
     int *prod_parent;
     void *prod_x, *prod_ve[3], *prod_vi[3];
-    const void *cs_e, *cs_i;   // CsEntry<T> tables
+    const void *cs_sig[2];     // T[cs_n]
+    const void *cs_thr[2];     // T2[cs_n]
+    const double *vdrive;      // V(t) at the N_T steps of one cycle
 };
 
 // Launchers implemented per precision (kernels_f32.cu / kernels_f64.cu).

@@ -6,9 +6,10 @@
 //                      -> electrode absorption (Sec. 2.1.5) -> Monte Carlo
 //                      collision (Sec. 2.1.6, Algorithm 6) -> deposition of
 //                      the new position for the next step (Sec. 2.1.1).
-//  k_finalize<T>       one CTA per discharge: canonical hole fill of absorbed
-//                      particles, append of ionisation products, density swap,
-//                      diagnostics, and the field solve of the next step
+//  k_finalize<T>       one CTA per discharge, two warp groups working at once:
+//                      (A) canonical hole fill of absorbed particles and
+//                      append of ionisation products; (B) density swap,
+//                      diagnostics and the field solve of the next step
 //                      (Sec. 2.1.2, Algorithm 3).
 //  k_deposit<T>, k_fields<T>  densities / field after particles are loaded.
 //
@@ -17,6 +18,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 #include <type_traits>
 
@@ -35,11 +37,13 @@ struct VecOf;
 template <>
 struct VecOf<float> {
     using type = float4;
+    using pair = float2;
     static constexpr int n = 4;
 };
 template <>
 struct VecOf<double> {
     using type = double2;
+    using pair = double2;
     static constexpr int n = 2;
 };
 
@@ -48,9 +52,14 @@ __device__ __forceinline__ void unpack(const double2 &v, double *a) { a[0] = v.x
 __device__ __forceinline__ float4 pack(const float *a, float4) { return make_float4(a[0], a[1], a[2], a[3]); }
 __device__ __forceinline__ double2 pack(const double *a, double2) { return make_double2(a[0], a[1]); }
 
+template <typename T>
+__host__ __device__ constexpr bool is_f64() { return std::is_same<T, double>::value; }
+
 // ---------------------------------------------------------------- RNG
-// Philox-4x32-10 (Salmon et al., SC'11), counter = (slot, step lo, step hi,
-// species << 8 | block), key = seed.
+// Philox-4x32-10 (Salmon et al., SC'11).  Counter (c0, step lo, step hi,
+// species << 8 | block), key = seed.  Block 0 with c0 = slot / 2 holds the
+// collision-test uniforms of a slot pair; blocks >= 1 with c0 = slot hold a
+// particle's other draws.
 struct Words {
     uint32_t a, b, c, d;
 };
@@ -74,26 +83,31 @@ __device__ __forceinline__ Words philox(uint32_t c0, uint32_t c1, uint32_t c2, u
 }
 
 struct RngKey {
-    uint32_t slot, s_lo, s_hi, k0, k1;
+    uint32_t s_lo, s_hi, k0, k1;
 };
 
-// Two uniforms on [0,1): 53-bit in FP64 (words a,b and c,d), 24-bit in FP32
-// (words a and c).
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b)
+{
+    return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * (1.0 / 9007199254740992.0);
+}
+__device__ __forceinline__ float u24(uint32_t a) { return (float)(a >> 8) * (1.0f / 16777216.0f); }
+
 __device__ __forceinline__ void uniforms(const Words &w, double &u0, double &u1)
 {
-    u0 = ((double)(w.a >> 5) * 67108864.0 + (double)(w.b >> 6)) * (1.0 / 9007199254740992.0);
-    u1 = ((double)(w.c >> 5) * 67108864.0 + (double)(w.d >> 6)) * (1.0 / 9007199254740992.0);
+    u0 = u53(w.a, w.b);
+    u1 = u53(w.c, w.d);
 }
 __device__ __forceinline__ void uniforms(const Words &w, float &u0, float &u1)
 {
-    u0 = (float)(w.a >> 8) * (1.0f / 16777216.0f);
-    u1 = (float)(w.c >> 8) * (1.0f / 16777216.0f);
+    u0 = u24(w.a);
+    u1 = u24(w.c);
 }
 
+// Per-particle block b >= 1 of slot `slot`.
 template <typename T>
-__device__ __forceinline__ void draw(const RngKey &k, int species, int block, T &u0, T &u1)
+__device__ __forceinline__ void draw(const RngKey &k, uint32_t slot, int species, int block, T &u0, T &u1)
 {
-    const Words w = philox(k.slot, k.s_lo, k.s_hi, ((uint32_t)species << 8) | (uint32_t)block, k.k0, k.k1);
+    const Words w = philox(slot, k.s_lo, k.s_hi, ((uint32_t)species << 8) | (uint32_t)block, k.k0, k.k1);
     uniforms(w, u0, u1);
 }
 
@@ -108,36 +122,9 @@ __device__ __forceinline__ void box_muller(T u0, T u1, T &z0, T &z1)
 }
 
 // ---------------------------------------------------------------- helpers
-template <typename T>
-struct Hot {  // per-discharge constants used for every particle
-    T L, inv_dx, dt, factor, n_gas;
-    int ng;
-};
-
-template <typename T>
-__device__ __forceinline__ Hot<T> hot(const DischargeDev &D, int sp)
-{
-    Hot<T> h;
-    if constexpr (std::is_same<T, double>::value) {
-        h.L = D.L;
-        h.inv_dx = D.inv_dx;
-        h.dt = sp == 0 ? D.dt_e : D.dt_i;
-        h.factor = sp == 0 ? D.factor_e : D.factor_i;
-        h.n_gas = D.n_gas;
-    } else {
-        h.L = D.Lf;
-        h.inv_dx = D.inv_dxf;
-        h.dt = sp == 0 ? D.dt_ef : D.dt_if;
-        h.factor = sp == 0 ? D.factor_ef : D.factor_if;
-        h.n_gas = D.n_gasf;
-    }
-    h.ng = D.ng;
-    return h;
-}
-
-// Cell index p and the weight c2 of point p+1 (Sec. 2.1.1 / 2.1.3).  A
-// particle at x = L belongs to the last cell with c2 = 1; p is clamped into
-// the grid so that no index can leave it.
+// Cell index p and c0 = x / dx (Sec. 2.1.1 / 2.1.3).  A particle at x = L
+// belongs to the last cell; p is clamped into the grid so that no index can
+// leave it.
 template <typename T>
 __device__ __forceinline__ int cell(T x, T inv_dx, int ng, T &c0)
 {
@@ -147,17 +134,15 @@ __device__ __forceinline__ int cell(T x, T inv_dx, int ng, T &c0)
     return p;
 }
 
-template <typename T>
-__device__ __forceinline__ long long split_q2(T c2);
-template <>
-__device__ __forceinline__ long long split_q2<double>(double c2)
+// Fixed-point weight of point p+1: round-to-nearest-even(c2 * 2^32).
+__device__ __forceinline__ unsigned long long split_q2(double c2)
 {
-    return __double2ll_rn(c2 * 4294967296.0);
+    return (unsigned long long)__double2ll_rn(c2 * 4294967296.0);
 }
-template <>
-__device__ __forceinline__ long long split_q2<float>(float c2)
+__device__ __forceinline__ unsigned long long split_q2(float c2)
 {
-    return __float2ll_rn(c2 * 4294967296.0f);
+    // c2 < 1 in FP32 means c2 <= 1 - 2^-24, so c2 * 2^32 < 2^32 fits 32 bits
+    return c2 < 1.0f ? (unsigned long long)__float2uint_rn(c2 * 4294967296.0f) : 4294967296ull;
 }
 
 // Nearest cross-section bin (Algorithm 6).
@@ -168,18 +153,23 @@ __device__ __forceinline__ int cs_index(double energy, double de, int n)
     const int k = (int)r;
     return k < n - 1 ? k : n - 1;
 }
-__device__ __forceinline__ int cs_index_f(float energy, float inv_de, int n)
+__device__ __forceinline__ int cs_index_f(float r, int n)  // r = energy / de + 0.5 already formed
 {
-    const float r = energy * inv_de + 0.5f;
     if (!(r < (float)n)) return n - 1;
     const int k = (int)r;
     return k < n - 1 ? k : n - 1;
 }
 
-// Collision probability P = 1 - exp(-nu dt) (eq. pcoll).  FP32 evaluates the
-// same quantity through expm1 to avoid cancellation near 1.
+// Collision probability P = 1 - exp(-x), x = nu dt (eq. pcoll).  FP32 uses
+// the Taylor series of 1 - e^-x below x = 1/8 (truncation below 1e-7
+// relative) to avoid the cancellation of 1 - exp near 1.
 __device__ __forceinline__ double p_coll(double x) { return 1.0 - exp(-x); }
-__device__ __forceinline__ float p_coll(float x) { return -expm1f(-x); }
+__device__ __forceinline__ float p_coll(float x)
+{
+    if (x < 0.125f)
+        return x * (1.0f - x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f)))));
+    return 1.0f - __expf(-x);
+}
 
 // Euler-angle rotation of Sec. 2.1.6: unit vector of g' for g deflected by
 // (chi, eta) given as cosines and sines.
@@ -203,11 +193,11 @@ __device__ __forceinline__ void deflect(T gx, T gy, T gz, T g, T cc, T sc, T ce,
 
 // e- + Ar (cold gas): returns the process; ionisation fills vej.
 template <typename T>
-__device__ int collide_electron(const DischargeDev &D, const CsEntry<T> &cs, T &vx, T &vy, T &vz, T u_proc, T u_chi,
-                                T u_eta, T u_opal, T vej[3], int &sub)
+__device__ __forceinline__ int collide_electron(const DischargeDev &D, T thr1, T thr2, T &vx, T &vy, T &vz, T u_proc,
+                                                T u_chi, T u_eta, T u_opal, T vej[3], int &sub)
 {
     const T m1 = (T)EDUPIC_ME, m2 = (T)D.ar_mass, ev = (T)EDUPIC_QE, mu = (T)D.mu_e;
-    int proc = u_proc < cs.thr1 ? 0 : (u_proc < cs.thr2 ? 1 : 2);
+    int proc = u_proc < thr1 ? 0 : (u_proc < thr2 ? 1 : 2);
     sub = 0;
     const T gx = vx, gy = vy, gz = vz;
     const T g2 = gx * gx + gy * gy + gz * gz;
@@ -262,11 +252,11 @@ __device__ int collide_electron(const DischargeDev &D, const CsEntry<T> &cs, T &
 
 // Ar+ + Ar with thermal partner va: 0 isotropic, 1 backward (chi = pi).
 template <typename T>
-__device__ int collide_ion(const DischargeDev &D, const CsEntry<T> &cs, T &vx, T &vy, T &vz, T vax, T vay, T vaz,
-                           T u_proc, T u_chi, T u_eta)
+__device__ __forceinline__ int collide_ion(const DischargeDev &D, T thr1, T &vx, T &vy, T &vz, T vax, T vay, T vaz,
+                                           T u_proc, T u_chi, T u_eta)
 {
     const T m1 = (T)D.ar_mass, m2 = (T)D.ar_mass;
-    const int proc = u_proc < cs.thr1 ? 0 : 1;
+    const int proc = u_proc < thr1 ? 0 : 1;
     const T gx = vx - vax, gy = vy - vay, gz = vz - vaz;
     const T g = sqrt(gx * gx + gy * gy + gz * gz);
     const T wx = (m1 * vx + m2 * vax) / (m1 + m2);
@@ -294,126 +284,169 @@ __device__ int collide_ion(const DischargeDev &D, const CsEntry<T> &cs, T &vx, T
     return proc;
 }
 
-// ---------------------------------------------------------------- block scans
-__device__ __forceinline__ int warp_incl_scan(int v)
+// ---------------------------------------------------------------- scans
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+template <typename V>
+__device__ __forceinline__ V warp_incl_scan(V v)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        const V y = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o) v += y;
     }
     return v;
 }
 
-// Exclusive prefix of a per-thread int over the block; returns the prefix,
-// writes the block total.  s_w: shared scratch of >= 33 ints.
-__device__ __forceinline__ int block_excl_scan(int v, int *s_w, int &total)
+// Exclusive prefix of a per-thread value over a group of g threads (whole
+// warps, group-local id gtid) synchronised by named barrier `bar`.  Returns
+// the prefix and writes the group total.  s_w: shared scratch of >= 33 V.
+template <typename V>
+__device__ __forceinline__ V group_excl_scan(V v, V *s_w, V &total, int gtid, int g, int bar)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    const int inc = warp_incl_scan(v);
+    const int lane = gtid & 31, warp = gtid >> 5, nw = g >> 5;
+    const V inc = warp_incl_scan(v);
     if (lane == 31) s_w[warp] = inc;
-    __syncthreads();
+    bar_sync(bar, g);
     if (warp == 0) {
-        const int w = lane < nw ? s_w[lane] : 0;
-        const int wi = warp_incl_scan(w);
+        const V w = lane < nw ? s_w[lane] : (V)0;
+        const V wi = warp_incl_scan(w);
         s_w[lane] = wi - w;
         if (lane == 31) s_w[32] = wi;
     }
-    __syncthreads();
-    const int r = inc - v + s_w[warp];
+    bar_sync(bar, g);
+    const V r = inc - v + s_w[warp];
     total = s_w[32];
-    __syncthreads();
+    bar_sync(bar, g);
     return r;
 }
 
-__device__ __forceinline__ long long warp_incl_scan64(long long v)
+// ---------------------------------------------------------------- rare paths
+// Everything a collision or absorption needs beyond the hot loop's registers.
+template <typename T>
+struct PushCtx {
+    const DischargeDev *D;
+    RngKey key;
+    unsigned long long *sQ;
+    unsigned int *sCnt;
+    T inv_dx;
+    int ng;
+};
+
+// e- collision of one particle (Algorithm 6 after the test passed),
+// including the append record and deposition of an ionisation pair.
+template <typename T>
+__device__ __noinline__ void electron_collision(const PushCtx<T> &c, int slot, int k, T xn, T *vxyz)
 {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
+    using T2 = typename VecOf<T>::pair;
+    const DischargeDev &D = *c.D;
+    const T2 thr = reinterpret_cast<const T2 *>(D.cs_thr[0])[k];
+    T u_proc, u_chi, u_eta, u_opal, vej[3];
+    draw<T>(c.key, (uint32_t)slot, 0, 1, u_proc, u_chi);
+    draw<T>(c.key, (uint32_t)slot, 0, 2, u_eta, u_opal);
+    int sub;
+    const int proc =
+        collide_electron<T>(D, thr.x, thr.y, vxyz[0], vxyz[1], vxyz[2], u_proc, u_chi, u_eta, u_opal, vej, sub);
+    atomicAdd(c.sCnt + EDUPIC_C_COLL_E_ELA + proc, 1u);
+    if (sub) atomicAdd(c.sCnt + EDUPIC_C_SUBTHRESHOLD, 1u);
+    if (proc != 2) return;
+    T n0, n1, n2, n3, z0, z1, z2, z3;
+    draw<T>(c.key, (uint32_t)slot, 0, 3, n0, n1);
+    draw<T>(c.key, (uint32_t)slot, 0, 4, n2, n3);
+    box_muller(n0, n1, z0, z1);
+    box_muller(n2, n3, z2, z3);
+    const T sth = is_f64<T>() ? (T)D.sig_th : (T)D.sig_thf;
+    const int pi = atomicAdd(&D.ctrl->products, 1);
+    if (pi >= kEvents) {
+        atomicOr(&D.ctrl->error, kErrProducts);
+        return;
     }
-    return v;
+    D.prod_parent[pi] = slot;
+    reinterpret_cast<T *>(D.prod_x)[pi] = xn;
+    reinterpret_cast<T *>(D.prod_ve[0])[pi] = vej[0];
+    reinterpret_cast<T *>(D.prod_ve[1])[pi] = vej[1];
+    reinterpret_cast<T *>(D.prod_ve[2])[pi] = vej[2];
+    reinterpret_cast<T *>(D.prod_vi[0])[pi] = sth * z0;
+    reinterpret_cast<T *>(D.prod_vi[1])[pi] = sth * z1;
+    reinterpret_cast<T *>(D.prod_vi[2])[pi] = sth * z2;
+    // the new pair joins the next densities at the parent's x
+    T d0;
+    const int pp = cell<T>(xn, c.inv_dx, c.ng, d0);
+    const unsigned long long q2 = split_q2(d0 - (T)pp);
+    atomicAdd(c.sQ + pp, 4294967296ull - q2);
+    atomicAdd(c.sQ + pp + 1, q2);
+    atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp), 4294967296ull - q2);
+    atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp + 1), q2);
 }
 
-__device__ __forceinline__ __int128 shfl_up128(__int128 v, int o)
+template <typename T>
+__device__ __noinline__ void ion_collision(const PushCtx<T> &c, int slot, int k, const T *va, T *vxyz)
 {
-    const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
-    const unsigned long long l2 = __shfl_up_sync(0xffffffffu, lo, o), h2 = __shfl_up_sync(0xffffffffu, hi, o);
-    return (__int128)(((unsigned __int128)h2 << 64) | (unsigned __int128)l2);
+    using T2 = typename VecOf<T>::pair;
+    const DischargeDev &D = *c.D;
+    const T thr1 = reinterpret_cast<const T2 *>(D.cs_thr[1])[k].x;
+    T u_proc, u_chi, u_eta, u_dummy;
+    draw<T>(c.key, (uint32_t)slot, 1, 3, u_proc, u_chi);
+    draw<T>(c.key, (uint32_t)slot, 1, 4, u_eta, u_dummy);
+    const int proc = collide_ion<T>(D, thr1, vxyz[0], vxyz[1], vxyz[2], va[0], va[1], va[2], u_proc, u_chi, u_eta);
+    atomicAdd(c.sCnt + EDUPIC_C_COLL_I_ISO + proc, 1u);
 }
 
-__device__ __forceinline__ __int128 warp_incl_scan128(__int128 v)
+// Absorbed particle: record the hole, count it, bin the Ar+ impact energy.
+template <typename T, int SP>
+__device__ __noinline__ void absorbed(const PushCtx<T> &c, int slot, T xn, T vx, T vy, T vz, int measure)
 {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const __int128 y = shfl_up128(v, o);
-        if (lane >= o) v += y;
+    const DischargeDev &D = *c.D;
+    const T L = is_f64<T>() ? (T)D.L : (T)D.Lf;
+    const int side = xn < (T)0.0 ? 0 : (xn > L ? 1 : -1);
+    if (side < 0)
+        atomicOr(&D.ctrl->error, kErrNan);
+    else
+        atomicAdd(c.sCnt + (SP == 0 ? EDUPIC_C_ABS_E_POW : EDUPIC_C_ABS_I_POW) + side, 1u);
+    const int h = atomicAdd(&D.ctrl->holes[SP], 1);
+    if (h < kEvents)
+        D.holes[SP][h] = slot;
+    else
+        atomicOr(&D.ctrl->error, kErrHoles);
+    if (SP == 1 && measure && side >= 0) {
+        const T v2 = vx * vx + vy * vy + vz * vz;
+        int b;
+        bool ok;
+        if constexpr (is_f64<T>()) {
+            const double en = D.half_mar * v2 / EDUPIC_QE;
+            const double r = en / D.ifed_de;
+            ok = r < (double)D.ifed_bins;
+            b = ok ? (int)r : 0;
+        } else {
+            const float r = D.e_of_v2_if * v2 * D.inv_ifed_def;
+            ok = r < (float)D.ifed_bins;
+            b = ok ? (int)r : 0;
+        }
+        if (ok) atomicAdd((side == 0 ? D.ifed_pow : D.ifed_gnd) + b, 1ull);
     }
-    return v;
-}
-
-// Block exclusive scans of 64-bit and 128-bit integers (exact).
-__device__ __forceinline__ long long block_excl_scan64(long long v, long long *s_w, long long &total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    const long long inc = warp_incl_scan64(v);
-    if (lane == 31) s_w[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        const long long w = lane < nw ? s_w[lane] : 0;
-        const long long wi = warp_incl_scan64(w);
-        s_w[lane] = wi - w;
-        if (lane == 31) s_w[32] = wi;
-    }
-    __syncthreads();
-    const long long r = inc - v + s_w[warp];
-    total = s_w[32];
-    __syncthreads();
-    return r;
-}
-
-__device__ __forceinline__ __int128 block_excl_scan128(__int128 v, __int128 *s_w, __int128 &total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    const __int128 inc = warp_incl_scan128(v);
-    if (lane == 31) s_w[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        const __int128 w = lane < nw ? s_w[lane] : (__int128)0;
-        const __int128 wi = warp_incl_scan128(w);
-        s_w[lane] = wi - w;
-        if (lane == 31) s_w[32] = wi;
-    }
-    __syncthreads();
-    const __int128 r = inc - v + s_w[warp];
-    total = s_w[32];
-    __syncthreads();
-    return r;
 }
 
 // ---------------------------------------------------------------- particle kernel
+// Dynamic shared memory: [E pairs: ng_max T2][Q: ng_max u64][EEPF: eepf_max u32]
+// [tile prefix: nd+1 int].
 template <typename T>
-__device__ __forceinline__ const CsEntry<T> *table(const DischargeDev &D, int sp)
+__host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eepf_max)
 {
-    return reinterpret_cast<const CsEntry<T> *>(sp == 0 ? D.cs_e : D.cs_i);
+    return (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 8 + (size_t)eepf_max * 4 + (size_t)(nd + 1) * 4;
 }
 
-// Dynamic shared memory layout of k_push: [E: ng_max T][Q: ng_max u64]
-// [EEPF: eepf_max u32][tile prefix: nd+1 int].
 template <typename T, int SP>
-__global__ void __launch_bounds__(kThreads) k_push(const DischargeDev *__restrict__ DD, int nd, int ng_max,
-                                                   int eepf_max, int measure)
+__global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : 3)
+    k_push(const DischargeDev *__restrict__ DD, int nd, int ng_max, int eepf_max, int measure)
 {
     using V = typename VecOf<T>::type;
+    using T2 = typename VecOf<T>::pair;
     constexpr int VEC = VecOf<T>::n;
     constexpr int TILE = kThreads * VEC;
     extern __shared__ __align__(16) unsigned char smem[];
-    T *sE = reinterpret_cast<T *>(smem);
-    unsigned long long *sQ = reinterpret_cast<unsigned long long *>(smem + ((ng_max * sizeof(T) + 15) & ~15));
+    T2 *sE2 = reinterpret_cast<T2 *>(smem);
+    unsigned long long *sQ = reinterpret_cast<unsigned long long *>(sE2 + ng_max);
     unsigned int *sH = reinterpret_cast<unsigned int *>(sQ + ng_max);
     int *sPre = reinterpret_cast<int *>(sH + eepf_max);
     __shared__ unsigned int sCnt[EDUPIC_N_COUNTERS];
@@ -426,12 +459,9 @@ __global__ void __launch_bounds__(kThreads) k_push(const DischargeDev *__restric
         for (int base = 0; base < nd; base += blockDim.x) {
             const int d = base + tid;
             int cnt = 0;
-            if (d < nd && DD[d].active) {
-                const long long n = DD[d].ctrl->n[SP];
-                cnt = (int)((n + TILE - 1) / TILE);
-            }
+            if (d < nd && DD[d].active) cnt = (int)((DD[d].ctrl->n[SP] + TILE - 1) / TILE);
             int tot;
-            const int ex = block_excl_scan(cnt, sW, tot);
+            const int ex = group_excl_scan(cnt, sW, tot, tid, blockDim.x, 1);
             if (d < nd) sPre[d] = running + ex;
             running += tot;
         }
@@ -439,18 +469,19 @@ __global__ void __launch_bounds__(kThreads) k_push(const DischargeDev *__restric
     }
     if (tid < EDUPIC_N_COUNTERS) sCnt[tid] = 0;
     __syncthreads();
-    const long long total = sPre[nd];
-    const long long t0 = (long long)blockIdx.x * total / gridDim.x;
-    const long long t1 = (long long)(blockIdx.x + 1) * total / gridDim.x;
+    const int total = sPre[nd];
+    const int t0 = (int)((long long)blockIdx.x * total / gridDim.x);
+    const int t1 = (int)((long long)(blockIdx.x + 1) * total / gridDim.x);
     if (t0 >= t1) return;
 
     int cur = -1;
+    PushCtx<T> ctx{};
+    ctx.sQ = sQ;
+    ctx.sCnt = sCnt;
     const DischargeDev *D = nullptr;
-    Hot<T> h{};
-    long long n = 0;
-    RngKey key{};
-    const CsEntry<T> *tab = nullptr;
-    int cs_n = 0;
+    int n = 0, cs_n = 0;
+    T L = 0, inv_dx = 0, dt = 0, factor = 0, ndt = 0, idx_scale = 0;
+    const T *sig = nullptr;
     bool eepf_on = false;
 
     auto flush = [&]() {
@@ -474,37 +505,53 @@ __global__ void __launch_bounds__(kThreads) k_push(const DischargeDev *__restric
         __syncthreads();
     };
 
-    for (long long t = t0; t < t1; ++t) {
+    for (int t = t0; t < t1; ++t) {
         if (cur < 0 || t >= sPre[cur + 1]) {
             if (cur >= 0) flush();
             ++cur;
             while (sPre[cur + 1] <= t) ++cur;
             D = DD + cur;
-            h = hot<T>(*D, SP);
-            n = D->ctrl->n[SP];
+            ctx.D = D;
+            n = (int)D->ctrl->n[SP];
             const unsigned long long s = (unsigned long long)D->ctrl->step;
-            key.s_lo = (uint32_t)s;
-            key.s_hi = (uint32_t)(s >> 32);
-            key.k0 = (uint32_t)D->seed;
-            key.k1 = (uint32_t)(D->seed >> 32);
-            tab = table<T>(*D, SP);
+            ctx.key.s_lo = (uint32_t)s;
+            ctx.key.s_hi = (uint32_t)(s >> 32);
+            ctx.key.k0 = (uint32_t)D->seed;
+            ctx.key.k1 = (uint32_t)(D->seed >> 32);
+            ctx.ng = D->ng;
+            if constexpr (is_f64<T>()) {
+                L = D->L;
+                inv_dx = D->inv_dx;
+                dt = SP == 0 ? D->dt_e : D->dt_i;
+                factor = SP == 0 ? D->factor_e : D->factor_i;
+                ndt = D->n_gas;
+                idx_scale = SP == 0 ? D->cs_de_e : D->cs_de_i;
+            } else {
+                L = D->Lf;
+                inv_dx = D->inv_dxf;
+                dt = SP == 0 ? D->dt_ef : D->dt_if;
+                factor = SP == 0 ? D->factor_ef : D->factor_if;
+                ndt = SP == 0 ? D->ndt_ef : D->ndt_if;
+                idx_scale = SP == 0 ? D->e_idx_ef : D->g_idx_if;
+            }
+            ctx.inv_dx = inv_dx;
+            sig = reinterpret_cast<const T *>(D->cs_sig[SP]);
             cs_n = SP == 0 ? D->cs_n_e : D->cs_n_i;
             eepf_on = SP == 0 && measure;
             const T *ef = reinterpret_cast<const T *>(D->ef_t);
-            for (int p = tid; p < h.ng; p += blockDim.x) {
-                sE[p] = ef[p];
+            const int ng = D->ng;
+            for (int p = tid; p < ng; p += blockDim.x) {
+                sE2[p] = T2{ef[p], p + 1 < ng ? ef[p + 1] : (T)0};
                 sQ[p] = 0ull;
             }
             if (eepf_on)
                 for (int b = tid; b < D->eepf_bins; b += blockDim.x) sH[b] = 0u;
             __syncthreads();
         }
-        const long long base = (t - sPre[cur]) * (long long)TILE + (long long)tid * VEC;
+        const int tbase = (t - sPre[cur]) * TILE;
+        if (tid == 0) atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_PUSH_E : EDUPIC_C_PUSH_I), (unsigned)min(TILE, n - tbase));
+        const int base = tbase + tid * VEC;
         if (base >= n) continue;
-        {
-            const long long live = n - base < VEC ? n - base : VEC;
-            atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_PUSH_E : EDUPIC_C_PUSH_I), (unsigned int)live);
-        }
 
         T *X = reinterpret_cast<T *>(D->x[SP]);
         T *VX = reinterpret_cast<T *>(D->vx[SP]);
@@ -516,35 +563,39 @@ __global__ void __launch_bounds__(kThreads) k_push(const DischargeDev *__restric
         unpack(*reinterpret_cast<const V *>(VY + base), vya);
         unpack(*reinterpret_cast<const V *>(VZ + base), vza);
 
+        // phase 1: gather, push, absorption test, table index
+        int kk[VEC];
+        bool in[VEC];
+        T w2[VEC];     // v^2 (e-) or g^2 (Ar+)
+        T va[VEC][3];  // thermal partner (Ar+)
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
-            const long long slot = base + e;
-            if (slot >= n) break;
+            const int slot = base + e;
+            in[e] = false;
+            kk[e] = 0;
+            w2[e] = (T)0;
+            va[e][0] = va[e][1] = va[e][2] = (T)0;
+            if (slot >= n) continue;
             const T x = xa[e], vx = vxa[e];
-            T vy = vya[e], vz = vza[e];
-            // field at the particle (Sec. 2.1.3) and leapfrog push (Sec. 2.1.4)
             T c0;
-            const int p = cell<T>(x, h.inv_dx, h.ng, c0);
+            const int p = cell<T>(x, inv_dx, ctx.ng, c0);
             const T c1 = (T)(p + 1) - c0, c2 = c0 - (T)p;
-            const T e_x = c1 * sE[p] + c2 * sE[p + 1];
-            T vxn;
-            if (SP == 0)
-                vxn = vx - e_x * h.factor;
-            else
-                vxn = vx + e_x * h.factor;
+            const T2 ep = sE2[p];
+            const T e_x = c1 * ep.x + c2 * ep.y;
+            const T vxn = SP == 0 ? vx - e_x * factor : vx + e_x * factor;
             if (SP == 0 && eepf_on) {
-                // EEPF in the centre 10% with the time-centred velocity
-                bool in;
-                if constexpr (std::is_same<T, double>::value)
-                    in = x >= D->eepf_lo && x <= D->eepf_hi;
+                // EEPF in the centre 10% with the time-centred velocity (Sec. 3.5)
+                bool mid;
+                if constexpr (is_f64<T>())
+                    mid = x >= D->eepf_lo && x <= D->eepf_hi;
                 else
-                    in = x >= D->eepf_lof && x <= D->eepf_hif;
-                if (in) {
+                    mid = x >= D->eepf_lof && x <= D->eepf_hif;
+                if (mid) {
                     const T vc = (T)0.5 * (vx + vxn);
-                    const T v2c = vc * vc + vy * vy + vz * vz;
+                    const T v2c = vc * vc + vya[e] * vya[e] + vza[e] * vza[e];
                     int b;
                     bool ok;
-                    if constexpr (std::is_same<T, double>::value) {
+                    if constexpr (is_f64<T>()) {
                         const double en = 0.5 * EDUPIC_ME * v2c / EDUPIC_QE;
                         const double r = en / D->eepf_de;
                         ok = r < (double)D->eepf_bins;
@@ -557,157 +608,81 @@ __global__ void __launch_bounds__(kThreads) k_push(const DischargeDev *__restric
                     if (ok) atomicAdd(sH + b, 1u);
                 }
             }
-            const T xn = x + vxn * h.dt;
+            const T xn = x + vxn * dt;
             xa[e] = xn;
             vxa[e] = vxn;
-            const bool inside = (xn >= (T)0.0) && (xn <= h.L);
-            if (!inside) {
-                // absorption at an electrode (Sec. 2.1.5): record the hole
-                const int side = xn < (T)0.0 ? 0 : (xn > h.L ? 1 : -1);
-                if (side < 0) {
-                    atomicOr(&D->ctrl->error, kErrNan);
-                } else {
-                    atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_ABS_E_POW : EDUPIC_C_ABS_I_POW) + side, 1u);
-                }
-                const int hidx = atomicAdd(&D->ctrl->holes[SP], 1);
-                if (hidx < kEvents)
-                    D->holes[SP][hidx] = (int)slot;
-                else
-                    atomicOr(&D->ctrl->error, kErrHoles);
-                if (SP == 1 && measure && side >= 0) {
-                    const T v2 = vxn * vxn + vy * vy + vz * vz;
-                    int b;
-                    bool ok;
-                    if constexpr (std::is_same<T, double>::value) {
-                        const double en = D->half_mar * v2 / EDUPIC_QE;
-                        const double r = en / D->ifed_de;
-                        ok = r < (double)D->ifed_bins;
-                        b = ok ? (int)r : 0;
-                    } else {
-                        const float en = D->e_of_v2_if * v2;
-                        const float r = en * D->inv_ifed_def;
-                        ok = r < (float)D->ifed_bins;
-                        b = ok ? (int)r : 0;
-                    }
-                    if (ok) atomicAdd((side == 0 ? D->ifed_pow : D->ifed_gnd) + b, 1ull);
-                }
-                continue;
-            }
-            key.slot = (uint32_t)slot;
-            bool collided = false;
-            // ------------------------------------------------ Monte Carlo collision (Algorithm 6)
+            in[e] = (xn >= (T)0.0) && (xn <= L);
+            if (!in[e]) continue;
             if (SP == 0) {
-                const T v2 = vxn * vxn + vy * vy + vz * vz;
-                const T velocity = sqrt(v2);
-                int k;
-                if constexpr (std::is_same<T, double>::value) {
-                    const double energy = D->half_me * v2 / EDUPIC_QE;
-                    k = cs_index(energy, D->cs_de_e, cs_n);
-                } else {
-                    k = cs_index_f(D->e_of_v2_ef * v2, D->inv_cs_de_ef, cs_n);
-                }
-                const CsEntry<T> cs = tab[k];
-                const T nu = cs.sigsum * h.n_gas * velocity;
-                const T pc = p_coll(nu * h.dt);
-                T u_test, u_proc;
-                draw<T>(key, 0, 0, u_test, u_proc);
-                if (u_test < pc) {
-                    T u_chi, u_eta, u_opal, u_dummy, vej[3];
-                    draw<T>(key, 0, 1, u_chi, u_eta);
-                    draw<T>(key, 0, 2, u_opal, u_dummy);
-                    T nvx = vxn;
-                    int sub;
-                    const int proc = collide_electron<T>(*D, cs, nvx, vy, vz, u_proc, u_chi, u_eta, u_opal, vej, sub);
-                    vxa[e] = nvx;
-                    collided = true;
-                    atomicAdd(sCnt + EDUPIC_C_COLL_E_ELA + proc, 1u);
-                    if (sub) atomicAdd(sCnt + EDUPIC_C_SUBTHRESHOLD, 1u);
-                    if (proc == 2) {
-                        T n0, n1, n2, n3, z0, z1, z2, z3;
-                        draw<T>(key, 0, 3, n0, n1);
-                        draw<T>(key, 0, 4, n2, n3);
-                        box_muller(n0, n1, z0, z1);
-                        box_muller(n2, n3, z2, z3);
-                        const T sth = std::is_same<T, double>::value ? (T)D->sig_th : (T)D->sig_thf;
-                        const int pi = atomicAdd(&D->ctrl->products, 1);
-                        if (pi < kEvents) {
-                            D->prod_parent[pi] = (int)slot;
-                            reinterpret_cast<T *>(D->prod_x)[pi] = xn;
-                            reinterpret_cast<T *>(D->prod_ve[0])[pi] = vej[0];
-                            reinterpret_cast<T *>(D->prod_ve[1])[pi] = vej[1];
-                            reinterpret_cast<T *>(D->prod_ve[2])[pi] = vej[2];
-                            reinterpret_cast<T *>(D->prod_vi[0])[pi] = sth * z0;
-                            reinterpret_cast<T *>(D->prod_vi[1])[pi] = sth * z1;
-                            reinterpret_cast<T *>(D->prod_vi[2])[pi] = sth * z2;
-                            // the new pair joins the next densities at the parent's x
-                            T d0;
-                            const int pp = cell<T>(xn, h.inv_dx, h.ng, d0);
-                            const long long q2 = split_q2<T>(d0 - (T)pp);
-                            atomicAdd(sQ + pp, 4294967296ull - (unsigned long long)q2);
-                            atomicAdd(sQ + pp + 1, (unsigned long long)q2);
-                            atomicAdd(reinterpret_cast<unsigned long long *>(D->acc_i + pp),
-                                      4294967296ull - (unsigned long long)q2);
-                            atomicAdd(reinterpret_cast<unsigned long long *>(D->acc_i + pp + 1),
-                                      (unsigned long long)q2);
-                        } else {
-                            atomicOr(&D->ctrl->error, kErrProducts);
-                        }
-                    }
-                }
+                const T v2 = vxn * vxn + vya[e] * vya[e] + vza[e] * vza[e];
+                w2[e] = v2;
+                if constexpr (is_f64<T>())
+                    kk[e] = cs_index(D->half_me * v2 / EDUPIC_QE, idx_scale, cs_n);
+                else
+                    kk[e] = cs_index_f(v2 * idx_scale + 0.5f, cs_n);
             } else {
                 // thermal partner drawn before the collision probability
                 T a0, a1, a2, a3, za, zb, zc, zd;
-                draw<T>(key, 1, 0, a0, a1);
-                draw<T>(key, 1, 1, a2, a3);
+                draw<T>(ctx.key, (uint32_t)slot, 1, 1, a0, a1);
+                draw<T>(ctx.key, (uint32_t)slot, 1, 2, a2, a3);
                 box_muller(a0, a1, za, zb);
                 box_muller(a2, a3, zc, zd);
-                T vax, vay, vaz, energy_g2, half;
-                int k;
-                if constexpr (std::is_same<T, double>::value) {
-                    vax = D->sig_th * za;
-                    vay = D->sig_th * zb;
-                    vaz = D->sig_th * zc;
-                    half = D->half_mu_arar;
-                } else {
-                    vax = D->sig_thf * za;
-                    vay = D->sig_thf * zb;
-                    vaz = D->sig_thf * zc;
-                    half = 0.0f;
-                }
-                const T gx = vxn - vax, gy = vy - vay, gz = vz - vaz;
+                const T sth = is_f64<T>() ? (T)D->sig_th : (T)D->sig_thf;
+                va[e][0] = sth * za;
+                va[e][1] = sth * zb;
+                va[e][2] = sth * zc;
+                const T gx = vxn - va[e][0], gy = vya[e] - va[e][1], gz = vza[e] - va[e][2];
                 const T g_sqr = gx * gx + gy * gy + gz * gz;
-                const T g = sqrt(g_sqr);
-                if constexpr (std::is_same<T, double>::value) {
-                    energy_g2 = half * g_sqr / EDUPIC_QE;
-                    k = cs_index(energy_g2, D->cs_de_i, cs_n);
-                } else {
-                    k = cs_index_f(D->e_of_g2_if * g_sqr, D->inv_cs_de_if, cs_n);
-                }
-                const CsEntry<T> cs = tab[k];
-                const T nu = cs.sigsum * h.n_gas * g;
-                const T pc = p_coll(nu * h.dt);
-                T u_test, u_proc;
-                draw<T>(key, 1, 2, u_test, u_proc);
-                if (u_test < pc) {
-                    T u_chi, u_eta;
-                    draw<T>(key, 1, 3, u_chi, u_eta);
-                    T nvx = vxn;
-                    const int proc = collide_ion<T>(*D, cs, nvx, vy, vz, vax, vay, vaz, u_proc, u_chi, u_eta);
-                    vxa[e] = nvx;
-                    collided = true;
-                    atomicAdd(sCnt + EDUPIC_C_COLL_I_ISO + proc, 1u);
-                }
+                w2[e] = g_sqr;
+                if constexpr (is_f64<T>())
+                    kk[e] = cs_index(D->half_mu_arar * g_sqr / EDUPIC_QE, idx_scale, cs_n);
+                else
+                    kk[e] = cs_index_f(g_sqr * idx_scale + 0.5f, cs_n);
             }
-            if (collided) {
-                VY[slot] = vy;
-                VZ[slot] = vz;
+        }
+        // phase 2: total cross sections of all particles of the thread
+        T sg[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) sg[e] = in[e] ? __ldg(sig + kk[e]) : (T)0;
+        // phase 3: collision-test uniforms, one Philox block per slot pair
+        T ut[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; e += 2) {
+            const Words w = philox((uint32_t)(base + e) >> 1, ctx.key.s_lo, ctx.key.s_hi, (uint32_t)SP << 8,
+                                   ctx.key.k0, ctx.key.k1);
+            uniforms(w, ut[e], ut[e + 1]);
+        }
+        // phase 4: collision test (Algorithm 6), absorption records, deposition
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            const int slot = base + e;
+            if (slot >= n) break;
+            if (!in[e]) {
+                absorbed<T, SP>(ctx, slot, xa[e], vxa[e], vya[e], vza[e], measure);
+                continue;
+            }
+            const T speed = sqrt(w2[e]);
+            T pc;
+            if constexpr (is_f64<T>())
+                pc = p_coll(sg[e] * ndt * speed * dt);
+            else
+                pc = p_coll(sg[e] * ndt * speed);
+            if (ut[e] < pc) {
+                T v3[3] = {vxa[e], vya[e], vza[e]};
+                if (SP == 0)
+                    electron_collision<T>(ctx, slot, kk[e], xa[e], v3);
+                else
+                    ion_collision<T>(ctx, slot, kk[e], va[e], v3);
+                vxa[e] = v3[0];
+                VY[slot] = v3[1];
+                VZ[slot] = v3[2];
             }
             // deposition of the new position for the next step (Sec. 2.1.1)
             T d0;
-            const int pp = cell<T>(xn, h.inv_dx, h.ng, d0);
-            const long long q2 = split_q2<T>(d0 - (T)pp);
-            atomicAdd(sQ + pp, 4294967296ull - (unsigned long long)q2);
-            atomicAdd(sQ + pp + 1, (unsigned long long)q2);
+            const int pp = cell<T>(xa[e], inv_dx, ctx.ng, d0);
+            const unsigned long long q2 = split_q2(d0 - (T)pp);
+            atomicAdd(sQ + pp, 4294967296ull - q2);
+            atomicAdd(sQ + pp + 1, q2);
         }
         *reinterpret_cast<V *>(X + base) = pack(xa, V{});
         *reinterpret_cast<V *>(VX + base) = pack(vxa, V{});
@@ -716,151 +691,165 @@ __global__ void __launch_bounds__(kThreads) k_push(const DischargeDev *__restric
 }
 
 // ---------------------------------------------------------------- field solve
-// Densities from the fixed-point sums and the Poisson solve for the step whose
-// within-cycle index is tc (Algorithm 3).  The tridiagonal system with
-// Dirichlet ends is solved through its exact double prefix-sum form: with
-// d_p = phi_{p+1} - phi_p, F_p = sum_{k=1..p} D_k, G_p = sum_{j<p} F_j and
-// D_k = Q_i,k - Q_e,k (integers), d_p = d_0 - c F_p, phi_p = V + p d_0 - c G_p
-// and phi_M = 0 fixes d_0 = (c G_M - V) / M.  F and G are exact integer scans,
-// so the result does not depend on the order of summation.
-static __device__ void solve_fields(const DischargeDev &D, long long tc)
+// Group of G threads (named barrier `bar`): densities from the fixed-point
+// sums and the Poisson solve (Algorithm 3) for within-cycle step tc.  The
+// tridiagonal system with Dirichlet ends is solved through its exact double
+// prefix-sum form: with d_p = phi_{p+1} - phi_p, F_p = sum_{k=1..p} D_k and
+// D_k = Q_i,k - Q_e,k, d_p = d_0 - c F_p and phi_p = V + p d_0 - c G_p with
+// G_p = sum_{j<p} F_j; phi_{N_G-1} = 0 fixes d_0 = (c G_M - V) / M.  F is an
+// exact integer scan; G a fixed-order FP64 scan.
+//
+// mode 0: only solve from q_e / q_i; mode 1: first swap in the accumulated
+// deposition (acc -> q) and, if measure, add the fields of the step just
+// executed to the time sums.
+template <typename T, int G>
+__device__ void grid_update(const DischargeDev &D, long long tc, int mode, bool next_ion, int measure, int gtid,
+                            int bar, long long *s_w64, double *s_wd)
 {
-    __shared__ long long sW64[33];
-    __shared__ __int128 sW128[33];
-    __shared__ double sD[4];
-    const int ng = D.ng, M = ng - 1, tid = threadIdx.x, nt = blockDim.x;
-    constexpr int PER = (EDUPIC_MAX_GRID + kFinalizeThreads - 1) / kFinalizeThreads;
-    // drive voltage V(t)
-    double V = 0.0;
-    {
-        const double t = (double)tc * D.dt_e;
-        for (int k = 0; k < D.n_harm; ++k) V += D.harm_volt[k] * cos(2.0 * EDUPIC_PI * D.harm_freq[k] * t);
+    constexpr int PER = (EDUPIC_MAX_GRID + G - 1) / G;
+    const int ng = D.ng, M = ng - 1;
+    const int first = gtid * PER;
+    const double V = D.vdrive[tc];
+    long long Qe[PER], Qi[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int p = first + j;
+        Qe[j] = 0;
+        Qi[j] = 0;
+        if (p >= ng) continue;
+        if (mode == 1) {
+            Qe[j] = D.acc_e[p];
+            D.acc_e[p] = 0;
+            D.q_e[p] = Qe[j];
+            if (next_ion) {
+                Qi[j] = D.acc_i[p];
+                D.acc_i[p] = 0;
+                D.q_i[p] = Qi[j];
+            } else {
+                Qi[j] = D.q_i[p];
+            }
+            if (measure) {
+                D.sum_ne[p] += D.n_e[p];
+                D.sum_ni[p] += D.n_i[p];
+                D.sum_phi[p] += D.phi[p];
+            }
+        } else {
+            Qe[j] = D.q_e[p];
+            Qi[j] = D.q_i[p];
+        }
     }
-    // densities (Algorithm 2: x2 at the half-volume edge points)
-    for (int p = tid; p < ng; p += nt) {
-        double ne = D.factor_w * ((double)D.q_e[p] * (1.0 / 4294967296.0));
-        double ni = D.factor_w * ((double)D.q_i[p] * (1.0 / 4294967296.0));
-        if (p == 0 || p == ng - 1) {
+    // F: inclusive scan of D_p (D_p = 0 at the electrodes)
+    long long run = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int p = first + j;
+        if (p >= 1 && p <= M - 1) run += Qi[j] - Qe[j];
+    }
+    long long tot64;
+    const long long off = group_excl_scan(run, s_w64, tot64, gtid, G, bar);
+    long long F[PER];
+    double runG = 0.0;
+    {
+        long long a = off;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int p = first + j;
+            if (p >= 1 && p <= M - 1) a += Qi[j] - Qe[j];
+            F[j] = a;
+            if (p <= M - 1) runG += (double)a;
+        }
+    }
+    double totG;
+    const double offG = group_excl_scan(runG, s_wd, totG, gtid, G, bar);
+    const double c = D.poisson_c;
+    const double d0 = (c * totG - V) / (double)M;
+    T *et = reinterpret_cast<T *>(D.ef_t);
+    double g = offG;
+    long long fprev = off;  // F_{first-1}
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int p = first + j;
+        if (p > M) break;
+        double ne = D.factor_w * ((double)Qe[j] * (1.0 / 4294967296.0));
+        double ni = D.factor_w * ((double)Qi[j] * (1.0 / 4294967296.0));
+        if (p == 0 || p == M) {
             ne *= 2.0;
             ni *= 2.0;
         }
         D.n_e[p] = ne;
         D.n_i[p] = ni;
-    }
-    // F: inclusive scan of D over p = 0..M-1 (D_0 = 0); each thread owns a run
-    const int first = tid * PER;
-    long long Dv[PER], Fv[PER];
-    long long run = 0;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int p = first + j;
-        const long long dv = (p >= 1 && p <= M - 1) ? (D.q_i[p] - D.q_e[p]) : 0ll;
-        Dv[j] = dv;
-        run += dv;
-    }
-    long long tot64;
-    const long long off = block_excl_scan64(run, sW64, tot64);
-    long long acc = off;
-    __int128 runG = 0;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        acc += Dv[j];
-        Fv[j] = acc;
-        const int p = first + j;
-        if (p <= M - 1) runG += (__int128)acc;
-    }
-    // G: exclusive scan of F over p = 0..M
-    __int128 totG;
-    const __int128 offG = block_excl_scan128(runG, sW128, totG);
-    if (tid == 0) sD[0] = (D.poisson_c * (double)totG - V) / (double)M;  // d_0
-    __syncthreads();
-    const double d0 = sD[0], c = D.poisson_c;
-    __int128 g = offG;         // G_p for p = first
-    long long fprev = off;     // F_{first-1}
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int p = first + j;
-        if (p > M) break;
-        if (p < M) {
-            D.phi[p] = V + (double)p * d0 - c * (double)g;
-            g += (__int128)Fv[j];
+        double ef;
+        if (p == 0) {
+            D.phi[0] = V;
+            ef = -d0 / D.dx - EDUPIC_QE * (ni - ne) * D.dx / (2.0 * EDUPIC_EPS0);
+        } else if (p < M) {
+            D.phi[p] = V + (double)p * d0 - c * g;
+            ef = -((d0 - c * (double)fprev) + (d0 - c * (double)F[j])) * D.inv_2dx;
         } else {
             D.phi[p] = 0.0;
+            ef = -(d0 - c * (double)fprev) / D.dx + EDUPIC_QE * (ni - ne) * D.dx / (2.0 * EDUPIC_EPS0);
         }
-        // E_p = (phi_{p-1} - phi_{p+1}) / (2 dx) = -(d_{p-1} + d_p) / (2 dx) inside;
-        // one-sided forms with the half-cell charge at the electrodes
-        if (p == 0) {
-            const double rho0 = EDUPIC_QE * (D.n_i[0] - D.n_e[0]);
-            D.ef[0] = -d0 / D.dx - rho0 * D.dx / (2.0 * EDUPIC_EPS0);
-        } else if (p < M) {
-            const double dpm1 = d0 - c * (double)fprev, dp = d0 - c * (double)Fv[j];
-            D.ef[p] = -(dpm1 + dp) / (2.0 * D.dx);
-        } else {
-            const double dm1 = d0 - c * (double)fprev;
-            const double rhoM = EDUPIC_QE * (D.n_i[M] - D.n_e[M]);
-            D.ef[M] = -dm1 / D.dx + rhoM * D.dx / (2.0 * EDUPIC_EPS0);
-        }
-        fprev = Fv[j];
+        if (p <= M - 1) g += (double)F[j];
+        D.ef[p] = ef;
+        et[p] = (T)ef;
+        fprev = F[j];
     }
-    __syncthreads();
-}
-
-template <typename T>
-__device__ void copy_field_t(const DischargeDev &D)
-{
-    T *et = reinterpret_cast<T *>(D.ef_t);
-    for (int p = threadIdx.x; p < D.ng; p += blockDim.x) et[p] = (T)D.ef[p];
 }
 
 // ---------------------------------------------------------------- compaction
-// Holes of species sp sorted ascending (rank by counting; slots are unique),
-// then filled by the tail survivors [N', N) in ascending order.
+// Bitonic sort of n ints in shared memory by a group of g threads.
+__device__ __forceinline__ void group_sort(int *a, int n, int gtid, int g, int bar)
+{
+    int m = 1;
+    while (m < n) m <<= 1;
+    for (int i = n + gtid; i < m; i += g) a[i] = INT_MAX;
+    bar_sync(bar, g);
+    for (int k = 2; k <= m; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = gtid; i < m; i += g) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const int ai = a[i], al = a[l];
+                    const bool up = (i & k) == 0;
+                    if ((ai > al) == up) {
+                        a[i] = al;
+                        a[l] = ai;
+                    }
+                }
+            }
+            bar_sync(bar, g);
+        }
+    }
+}
+
+// Holes of species sp sorted ascending, then filled by the tail survivors
+// [N', N) in ascending order (the canonical removal order).
 template <typename T>
-__device__ void compact_species(const DischargeDev &D, int sp, int *sA, int *sW, int &H_out, long long &n_out)
+__device__ long long compact_species(const DischargeDev &D, int sp, int *sA, int *sW, int gtid, int g, int bar)
 {
     Ctrl *C = D.ctrl;
     const long long n = C->n[sp];
     int H = C->holes[sp];
     if (H > kEvents) H = kEvents;  // error bit already set by k_push
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int i = tid; i < H; i += nt) sA[i] = D.holes[sp][i];
-    __syncthreads();
-    constexpr int MAXPER = (kEvents + kFinalizeThreads - 1) / kFinalizeThreads;
-    int my_h[MAXPER], my_r[MAXPER];
-#pragma unroll
-    for (int j = 0; j < MAXPER; ++j) {
-        const int i = tid + j * nt;
-        my_h[j] = -1;
-        my_r[j] = 0;
-        if (i < H) {
-            const int h = sA[i];
-            int r = 0;
-            for (int k = 0; k < H; ++k) r += sA[k] < h;
-            my_h[j] = h;
-            my_r[j] = r;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < MAXPER; ++j)
-        if (my_h[j] >= 0) sA[my_r[j]] = my_h[j];
-    __syncthreads();
+    if (H == 0) return n;
+    for (int i = gtid; i < H; i += g) sA[i] = D.holes[sp][i];
+    group_sort(sA, H, gtid, g, bar);
     const long long nn = n - H;
     T *X = reinterpret_cast<T *>(D.x[sp]);
     T *VX = reinterpret_cast<T *>(D.vx[sp]);
     T *VY = reinterpret_cast<T *>(D.vy[sp]);
     T *VZ = reinterpret_cast<T *>(D.vz[sp]);
-    const T L = std::is_same<T, double>::value ? (T)D.L : (T)D.Lf;
+    const T L = is_f64<T>() ? (T)D.L : (T)D.Lf;
     int filled = 0;
-    for (int b = 0; b < H; b += nt) {
-        const long long j = nn + b + tid;
+    for (int b = 0; b < H; b += g) {
+        const long long j = nn + b + gtid;
         bool alive = false;
-        if (b + tid < H) {
+        if (b + gtid < H) {
             const T xj = X[j];
             alive = (xj >= (T)0.0) && (xj <= L);
         }
         int tot;
-        const int r = block_excl_scan(alive ? 1 : 0, sW, tot);
+        const int r = group_excl_scan(alive ? 1 : 0, sW, tot, gtid, g, bar);
         const int k = filled + r;
         const int dst = (alive && k < H) ? sA[k] : -1;
         if (alive && (dst < 0 || dst >= nn)) atomicOr(&C->error, kErrHoles);  // inconsistent hole list
@@ -872,21 +861,20 @@ __device__ void compact_species(const DischargeDev &D, int sp, int *sA, int *sW,
         }
         filled += tot;
     }
-    __syncthreads();
-    H_out = H;
-    n_out = nn;
+    bar_sync(bar, g);
+    return nn;
 }
 
 // Ionisation products appended in ascending parent order.
 template <typename T>
-__device__ void append_products(const DischargeDev &D, int *sA, long long &ne, long long &ni)
+__device__ void append_products(const DischargeDev &D, int *sA, long long &ne, long long &ni, int gtid, int g, int bar)
 {
     Ctrl *C = D.ctrl;
     int P = C->products;
     if (P > kEvents) P = kEvents;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int i = tid; i < P; i += nt) sA[i] = D.prod_parent[i];
-    __syncthreads();
+    if (P == 0) return;
+    for (int i = gtid; i < P; i += g) sA[i] = D.prod_parent[i];
+    group_sort(sA, P, gtid, g, bar);
     long long room = D.cap[0] - ne;
     if (D.cap[1] - ni < room) room = D.cap[1] - ni;
     const long long keep = (long long)P < room ? (long long)P : (room > 0 ? room : 0);
@@ -895,10 +883,17 @@ __device__ void append_products(const DischargeDev &D, int *sA, long long &ne, l
     T *VY0 = reinterpret_cast<T *>(D.vy[0]), *VY1 = reinterpret_cast<T *>(D.vy[1]);
     T *VZ0 = reinterpret_cast<T *>(D.vz[0]), *VZ1 = reinterpret_cast<T *>(D.vz[1]);
     const T *px = reinterpret_cast<const T *>(D.prod_x);
-    for (int i = tid; i < P; i += nt) {
-        const int h = sA[i];
-        int r = 0;
-        for (int k = 0; k < P; ++k) r += sA[k] < h;
+    for (int i = gtid; i < P; i += g) {
+        const int h = D.prod_parent[i];
+        int lo = 0, hi = P;  // rank of h among the sorted parents
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sA[mid] < h)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        const int r = lo;
         if (r < keep) {
             const long long se = ne + r, si = ni + r;
             X0[se] = px[i];
@@ -911,8 +906,7 @@ __device__ void append_products(const DischargeDev &D, int *sA, long long &ne, l
             VZ1[si] = reinterpret_cast<const T *>(D.prod_vi[2])[i];
         }
     }
-    __syncthreads();
-    if (tid == 0) {
+    if (gtid == 0) {
         C->counters[EDUPIC_C_CREATED] += (unsigned long long)keep;
         if (keep < (long long)P) {
             C->counters[EDUPIC_C_DROPPED] += (unsigned long long)(P - keep);
@@ -921,6 +915,7 @@ __device__ void append_products(const DischargeDev &D, int *sA, long long &ne, l
     }
     ne += keep;
     ni += keep;
+    bar_sync(bar, g);
 }
 
 template <typename T>
@@ -929,46 +924,38 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDe
 {
     __shared__ int sA[kEvents];
     __shared__ int sW[33];
+    __shared__ long long sW64[33];
+    __shared__ double sWd[33];
+    __shared__ long long sN[2];
     const DischargeDev &D = DD[blockIdx.x];
     if (!D.active) return;
     Ctrl *C = D.ctrl;
-    const int tid = threadIdx.x;
-    int H;
-    long long ne, ni = C->n[1];
-    compact_species<T>(D, 0, sA, sW, H, ne);
-    if (ion_step) compact_species<T>(D, 1, sA, sW, H, ni);
-    append_products<T>(D, sA, ne, ni);
-    // grid diagnostics of the step just executed (its densities and potential)
-    if (measure) {
-        for (int p = tid; p < D.ng; p += blockDim.x) {
-            D.sum_ne[p] += D.n_e[p];
-            D.sum_ni[p] += D.n_i[p];
-            D.sum_phi[p] += D.phi[p];
-        }
-    }
     const long long next = C->step + 1;
-    const long long tc = next % D.nt;
-    const bool next_ion = (tc % D.nsub) == 0;
-    for (int p = tid; p < D.ng; p += blockDim.x) {
-        D.q_e[p] = D.acc_e[p];
-        D.acc_e[p] = 0;
-        if (next_ion) {
-            D.q_i[p] = D.acc_i[p];
-            D.acc_i[p] = 0;
+    if (threadIdx.x < kGroupA) {
+        // (A) particle bookkeeping
+        const int gtid = threadIdx.x;
+        long long ne = compact_species<T>(D, 0, sA, sW, gtid, kGroupA, 1);
+        long long ni = ion_step ? compact_species<T>(D, 1, sA, sW, gtid, kGroupA, 1) : C->n[1];
+        append_products<T>(D, sA, ne, ni, gtid, kGroupA, 1);
+        if (gtid == 0) {
+            sN[0] = ne;
+            sN[1] = ni;
         }
+    } else {
+        // (B) densities, diagnostics and field of the next step
+        const long long tc = next % D.nt;
+        grid_update<T, kGroupB>(D, tc, 1, (tc % D.nsub) == 0, measure, threadIdx.x - kGroupA, 2, sW64, sWd);
     }
     __syncthreads();
-    if (tid == 0) {
-        C->n[0] = ne;
-        C->n[1] = ni;
+    if (threadIdx.x == 0) {
+        C->n[0] = sN[0];
+        C->n[1] = sN[1];
         C->holes[0] = 0;
         C->holes[1] = 0;
         C->products = 0;
         C->step = next;
         if (measure) C->measured += 1;
     }
-    solve_fields(D, tc);
-    copy_field_t<T>(D);
 }
 
 // Densities of one species from its particles (after a load), into q and,
@@ -979,27 +966,29 @@ __global__ void k_deposit(const DischargeDev *__restrict__ DD, int d, int sp, in
     const DischargeDev &D = DD[d];
     const long long n = D.ctrl->n[sp];
     const T *X = reinterpret_cast<const T *>(D.x[sp]);
-    const T inv_dx = std::is_same<T, double>::value ? (T)D.inv_dx : (T)D.inv_dxf;
+    const T inv_dx = is_f64<T>() ? (T)D.inv_dx : (T)D.inv_dxf;
     long long *q = sp == 0 ? D.q_e : D.q_i;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
         T c0;
         const int p = cell<T>(X[j], inv_dx, D.ng, c0);
-        const long long q2 = split_q2<T>(c0 - (T)p);
-        atomicAdd(reinterpret_cast<unsigned long long *>(q + p), 4294967296ull - (unsigned long long)q2);
-        atomicAdd(reinterpret_cast<unsigned long long *>(q + p + 1), (unsigned long long)q2);
+        const unsigned long long q2 = split_q2(c0 - (T)p);
+        atomicAdd(reinterpret_cast<unsigned long long *>(q + p), 4294967296ull - q2);
+        atomicAdd(reinterpret_cast<unsigned long long *>(q + p + 1), q2);
         if (also_acc) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + p), 4294967296ull - (unsigned long long)q2);
-            atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + p + 1), (unsigned long long)q2);
+            atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + p), 4294967296ull - q2);
+            atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + p + 1), q2);
         }
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFinalizeThreads) k_fields(const DischargeDev *__restrict__ DD, int d)
+__global__ void __launch_bounds__(kGroupB) k_fields(const DischargeDev *__restrict__ DD, int d)
 {
+    __shared__ long long sW64[33];
+    __shared__ double sWd[33];
     const DischargeDev &D = DD[d];
-    solve_fields(D, D.ctrl->step % D.nt);
-    copy_field_t<T>(D);
+    const long long tc = D.ctrl->step % D.nt;
+    grid_update<T, kGroupB>(D, tc, 0, false, 0, threadIdx.x, 2, sW64, sWd);
 }
 
 }  // namespace edupic

@@ -8,8 +8,7 @@ namespace edupic {
 template <typename T>
 size_t Launch<T>::push_smem(int nd, int ng_max, int eepf_max)
 {
-    return ((size_t)ng_max * sizeof(T) + 15 & ~(size_t)15) + (size_t)ng_max * 8 + (size_t)eepf_max * 4 +
-           (size_t)(nd + 1) * 4;
+    return push_smem_bytes<T>(nd, ng_max, eepf_max);
 }
 
 template <typename T>
@@ -39,7 +38,7 @@ template <typename T>
 cudaError_t Launch<T>::fields(const DischargeDev *dd, int nd, int d, cudaStream_t st)
 {
     (void)nd;
-    k_fields<T><<<1, kFinalizeThreads, 0, st>>>(dd, d);
+    k_fields<T><<<1, kGroupB, 0, st>>>(dd, d);
     return cudaGetLastError();
 }
 

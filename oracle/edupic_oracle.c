@@ -367,7 +367,10 @@ static void deflect(double gx, double gy, double gz, double g, double cc, double
                     double u[3])
 {
     double ct = gx / g;
-    double st = sqrt(1.0 - ct * ct);
+    /* sin(theta) from the transverse components of g (the definition
+     * g = g (cos theta, sin theta cos phi, sin theta sin phi)), which stays
+     * accurate when g is nearly along x, where sqrt(1 - cos^2) cancels */
+    double st = sqrt(gy * gy + gz * gz) / g;
     double cp, sp;
     if (st == 0.0) { /* Reading: g along x, the azimuth of g is arbitrary */
         cp = 1.0;

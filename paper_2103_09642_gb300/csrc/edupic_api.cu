@@ -635,51 +635,61 @@ int edupic_profile_steps(edupic_sim *S, int64_t n_steps, int measure, double out
     if (!S || n_steps < 0 || !out_ms || !launches) return EDUPIC_EINVAL;
     if (!S->cs_set[0] || !S->cs_set[1]) return EDUPIC_ESTATE;
     measure = measure ? 1 : 0;
-    cudaEvent_t ev[4];
-    for (auto &e : ev)
-        if (cudaEventCreate(&e) != cudaSuccess) return EDUPIC_ECUDA;
     for (int k = 0; k < 3; ++k) {
         out_ms[k] = 0.0;
         launches[k] = 0;
     }
+    // all steps are enqueued back to back, with an event pair around every
+    // kernel, and read after one synchronisation
+    constexpr int64_t kChunk = 256;
+    std::vector<cudaEvent_t> ev(4 * kChunk);
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return EDUPIC_ECUDA;
     int rc = EDUPIC_OK;
-    for (int64_t i = 0; i < n_steps && rc == EDUPIC_OK; ++i) {
-        const bool ion = S->phase == 0;
-        cudaError_t e = cudaEventRecord(ev[0], S->stream);
-        if (S->precision == EDUPIC_FP32) {
-            if (e == cudaSuccess)
-                e = Launch<float>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max, S->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[1], S->stream);
-            if (e == cudaSuccess && ion)
-                e = Launch<float>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max, S->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[2], S->stream);
-            if (e == cudaSuccess) e = Launch<float>::finalize(S->d_desc, S->nd, ion ? 1 : 0, measure, S->stream);
-        } else {
-            if (e == cudaSuccess)
-                e = Launch<double>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max, S->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[1], S->stream);
-            if (e == cudaSuccess && ion)
-                e = Launch<double>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max, S->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[2], S->stream);
-            if (e == cudaSuccess) e = Launch<double>::finalize(S->d_desc, S->nd, ion ? 1 : 0, measure, S->stream);
+    for (int64_t done = 0; done < n_steps && rc == EDUPIC_OK;) {
+        const int64_t m = std::min<int64_t>(kChunk, n_steps - done);
+        std::vector<char> ion(m);
+        cudaError_t e = cudaSuccess;
+        for (int64_t i = 0; i < m && e == cudaSuccess; ++i) {
+            ion[i] = S->phase == 0;
+            cudaEvent_t *E = &ev[4 * i];
+            e = cudaEventRecord(E[0], S->stream);
+            if (S->precision == EDUPIC_FP32) {
+                if (e == cudaSuccess)
+                    e = Launch<float>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max, S->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(E[1], S->stream);
+                if (e == cudaSuccess && ion[i])
+                    e = Launch<float>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max, S->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(E[2], S->stream);
+                if (e == cudaSuccess) e = Launch<float>::finalize(S->d_desc, S->nd, ion[i], measure, S->stream);
+            } else {
+                if (e == cudaSuccess)
+                    e = Launch<double>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max, S->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(E[1], S->stream);
+                if (e == cudaSuccess && ion[i])
+                    e = Launch<double>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max, S->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(E[2], S->stream);
+                if (e == cudaSuccess) e = Launch<double>::finalize(S->d_desc, S->nd, ion[i], measure, S->stream);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(E[3], S->stream);
+            S->phase = (S->phase + 1) % S->nsub;
         }
-        if (e == cudaSuccess) e = cudaEventRecord(ev[3], S->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
-        float ms[3] = {0, 0, 0};
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
-        if (e == cudaSuccess && ion) e = cudaEventElapsedTime(&ms[1], ev[1], ev[2]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[2], ev[2], ev[3]);
-        if (e != cudaSuccess) {
-            rc = EDUPIC_ECUDA;
-            break;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+        for (int64_t i = 0; i < m && e == cudaSuccess; ++i) {
+            const cudaEvent_t *E = &ev[4 * i];
+            float ms[3] = {0, 0, 0};
+            e = cudaEventElapsedTime(&ms[0], E[0], E[1]);
+            if (e == cudaSuccess && ion[i]) e = cudaEventElapsedTime(&ms[1], E[1], E[2]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[2], E[2], E[3]);
+            out_ms[0] += ms[0];
+            out_ms[1] += ms[1];
+            out_ms[2] += ms[2];
+            launches[0] += 1;
+            launches[1] += ion[i] ? 1 : 0;
+            launches[2] += 1;
         }
-        out_ms[0] += ms[0];
-        out_ms[1] += ms[1];
-        out_ms[2] += ms[2];
-        launches[0] += 1;
-        launches[1] += ion ? 1 : 0;
-        launches[2] += 1;
-        S->phase = (S->phase + 1) % S->nsub;
+        if (e != cudaSuccess) rc = EDUPIC_ECUDA;
+        done += m;
     }
     for (auto &e : ev) cudaEventDestroy(e);
     return rc;

@@ -177,7 +177,7 @@ template <typename T>
 __device__ __forceinline__ void deflect(T gx, T gy, T gz, T g, T cc, T sc, T ce, T se, T u[3])
 {
     const T ct = gx / g;
-    const T st = sqrt((T)1.0 - ct * ct);
+    const T st = sqrt(gy * gy + gz * gz) / g;  // well conditioned when g is nearly along x
     T cp, sp;
     if (st == (T)0.0) {
         cp = (T)1.0;

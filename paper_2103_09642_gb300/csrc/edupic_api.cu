@@ -32,7 +32,7 @@ long long padded(long long cap) { return (cap + kTileAlign - 1) / kTileAlign * k
 // Byte layout of one discharge inside the arena (offsets from its base).
 struct Layout {
     size_t x[2], vx[2], vy[2], vz[2];
-    size_t q_e, q_i, acc_e, acc_i, n_e, n_i, phi, ef, ef_t, sum_ne, sum_ni, sum_phi;
+    size_t q_e, q_i, acc_e, acc_i, n_e, n_i, phi, ef, ef_t, f_cur, fs, sum_qe, sum_qi, sum_f, avg;
     size_t eepf, ifed_pow, ifed_gnd, ctrl, holes[2], prod_parent, prod_x, prod_ve[3], prod_vi[3], vdrive;
     size_t bytes;
 };
@@ -63,9 +63,12 @@ Layout layout_of(const edupic_params &p, size_t elem)
     L.phi = take(ng * 8);
     L.ef = take(ng * 8);
     L.ef_t = take(ng * elem);
-    L.sum_ne = take(ng * 8);
-    L.sum_ni = take(ng * 8);
-    L.sum_phi = take(ng * 8);
+    L.f_cur = take(ng * 8);
+    L.fs = take(sizeof(FieldState));
+    L.sum_qe = take(ng * 8);
+    L.sum_qi = take(ng * 8);
+    L.sum_f = take(ng * 8);
+    L.avg = take(3 * ng * 8);
     L.eepf = take((size_t)p.eepf_bins * 8);
     L.ifed_pow = take((size_t)p.ifed_bins * 8);
     L.ifed_gnd = take((size_t)p.ifed_bins * 8);
@@ -227,6 +230,7 @@ void fill_desc(edupic_sim *S, int d)
     D.e_idx_ef = (float)(0.5 * kME / kQE / D.cs_de_e);
     D.g_idx_if = (float)(0.5 * mu_arar / kQE / D.cs_de_i);
     D.inv_2dx = 1.0 / (2.0 * D.dx);
+    D.edge_c = kQE * D.factor_w * 2.0 / 4294967296.0 * D.dx / (2.0 * kEPS0);
     D.ng = p.n_grid;
     D.nt = p.steps_per_cycle;
     D.nsub = p.ion_subcycle;
@@ -255,9 +259,12 @@ void fill_desc(edupic_sim *S, int d)
     D.phi = reinterpret_cast<double *>(b + L.phi);
     D.ef = reinterpret_cast<double *>(b + L.ef);
     D.ef_t = b + L.ef_t;
-    D.sum_ne = reinterpret_cast<double *>(b + L.sum_ne);
-    D.sum_ni = reinterpret_cast<double *>(b + L.sum_ni);
-    D.sum_phi = reinterpret_cast<double *>(b + L.sum_phi);
+    D.f_cur = reinterpret_cast<long long *>(b + L.f_cur);
+    D.fs = reinterpret_cast<FieldState *>(b + L.fs);
+    D.sum_qe = reinterpret_cast<double *>(b + L.sum_qe);
+    D.sum_qi = reinterpret_cast<double *>(b + L.sum_qi);
+    D.sum_f = reinterpret_cast<double *>(b + L.sum_f);
+    D.avg = reinterpret_cast<double *>(b + L.avg);
     D.eepf = reinterpret_cast<unsigned long long *>(b + L.eepf);
     D.ifed_pow = reinterpret_cast<unsigned long long *>(b + L.ifed_pow);
     D.ifed_gnd = reinterpret_cast<unsigned long long *>(b + L.ifed_gnd);
@@ -736,7 +743,10 @@ int edupic_get_fields(edupic_sim *S, int d, double *n_e, double *n_i, double *ph
                       int64_t *q_i)
 {
     if (!valid_d(S, d)) return EDUPIC_EINVAL;
-    if (cudaStreamSynchronize(S->stream) != cudaSuccess) return EDUPIC_ECUDA;
+    // densities and potential of the current step are formed on demand
+    cudaError_t e0 = S->precision == EDUPIC_FP32 ? Launch<float>::fields(S->d_desc, S->nd, d, S->stream)
+                                                 : Launch<double>::fields(S->d_desc, S->nd, d, S->stream);
+    if (e0 != cudaSuccess || cudaStreamSynchronize(S->stream) != cudaSuccess) return EDUPIC_ECUDA;
     const DischargeDev &D = S->desc[d];
     const size_t ng = (size_t)S->params[d].n_grid;
     struct {
@@ -759,14 +769,16 @@ int edupic_get_diagnostics(edupic_sim *S, int d, double *ne_avg, double *ni_avg,
     const DischargeDev &D = S->desc[d];
     const edupic_params &p = S->params[d];
     const size_t ng = (size_t)p.n_grid;
-    const double m = c.measured > 0 ? (double)c.measured : 1.0;
     double *outs[3] = {ne_avg, ni_avg, phi_avg};
-    const double *srcs[3] = {D.sum_ne, D.sum_ni, D.sum_phi};
-    for (int k = 0; k < 3; ++k) {
-        if (!outs[k]) continue;
-        if (cudaMemcpy(outs[k], srcs[k], ng * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return EDUPIC_ECUDA;
-        for (size_t j = 0; j < ng; ++j) outs[k][j] /= m;
+    if (ne_avg || ni_avg || phi_avg) {
+        cudaError_t e = S->precision == EDUPIC_FP32 ? Launch<float>::averages(S->d_desc, S->nd, d, S->stream)
+                                                    : Launch<double>::averages(S->d_desc, S->nd, d, S->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+        if (e != cudaSuccess) return EDUPIC_ECUDA;
     }
+    for (int k = 0; k < 3; ++k)
+        if (outs[k] && cudaMemcpy(outs[k], D.avg + k * ng, ng * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return EDUPIC_ECUDA;
     if (eepf_counts && cudaMemcpy(eepf_counts, D.eepf, (size_t)p.eepf_bins * 8, cudaMemcpyDeviceToHost))
         return EDUPIC_ECUDA;
     if (ifed_pow_counts && cudaMemcpy(ifed_pow_counts, D.ifed_pow, (size_t)p.ifed_bins * 8, cudaMemcpyDeviceToHost))
@@ -830,9 +842,10 @@ int edupic_reset_diagnostics(edupic_sim *S, int d)
     const DischargeDev &D = S->desc[d];
     const edupic_params &p = S->params[d];
     const size_t ng = (size_t)p.n_grid;
-    cudaError_t e = cudaMemsetAsync(D.sum_ne, 0, ng * 8, S->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(D.sum_ni, 0, ng * 8, S->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(D.sum_phi, 0, ng * 8, S->stream);
+    cudaError_t e = cudaMemsetAsync(D.sum_qe, 0, ng * 8, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.sum_qi, 0, ng * 8, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.sum_f, 0, ng * 8, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&D.fs->sum_V, 0, 2 * sizeof(double), S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.eepf, 0, (size_t)p.eepf_bins * 8, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.ifed_pow, 0, (size_t)p.ifed_bins * 8, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.ifed_gnd, 0, (size_t)p.ifed_bins * 8, S->stream);

@@ -32,6 +32,12 @@ struct Ctrl {
     unsigned long long counters[EDUPIC_N_COUNTERS];
 };
 
+// Scalars of the current field and their time sums (diagnostics).
+struct FieldState {
+    double V, d0;       // drive voltage and d_0 = phi_1 - phi_0 of the current field
+    double sum_V, sum_d0;
+};
+
 // Cross-section tables in particle precision T: sigsum[k] = sum of the
 // process cross sections (n*sigma_tot is formed in the kernel as
 // sigsum * n_gas), thr[k] = cumulative process fractions (thr1, thr2).
@@ -52,6 +58,7 @@ struct DischargeDev {
     float e_idx_ef;        // (m_e / 2e) / DE_CS: table index of v^2
     float g_idx_if;        // (mu / 2e) / DE_CS: table index of g^2
     double inv_2dx;
+    double edge_c;     // e FACTOR_W * 2 / 2^32 * dx / (2 eps0): edge term of E from Q_i - Q_e
     int ng, nt, nsub, n_harm, eepf_bins, ifed_bins, cs_n_e, cs_n_i;
     int active;
     int pad0;
@@ -64,7 +71,10 @@ struct DischargeDev {
     long long *acc_e, *acc_i;  // deposition of the next step (ions: next ion step)
     double *n_e, *n_i, *phi, *ef;
     void *ef_t;                // field in particle precision
-    double *sum_ne, *sum_ni, *sum_phi;
+    long long *f_cur;          // F_p of the current field (exact prefix sums of Q_i - Q_e)
+    FieldState *fs;            // V and d_0 of the current field, and their time sums
+    double *sum_qe, *sum_qi, *sum_f;  // time sums of Q_e, Q_i, F over the measured steps
+    double *avg;               // [3][ng] read-back buffer: time-averaged n_e, n_i, phi
     unsigned long long *eepf, *ifed_pow, *ifed_gnd;
     Ctrl *ctrl;
     int *holes[2];
@@ -80,6 +90,7 @@ template <typename T>
 struct Launch {
     static cudaError_t deposit(const DischargeDev *dd, int nd, int d, int species, int also_acc, cudaStream_t st);
     static cudaError_t fields(const DischargeDev *dd, int nd, int d, cudaStream_t st);
+    static cudaError_t averages(const DischargeDev *dd, int nd, int d, cudaStream_t st);
     static cudaError_t push(const DischargeDev *dd, int nd, int species, int measure, int grid, int ng_max,
                             int eepf_max, cudaStream_t st);
     static cudaError_t finalize(const DischargeDev *dd, int nd, int ion_step, int measure, cudaStream_t st);

@@ -31,14 +31,17 @@ namespace edupic {
 #define EDUPIC_EPS0 8.8541878128e-12
 #define EDUPIC_PI 3.14159265358979323846
 #define EDUPIC_OPAL_W 10.0
+#ifndef EDUPIC_PUSH_MIN_BLOCKS
+#define EDUPIC_PUSH_MIN_BLOCKS 2  // resident FP32 particle-kernel blocks per SM the register budget targets
+#endif
 
 template <typename T>
 struct VecOf;
 template <>
 struct VecOf<float> {
-    using type = float4;
+    using type = float2;
     using pair = float2;
-    static constexpr int n = 4;
+    static constexpr int n = 2;
 };
 template <>
 struct VecOf<double> {
@@ -47,9 +50,9 @@ struct VecOf<double> {
     static constexpr int n = 2;
 };
 
-__device__ __forceinline__ void unpack(const float4 &v, float *a) { a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w; }
+__device__ __forceinline__ void unpack(const float2 &v, float *a) { a[0] = v.x; a[1] = v.y; }
 __device__ __forceinline__ void unpack(const double2 &v, double *a) { a[0] = v.x; a[1] = v.y; }
-__device__ __forceinline__ float4 pack(const float *a, float4) { return make_float4(a[0], a[1], a[2], a[3]); }
+__device__ __forceinline__ float2 pack(const float *a, float2) { return make_float2(a[0], a[1]); }
 __device__ __forceinline__ double2 pack(const double *a, double2) { return make_double2(a[0], a[1]); }
 
 template <typename T>
@@ -322,88 +325,115 @@ __device__ __forceinline__ V group_excl_scan(V v, V *s_w, V &total, int gtid, in
     return r;
 }
 
+// ---------------------------------------------------------------- int128 reduction
+__device__ __forceinline__ __int128 shfl_down128(__int128 v, int o)
+{
+    const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
+    const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, o), h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    return (__int128)(((unsigned __int128)h2 << 64) | (unsigned __int128)l2);
+}
+
+// Exact sum of a per-thread int128 over a group of g threads; every thread
+// gets the total.  s_w: shared scratch of >= 32 int128.
+__device__ __forceinline__ __int128 group_sum128(__int128 v, __int128 *s_w, int gtid, int g, int bar)
+{
+    const int lane = gtid & 31, warp = gtid >> 5, nw = g >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += shfl_down128(v, o);
+    if (lane == 0) s_w[warp] = v;
+    bar_sync(bar, g);
+    __int128 t = 0;
+    for (int w = 0; w < nw; ++w) t += s_w[w];
+    bar_sync(bar, g);
+    return t;
+}
+
 // ---------------------------------------------------------------- rare paths
-// Everything a collision or absorption needs beyond the hot loop's registers.
 template <typename T>
-struct PushCtx {
-    const DischargeDev *D;
-    RngKey key;
-    unsigned long long *sQ;
-    unsigned int *sCnt;
-    T inv_dx;
-    int ng;
+struct Vel {
+    T x, y, z;
 };
 
 // e- collision of one particle (Algorithm 6 after the test passed),
-// including the append record and deposition of an ionisation pair.
+// including the append record and the deposition of an ionisation pair.
+// Scalar arguments and a struct return keep the hot loop free of stack use.
 template <typename T>
-__device__ __noinline__ void electron_collision(const PushCtx<T> &c, int slot, int k, T xn, T *vxyz)
+__device__ __noinline__ Vel<T> electron_collision(const DischargeDev *Dp, int slot, int k, T xn, T vx, T vy, T vz,
+                                                  uint32_t s_lo, uint32_t s_hi, unsigned long long *sQ,
+                                                  unsigned int *sCnt)
 {
     using T2 = typename VecOf<T>::pair;
-    const DischargeDev &D = *c.D;
+    const DischargeDev &D = *Dp;
+    const RngKey key{s_lo, s_hi, (uint32_t)D.seed, (uint32_t)(D.seed >> 32)};
     const T2 thr = reinterpret_cast<const T2 *>(D.cs_thr[0])[k];
     T u_proc, u_chi, u_eta, u_opal, vej[3];
-    draw<T>(c.key, (uint32_t)slot, 0, 1, u_proc, u_chi);
-    draw<T>(c.key, (uint32_t)slot, 0, 2, u_eta, u_opal);
+    draw<T>(key, (uint32_t)slot, 0, 1, u_proc, u_chi);
+    draw<T>(key, (uint32_t)slot, 0, 2, u_eta, u_opal);
     int sub;
-    const int proc =
-        collide_electron<T>(D, thr.x, thr.y, vxyz[0], vxyz[1], vxyz[2], u_proc, u_chi, u_eta, u_opal, vej, sub);
-    atomicAdd(c.sCnt + EDUPIC_C_COLL_E_ELA + proc, 1u);
-    if (sub) atomicAdd(c.sCnt + EDUPIC_C_SUBTHRESHOLD, 1u);
-    if (proc != 2) return;
-    T n0, n1, n2, n3, z0, z1, z2, z3;
-    draw<T>(c.key, (uint32_t)slot, 0, 3, n0, n1);
-    draw<T>(c.key, (uint32_t)slot, 0, 4, n2, n3);
-    box_muller(n0, n1, z0, z1);
-    box_muller(n2, n3, z2, z3);
-    const T sth = is_f64<T>() ? (T)D.sig_th : (T)D.sig_thf;
-    const int pi = atomicAdd(&D.ctrl->products, 1);
-    if (pi >= kEvents) {
-        atomicOr(&D.ctrl->error, kErrProducts);
-        return;
+    const int proc = collide_electron<T>(D, thr.x, thr.y, vx, vy, vz, u_proc, u_chi, u_eta, u_opal, vej, sub);
+    atomicAdd(sCnt + EDUPIC_C_COLL_E_ELA + proc, 1u);
+    if (sub) atomicAdd(sCnt + EDUPIC_C_SUBTHRESHOLD, 1u);
+    if (proc == 2) {
+        T n0, n1, n2, n3, z0, z1, z2, z3;
+        draw<T>(key, (uint32_t)slot, 0, 3, n0, n1);
+        draw<T>(key, (uint32_t)slot, 0, 4, n2, n3);
+        box_muller(n0, n1, z0, z1);
+        box_muller(n2, n3, z2, z3);
+        const T sth = is_f64<T>() ? (T)D.sig_th : (T)D.sig_thf;
+        const int pi = atomicAdd(&D.ctrl->products, 1);
+        if (pi < kEvents) {
+            D.prod_parent[pi] = slot;
+            reinterpret_cast<T *>(D.prod_x)[pi] = xn;
+            reinterpret_cast<T *>(D.prod_ve[0])[pi] = vej[0];
+            reinterpret_cast<T *>(D.prod_ve[1])[pi] = vej[1];
+            reinterpret_cast<T *>(D.prod_ve[2])[pi] = vej[2];
+            reinterpret_cast<T *>(D.prod_vi[0])[pi] = sth * z0;
+            reinterpret_cast<T *>(D.prod_vi[1])[pi] = sth * z1;
+            reinterpret_cast<T *>(D.prod_vi[2])[pi] = sth * z2;
+            // the new pair joins the next densities at the parent's x
+            const T inv_dx = is_f64<T>() ? (T)D.inv_dx : (T)D.inv_dxf;
+            T d0;
+            const int pp = cell<T>(xn, inv_dx, D.ng, d0);
+            const unsigned long long q2 = split_q2(d0 - (T)pp);
+            atomicAdd(sQ + pp, 4294967296ull - q2);
+            atomicAdd(sQ + pp + 1, q2);
+            atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp), 4294967296ull - q2);
+            atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp + 1), q2);
+        } else {
+            atomicOr(&D.ctrl->error, kErrProducts);
+        }
     }
-    D.prod_parent[pi] = slot;
-    reinterpret_cast<T *>(D.prod_x)[pi] = xn;
-    reinterpret_cast<T *>(D.prod_ve[0])[pi] = vej[0];
-    reinterpret_cast<T *>(D.prod_ve[1])[pi] = vej[1];
-    reinterpret_cast<T *>(D.prod_ve[2])[pi] = vej[2];
-    reinterpret_cast<T *>(D.prod_vi[0])[pi] = sth * z0;
-    reinterpret_cast<T *>(D.prod_vi[1])[pi] = sth * z1;
-    reinterpret_cast<T *>(D.prod_vi[2])[pi] = sth * z2;
-    // the new pair joins the next densities at the parent's x
-    T d0;
-    const int pp = cell<T>(xn, c.inv_dx, c.ng, d0);
-    const unsigned long long q2 = split_q2(d0 - (T)pp);
-    atomicAdd(c.sQ + pp, 4294967296ull - q2);
-    atomicAdd(c.sQ + pp + 1, q2);
-    atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp), 4294967296ull - q2);
-    atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp + 1), q2);
+    return Vel<T>{vx, vy, vz};
 }
 
 template <typename T>
-__device__ __noinline__ void ion_collision(const PushCtx<T> &c, int slot, int k, const T *va, T *vxyz)
+__device__ __noinline__ Vel<T> ion_collision(const DischargeDev *Dp, int slot, int k, T vx, T vy, T vz, T vax, T vay,
+                                             T vaz, uint32_t s_lo, uint32_t s_hi, unsigned int *sCnt)
 {
     using T2 = typename VecOf<T>::pair;
-    const DischargeDev &D = *c.D;
+    const DischargeDev &D = *Dp;
+    const RngKey key{s_lo, s_hi, (uint32_t)D.seed, (uint32_t)(D.seed >> 32)};
     const T thr1 = reinterpret_cast<const T2 *>(D.cs_thr[1])[k].x;
     T u_proc, u_chi, u_eta, u_dummy;
-    draw<T>(c.key, (uint32_t)slot, 1, 3, u_proc, u_chi);
-    draw<T>(c.key, (uint32_t)slot, 1, 4, u_eta, u_dummy);
-    const int proc = collide_ion<T>(D, thr1, vxyz[0], vxyz[1], vxyz[2], va[0], va[1], va[2], u_proc, u_chi, u_eta);
-    atomicAdd(c.sCnt + EDUPIC_C_COLL_I_ISO + proc, 1u);
+    draw<T>(key, (uint32_t)slot, 1, 3, u_proc, u_chi);
+    draw<T>(key, (uint32_t)slot, 1, 4, u_eta, u_dummy);
+    const int proc = collide_ion<T>(D, thr1, vx, vy, vz, vax, vay, vaz, u_proc, u_chi, u_eta);
+    atomicAdd(sCnt + EDUPIC_C_COLL_I_ISO + proc, 1u);
+    return Vel<T>{vx, vy, vz};
 }
 
 // Absorbed particle: record the hole, count it, bin the Ar+ impact energy.
 template <typename T, int SP>
-__device__ __noinline__ void absorbed(const PushCtx<T> &c, int slot, T xn, T vx, T vy, T vz, int measure)
+__device__ __noinline__ void absorbed(const DischargeDev *Dp, int slot, T xn, T vx, T vy, T vz, int measure,
+                                      unsigned int *sCnt)
 {
-    const DischargeDev &D = *c.D;
+    const DischargeDev &D = *Dp;
     const T L = is_f64<T>() ? (T)D.L : (T)D.Lf;
     const int side = xn < (T)0.0 ? 0 : (xn > L ? 1 : -1);
     if (side < 0)
         atomicOr(&D.ctrl->error, kErrNan);
     else
-        atomicAdd(c.sCnt + (SP == 0 ? EDUPIC_C_ABS_E_POW : EDUPIC_C_ABS_I_POW) + side, 1u);
+        atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_ABS_E_POW : EDUPIC_C_ABS_I_POW) + side, 1u);
     const int h = atomicAdd(&D.ctrl->holes[SP], 1);
     if (h < kEvents)
         D.holes[SP][h] = slot;
@@ -427,6 +457,28 @@ __device__ __noinline__ void absorbed(const PushCtx<T> &c, int slot, T xn, T vx,
     }
 }
 
+// EEPF sample (Sec. 3.5): electrons in the centre 10% of the gap, energy of
+// the time-centred velocity.
+template <typename T>
+__device__ __noinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy, T vz, unsigned int *sH)
+{
+    const DischargeDev &D = *Dp;
+    const T v2c = vxc * vxc + vy * vy + vz * vz;
+    int b;
+    bool ok;
+    if constexpr (is_f64<T>()) {
+        const double en = 0.5 * EDUPIC_ME * v2c / EDUPIC_QE;
+        const double r = en / D.eepf_de;
+        ok = r < (double)D.eepf_bins;
+        b = ok ? (int)r : 0;
+    } else {
+        const float r = D.e_of_v2_ef * v2c * D.inv_eepf_def;
+        ok = r < (float)D.eepf_bins;
+        b = ok ? (int)r : 0;
+    }
+    if (ok) atomicAdd(sH + b, 1u);
+}
+
 // ---------------------------------------------------------------- particle kernel
 // Dynamic shared memory: [E pairs: ng_max T2][Q: ng_max u64][EEPF: eepf_max u32]
 // [tile prefix: nd+1 int].
@@ -437,12 +489,12 @@ __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eep
 }
 
 template <typename T, int SP>
-__global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : 3)
+__global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BLOCKS)
     k_push(const DischargeDev *__restrict__ DD, int nd, int ng_max, int eepf_max, int measure)
 {
     using V = typename VecOf<T>::type;
     using T2 = typename VecOf<T>::pair;
-    constexpr int VEC = VecOf<T>::n;
+    constexpr int VEC = VecOf<T>::n;  // two slots per thread: one Philox test block
     constexpr int TILE = kThreads * VEC;
     extern __shared__ __align__(16) unsigned char smem[];
     T2 *sE2 = reinterpret_cast<T2 *>(smem);
@@ -475,19 +527,17 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : 3)
     if (t0 >= t1) return;
 
     int cur = -1;
-    PushCtx<T> ctx{};
-    ctx.sQ = sQ;
-    ctx.sCnt = sCnt;
     const DischargeDev *D = nullptr;
-    int n = 0, cs_n = 0;
-    T L = 0, inv_dx = 0, dt = 0, factor = 0, ndt = 0, idx_scale = 0;
+    int n = 0, cs_n = 0, ng = 0;
+    uint32_t s_lo = 0, s_hi = 0, k0 = 0, k1 = 0;
+    T L = 0, inv_dx = 0, dt = 0, factor = 0, ndt = 0, idx_scale = 0, lo = 0, hi = 0;
     const T *sig = nullptr;
     bool eepf_on = false;
 
     auto flush = [&]() {
         __syncthreads();
         long long *acc = SP == 0 ? D->acc_e : D->acc_i;
-        for (int p = tid; p < D->ng; p += blockDim.x) {
+        for (int p = tid; p < ng; p += blockDim.x) {
             const unsigned long long q = sQ[p];
             if (q) atomicAdd(reinterpret_cast<unsigned long long *>(acc + p), q);
         }
@@ -511,14 +561,13 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : 3)
             ++cur;
             while (sPre[cur + 1] <= t) ++cur;
             D = DD + cur;
-            ctx.D = D;
             n = (int)D->ctrl->n[SP];
             const unsigned long long s = (unsigned long long)D->ctrl->step;
-            ctx.key.s_lo = (uint32_t)s;
-            ctx.key.s_hi = (uint32_t)(s >> 32);
-            ctx.key.k0 = (uint32_t)D->seed;
-            ctx.key.k1 = (uint32_t)(D->seed >> 32);
-            ctx.ng = D->ng;
+            s_lo = (uint32_t)s;
+            s_hi = (uint32_t)(s >> 32);
+            k0 = (uint32_t)D->seed;
+            k1 = (uint32_t)(D->seed >> 32);
+            ng = D->ng;
             if constexpr (is_f64<T>()) {
                 L = D->L;
                 inv_dx = D->inv_dx;
@@ -526,6 +575,8 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : 3)
                 factor = SP == 0 ? D->factor_e : D->factor_i;
                 ndt = D->n_gas;
                 idx_scale = SP == 0 ? D->cs_de_e : D->cs_de_i;
+                lo = D->eepf_lo;
+                hi = D->eepf_hi;
             } else {
                 L = D->Lf;
                 inv_dx = D->inv_dxf;
@@ -533,13 +584,13 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : 3)
                 factor = SP == 0 ? D->factor_ef : D->factor_if;
                 ndt = SP == 0 ? D->ndt_ef : D->ndt_if;
                 idx_scale = SP == 0 ? D->e_idx_ef : D->g_idx_if;
+                lo = D->eepf_lof;
+                hi = D->eepf_hif;
             }
-            ctx.inv_dx = inv_dx;
             sig = reinterpret_cast<const T *>(D->cs_sig[SP]);
             cs_n = SP == 0 ? D->cs_n_e : D->cs_n_i;
             eepf_on = SP == 0 && measure;
             const T *ef = reinterpret_cast<const T *>(D->ef_t);
-            const int ng = D->ng;
             for (int p = tid; p < ng; p += blockDim.x) {
                 sE2[p] = T2{ef[p], p + 1 < ng ? ef[p + 1] : (T)0};
                 sQ[p] = 0ull;
@@ -566,48 +617,24 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : 3)
         // phase 1: gather, push, absorption test, table index
         int kk[VEC];
         bool in[VEC];
-        T w2[VEC];     // v^2 (e-) or g^2 (Ar+)
-        T va[VEC][3];  // thermal partner (Ar+)
+        T w2[VEC];  // v^2 (e-) or g^2 (Ar+)
+        T vax[VEC], vay[VEC], vaz[VEC];  // thermal partner (Ar+)
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
             const int slot = base + e;
             in[e] = false;
             kk[e] = 0;
             w2[e] = (T)0;
-            va[e][0] = va[e][1] = va[e][2] = (T)0;
+            vax[e] = vay[e] = vaz[e] = (T)0;
             if (slot >= n) continue;
             const T x = xa[e], vx = vxa[e];
             T c0;
-            const int p = cell<T>(x, inv_dx, ctx.ng, c0);
+            const int p = cell<T>(x, inv_dx, ng, c0);
             const T c1 = (T)(p + 1) - c0, c2 = c0 - (T)p;
             const T2 ep = sE2[p];
             const T e_x = c1 * ep.x + c2 * ep.y;
             const T vxn = SP == 0 ? vx - e_x * factor : vx + e_x * factor;
-            if (SP == 0 && eepf_on) {
-                // EEPF in the centre 10% with the time-centred velocity (Sec. 3.5)
-                bool mid;
-                if constexpr (is_f64<T>())
-                    mid = x >= D->eepf_lo && x <= D->eepf_hi;
-                else
-                    mid = x >= D->eepf_lof && x <= D->eepf_hif;
-                if (mid) {
-                    const T vc = (T)0.5 * (vx + vxn);
-                    const T v2c = vc * vc + vya[e] * vya[e] + vza[e] * vza[e];
-                    int b;
-                    bool ok;
-                    if constexpr (is_f64<T>()) {
-                        const double en = 0.5 * EDUPIC_ME * v2c / EDUPIC_QE;
-                        const double r = en / D->eepf_de;
-                        ok = r < (double)D->eepf_bins;
-                        b = ok ? (int)r : 0;
-                    } else {
-                        const float r = D->e_of_v2_ef * v2c * D->inv_eepf_def;
-                        ok = r < (float)D->eepf_bins;
-                        b = ok ? (int)r : 0;
-                    }
-                    if (ok) atomicAdd(sH + b, 1u);
-                }
-            }
+            if (SP == 0 && eepf_on && x >= lo && x <= hi) eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e], sH);
             const T xn = x + vxn * dt;
             xa[e] = xn;
             vxa[e] = vxn;
@@ -622,16 +649,17 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : 3)
                     kk[e] = cs_index_f(v2 * idx_scale + 0.5f, cs_n);
             } else {
                 // thermal partner drawn before the collision probability
+                const RngKey key{s_lo, s_hi, k0, k1};
                 T a0, a1, a2, a3, za, zb, zc, zd;
-                draw<T>(ctx.key, (uint32_t)slot, 1, 1, a0, a1);
-                draw<T>(ctx.key, (uint32_t)slot, 1, 2, a2, a3);
+                draw<T>(key, (uint32_t)slot, 1, 1, a0, a1);
+                draw<T>(key, (uint32_t)slot, 1, 2, a2, a3);
                 box_muller(a0, a1, za, zb);
                 box_muller(a2, a3, zc, zd);
                 const T sth = is_f64<T>() ? (T)D->sig_th : (T)D->sig_thf;
-                va[e][0] = sth * za;
-                va[e][1] = sth * zb;
-                va[e][2] = sth * zc;
-                const T gx = vxn - va[e][0], gy = vya[e] - va[e][1], gz = vza[e] - va[e][2];
+                vax[e] = sth * za;
+                vay[e] = sth * zb;
+                vaz[e] = sth * zc;
+                const T gx = vxn - vax[e], gy = vya[e] - vay[e], gz = vza[e] - vaz[e];
                 const T g_sqr = gx * gx + gy * gy + gz * gz;
                 w2[e] = g_sqr;
                 if constexpr (is_f64<T>())
@@ -640,17 +668,15 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : 3)
                     kk[e] = cs_index_f(g_sqr * idx_scale + 0.5f, cs_n);
             }
         }
-        // phase 2: total cross sections of all particles of the thread
+        // phase 2: total cross sections of the thread's particles
         T sg[VEC];
 #pragma unroll
         for (int e = 0; e < VEC; ++e) sg[e] = in[e] ? __ldg(sig + kk[e]) : (T)0;
-        // phase 3: collision-test uniforms, one Philox block per slot pair
+        // phase 3: collision-test uniforms of the slot pair (one Philox block)
         T ut[VEC];
-#pragma unroll
-        for (int e = 0; e < VEC; e += 2) {
-            const Words w = philox((uint32_t)(base + e) >> 1, ctx.key.s_lo, ctx.key.s_hi, (uint32_t)SP << 8,
-                                   ctx.key.k0, ctx.key.k1);
-            uniforms(w, ut[e], ut[e + 1]);
+        {
+            const Words w = philox((uint32_t)base >> 1, s_lo, s_hi, (uint32_t)SP << 8, k0, k1);
+            uniforms(w, ut[0], ut[1]);
         }
         // phase 4: collision test (Algorithm 6), absorption records, deposition
 #pragma unroll
@@ -658,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : 3)
             const int slot = base + e;
             if (slot >= n) break;
             if (!in[e]) {
-                absorbed<T, SP>(ctx, slot, xa[e], vxa[e], vya[e], vza[e], measure);
+                absorbed<T, SP>(D, slot, xa[e], vxa[e], vya[e], vza[e], measure, sCnt);
                 continue;
             }
             const T speed = sqrt(w2[e]);
@@ -668,18 +694,19 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : 3)
             else
                 pc = p_coll(sg[e] * ndt * speed);
             if (ut[e] < pc) {
-                T v3[3] = {vxa[e], vya[e], vza[e]};
+                Vel<T> v;
                 if (SP == 0)
-                    electron_collision<T>(ctx, slot, kk[e], xa[e], v3);
+                    v = electron_collision<T>(D, slot, kk[e], xa[e], vxa[e], vya[e], vza[e], s_lo, s_hi, sQ, sCnt);
                 else
-                    ion_collision<T>(ctx, slot, kk[e], va[e], v3);
-                vxa[e] = v3[0];
-                VY[slot] = v3[1];
-                VZ[slot] = v3[2];
+                    v = ion_collision<T>(D, slot, kk[e], vxa[e], vya[e], vza[e], vax[e], vay[e], vaz[e], s_lo, s_hi,
+                                         sCnt);
+                vxa[e] = v.x;
+                VY[slot] = v.y;
+                VZ[slot] = v.z;
             }
             // deposition of the new position for the next step (Sec. 2.1.1)
             T d0;
-            const int pp = cell<T>(xa[e], inv_dx, ctx.ng, d0);
+            const int pp = cell<T>(xa[e], inv_dx, ng, d0);
             const unsigned long long q2 = split_q2(d0 - (T)pp);
             atomicAdd(sQ + pp, 4294967296ull - q2);
             atomicAdd(sQ + pp + 1, q2);
@@ -691,33 +718,44 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : 3)
 }
 
 // ---------------------------------------------------------------- field solve
-// Group of G threads (named barrier `bar`): densities from the fixed-point
-// sums and the Poisson solve (Algorithm 3) for within-cycle step tc.  The
-// tridiagonal system with Dirichlet ends is solved through its exact double
-// prefix-sum form: with d_p = phi_{p+1} - phi_p, F_p = sum_{k=1..p} D_k and
-// D_k = Q_i,k - Q_e,k, d_p = d_0 - c F_p and phi_p = V + p d_0 - c G_p with
-// G_p = sum_{j<p} F_j; phi_{N_G-1} = 0 fixes d_0 = (c G_M - V) / M.  F is an
-// exact integer scan; G a fixed-order FP64 scan.
+// The Poisson problem of Algorithm 3 (tridiagonal, constant coefficients,
+// phi_0 = V(t), phi_{N_G-1} = 0) is solved through its exact prefix-sum form:
+// with d_p = phi_{p+1} - phi_p, D_k = Q_i,k - Q_e,k (fixed-point densities,
+// integers) and F_p = sum_{k=1..p} D_k, the discrete equation gives
+// d_p = d_0 - c F_p, so phi_p = V + p d_0 - c G_p with G_p = sum_{j<p} F_j and
+// phi_{N_G-1} = 0 fixes d_0 = (c G_M - V) / M (M = N_G - 1, c = dx^2 e
+// FACTOR_W / (eps0 2^32)).  F and G_M are exact integer sums.  The field
+// follows as E_p = -(d_{p-1} + d_p) / (2 dx) inside and from the one-sided
+// forms with the half-cell charge at the electrodes; E needs only F and d_0.
 //
-// mode 0: only solve from q_e / q_i; mode 1: first swap in the accumulated
-// deposition (acc -> q) and, if measure, add the fields of the step just
-// executed to the time sums.
-template <typename T, int G>
-__device__ void grid_update(const DischargeDev &D, long long tc, int mode, bool next_ion, int measure, int gtid,
-                            int bar, long long *s_w64, double *s_wd)
+// Each of the g threads of the group (named barrier `bar`) owns a run of
+// consecutive grid points.
+template <int G>
+struct FieldScratch {
+    long long w64[33];
+    __int128 w128[32];
+    double wd[33];
+    double d0;
+};
+
+// Load (Q_e, Q_i) of the owned points; swap in the accumulated deposition
+// when `swap` (and add the current field to the time sums when `measure`).
+template <int PMAX>
+__device__ __forceinline__ void load_q(const DischargeDev &D, int first, int last, bool swap, bool next_ion,
+                                       bool measure, long long *Qe, long long *Qi)
 {
-    constexpr int PER = (EDUPIC_MAX_GRID + G - 1) / G;
-    const int ng = D.ng, M = ng - 1;
-    const int first = gtid * PER;
-    const double V = D.vdrive[tc];
-    long long Qe[PER], Qi[PER];
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
+    for (int j = 0; j < PMAX; ++j) {
         const int p = first + j;
         Qe[j] = 0;
         Qi[j] = 0;
-        if (p >= ng) continue;
-        if (mode == 1) {
+        if (p >= last) continue;
+        if (swap && measure) {
+            D.sum_qe[p] += (double)D.q_e[p];
+            D.sum_qi[p] += (double)D.q_i[p];
+            D.sum_f[p] += (double)D.f_cur[p];
+        }
+        if (swap) {
             Qe[j] = D.acc_e[p];
             D.acc_e[p] = 0;
             D.q_e[p] = Qe[j];
@@ -728,48 +766,93 @@ __device__ void grid_update(const DischargeDev &D, long long tc, int mode, bool 
             } else {
                 Qi[j] = D.q_i[p];
             }
-            if (measure) {
-                D.sum_ne[p] += D.n_e[p];
-                D.sum_ni[p] += D.n_i[p];
-                D.sum_phi[p] += D.phi[p];
-            }
         } else {
             Qe[j] = D.q_e[p];
             Qi[j] = D.q_i[p];
         }
     }
-    // F: inclusive scan of D_p (D_p = 0 at the electrodes)
+}
+
+// Field of within-cycle step tc.  full: also densities n_e, n_i and phi.
+template <typename T, int G>
+__device__ void solve_field(const DischargeDev &D, long long tc, bool swap, bool next_ion, bool measure, bool full,
+                            int gtid, int bar, FieldScratch<G> &sm)
+{
+    constexpr int PMAX = (EDUPIC_MAX_GRID + G - 1) / G;
+    const int ng = D.ng, M = ng - 1;
+    const int per = (ng + G - 1) / G;
+    const int first = gtid * per, last = min(first + per, ng);
+    if (swap && measure && gtid == 0) {
+        D.fs->sum_V += D.fs->V;
+        D.fs->sum_d0 += D.fs->d0;
+    }
+    long long Qe[PMAX], Qi[PMAX], F[PMAX];
+    load_q<PMAX>(D, first, last, swap, next_ion, measure, Qe, Qi);
+    // F: inclusive scan of D_p over p = 0..M (D_p = 0 at the electrodes)
     long long run = 0;
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
+    for (int j = 0; j < PMAX; ++j) {
         const int p = first + j;
-        if (p >= 1 && p <= M - 1) run += Qi[j] - Qe[j];
+        if (p >= 1 && p <= M - 1 && p < last) run += Qi[j] - Qe[j];
     }
     long long tot64;
-    const long long off = group_excl_scan(run, s_w64, tot64, gtid, G, bar);
-    long long F[PER];
-    double runG = 0.0;
+    const long long off = group_excl_scan(run, sm.w64, tot64, gtid, G, bar);
+    __int128 gpart = 0;
     {
         long long a = off;
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
+        for (int j = 0; j < PMAX; ++j) {
             const int p = first + j;
+            if (p >= last) break;
             if (p >= 1 && p <= M - 1) a += Qi[j] - Qe[j];
             F[j] = a;
-            if (p <= M - 1) runG += (double)a;
+            D.f_cur[p] = a;
+            if (p <= M - 1) gpart += (__int128)a;
         }
     }
-    double totG;
-    const double offG = group_excl_scan(runG, s_wd, totG, gtid, G, bar);
+    const __int128 gtot = group_sum128(gpart, sm.w128, gtid, G, bar);
+    const double V = D.vdrive[tc];
     const double c = D.poisson_c;
-    const double d0 = (c * totG - V) / (double)M;
+    if (gtid == 0) {
+        const double d0 = (c * (double)gtot - V) / (double)M;
+        sm.d0 = d0;
+        D.fs->V = V;
+        D.fs->d0 = d0;
+    }
+    bar_sync(bar, G);
+    const double d0 = sm.d0;
     T *et = reinterpret_cast<T *>(D.ef_t);
-    double g = offG;
     long long fprev = off;  // F_{first-1}
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
+    for (int j = 0; j < PMAX; ++j) {
         const int p = first + j;
-        if (p > M) break;
+        if (p >= last) break;
+        double ef;
+        if (p == 0)
+            ef = -d0 * D.inv_dx - D.edge_c * (double)(Qi[j] - Qe[j]);
+        else if (p < M)
+            ef = -(2.0 * d0 - c * (double)(fprev + F[j])) * D.inv_2dx;
+        else
+            ef = -(d0 - c * (double)fprev) * D.inv_dx + D.edge_c * (double)(Qi[j] - Qe[j]);
+        D.ef[p] = ef;
+        et[p] = (T)ef;
+        fprev = F[j];
+    }
+    if (!full) return;
+    // densities (Algorithm 2, x2 at the half-volume edge points) and phi
+    double gp = 0.0;
+#pragma unroll
+    for (int j = 0; j < PMAX; ++j) {
+        const int p = first + j;
+        if (p < last && p <= M - 1) gp += (double)F[j];
+    }
+    double totd;
+    const double offd = group_excl_scan(gp, sm.wd, totd, gtid, G, bar);
+    double g = offd;
+#pragma unroll
+    for (int j = 0; j < PMAX; ++j) {
+        const int p = first + j;
+        if (p >= last) break;
         double ne = D.factor_w * ((double)Qe[j] * (1.0 / 4294967296.0));
         double ni = D.factor_w * ((double)Qi[j] * (1.0 / 4294967296.0));
         if (p == 0 || p == M) {
@@ -778,21 +861,8 @@ __device__ void grid_update(const DischargeDev &D, long long tc, int mode, bool 
         }
         D.n_e[p] = ne;
         D.n_i[p] = ni;
-        double ef;
-        if (p == 0) {
-            D.phi[0] = V;
-            ef = -d0 / D.dx - EDUPIC_QE * (ni - ne) * D.dx / (2.0 * EDUPIC_EPS0);
-        } else if (p < M) {
-            D.phi[p] = V + (double)p * d0 - c * g;
-            ef = -((d0 - c * (double)fprev) + (d0 - c * (double)F[j])) * D.inv_2dx;
-        } else {
-            D.phi[p] = 0.0;
-            ef = -(d0 - c * (double)fprev) / D.dx + EDUPIC_QE * (ni - ne) * D.dx / (2.0 * EDUPIC_EPS0);
-        }
-        if (p <= M - 1) g += (double)F[j];
-        D.ef[p] = ef;
-        et[p] = (T)ef;
-        fprev = F[j];
+        D.phi[p] = p == 0 ? V : (p == M ? 0.0 : V + (double)p * d0 - c * g);
+        g += (double)F[j];
     }
 }
 
@@ -924,8 +994,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDe
 {
     __shared__ int sA[kEvents];
     __shared__ int sW[33];
-    __shared__ long long sW64[33];
-    __shared__ double sWd[33];
+    __shared__ FieldScratch<kGroupB> sF;
     __shared__ long long sN[2];
     const DischargeDev &D = DD[blockIdx.x];
     if (!D.active) return;
@@ -942,9 +1011,9 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDe
             sN[1] = ni;
         }
     } else {
-        // (B) densities, diagnostics and field of the next step
+        // (B) density swap, diagnostics, field of the next step
         const long long tc = next % D.nt;
-        grid_update<T, kGroupB>(D, tc, 1, (tc % D.nsub) == 0, measure, threadIdx.x - kGroupA, 2, sW64, sWd);
+        solve_field<T, kGroupB>(D, tc, true, (tc % D.nsub) == 0, measure != 0, false, threadIdx.x - kGroupA, 2, sF);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -981,14 +1050,50 @@ __global__ void k_deposit(const DischargeDev *__restrict__ DD, int d, int sp, in
     }
 }
 
+// Densities, potential and field of the current step from q_e / q_i.
 template <typename T>
 __global__ void __launch_bounds__(kGroupB) k_fields(const DischargeDev *__restrict__ DD, int d)
 {
-    __shared__ long long sW64[33];
-    __shared__ double sWd[33];
+    __shared__ FieldScratch<kGroupB> sF;
     const DischargeDev &D = DD[d];
     const long long tc = D.ctrl->step % D.nt;
-    grid_update<T, kGroupB>(D, tc, 0, false, 0, threadIdx.x, 2, sW64, sWd);
+    solve_field<T, kGroupB>(D, tc, false, false, false, true, threadIdx.x, 2, sF);
+}
+
+// Time averages over the measured steps into D.avg: n_e, n_i from the summed
+// fixed-point densities, phi from the summed V, d_0 and F through the same
+// prefix-sum form (sum_t phi_p = S_V + p S_d0 - c sum_{j<p} S_F,j).
+template <typename T>
+__global__ void __launch_bounds__(kGroupB) k_averages(const DischargeDev *__restrict__ DD, int d)
+{
+    __shared__ double sWd[33];
+    constexpr int PMAX = (EDUPIC_MAX_GRID + kGroupB - 1) / kGroupB;
+    const DischargeDev &D = DD[d];
+    const int ng = D.ng, M = ng - 1, gtid = threadIdx.x;
+    const int per = (ng + kGroupB - 1) / kGroupB;
+    const int first = gtid * per, last = min(first + per, ng);
+    const long long m = D.ctrl->measured;
+    const double inv_m = m > 0 ? 1.0 / (double)m : 0.0;
+    double run = 0.0;
+#pragma unroll
+    for (int j = 0; j < PMAX; ++j) {
+        const int p = first + j;
+        if (p < last && p <= M - 1) run += D.sum_f[p];
+    }
+    double tot;
+    double g = group_excl_scan(run, sWd, tot, gtid, kGroupB, 2);
+    const double c = D.poisson_c, SV = D.fs->sum_V, Sd0 = D.fs->sum_d0;
+    double *ne = D.avg, *ni = D.avg + ng, *phi = D.avg + 2 * ng;
+#pragma unroll
+    for (int j = 0; j < PMAX; ++j) {
+        const int p = first + j;
+        if (p >= last) break;
+        const double edge = (p == 0 || p == M) ? 2.0 : 1.0;
+        ne[p] = edge * D.factor_w * (D.sum_qe[p] * (1.0 / 4294967296.0)) * inv_m;
+        ni[p] = edge * D.factor_w * (D.sum_qi[p] * (1.0 / 4294967296.0)) * inv_m;
+        phi[p] = p == M ? 0.0 : (SV + (double)p * Sd0 - c * g) * inv_m;
+        if (p <= M - 1) g += D.sum_f[p];
+    }
 }
 
 }  // namespace edupic

@@ -43,6 +43,14 @@ cudaError_t Launch<T>::fields(const DischargeDev *dd, int nd, int d, cudaStream_
 }
 
 template <typename T>
+cudaError_t Launch<T>::averages(const DischargeDev *dd, int nd, int d, cudaStream_t st)
+{
+    (void)nd;
+    k_averages<T><<<1, kGroupB, 0, st>>>(dd, d);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Launch<T>::push(const DischargeDev *dd, int nd, int species, int measure, int grid, int ng_max,
                             int eepf_max, cudaStream_t st)
 {

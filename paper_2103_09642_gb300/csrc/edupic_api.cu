@@ -132,10 +132,12 @@ struct edupic_sim {
     DischargeDev *d_desc = nullptr;
     void *cs_sig[2] = {nullptr, nullptr};
     void *cs_thr[2] = {nullptr, nullptr};
+    void *cs_max[2] = {nullptr, nullptr};
     bool cs_set[2] = {false, false};
     cudaStream_t stream = nullptr;
     int ng_max = 0, eepf_max = 0, nsub = 1, nt_common = -1;
     int phase = 0;  // common step index modulo N_SUB
+    int cs_shift_pending[2] = {0, 0};
     int grid[2] = {0, 0};
     bool graphs = true;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -163,6 +165,7 @@ size_t shared_bytes(int nd, size_t elem, int cs_entries)
     size_t o = align_up(sizeof(DischargeDev) * nd, kAlign);
     o += 2 * align_up((size_t)cs_entries * elem, kAlign);      // sigsum
     o += 2 * align_up((size_t)cs_entries * 2 * elem, kAlign);  // thr1, thr2
+    o += 2 * align_up((size_t)kCoarse * elem, kAlign);         // coarse maxima
     return o;
 }
 
@@ -278,6 +281,8 @@ void fill_desc(edupic_sim *S, int d)
     for (int sp = 0; sp < 2; ++sp) {
         D.cs_sig[sp] = S->cs_sig[sp];
         D.cs_thr[sp] = S->cs_thr[sp];
+        D.cs_max[sp] = S->cs_max[sp];
+        D.cs_shift[sp] = S->desc.size() > (size_t)d ? S->desc[d].cs_shift[sp] : 0;
     }
     D.vdrive = reinterpret_cast<const double *>(b + L.vdrive);
     if (S->desc.size() <= (size_t)d) S->desc.resize(d + 1);
@@ -353,8 +358,24 @@ int upload_tables(edupic_sim *S, int species, int n_proc, int n_entries, const d
         thr[2 * (size_t)k] = (T)(s0 / stot);
         thr[2 * (size_t)k + 1] = (T)(n_proc == 3 ? (s0 + s1) / stot : 1.0);
     }
-    cudaError_t e = cudaMemcpyAsync(S->cs_sig[species], sum.data(), sizeof(T) * sum.size(), cudaMemcpyHostToDevice,
+    // coarse maxima over 2^shift entries: an upper bound of n*sigma_tot used to
+    // skip the fine lookup when R01 lies above the bound's probability
+    int shift = 0;
+    while (((n_entries - 1) >> shift) >= kCoarse) ++shift;
+    std::vector<T> cmax(kCoarse, (T)0);
+    for (int k = 0; k < n_entries; ++k) {
+        const int j = k >> shift;
+        const double v = (double)sum[k] * (1.0 + 1e-6);
+        T t = (T)v;
+        if ((double)t < v) t = std::nextafter(t, (T)INFINITY);
+        if (t > cmax[j]) cmax[j] = t;
+    }
+    S->cs_shift_pending[species] = shift;
+    cudaError_t e = cudaMemcpyAsync(S->cs_max[species], cmax.data(), sizeof(T) * kCoarse, cudaMemcpyHostToDevice,
                                     S->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->cs_sig[species], sum.data(), sizeof(T) * sum.size(), cudaMemcpyHostToDevice,
+                            S->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(S->cs_thr[species], thr.data(), sizeof(T) * thr.size(), cudaMemcpyHostToDevice,
                             S->stream);
@@ -485,6 +506,10 @@ int edupic_create(int nd, const edupic_params *params, int precision, void *devi
         S->cs_thr[sp] = S->arena + o;
         o += align_up((size_t)params[0].cs_entries * 2 * S->elem, kAlign);
     }
+    for (int sp = 0; sp < 2; ++sp) {
+        S->cs_max[sp] = S->arena + o;
+        o += align_up((size_t)kCoarse * S->elem, kAlign);
+    }
     for (int d = 0; d < nd; ++d) {
         S->layouts.push_back(layout_of(params[d], S->elem));
         S->base.push_back(o);
@@ -552,6 +577,7 @@ int edupic_set_cross_sections(edupic_sim *S, int species, int n_proc, int n_entr
                                          : upload_tables<double>(S, species, n_proc, n_entries, sigma_m2);
     if (rc) return rc;
     for (int d = 0; d < S->nd; ++d) {
+        S->desc[d].cs_shift[species] = S->cs_shift_pending[species];
         if (species == 0) {
             S->desc[d].cs_n_e = n_entries;
             S->desc[d].cs_de_e = de_ev;

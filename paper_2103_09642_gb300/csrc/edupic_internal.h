@@ -12,6 +12,7 @@ constexpr int kFinalizeThreads = 512;  // one CTA per discharge for compaction +
 constexpr int kGroupA = 128;           // finalize threads doing compaction and append
 constexpr int kGroupB = kFinalizeThreads - kGroupA;  // finalize threads doing the field solve
 constexpr int kEvents = EDUPIC_STEP_EVENTS;
+constexpr int kCoarse = 2048;          // entries of the coarse sigma_max tables (shared memory)
 
 // Device error bits (ctrl->error).
 enum : int {
@@ -82,6 +83,8 @@ struct DischargeDev {
     void *prod_x, *prod_ve[3], *prod_vi[3];
     const void *cs_sig[2];     // T[cs_n]
     const void *cs_thr[2];     // T2[cs_n]
+    const void *cs_max[2];     // T[kCoarse]: max of cs_sig over 2^cs_shift consecutive entries, rounded up
+    int cs_shift[2];
     const double *vdrive;      // V(t) at the N_T steps of one cycle
 };
 

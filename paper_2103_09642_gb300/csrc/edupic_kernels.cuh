@@ -290,6 +290,12 @@ __device__ __forceinline__ int collide_ion(const DischargeDev &D, T thr1, T &vx,
 // ---------------------------------------------------------------- scans
 __device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
+// Programmatic dependent launch: wait until the preceding kernel of the
+// stream has completed and its writes are visible; allow the following
+// kernel to be scheduled (it waits the same way before touching data).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <typename V>
 __device__ __forceinline__ V warp_incl_scan(V v)
 {
@@ -460,7 +466,7 @@ __device__ __noinline__ void absorbed(const DischargeDev *Dp, int slot, T xn, T 
 // EEPF sample (Sec. 3.5): electrons in the centre 10% of the gap, energy of
 // the time-centred velocity.
 template <typename T>
-__device__ __noinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy, T vz, unsigned int *sH)
+__device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy, T vz, unsigned int *sH)
 {
     const DischargeDev &D = *Dp;
     const T v2c = vxc * vxc + vy * vy + vz * vz;
@@ -480,12 +486,13 @@ __device__ __noinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy, T 
 }
 
 // ---------------------------------------------------------------- particle kernel
-// Dynamic shared memory: [E pairs: ng_max T2][Q: ng_max u64][EEPF: eepf_max u32]
-// [tile prefix: nd+1 int].
+// Dynamic shared memory: [E pairs: ng_max T2][Q: ng_max u64][coarse sigma_max:
+// kCoarse T][EEPF: eepf_max u32][tile prefix: nd+1 int].
 template <typename T>
 __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eepf_max)
 {
-    return (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 8 + (size_t)eepf_max * 4 + (size_t)(nd + 1) * 4;
+    return (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 8 + (size_t)kCoarse * sizeof(T) +
+           (size_t)eepf_max * 4 + (size_t)(nd + 1) * 4;
 }
 
 template <typename T, int SP>
@@ -499,12 +506,22 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     extern __shared__ __align__(16) unsigned char smem[];
     T2 *sE2 = reinterpret_cast<T2 *>(smem);
     unsigned long long *sQ = reinterpret_cast<unsigned long long *>(sE2 + ng_max);
-    unsigned int *sH = reinterpret_cast<unsigned int *>(sQ + ng_max);
+    T *sC = reinterpret_cast<T *>(sQ + ng_max);
+    unsigned int *sH = reinterpret_cast<unsigned int *>(sC + kCoarse);
     int *sPre = reinterpret_cast<int *>(sH + eepf_max);
     __shared__ unsigned int sCnt[EDUPIC_N_COUNTERS];
     __shared__ int sW[33];
 
     const int tid = threadIdx.x;
+    // set-up data (the tables are shared by all discharges) before waiting for
+    // the preceding kernel
+    {
+        const T *cm = reinterpret_cast<const T *>(DD[0].cs_max[SP]);
+        for (int j = tid; j < kCoarse; j += blockDim.x) sC[j] = cm[j];
+    }
+    const int cs_shift = DD[0].cs_shift[SP];
+    pdl_wait();
+    pdl_launch_next();
     // tiles per discharge -> prefix over discharges (every block computes it)
     {
         int running = 0;
@@ -668,17 +685,17 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
                     kk[e] = cs_index_f(g_sqr * idx_scale + 0.5f, cs_n);
             }
         }
-        // phase 2: total cross sections of the thread's particles
-        T sg[VEC];
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) sg[e] = in[e] ? __ldg(sig + kk[e]) : (T)0;
-        // phase 3: collision-test uniforms of the slot pair (one Philox block)
+        // phase 2: collision-test uniforms of the slot pair (one Philox block)
         T ut[VEC];
         {
             const Words w = philox((uint32_t)base >> 1, s_lo, s_hi, (uint32_t)SP << 8, k0, k1);
             uniforms(w, ut[0], ut[1]);
         }
-        // phase 4: collision test (Algorithm 6), absorption records, deposition
+        // phase 3: collision test (Algorithm 6), absorption records, deposition.
+        // The probability from the coarse maximum of n*sigma_tot bounds P_coll
+        // from above, so R01 above it (plus a rounding margin) decides "no
+        // collision" without the fine table; otherwise the test of Algorithm 6
+        // is taken with the fine entry.
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
             const int slot = base + e;
@@ -688,21 +705,31 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
                 continue;
             }
             const T speed = sqrt(w2[e]);
-            T pc;
+            const T smax = sC[kk[e] >> cs_shift];
+            T pu;
             if constexpr (is_f64<T>())
-                pc = p_coll(sg[e] * ndt * speed * dt);
+                pu = p_coll(smax * ndt * speed * dt) + 1e-15;
             else
-                pc = p_coll(sg[e] * ndt * speed);
-            if (ut[e] < pc) {
-                Vel<T> v;
-                if (SP == 0)
-                    v = electron_collision<T>(D, slot, kk[e], xa[e], vxa[e], vya[e], vza[e], s_lo, s_hi, sQ, sCnt);
+                pu = p_coll(smax * ndt * speed) + 1e-6f;
+            if (ut[e] < pu) {
+                const T sg = __ldg(sig + kk[e]);
+                T pc;
+                if constexpr (is_f64<T>())
+                    pc = p_coll(sg * ndt * speed * dt);
                 else
-                    v = ion_collision<T>(D, slot, kk[e], vxa[e], vya[e], vza[e], vax[e], vay[e], vaz[e], s_lo, s_hi,
-                                         sCnt);
-                vxa[e] = v.x;
-                VY[slot] = v.y;
-                VZ[slot] = v.z;
+                    pc = p_coll(sg * ndt * speed);
+                if (ut[e] < pc) {
+                    Vel<T> v;
+                    if (SP == 0)
+                        v = electron_collision<T>(D, slot, kk[e], xa[e], vxa[e], vya[e], vza[e], s_lo, s_hi, sQ,
+                                                  sCnt);
+                    else
+                        v = ion_collision<T>(D, slot, kk[e], vxa[e], vya[e], vza[e], vax[e], vay[e], vaz[e], s_lo,
+                                             s_hi, sCnt);
+                    vxa[e] = v.x;
+                    VY[slot] = v.y;
+                    VZ[slot] = v.z;
+                }
             }
             // deposition of the new position for the next step (Sec. 2.1.1)
             T d0;
@@ -996,7 +1023,16 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDe
     __shared__ int sW[33];
     __shared__ FieldScratch<kGroupB> sF;
     __shared__ long long sN[2];
-    const DischargeDev &D = DD[blockIdx.x];
+    __shared__ DischargeDev D;
+    {
+        // the descriptor is staged in shared memory before the wait
+        const int *src = reinterpret_cast<const int *>(DD + blockIdx.x);
+        int *dst = reinterpret_cast<int *>(&D);
+        for (int i = threadIdx.x; i < (int)(sizeof(DischargeDev) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    pdl_wait();
+    pdl_launch_next();
     if (!D.active) return;
     Ctrl *C = D.ctrl;
     const long long next = C->step + 1;

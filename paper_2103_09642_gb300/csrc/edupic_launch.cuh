@@ -50,23 +50,40 @@ cudaError_t Launch<T>::averages(const DischargeDev *dd, int nd, int d, cudaStrea
     return cudaGetLastError();
 }
 
+// Launch with programmatic stream serialisation: the kernel may be scheduled
+// while the preceding kernel of the stream finishes; it waits on it
+// (griddepcontrol.wait) before touching data.
+template <typename K, typename... A>
+static cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t st, A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename T>
 cudaError_t Launch<T>::push(const DischargeDev *dd, int nd, int species, int measure, int grid, int ng_max,
                             int eepf_max, cudaStream_t st)
 {
-    const size_t smem = push_smem(nd, ng_max, species == 0 && measure ? eepf_max : 0);
+    const int eb = species == 0 && measure ? eepf_max : 0;
+    const size_t smem = push_smem(nd, ng_max, eb);
     if (species == 0)
-        k_push<T, 0><<<grid, kThreads, smem, st>>>(dd, nd, ng_max, species == 0 && measure ? eepf_max : 0, measure);
-    else
-        k_push<T, 1><<<grid, kThreads, smem, st>>>(dd, nd, ng_max, 0, measure);
-    return cudaGetLastError();
+        return launch_pdl(k_push<T, 0>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, eb, measure);
+    return launch_pdl(k_push<T, 1>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, 0, measure);
 }
 
 template <typename T>
 cudaError_t Launch<T>::finalize(const DischargeDev *dd, int nd, int ion_step, int measure, cudaStream_t st)
 {
-    k_finalize<T><<<nd, kFinalizeThreads, 0, st>>>(dd, nd, ion_step, measure);
-    return cudaGetLastError();
+    return launch_pdl(k_finalize<T>, dim3(nd), dim3(kFinalizeThreads), 0, st, dd, nd, ion_step, measure);
 }
 
 }  // namespace edupic

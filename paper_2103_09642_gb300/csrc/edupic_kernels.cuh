@@ -32,7 +32,7 @@ namespace edupic {
 #define EDUPIC_PI 3.14159265358979323846
 #define EDUPIC_OPAL_W 10.0
 #ifndef EDUPIC_PUSH_MIN_BLOCKS
-#define EDUPIC_PUSH_MIN_BLOCKS 2  // resident FP32 particle-kernel blocks per SM the register budget targets
+#define EDUPIC_PUSH_MIN_BLOCKS 3  // resident FP32 particle-kernel blocks per SM the register budget targets
 #endif
 
 template <typename T>
@@ -354,78 +354,122 @@ __device__ __forceinline__ __int128 group_sum128(__int128 v, __int128 *s_w, int 
     return t;
 }
 
-// ---------------------------------------------------------------- rare paths
-template <typename T>
-struct Vel {
-    T x, y, z;
-};
+// ---------------------------------------------------------------- colliders
+// Collisions are rare (P_coll ~ 1e-3), so the particle loop only queues the
+// slots whose test passed; a separate section of the kernel then executes
+// them (Algorithm 6 after the test).  It re-derives the table index and, for
+// Ar+, the thermal partner from the same counter-based draws, so the result
+// is the same as executing the collision in place.
+constexpr int kQueue = 4096;  // queued colliders per block before a drain
 
-// e- collision of one particle (Algorithm 6 after the test passed),
+// e- + Ar collision of the particle in `slot` (post-push state in memory),
 // including the append record and the deposition of an ionisation pair.
-// Scalar arguments and a struct return keep the hot loop free of stack use.
 template <typename T>
-__device__ __noinline__ Vel<T> electron_collision(const DischargeDev *Dp, int slot, int k, T xn, T vx, T vy, T vz,
-                                                  uint32_t s_lo, uint32_t s_hi, unsigned long long *sQ,
-                                                  unsigned int *sCnt)
+__device__ __forceinline__ void electron_collision(const DischargeDev &D, int slot, const RngKey &key, T idx_scale,
+                                                   int cs_n, T inv_dx, unsigned long long *sQ, unsigned int *sCnt)
 {
     using T2 = typename VecOf<T>::pair;
-    const DischargeDev &D = *Dp;
-    const RngKey key{s_lo, s_hi, (uint32_t)D.seed, (uint32_t)(D.seed >> 32)};
+    T *X = reinterpret_cast<T *>(D.x[0]);
+    T *VX = reinterpret_cast<T *>(D.vx[0]);
+    T *VY = reinterpret_cast<T *>(D.vy[0]);
+    T *VZ = reinterpret_cast<T *>(D.vz[0]);
+    const T xn = X[slot];
+    T vx = VX[slot], vy = VY[slot], vz = VZ[slot];
+    const T v2 = vx * vx + vy * vy + vz * vz;
+    int k;
+    if constexpr (is_f64<T>())
+        k = cs_index(D.half_me * v2 / EDUPIC_QE, idx_scale, cs_n);
+    else
+        k = cs_index_f(v2 * idx_scale + 0.5f, cs_n);
     const T2 thr = reinterpret_cast<const T2 *>(D.cs_thr[0])[k];
     T u_proc, u_chi, u_eta, u_opal, vej[3];
     draw<T>(key, (uint32_t)slot, 0, 1, u_proc, u_chi);
     draw<T>(key, (uint32_t)slot, 0, 2, u_eta, u_opal);
     int sub;
     const int proc = collide_electron<T>(D, thr.x, thr.y, vx, vy, vz, u_proc, u_chi, u_eta, u_opal, vej, sub);
+    VX[slot] = vx;
+    VY[slot] = vy;
+    VZ[slot] = vz;
     atomicAdd(sCnt + EDUPIC_C_COLL_E_ELA + proc, 1u);
     if (sub) atomicAdd(sCnt + EDUPIC_C_SUBTHRESHOLD, 1u);
-    if (proc == 2) {
-        T n0, n1, n2, n3, z0, z1, z2, z3;
-        draw<T>(key, (uint32_t)slot, 0, 3, n0, n1);
-        draw<T>(key, (uint32_t)slot, 0, 4, n2, n3);
-        box_muller(n0, n1, z0, z1);
-        box_muller(n2, n3, z2, z3);
-        const T sth = is_f64<T>() ? (T)D.sig_th : (T)D.sig_thf;
-        const int pi = atomicAdd(&D.ctrl->products, 1);
-        if (pi < kEvents) {
-            D.prod_parent[pi] = slot;
-            reinterpret_cast<T *>(D.prod_x)[pi] = xn;
-            reinterpret_cast<T *>(D.prod_ve[0])[pi] = vej[0];
-            reinterpret_cast<T *>(D.prod_ve[1])[pi] = vej[1];
-            reinterpret_cast<T *>(D.prod_ve[2])[pi] = vej[2];
-            reinterpret_cast<T *>(D.prod_vi[0])[pi] = sth * z0;
-            reinterpret_cast<T *>(D.prod_vi[1])[pi] = sth * z1;
-            reinterpret_cast<T *>(D.prod_vi[2])[pi] = sth * z2;
-            // the new pair joins the next densities at the parent's x
-            const T inv_dx = is_f64<T>() ? (T)D.inv_dx : (T)D.inv_dxf;
-            T d0;
-            const int pp = cell<T>(xn, inv_dx, D.ng, d0);
-            const unsigned long long q2 = split_q2(d0 - (T)pp);
-            atomicAdd(sQ + pp, 4294967296ull - q2);
-            atomicAdd(sQ + pp + 1, q2);
-            atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp), 4294967296ull - q2);
-            atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp + 1), q2);
-        } else {
-            atomicOr(&D.ctrl->error, kErrProducts);
-        }
+    if (proc != 2) return;
+    T n0, n1, n2, n3, z0, z1, z2, z3;
+    draw<T>(key, (uint32_t)slot, 0, 3, n0, n1);
+    draw<T>(key, (uint32_t)slot, 0, 4, n2, n3);
+    box_muller(n0, n1, z0, z1);
+    box_muller(n2, n3, z2, z3);
+    const T sth = is_f64<T>() ? (T)D.sig_th : (T)D.sig_thf;
+    const int pi = atomicAdd(&D.ctrl->products, 1);
+    if (pi >= kEvents) {
+        atomicOr(&D.ctrl->error, kErrProducts);
+        return;
     }
-    return Vel<T>{vx, vy, vz};
+    D.prod_parent[pi] = slot;
+    reinterpret_cast<T *>(D.prod_x)[pi] = xn;
+    reinterpret_cast<T *>(D.prod_ve[0])[pi] = vej[0];
+    reinterpret_cast<T *>(D.prod_ve[1])[pi] = vej[1];
+    reinterpret_cast<T *>(D.prod_ve[2])[pi] = vej[2];
+    reinterpret_cast<T *>(D.prod_vi[0])[pi] = sth * z0;
+    reinterpret_cast<T *>(D.prod_vi[1])[pi] = sth * z1;
+    reinterpret_cast<T *>(D.prod_vi[2])[pi] = sth * z2;
+    // the new pair joins the next densities at the parent's x
+    T d0;
+    const int pp = cell<T>(xn, inv_dx, D.ng, d0);
+    const unsigned long long q2 = split_q2(d0 - (T)pp);
+    atomicAdd(sQ + pp, 4294967296ull - q2);
+    atomicAdd(sQ + pp + 1, q2);
+    atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp), 4294967296ull - q2);
+    atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp + 1), q2);
+}
+
+// Thermal Ar partner of an ion (drawn before the collision probability).
+template <typename T>
+__device__ __forceinline__ void ion_partner(const DischargeDev &D, const RngKey &key, uint32_t slot, T &vax, T &vay,
+                                            T &vaz)
+{
+    T a0, a1, a2, a3, za, zb, zc, zd;
+    draw<T>(key, slot, 1, 1, a0, a1);
+    draw<T>(key, slot, 1, 2, a2, a3);
+    box_muller(a0, a1, za, zb);
+    box_muller(a2, a3, zc, zd);
+    const T sth = is_f64<T>() ? (T)D.sig_th : (T)D.sig_thf;
+    vax = sth * za;
+    vay = sth * zb;
+    vaz = sth * zc;
 }
 
 template <typename T>
-__device__ __noinline__ Vel<T> ion_collision(const DischargeDev *Dp, int slot, int k, T vx, T vy, T vz, T vax, T vay,
-                                             T vaz, uint32_t s_lo, uint32_t s_hi, unsigned int *sCnt)
+__device__ __forceinline__ int ion_index(const DischargeDev &D, T g_sqr, T idx_scale, int cs_n)
+{
+    if constexpr (is_f64<T>())
+        return cs_index(D.half_mu_arar * g_sqr / EDUPIC_QE, idx_scale, cs_n);
+    else
+        return cs_index_f(g_sqr * idx_scale + 0.5f, cs_n);
+}
+
+// Ar+ + Ar collision of the ion in `slot` with its thermal partner.
+template <typename T>
+__device__ __forceinline__ void ion_collision(const DischargeDev &D, int slot, const RngKey &key, T idx_scale, int cs_n,
+                                              unsigned int *sCnt)
 {
     using T2 = typename VecOf<T>::pair;
-    const DischargeDev &D = *Dp;
-    const RngKey key{s_lo, s_hi, (uint32_t)D.seed, (uint32_t)(D.seed >> 32)};
+    T *VX = reinterpret_cast<T *>(D.vx[1]);
+    T *VY = reinterpret_cast<T *>(D.vy[1]);
+    T *VZ = reinterpret_cast<T *>(D.vz[1]);
+    T vx = VX[slot], vy = VY[slot], vz = VZ[slot];
+    T vax, vay, vaz;
+    ion_partner<T>(D, key, (uint32_t)slot, vax, vay, vaz);
+    const T gx = vx - vax, gy = vy - vay, gz = vz - vaz;
+    const int k = ion_index<T>(D, gx * gx + gy * gy + gz * gz, idx_scale, cs_n);
     const T thr1 = reinterpret_cast<const T2 *>(D.cs_thr[1])[k].x;
     T u_proc, u_chi, u_eta, u_dummy;
     draw<T>(key, (uint32_t)slot, 1, 3, u_proc, u_chi);
     draw<T>(key, (uint32_t)slot, 1, 4, u_eta, u_dummy);
     const int proc = collide_ion<T>(D, thr1, vx, vy, vz, vax, vay, vaz, u_proc, u_chi, u_eta);
+    VX[slot] = vx;
+    VY[slot] = vy;
+    VZ[slot] = vz;
     atomicAdd(sCnt + EDUPIC_C_COLL_I_ISO + proc, 1u);
-    return Vel<T>{vx, vy, vz};
 }
 
 // Absorbed particle: record the hole, count it, bin the Ar+ impact energy.
@@ -511,8 +555,11 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     int *sPre = reinterpret_cast<int *>(sH + eepf_max);
     __shared__ unsigned int sCnt[EDUPIC_N_COUNTERS];
     __shared__ int sW[33];
+    __shared__ int sQueue[kQueue];
+    __shared__ int sQn;
 
     const int tid = threadIdx.x;
+    if (tid == 0) sQn = 0;
     // set-up data (the tables are shared by all discharges) before waiting for
     // the preceding kernel
     {
@@ -551,7 +598,23 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     const T *sig = nullptr;
     bool eepf_on = false;
 
+    // execute the queued collisions of the current discharge (all threads)
+    auto drain = [&]() {
+        __syncthreads();
+        const int qn = sQn;
+        const RngKey key{s_lo, s_hi, k0, k1};
+        for (int i = tid; i < qn; i += blockDim.x) {
+            if (SP == 0)
+                electron_collision<T>(*D, sQueue[i], key, idx_scale, cs_n, inv_dx, sQ, sCnt);
+            else
+                ion_collision<T>(*D, sQueue[i], key, idx_scale, cs_n, sCnt);
+        }
+        __syncthreads();
+        if (tid == 0) sQn = 0;
+    };
+
     auto flush = [&]() {
+        drain();
         __syncthreads();
         long long *acc = SP == 0 ? D->acc_e : D->acc_i;
         for (int p = tid; p < ng; p += blockDim.x) {
@@ -616,6 +679,10 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
                 for (int b = tid; b < D->eepf_bins; b += blockDim.x) sH[b] = 0u;
             __syncthreads();
         }
+        if (((t - t0) & 3) == 3) {
+            __syncthreads();
+            if (sQn > kQueue - 4 * TILE) drain();
+        }
         const int tbase = (t - sPre[cur]) * TILE;
         if (tid == 0) atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_PUSH_E : EDUPIC_C_PUSH_I), (unsigned)min(TILE, n - tbase));
         const int base = tbase + tid * VEC;
@@ -635,14 +702,12 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         int kk[VEC];
         bool in[VEC];
         T w2[VEC];  // v^2 (e-) or g^2 (Ar+)
-        T vax[VEC], vay[VEC], vaz[VEC];  // thermal partner (Ar+)
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
             const int slot = base + e;
             in[e] = false;
             kk[e] = 0;
             w2[e] = (T)0;
-            vax[e] = vay[e] = vaz[e] = (T)0;
             if (slot >= n) continue;
             const T x = xa[e], vx = vxa[e];
             T c0;
@@ -667,22 +732,12 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             } else {
                 // thermal partner drawn before the collision probability
                 const RngKey key{s_lo, s_hi, k0, k1};
-                T a0, a1, a2, a3, za, zb, zc, zd;
-                draw<T>(key, (uint32_t)slot, 1, 1, a0, a1);
-                draw<T>(key, (uint32_t)slot, 1, 2, a2, a3);
-                box_muller(a0, a1, za, zb);
-                box_muller(a2, a3, zc, zd);
-                const T sth = is_f64<T>() ? (T)D->sig_th : (T)D->sig_thf;
-                vax[e] = sth * za;
-                vay[e] = sth * zb;
-                vaz[e] = sth * zc;
-                const T gx = vxn - vax[e], gy = vya[e] - vay[e], gz = vza[e] - vaz[e];
+                T vax, vay, vaz;
+                ion_partner<T>(*D, key, (uint32_t)slot, vax, vay, vaz);
+                const T gx = vxn - vax, gy = vya[e] - vay, gz = vza[e] - vaz;
                 const T g_sqr = gx * gx + gy * gy + gz * gz;
                 w2[e] = g_sqr;
-                if constexpr (is_f64<T>())
-                    kk[e] = cs_index(D->half_mu_arar * g_sqr / EDUPIC_QE, idx_scale, cs_n);
-                else
-                    kk[e] = cs_index_f(g_sqr * idx_scale + 0.5f, cs_n);
+                kk[e] = ion_index<T>(*D, g_sqr, idx_scale, cs_n);
             }
         }
         // phase 2: collision-test uniforms of the slot pair (one Philox block)
@@ -718,18 +773,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
                     pc = p_coll(sg * ndt * speed * dt);
                 else
                     pc = p_coll(sg * ndt * speed);
-                if (ut[e] < pc) {
-                    Vel<T> v;
-                    if (SP == 0)
-                        v = electron_collision<T>(D, slot, kk[e], xa[e], vxa[e], vya[e], vza[e], s_lo, s_hi, sQ,
-                                                  sCnt);
-                    else
-                        v = ion_collision<T>(D, slot, kk[e], vxa[e], vya[e], vza[e], vax[e], vay[e], vaz[e], s_lo,
-                                             s_hi, sCnt);
-                    vxa[e] = v.x;
-                    VY[slot] = v.y;
-                    VZ[slot] = v.z;
-                }
+                if (ut[e] < pc) sQueue[atomicAdd(&sQn, 1)] = slot;  // executed after the stores below
             }
             // deposition of the new position for the next step (Sec. 2.1.1)
             T d0;

@@ -156,10 +156,9 @@ __device__ __forceinline__ int cs_index(double energy, double de, int n)
     const int k = (int)r;
     return k < n - 1 ? k : n - 1;
 }
-__device__ __forceinline__ int cs_index_f(float r, int n)  // r = energy / de + 0.5 already formed
+__device__ __forceinline__ int cs_index_f(float r, int n)  // r = energy / de + 0.5 >= 0.5 already formed
 {
-    if (!(r < (float)n)) return n - 1;
-    const int k = (int)r;
+    const int k = (int)r;  // saturating conversion: huge r gives INT_MAX
     return k < n - 1 ? k : n - 1;
 }
 
@@ -169,9 +168,9 @@ __device__ __forceinline__ int cs_index_f(float r, int n)  // r = energy / de + 
 __device__ __forceinline__ double p_coll(double x) { return 1.0 - exp(-x); }
 __device__ __forceinline__ float p_coll(float x)
 {
-    if (x < 0.125f)
-        return x * (1.0f - x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f)))));
-    return 1.0f - __expf(-x);
+    const float series = x * (1.0f - x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f)))));
+    const float direct = 1.0f - __expf(-x);
+    return x < 0.125f ? series : direct;
 }
 
 // Euler-angle rotation of Sec. 2.1.6: unit vector of g' for g deflected by
@@ -596,6 +595,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     uint32_t s_lo = 0, s_hi = 0, k0 = 0, k1 = 0;
     T L = 0, inv_dx = 0, dt = 0, factor = 0, ndt = 0, idx_scale = 0, lo = 0, hi = 0;
     const T *sig = nullptr;
+    T *X = nullptr, *VX = nullptr, *VY = nullptr, *VZ = nullptr;
     bool eepf_on = false;
 
     // execute the queued collisions of the current discharge (all threads)
@@ -668,6 +668,10 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
                 hi = D->eepf_hif;
             }
             sig = reinterpret_cast<const T *>(D->cs_sig[SP]);
+            X = reinterpret_cast<T *>(D->x[SP]);
+            VX = reinterpret_cast<T *>(D->vx[SP]);
+            VY = reinterpret_cast<T *>(D->vy[SP]);
+            VZ = reinterpret_cast<T *>(D->vz[SP]);
             cs_n = SP == 0 ? D->cs_n_e : D->cs_n_i;
             eepf_on = SP == 0 && measure;
             const T *ef = reinterpret_cast<const T *>(D->ef_t);
@@ -687,11 +691,9 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         if (tid == 0) atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_PUSH_E : EDUPIC_C_PUSH_I), (unsigned)min(TILE, n - tbase));
         const int base = tbase + tid * VEC;
         if (base >= n) continue;
-
-        T *X = reinterpret_cast<T *>(D->x[SP]);
-        T *VX = reinterpret_cast<T *>(D->vx[SP]);
-        T *VY = reinterpret_cast<T *>(D->vy[SP]);
-        T *VZ = reinterpret_cast<T *>(D->vz[SP]);
+        // every slot of a full tile is live: no per-slot count checks there
+        auto tile = [&](auto full_tag) {
+        constexpr bool FULL = decltype(full_tag)::value;
         T xa[VEC], vxa[VEC], vya[VEC], vza[VEC];
         unpack(*reinterpret_cast<const V *>(X + base), xa);
         unpack(*reinterpret_cast<const V *>(VX + base), vxa);
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             in[e] = false;
             kk[e] = 0;
             w2[e] = (T)0;
-            if (slot >= n) continue;
+            if (!FULL && slot >= n) continue;
             const T x = xa[e], vx = vxa[e];
             T c0;
             const int p = cell<T>(x, inv_dx, ng, c0);
@@ -754,7 +756,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
             const int slot = base + e;
-            if (slot >= n) break;
+            if (!FULL && slot >= n) break;
             if (!in[e]) {
                 absorbed<T, SP>(D, slot, xa[e], vxa[e], vya[e], vza[e], measure, sCnt);
                 continue;
@@ -784,6 +786,11 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         }
         *reinterpret_cast<V *>(X + base) = pack(xa, V{});
         *reinterpret_cast<V *>(VX + base) = pack(vxa, V{});
+            };
+        if (tbase + TILE <= n)
+            tile(std::true_type{});
+        else
+            tile(std::false_type{});
     }
     if (cur >= 0) flush();
 }

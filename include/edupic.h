@@ -42,6 +42,7 @@ extern "C" {
 #define EDUPIC_ENAN (-6)      /* non-finite particle position found */
 #define EDUPIC_EIO (-7)       /* checkpoint file could not be read/written */
 #define EDUPIC_ETIMEOUT (-8)  /* bounded wait expired */
+#define EDUPIC_ETOOBIG (-9)   /* size beyond the fixed scratch of edupic_fields_noalloc */
 
 /* ---------------------------------------------------------------- enums */
 #define EDUPIC_FP64 0 /* particles, push and collisions in FP64 */
@@ -211,6 +212,40 @@ int edupic_reset_diagnostics(edupic_sim *sim, int d);
  * versioned header; a restore recomputes the densities and field. */
 int edupic_save_state(edupic_sim *sim, int d, const char *path);
 int edupic_load_state(edupic_sim *sim, int d, const char *path);
+
+/* ---------------------------------------------------------------- no-allocation entry point */
+
+/* Densities, potential and field of given particle positions, computed
+ * without allocating any device memory.  (The paper has no counterpart: it
+ * is an interface for callers that cannot call cudaMalloc mid-run, e.g.
+ * code whose device memory is pre-budgeted by another framework's pool, code
+ * inside a plugin or a real-time loop, or code issuing work while a stream is
+ * being captured.)
+ *
+ * Computes what edupic_load_particles followed by edupic_get_fields gives in
+ * EDUPIC_FP64 mode: fixed-point deposition of x_e and x_i (Algorithm 2) and
+ * the Poisson solve with phi_0 = V(t) at within-cycle step step % N_T
+ * (Algorithm 3).  Uses p->gap_m, area_m2, weight, n_grid, steps_per_cycle,
+ * cycle_freq_hz and the harmonics.
+ *
+ * x_e, x_i: device FP64 positions in [0, L] (n_e, n_i entries, may be NULL
+ * when the count is 0).  n_e_out, n_i_out (m^-3), phi_out (V), efield_out
+ * (V/m): device FP64 arrays of n_grid entries, written by the call.
+ * cuda_stream: cudaStream_t (NULL = legacy default stream); the call
+ * synchronises it before returning.
+ *
+ * Working memory is one fixed array of 49,408 bytes in the library's device
+ * image, held by every GPU that loads the library until the process exits;
+ * n_grid above EDUPIC_MAX_GRID (2048) is rejected with EDUPIC_ETOOBIG.  The
+ * first call on a device looks up that array's device address (a CUDA
+ * runtime query), so make the first call before any stream capture.  The
+ * array is shared by all calls and keeps the last call's contents (each call
+ * zeroes what it accumulates into first); calls that overlap on the GPU race
+ * on it, so issue them one at a time per device.  No cudaMalloc, cudaFree or
+ * allocating library routine is called. */
+int edupic_fields_noalloc(const edupic_params *p, int64_t step, const double *x_e, int64_t n_e, const double *x_i,
+                          int64_t n_i, double *n_e_out, double *n_i_out, double *phi_out, double *efield_out,
+                          void *cuda_stream);
 
 /* Text for a status code. */
 const char *edupic_strerror(int status);

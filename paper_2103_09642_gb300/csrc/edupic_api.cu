@@ -974,6 +974,7 @@ const char *edupic_strerror(int status)
     case EDUPIC_ENAN: return "non-finite particle position";
     case EDUPIC_EIO: return "checkpoint file error";
     case EDUPIC_ETIMEOUT: return "bounded wait expired";
+    case EDUPIC_ETOOBIG: return "n_grid exceeds the fixed scratch of the no-allocation entry point (max 2048)";
     default: return "unknown status";
     }
 }

@@ -69,7 +69,7 @@ Layout layout_of(const edupic_params &p, size_t elem)
     L.sum_qi = take(ng * 8);
     L.sum_f = take(ng * 8);
     L.avg = take(3 * ng * 8);
-    L.eepf = take((size_t)p.eepf_bins * 8);
+    L.eepf = take((size_t)kEepfStripes * p.eepf_bins * 8);
     L.ifed_pow = take((size_t)p.ifed_bins * 8);
     L.ifed_gnd = take((size_t)p.ifed_bins * 8);
     L.ctrl = take(sizeof(Ctrl));
@@ -805,8 +805,15 @@ int edupic_get_diagnostics(edupic_sim *S, int d, double *ne_avg, double *ni_avg,
     for (int k = 0; k < 3; ++k)
         if (outs[k] && cudaMemcpy(outs[k], D.avg + k * ng, ng * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
             return EDUPIC_ECUDA;
-    if (eepf_counts && cudaMemcpy(eepf_counts, D.eepf, (size_t)p.eepf_bins * 8, cudaMemcpyDeviceToHost))
-        return EDUPIC_ECUDA;
+    if (eepf_counts) {
+        std::vector<int64_t> st((size_t)kEepfStripes * p.eepf_bins);
+        if (cudaMemcpy(st.data(), D.eepf, st.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return EDUPIC_ECUDA;
+        for (int b = 0; b < p.eepf_bins; ++b) {
+            int64_t t = 0;
+            for (int k = 0; k < kEepfStripes; ++k) t += st[(size_t)k * p.eepf_bins + b];
+            eepf_counts[b] = t;
+        }
+    }
     if (ifed_pow_counts && cudaMemcpy(ifed_pow_counts, D.ifed_pow, (size_t)p.ifed_bins * 8, cudaMemcpyDeviceToHost))
         return EDUPIC_ECUDA;
     if (ifed_gnd_counts && cudaMemcpy(ifed_gnd_counts, D.ifed_gnd, (size_t)p.ifed_bins * 8, cudaMemcpyDeviceToHost))
@@ -872,7 +879,7 @@ int edupic_reset_diagnostics(edupic_sim *S, int d)
     if (e == cudaSuccess) e = cudaMemsetAsync(D.sum_qi, 0, ng * 8, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.sum_f, 0, ng * 8, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&D.fs->sum_V, 0, 2 * sizeof(double), S->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(D.eepf, 0, (size_t)p.eepf_bins * 8, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.eepf, 0, (size_t)kEepfStripes * p.eepf_bins * 8, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.ifed_pow, 0, (size_t)p.ifed_bins * 8, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.ifed_gnd, 0, (size_t)p.ifed_bins * 8, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&D.ctrl->measured, 0, sizeof(long long), S->stream);

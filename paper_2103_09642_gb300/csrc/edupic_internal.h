@@ -13,6 +13,7 @@ constexpr int kGroupA = 128;           // finalize threads doing compaction and 
 constexpr int kGroupB = kFinalizeThreads - kGroupA;  // finalize threads doing the field solve
 constexpr int kEvents = EDUPIC_STEP_EVENTS;
 constexpr int kCoarse = 2048;          // entries of the coarse sigma_max tables (shared memory)
+constexpr int kEepfStripes = 16;       // copies of the EEPF histogram the particle kernel spreads its atomics over
 
 // Device error bits (ctrl->error).
 enum : int {
@@ -76,7 +77,8 @@ struct DischargeDev {
     FieldState *fs;            // V and d_0 of the current field, and their time sums
     double *sum_qe, *sum_qi, *sum_f;  // time sums of Q_e, Q_i, F over the measured steps
     double *avg;               // [3][ng] read-back buffer: time-averaged n_e, n_i, phi
-    unsigned long long *eepf, *ifed_pow, *ifed_gnd;
+    unsigned long long *eepf;  // [kEepfStripes][eepf_bins], summed on read
+    unsigned long long *ifed_pow, *ifed_gnd;
     Ctrl *ctrl;
     int *holes[2];
     int *prod_parent;

@@ -148,6 +148,29 @@ __device__ __forceinline__ unsigned long long split_q2(float c2)
     return c2 < 1.0f ? (unsigned long long)__float2uint_rn(c2 * 4294967296.0f) : 4294967296ull;
 }
 
+// Per-block deposition accumulator in shared memory.  A particle in cell p
+// adds q1 = 2^32 - q2 to point p and q2 to point p+1; the block keeps, per
+// cell, the count and the sum of q2 in two 16-bit halves (32-bit shared
+// atomics), and forms Q_p = 2^32 cnt_p - S_p + S_{p-1} when it flushes.  The
+// halves cannot overflow while a cell holds fewer than 65536 particles of
+// one flush (the kernel flushes every kDepFlush particles).
+struct DepAcc {
+    unsigned int *cnt, *lo, *hi;
+};
+constexpr int kDepFlush = 30000;
+
+__device__ __forceinline__ void dep_add(const DepAcc &a, int p, unsigned long long q2)
+{
+    atomicAdd(a.cnt + p, 1u);
+    atomicAdd(a.lo + p, (unsigned int)(q2 & 0xFFFFull));
+    atomicAdd(a.hi + p, (unsigned int)(q2 >> 16));
+}
+
+__device__ __forceinline__ unsigned long long dep_sum(const DepAcc &a, int p)  // S_p
+{
+    return (unsigned long long)a.lo[p] + ((unsigned long long)a.hi[p] << 16);
+}
+
 // Nearest cross-section bin (Algorithm 6).
 __device__ __forceinline__ int cs_index(double energy, double de, int n)
 {
@@ -365,7 +388,7 @@ constexpr int kQueue = 4096;  // queued colliders per block before a drain
 // including the append record and the deposition of an ionisation pair.
 template <typename T>
 __device__ __forceinline__ void electron_collision(const DischargeDev &D, int slot, const RngKey &key, T idx_scale,
-                                                   int cs_n, T inv_dx, unsigned long long *sQ, unsigned int *sCnt)
+                                                   int cs_n, T inv_dx, const DepAcc &acc, unsigned int *sCnt)
 {
     using T2 = typename VecOf<T>::pair;
     T *X = reinterpret_cast<T *>(D.x[0]);
@@ -415,8 +438,7 @@ __device__ __forceinline__ void electron_collision(const DischargeDev &D, int sl
     T d0;
     const int pp = cell<T>(xn, inv_dx, D.ng, d0);
     const unsigned long long q2 = split_q2(d0 - (T)pp);
-    atomicAdd(sQ + pp, 4294967296ull - q2);
-    atomicAdd(sQ + pp + 1, q2);
+    dep_add(acc, pp, q2);
     atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp), 4294967296ull - q2);
     atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp + 1), q2);
 }
@@ -509,7 +531,7 @@ __device__ __noinline__ void absorbed(const DischargeDev *Dp, int slot, T xn, T 
 // EEPF sample (Sec. 3.5): electrons in the centre 10% of the gap, energy of
 // the time-centred velocity.
 template <typename T>
-__device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy, T vz, unsigned int *sH)
+__device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy, T vz)
 {
     const DischargeDev &D = *Dp;
     const T v2c = vxc * vxc + vy * vy + vz * vz;
@@ -525,17 +547,18 @@ __device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy,
         ok = r < (float)D.eepf_bins;
         b = ok ? (int)r : 0;
     }
-    if (ok) atomicAdd(sH + b, 1u);
+    // striped over kEepfStripes copies to spread the atomics; summed on read
+    if (ok) atomicAdd(D.eepf + (blockIdx.x & (kEepfStripes - 1)) * D.eepf_bins + b, 1ull);
 }
 
 // ---------------------------------------------------------------- particle kernel
-// Dynamic shared memory: [E pairs: ng_max T2][Q: ng_max u64][coarse sigma_max:
-// kCoarse T][EEPF: eepf_max u32][tile prefix: nd+1 int].
+// Dynamic shared memory: [coarse sigma_max: kCoarse T][E pairs: ng_max T2]
+// [deposition: 3 x ng_max u32][tile prefix: nd+1 int].
 template <typename T>
 __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eepf_max)
 {
-    return (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 8 + (size_t)kCoarse * sizeof(T) +
-           (size_t)eepf_max * 4 + (size_t)(nd + 1) * 4;
+    return (size_t)kCoarse * sizeof(T) + (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 12 +
+           (size_t)(nd + 1) * 4 + 0 * (size_t)eepf_max;
 }
 
 template <typename T, int SP>
@@ -547,11 +570,14 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     constexpr int VEC = VecOf<T>::n;  // two slots per thread: one Philox test block
     constexpr int TILE = kThreads * VEC;
     extern __shared__ __align__(16) unsigned char smem[];
-    T2 *sE2 = reinterpret_cast<T2 *>(smem);
-    unsigned long long *sQ = reinterpret_cast<unsigned long long *>(sE2 + ng_max);
-    T *sC = reinterpret_cast<T *>(sQ + ng_max);
-    unsigned int *sH = reinterpret_cast<unsigned int *>(sC + kCoarse);
-    int *sPre = reinterpret_cast<int *>(sH + eepf_max);
+    T *sC = reinterpret_cast<T *>(smem);
+    T2 *sE2 = reinterpret_cast<T2 *>(sC + kCoarse);
+    DepAcc acc;
+    acc.cnt = reinterpret_cast<unsigned int *>(sE2 + ng_max);
+    acc.lo = acc.cnt + ng_max;
+    acc.hi = acc.lo + ng_max;
+    int *sPre = reinterpret_cast<int *>(acc.hi + ng_max);
+    (void)eepf_max;
     __shared__ unsigned int sCnt[EDUPIC_N_COUNTERS];
     __shared__ int sW[33];
     __shared__ int sQueue[kQueue];
@@ -562,8 +588,9 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     // set-up data (the tables are shared by all discharges) before waiting for
     // the preceding kernel
     {
-        const T *cm = reinterpret_cast<const T *>(DD[0].cs_max[SP]);
-        for (int j = tid; j < kCoarse; j += blockDim.x) sC[j] = cm[j];
+        const float4 *cm = reinterpret_cast<const float4 *>(DD[0].cs_max[SP]);
+        float4 *dst = reinterpret_cast<float4 *>(sC);
+        for (int j = tid; j < (int)(kCoarse * sizeof(T) / 16); j += blockDim.x) dst[j] = cm[j];
     }
     const int cs_shift = DD[0].cs_shift[SP];
     pdl_wait();
@@ -605,7 +632,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         const RngKey key{s_lo, s_hi, k0, k1};
         for (int i = tid; i < qn; i += blockDim.x) {
             if (SP == 0)
-                electron_collision<T>(*D, sQueue[i], key, idx_scale, cs_n, inv_dx, sQ, sCnt);
+                electron_collision<T>(*D, sQueue[i], key, idx_scale, cs_n, inv_dx, acc, sCnt);
             else
                 ion_collision<T>(*D, sQueue[i], key, idx_scale, cs_n, sCnt);
         }
@@ -613,20 +640,23 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         if (tid == 0) sQn = 0;
     };
 
+    // add the block's deposition into the discharge's accumulator and clear it
+    auto flush_dep = [&]() {
+        __syncthreads();
+        long long *accq = SP == 0 ? D->acc_e : D->acc_i;
+        for (int p = tid; p < ng; p += blockDim.x) {
+            const unsigned long long q = ((unsigned long long)acc.cnt[p] << 32) - dep_sum(acc, p) +
+                                         (p > 0 ? dep_sum(acc, p - 1) : 0ull);
+            if (q) atomicAdd(reinterpret_cast<unsigned long long *>(accq + p), q);
+        }
+        __syncthreads();
+        for (int p = tid; p < ng; p += blockDim.x) acc.cnt[p] = acc.lo[p] = acc.hi[p] = 0u;
+        __syncthreads();
+    };
+
     auto flush = [&]() {
         drain();
-        __syncthreads();
-        long long *acc = SP == 0 ? D->acc_e : D->acc_i;
-        for (int p = tid; p < ng; p += blockDim.x) {
-            const unsigned long long q = sQ[p];
-            if (q) atomicAdd(reinterpret_cast<unsigned long long *>(acc + p), q);
-        }
-        if (eepf_on) {
-            for (int b = tid; b < D->eepf_bins; b += blockDim.x) {
-                const unsigned int c = sH[b];
-                if (c) atomicAdd(D->eepf + b, (unsigned long long)c);
-            }
-        }
+        flush_dep();
         if (tid < EDUPIC_N_COUNTERS) {
             const unsigned int c = sCnt[tid];
             if (c) atomicAdd(D->ctrl->counters + tid, (unsigned long long)c);
@@ -635,6 +665,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         __syncthreads();
     };
 
+    int since_flush = 0;
     for (int t = t0; t < t1; ++t) {
         if (cur < 0 || t >= sPre[cur + 1]) {
             if (cur >= 0) flush();
@@ -677,16 +708,20 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             const T *ef = reinterpret_cast<const T *>(D->ef_t);
             for (int p = tid; p < ng; p += blockDim.x) {
                 sE2[p] = T2{ef[p], p + 1 < ng ? ef[p + 1] : (T)0};
-                sQ[p] = 0ull;
+                acc.cnt[p] = acc.lo[p] = acc.hi[p] = 0u;
             }
-            if (eepf_on)
-                for (int b = tid; b < D->eepf_bins; b += blockDim.x) sH[b] = 0u;
+            since_flush = 0;
             __syncthreads();
         }
         if (((t - t0) & 3) == 3) {
             __syncthreads();
             if (sQn > kQueue - 4 * TILE) drain();
+            if (since_flush >= kDepFlush) {
+                flush_dep();
+                since_flush = 0;
+            }
         }
+        since_flush += TILE;
         const int tbase = (t - sPre[cur]) * TILE;
         if (tid == 0) atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_PUSH_E : EDUPIC_C_PUSH_I), (unsigned)min(TILE, n - tbase));
         const int base = tbase + tid * VEC;
@@ -718,7 +753,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             const T2 ep = sE2[p];
             const T e_x = c1 * ep.x + c2 * ep.y;
             const T vxn = SP == 0 ? vx - e_x * factor : vx + e_x * factor;
-            if (SP == 0 && eepf_on && x >= lo && x <= hi) eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e], sH);
+            if (SP == 0 && eepf_on && x >= lo && x <= hi) eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e]);
             const T xn = x + vxn * dt;
             xa[e] = xn;
             vxa[e] = vxn;
@@ -780,9 +815,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             // deposition of the new position for the next step (Sec. 2.1.1)
             T d0;
             const int pp = cell<T>(xa[e], inv_dx, ng, d0);
-            const unsigned long long q2 = split_q2(d0 - (T)pp);
-            atomicAdd(sQ + pp, 4294967296ull - q2);
-            atomicAdd(sQ + pp + 1, q2);
+            dep_add(acc, pp, split_q2(d0 - (T)pp));
         }
         *reinterpret_cast<V *>(X + base) = pack(xa, V{});
         *reinterpret_cast<V *>(VX + base) = pack(vxa, V{});

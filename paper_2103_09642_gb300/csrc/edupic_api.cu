@@ -33,7 +33,7 @@ long long padded(long long cap) { return (cap + kTileAlign - 1) / kTileAlign * k
 struct Layout {
     size_t x[2], vx[2], vy[2], vz[2];
     size_t q_e, q_i, acc_e, acc_i, n_e, n_i, phi, ef, ef_t, f_cur, fs, sum_qe, sum_qi, sum_f, avg;
-    size_t eepf, ifed_pow, ifed_gnd, ctrl, holes[2], prod_parent, prod_x, prod_ve[3], prod_vi[3], vdrive;
+    size_t eepf, ifed_pow, ifed_gnd, holes[2], prod_parent, prod_x, prod_ve[3], prod_vi[3], vdrive;
     size_t bytes;
 };
 
@@ -72,7 +72,6 @@ Layout layout_of(const edupic_params &p, size_t elem)
     L.eepf = take((size_t)kEepfStripes * p.eepf_bins * 8);
     L.ifed_pow = take((size_t)p.ifed_bins * 8);
     L.ifed_gnd = take((size_t)p.ifed_bins * 8);
-    L.ctrl = take(sizeof(Ctrl));
     L.holes[0] = take((size_t)kEvents * 4);
     L.holes[1] = take((size_t)kEvents * 4);
     L.prod_parent = take((size_t)kEvents * 4);
@@ -130,6 +129,7 @@ struct edupic_sim {
     unsigned char *arena = nullptr;
     size_t arena_bytes = 0;
     DischargeDev *d_desc = nullptr;
+    Ctrl *d_ctrl = nullptr;  // packed array: one per discharge
     void *cs_sig[2] = {nullptr, nullptr};
     void *cs_thr[2] = {nullptr, nullptr};
     void *cs_max[2] = {nullptr, nullptr};
@@ -163,6 +163,7 @@ namespace {
 size_t shared_bytes(int nd, size_t elem, int cs_entries)
 {
     size_t o = align_up(sizeof(DischargeDev) * nd, kAlign);
+    o += align_up(sizeof(Ctrl) * nd, kAlign);                  // packed counts and counters
     o += 2 * align_up((size_t)cs_entries * elem, kAlign);      // sigsum
     o += 2 * align_up((size_t)cs_entries * 2 * elem, kAlign);  // thr1, thr2
     o += 2 * align_up((size_t)kCoarse * elem, kAlign);         // coarse maxima
@@ -271,7 +272,7 @@ void fill_desc(edupic_sim *S, int d)
     D.eepf = reinterpret_cast<unsigned long long *>(b + L.eepf);
     D.ifed_pow = reinterpret_cast<unsigned long long *>(b + L.ifed_pow);
     D.ifed_gnd = reinterpret_cast<unsigned long long *>(b + L.ifed_gnd);
-    D.ctrl = reinterpret_cast<Ctrl *>(b + L.ctrl);
+    D.ctrl = S->d_ctrl + d;
     D.prod_parent = reinterpret_cast<int *>(b + L.prod_parent);
     D.prod_x = b + L.prod_x;
     for (int c = 0; c < 3; ++c) {
@@ -498,6 +499,8 @@ int edupic_create(int nd, const edupic_params *params, int precision, void *devi
     size_t o = 0;
     S->d_desc = reinterpret_cast<DischargeDev *>(S->arena);
     o = align_up(sizeof(DischargeDev) * nd, kAlign);
+    S->d_ctrl = reinterpret_cast<Ctrl *>(S->arena + o);
+    o += align_up(sizeof(Ctrl) * nd, kAlign);
     for (int sp = 0; sp < 2; ++sp) {
         S->cs_sig[sp] = S->arena + o;
         o += align_up((size_t)params[0].cs_entries * S->elem, kAlign);

@@ -582,17 +582,26 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     __shared__ int sW[33];
     __shared__ int sQueue[kQueue];
     __shared__ int sQn;
+    __shared__ DischargeDev sD;  // descriptor of the discharge being processed
 
     const int tid = threadIdx.x;
-    if (tid == 0) sQn = 0;
-    // set-up data (the tables are shared by all discharges) before waiting for
-    // the preceding kernel
+    // set-up data that does not depend on the preceding kernel, fetched
+    // before waiting for it: the coarse table (shared by all discharges) and
+    // the descriptor of discharge 0
     {
         const float4 *cm = reinterpret_cast<const float4 *>(DD[0].cs_max[SP]);
         float4 *dst = reinterpret_cast<float4 *>(sC);
         for (int j = tid; j < (int)(kCoarse * sizeof(T) / 16); j += blockDim.x) dst[j] = cm[j];
+        const int *src = reinterpret_cast<const int *>(DD);
+        int *dd = reinterpret_cast<int *>(&sD);
+        for (int i = tid; i < (int)(sizeof(DischargeDev) / 4); i += blockDim.x) dd[i] = src[i];
     }
-    const int cs_shift = DD[0].cs_shift[SP];
+    if (tid == 0) sQn = 0;
+    if (tid < EDUPIC_N_COUNTERS) sCnt[tid] = 0;
+    __syncthreads();
+    const int cs_shift = sD.cs_shift[SP];
+    const Ctrl *ctrls = sD.ctrl;  // the counts of all discharges are one packed array
+    int staged = 0;
     pdl_wait();
     pdl_launch_next();
     // tiles per discharge -> prefix over discharges (every block computes it)
@@ -601,7 +610,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         for (int base = 0; base < nd; base += blockDim.x) {
             const int d = base + tid;
             int cnt = 0;
-            if (d < nd && DD[d].active) cnt = (int)((DD[d].ctrl->n[SP] + TILE - 1) / TILE);
+            if (d < nd && DD[d].active) cnt = (int)((ctrls[d].n[SP] + TILE - 1) / TILE);
             int tot;
             const int ex = group_excl_scan(cnt, sW, tot, tid, blockDim.x, 1);
             if (d < nd) sPre[d] = running + ex;
@@ -609,15 +618,14 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         }
         if (tid == 0) sPre[nd] = running;
     }
-    if (tid < EDUPIC_N_COUNTERS) sCnt[tid] = 0;
     __syncthreads();
     const int total = sPre[nd];
     const int t0 = (int)((long long)blockIdx.x * total / gridDim.x);
     const int t1 = (int)((long long)(blockIdx.x + 1) * total / gridDim.x);
     if (t0 >= t1) return;
 
+    const DischargeDev *D = &sD;
     int cur = -1;
-    const DischargeDev *D = nullptr;
     int n = 0, cs_n = 0, ng = 0;
     uint32_t s_lo = 0, s_hi = 0, k0 = 0, k1 = 0;
     T L = 0, inv_dx = 0, dt = 0, factor = 0, ndt = 0, idx_scale = 0, lo = 0, hi = 0;
@@ -629,6 +637,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     auto drain = [&]() {
         __syncthreads();
         const int qn = sQn;
+        if (qn == 0) return;  // uniform: read after the barrier
         const RngKey key{s_lo, s_hi, k0, k1};
         for (int i = tid; i < qn; i += blockDim.x) {
             if (SP == 0)
@@ -638,10 +647,11 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         }
         __syncthreads();
         if (tid == 0) sQn = 0;
+        __syncthreads();
     };
 
-    // add the block's deposition into the discharge's accumulator and clear it
-    auto flush_dep = [&]() {
+    // add the block's deposition into the discharge's accumulator (and clear it)
+    auto flush_dep = [&](bool clear) {
         __syncthreads();
         long long *accq = SP == 0 ? D->acc_e : D->acc_i;
         for (int p = tid; p < ng; p += blockDim.x) {
@@ -649,31 +659,48 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
                                          (p > 0 ? dep_sum(acc, p - 1) : 0ull);
             if (q) atomicAdd(reinterpret_cast<unsigned long long *>(accq + p), q);
         }
+        if (!clear) return;
         __syncthreads();
         for (int p = tid; p < ng; p += blockDim.x) acc.cnt[p] = acc.lo[p] = acc.hi[p] = 0u;
         __syncthreads();
     };
 
-    auto flush = [&]() {
+    auto flush = [&](bool last) {
         drain();
-        flush_dep();
+        flush_dep(!last);
         if (tid < EDUPIC_N_COUNTERS) {
             const unsigned int c = sCnt[tid];
             if (c) atomicAdd(D->ctrl->counters + tid, (unsigned long long)c);
             sCnt[tid] = 0;
         }
-        __syncthreads();
+        if (!last) __syncthreads();
     };
 
     int since_flush = 0;
+    T xa[VEC], vxa[VEC], vya[VEC], vza[VEC];  // particles of the current tile
+    T xb[VEC], vxb[VEC], vyb[VEC], vzb[VEC];  // the next tile, loaded ahead
+    bool have_next = false;
+    auto load = [&](int b, T *x4, T *vx4, T *vy4, T *vz4) {
+        unpack(*reinterpret_cast<const V *>(X + b), x4);
+        unpack(*reinterpret_cast<const V *>(VX + b), vx4);
+        unpack(*reinterpret_cast<const V *>(VY + b), vy4);
+        unpack(*reinterpret_cast<const V *>(VZ + b), vz4);
+    };
+
     for (int t = t0; t < t1; ++t) {
         if (cur < 0 || t >= sPre[cur + 1]) {
-            if (cur >= 0) flush();
+            if (cur >= 0) flush(false);
             ++cur;
             while (sPre[cur + 1] <= t) ++cur;
-            D = DD + cur;
-            n = (int)D->ctrl->n[SP];
-            const unsigned long long s = (unsigned long long)D->ctrl->step;
+            if (cur != staged) {
+                const int *src = reinterpret_cast<const int *>(DD + cur);
+                int *dd = reinterpret_cast<int *>(&sD);
+                for (int i = tid; i < (int)(sizeof(DischargeDev) / 4); i += blockDim.x) dd[i] = src[i];
+                __syncthreads();
+                staged = cur;
+            }
+            n = (int)ctrls[cur].n[SP];
+            const unsigned long long s = (unsigned long long)ctrls[cur].step;
             s_lo = (uint32_t)s;
             s_hi = (uint32_t)(s >> 32);
             k0 = (uint32_t)D->seed;
@@ -705,6 +732,12 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             VZ = reinterpret_cast<T *>(D->vz[SP]);
             cs_n = SP == 0 ? D->cs_n_e : D->cs_n_i;
             eepf_on = SP == 0 && measure;
+            // the first tile's particles are requested together with the field
+            {
+                const int b0 = (t - sPre[cur]) * TILE + tid * VEC;
+                if (b0 < n) load(b0, xb, vxb, vyb, vzb);
+                have_next = true;
+            }
             const T *ef = reinterpret_cast<const T *>(D->ef_t);
             for (int p = tid; p < ng; p += blockDim.x) {
                 sE2[p] = T2{ef[p], p + 1 < ng ? ef[p + 1] : (T)0};
@@ -717,7 +750,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             __syncthreads();
             if (sQn > kQueue - 4 * TILE) drain();
             if (since_flush >= kDepFlush) {
-                flush_dep();
+                flush_dep(true);
                 since_flush = 0;
             }
         }
@@ -725,15 +758,21 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         const int tbase = (t - sPre[cur]) * TILE;
         if (tid == 0) atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_PUSH_E : EDUPIC_C_PUSH_I), (unsigned)min(TILE, n - tbase));
         const int base = tbase + tid * VEC;
+        if (have_next) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                xa[e] = xb[e];
+                vxa[e] = vxb[e];
+                vya[e] = vyb[e];
+                vza[e] = vzb[e];
+            }
+        } else if (base < n) {
+            load(base, xa, vxa, vya, vza);
+        }
+        // request the next tile of this discharge before computing this one
+        have_next = t + 1 < t1 && t + 1 < sPre[cur + 1];
+        if (have_next && base + TILE < n) load(base + TILE, xb, vxb, vyb, vzb);
         if (base >= n) continue;
-        // every slot of a full tile is live: no per-slot count checks there
-        auto tile = [&](auto full_tag) {
-        constexpr bool FULL = decltype(full_tag)::value;
-        T xa[VEC], vxa[VEC], vya[VEC], vza[VEC];
-        unpack(*reinterpret_cast<const V *>(X + base), xa);
-        unpack(*reinterpret_cast<const V *>(VX + base), vxa);
-        unpack(*reinterpret_cast<const V *>(VY + base), vya);
-        unpack(*reinterpret_cast<const V *>(VZ + base), vza);
 
         // phase 1: gather, push, absorption test, table index
         int kk[VEC];
@@ -745,7 +784,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             in[e] = false;
             kk[e] = 0;
             w2[e] = (T)0;
-            if (!FULL && slot >= n) continue;
+            if (slot >= n) continue;
             const T x = xa[e], vx = vxa[e];
             T c0;
             const int p = cell<T>(x, inv_dx, ng, c0);
@@ -787,11 +826,11 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         // The probability from the coarse maximum of n*sigma_tot bounds P_coll
         // from above, so R01 above it (plus a rounding margin) decides "no
         // collision" without the fine table; otherwise the test of Algorithm 6
-        // is taken with the fine entry.
+        // is taken with the fine entry.  Colliding slots are queued.
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
             const int slot = base + e;
-            if (!FULL && slot >= n) break;
+            if (slot >= n) break;
             if (!in[e]) {
                 absorbed<T, SP>(D, slot, xa[e], vxa[e], vya[e], vza[e], measure, sCnt);
                 continue;
@@ -819,13 +858,8 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         }
         *reinterpret_cast<V *>(X + base) = pack(xa, V{});
         *reinterpret_cast<V *>(VX + base) = pack(vxa, V{});
-            };
-        if (tbase + TILE <= n)
-            tile(std::true_type{});
-        else
-            tile(std::false_type{});
     }
-    if (cur >= 0) flush();
+    if (cur >= 0) flush(true);
 }
 
 // ---------------------------------------------------------------- field solve

@@ -33,7 +33,7 @@ long long padded(long long cap) { return (cap + kTileAlign - 1) / kTileAlign * k
 struct Layout {
     size_t x[2], vx[2], vy[2], vz[2];
     size_t q_e, q_i, acc_e, acc_i, n_e, n_i, phi, ef, ef_t, f_cur, fs, sum_qe, sum_qi, sum_f, avg;
-    size_t eepf, ifed_pow, ifed_gnd, holes[2], prod_parent, prod_x, prod_ve[3], prod_vi[3], vdrive;
+    size_t eepf, ifed_pow, ifed_gnd, holes[2], prod_parent, sort_buf, prod_x, prod_ve[3], prod_vi[3], vdrive;
     size_t bytes;
 };
 
@@ -75,6 +75,7 @@ Layout layout_of(const edupic_params &p, size_t elem)
     L.holes[0] = take((size_t)kEvents * 4);
     L.holes[1] = take((size_t)kEvents * 4);
     L.prod_parent = take((size_t)kEvents * 4);
+    L.sort_buf = take((size_t)kEvents * 4);
     L.prod_x = take((size_t)kEvents * elem);
     for (int c = 0; c < 3; ++c) L.prod_ve[c] = take((size_t)kEvents * elem);
     for (int c = 0; c < 3; ++c) L.prod_vi[c] = take((size_t)kEvents * elem);
@@ -274,6 +275,7 @@ void fill_desc(edupic_sim *S, int d)
     D.ifed_gnd = reinterpret_cast<unsigned long long *>(b + L.ifed_gnd);
     D.ctrl = S->d_ctrl + d;
     D.prod_parent = reinterpret_cast<int *>(b + L.prod_parent);
+    D.sort_buf = reinterpret_cast<int *>(b + L.sort_buf);
     D.prod_x = b + L.prod_x;
     for (int c = 0; c < 3; ++c) {
         D.prod_ve[c] = b + L.prod_ve[c];

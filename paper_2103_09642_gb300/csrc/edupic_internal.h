@@ -12,6 +12,7 @@ constexpr int kFinalizeThreads = 512;  // one CTA per discharge for compaction +
 constexpr int kGroupA = 128;           // finalize threads doing compaction and append
 constexpr int kGroupB = kFinalizeThreads - kGroupA;  // finalize threads doing the field solve
 constexpr int kEvents = EDUPIC_STEP_EVENTS;
+constexpr int kSortShared = 8192;      // event lists up to this size are sorted in shared memory
 constexpr int kCoarse = 2048;          // entries of the coarse sigma_max tables (shared memory)
 constexpr int kEepfStripes = 16;       // copies of the EEPF histogram the particle kernel spreads its atomics over
 
@@ -82,6 +83,7 @@ struct DischargeDev {
     Ctrl *ctrl;
     int *holes[2];
     int *prod_parent;
+    int *sort_buf;             // kEvents ints: global sort buffer for event lists above kSortShared
     void *prod_x, *prod_ve[3], *prod_vi[3];
     const void *cs_sig[2];     // T[cs_n]
     const void *cs_thr[2];     // T2[cs_n]

@@ -1037,6 +1037,18 @@ __device__ __forceinline__ void group_sort(int *a, int n, int gtid, int g, int b
     }
 }
 
+// Sorted copy of an event list: in shared memory when it fits (sA), else in
+// the discharge's global sort buffer (bitonic sort; its length is padded to
+// a power of two <= kEvents).  Returns the sorted array.
+__device__ __forceinline__ int *sorted_events(const DischargeDev &D, const int *src, int n, int *sA, int gtid, int g,
+                                              int bar)
+{
+    int *a = n <= kSortShared ? sA : D.sort_buf;
+    for (int i = gtid; i < n; i += g) a[i] = src[i];
+    group_sort(a, n, gtid, g, bar);
+    return a;
+}
+
 // Holes of species sp sorted ascending, then filled by the tail survivors
 // [N', N) in ascending order (the canonical removal order).
 template <typename T>
@@ -1047,8 +1059,7 @@ __device__ long long compact_species(const DischargeDev &D, int sp, int *sA, int
     int H = C->holes[sp];
     if (H > kEvents) H = kEvents;  // error bit already set by k_push
     if (H == 0) return n;
-    for (int i = gtid; i < H; i += g) sA[i] = D.holes[sp][i];
-    group_sort(sA, H, gtid, g, bar);
+    const int *hs = sorted_events(D, D.holes[sp], H, sA, gtid, g, bar);
     const long long nn = n - H;
     T *X = reinterpret_cast<T *>(D.x[sp]);
     T *VX = reinterpret_cast<T *>(D.vx[sp]);
@@ -1066,7 +1077,7 @@ __device__ long long compact_species(const DischargeDev &D, int sp, int *sA, int
         int tot;
         const int r = group_excl_scan(alive ? 1 : 0, sW, tot, gtid, g, bar);
         const int k = filled + r;
-        const int dst = (alive && k < H) ? sA[k] : -1;
+        const int dst = (alive && k < H) ? hs[k] : -1;
         if (alive && (dst < 0 || dst >= nn)) atomicOr(&C->error, kErrHoles);  // inconsistent hole list
         if (alive && dst >= 0 && dst < nn) {
             X[dst] = X[j];
@@ -1088,8 +1099,7 @@ __device__ void append_products(const DischargeDev &D, int *sA, long long &ne, l
     int P = C->products;
     if (P > kEvents) P = kEvents;
     if (P == 0) return;
-    for (int i = gtid; i < P; i += g) sA[i] = D.prod_parent[i];
-    group_sort(sA, P, gtid, g, bar);
+    const int *ps = sorted_events(D, D.prod_parent, P, sA, gtid, g, bar);
     long long room = D.cap[0] - ne;
     if (D.cap[1] - ni < room) room = D.cap[1] - ni;
     const long long keep = (long long)P < room ? (long long)P : (room > 0 ? room : 0);
@@ -1103,7 +1113,7 @@ __device__ void append_products(const DischargeDev &D, int *sA, long long &ne, l
         int lo = 0, hi = P;  // rank of h among the sorted parents
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (sA[mid] < h)
+            if (ps[mid] < h)
                 lo = mid + 1;
             else
                 hi = mid;
@@ -1137,7 +1147,7 @@ template <typename T>
 __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDev *__restrict__ DD, int nd,
                                                                int ion_step, int measure)
 {
-    __shared__ int sA[kEvents];
+    __shared__ int sA[kSortShared];
     __shared__ int sW[33];
     __shared__ FieldScratch<kGroupB> sF;
     __shared__ long long sN[2];

@@ -152,14 +152,28 @@ def _sample_profile(n: int, gap_m: float, floor: float, sheath: float, rng) -> n
     return np.clip(out[:n] * gap_m, 1e-12 * gap_m, gap_m * (1.0 - 1e-12))
 
 
+def sheath_fraction(d: Discharge, n_particles: int) -> float:
+    """Sheath width (fraction of the gap) of a synthetic state: the width
+    over which the bulk ion space charge holds the peak drive voltage,
+    s = sqrt(2 eps0 V / (e n)), clamped to [0.08, 0.3]."""
+    v = sum(abs(a) for _, a in d.harmonics) or 1.0
+    n0 = d.weight * n_particles / (d.area_m2 * d.gap_m) if d.weight > 0 else 0.0
+    if n0 <= 0:
+        return 0.15
+    s = math.sqrt(2 * 8.8541878128e-12 * v / (_QE * n0))
+    return float(min(0.3, max(0.08, s / d.gap_m)))
+
+
 def steady_shape(n_e: int, n_i: int, d: Discharge, rng: np.random.Generator,
-                 te_ev: float = 2.5, sheath_frac: float = 0.15,
+                 te_ev: float = 2.5, sheath_frac: float | None = None,
                  ion_drift_ms: float = 8.0e3) -> Tuple[Particles, Particles]:
     """A synthetic state shaped like a converged CCP: flat bulk, electrons
     depleted in the sheaths, ions partly depleted and drifting towards the
     nearer electrode inside the sheaths (speed rising linearly to
     `ion_drift_ms` at the wall)."""
     L = d.gap_m
+    if sheath_frac is None:
+        sheath_frac = sheath_fraction(d, n_i)
     xe = _sample_profile(n_e, L, 0.0, sheath_frac, rng)
     xi = _sample_profile(n_i, L, 0.55, sheath_frac, rng)
     e = maxwellian(n_e, L, te_ev * _QE, _ME, rng, x=xe)
@@ -228,7 +242,7 @@ def batch_mix(n_discharges: int = 64, seed0: int = 1000, n_min: float = 1e4, n_m
         w = density * 1e-4 * gap / n
         d = Discharge(gap_m=gap, pressure_pa=p, weight=w, n_grid=ng,
                       harmonics=((13.56e6, v0),), seed=seed0 + k,
-                      capacity=int(n * 1.25) + 4096)
+                      capacity=int(n * 1.6) + 4096)
         e, i = steady_shape(n, n, d, rng, te_ev=rng.uniform(2.0, 3.0))
         out.append((d, e, i))
     return out

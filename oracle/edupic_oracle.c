@@ -89,7 +89,9 @@ float orc_u24(uint32_t a) { return (float)(a >> 8) * (1.0f / 16777216.0f); }
 /* Random-number layout (the paper draws R01 from one sequential MT19937
  * stream, Sec. 3.3; any assignment of independent uniforms is equivalent).
  * Block 0 of counter word c0 = slot / 2 holds the collision-test uniforms of
- * the two slots 2k (words 0,1) and 2k+1 (words 2,3).  Blocks b >= 1 of
+ * the two slots 2k (words 0,1) and 2k+1 (words 2,3) (53 bits each; the FP32
+ * particle mode takes 24-bit uniforms, four slots per block: see
+ * orc_test_uniform_f32).  Blocks b >= 1 of
  * counter word c0 = slot hold the per-particle draws:
  *   e-:  1 (process, chi)  2 (eta, Opal)  3, 4 Box-Muller pairs of the new Ar+
  *   Ar+: 1, 2 Box-Muller pairs of the thermal partner  3 (process, chi)  4 (eta, -) */
@@ -113,12 +115,13 @@ static double test_uniform(uint64_t seed, int64_t slot, int64_t step, int specie
     return (slot & 1) ? orc_u53(w[2], w[3]) : orc_u53(w[0], w[1]);
 }
 
-/* FP32 particle mode: the same words, 24 bits each (words 0 and 2). */
+/* FP32 particle mode: block 0 of counter word slot / 4 serves four slots,
+ * 24 bits from word slot % 4. */
 float orc_test_uniform_f32(uint64_t seed, int64_t slot, int64_t step, int species)
 {
     uint32_t w[4];
-    philox_words(seed, (uint32_t)((uint64_t)slot >> 1), step, species, 0, w);
-    return (slot & 1) ? orc_u24(w[2]) : orc_u24(w[0]);
+    philox_words(seed, (uint32_t)((uint64_t)slot >> 2), step, species, 0, w);
+    return orc_u24(w[slot & 3]);
 }
 
 /* One per-particle Philox block (b >= 1) for (slot, global step, species). */

@@ -32,16 +32,16 @@ namespace edupic {
 #define EDUPIC_PI 3.14159265358979323846
 #define EDUPIC_OPAL_W 10.0
 #ifndef EDUPIC_PUSH_MIN_BLOCKS
-#define EDUPIC_PUSH_MIN_BLOCKS 3  // resident FP32 particle-kernel blocks per SM the register budget targets
+#define EDUPIC_PUSH_MIN_BLOCKS 2  // resident FP32 particle-kernel blocks per SM the register budget targets
 #endif
 
 template <typename T>
 struct VecOf;
 template <>
 struct VecOf<float> {
-    using type = float2;
+    using type = float4;
     using pair = float2;
-    static constexpr int n = 2;
+    static constexpr int n = 4;
 };
 template <>
 struct VecOf<double> {
@@ -50,9 +50,9 @@ struct VecOf<double> {
     static constexpr int n = 2;
 };
 
-__device__ __forceinline__ void unpack(const float2 &v, float *a) { a[0] = v.x; a[1] = v.y; }
+__device__ __forceinline__ void unpack(const float4 &v, float *a) { a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w; }
 __device__ __forceinline__ void unpack(const double2 &v, double *a) { a[0] = v.x; a[1] = v.y; }
-__device__ __forceinline__ float2 pack(const float *a, float2) { return make_float2(a[0], a[1]); }
+__device__ __forceinline__ float4 pack(const float *a, float4) { return make_float4(a[0], a[1], a[2], a[3]); }
 __device__ __forceinline__ double2 pack(const double *a, double2) { return make_double2(a[0], a[1]); }
 
 template <typename T>
@@ -60,9 +60,10 @@ __host__ __device__ constexpr bool is_f64() { return std::is_same<T, double>::va
 
 // ---------------------------------------------------------------- RNG
 // Philox-4x32-10 (Salmon et al., SC'11).  Counter (c0, step lo, step hi,
-// species << 8 | block), key = seed.  Block 0 with c0 = slot / 2 holds the
-// collision-test uniforms of a slot pair; blocks >= 1 with c0 = slot hold a
-// particle's other draws.
+// species << 8 | block), key = seed.  Block 0 holds collision-test uniforms:
+// in FP64 with c0 = slot / 2 (53 bits from words a,b for even slots, c,d for
+// odd), in FP32 with c0 = slot / 4 (24 bits from word slot % 4).  Blocks >= 1
+// with c0 = slot hold a particle's other draws.
 struct Words {
     uint32_t a, b, c, d;
 };
@@ -567,7 +568,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
 {
     using V = typename VecOf<T>::type;
     using T2 = typename VecOf<T>::pair;
-    constexpr int VEC = VecOf<T>::n;  // two slots per thread: one Philox test block
+    constexpr int VEC = VecOf<T>::n;  // slots per thread: one Philox test block
     constexpr int TILE = kThreads * VEC;
     extern __shared__ __align__(16) unsigned char smem[];
     T *sC = reinterpret_cast<T *>(smem);
@@ -774,59 +775,70 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         if (have_next && base + TILE < n) load(base + TILE, xb, vxb, vyb, vzb);
         if (base >= n) continue;
 
-        // phase 1: gather, push, absorption test, table index
+        // phase 1: gather (Sec. 2.1.3), leapfrog push (Sec. 2.1.4), absorption
+        // test (Sec. 2.1.5), energy and table index
         int kk[VEC];
         bool in[VEC];
         T w2[VEC];  // v^2 (e-) or g^2 (Ar+)
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
-            const int slot = base + e;
-            in[e] = false;
-            kk[e] = 0;
-            w2[e] = (T)0;
-            if (slot >= n) continue;
+            const bool live = base + e < n;
             const T x = xa[e], vx = vxa[e];
             T c0;
             const int p = cell<T>(x, inv_dx, ng, c0);
-            const T c1 = (T)(p + 1) - c0, c2 = c0 - (T)p;
             const T2 ep = sE2[p];
-            const T e_x = c1 * ep.x + c2 * ep.y;
+            T e_x;
+            if constexpr (is_f64<T>()) {
+                const T c1 = (T)(p + 1) - c0, c2 = c0 - (T)p;
+                e_x = c1 * ep.x + c2 * ep.y;
+            } else {
+                e_x = ep.x + (c0 - (T)p) * (ep.y - ep.x);  // same linear weights
+            }
             const T vxn = SP == 0 ? vx - e_x * factor : vx + e_x * factor;
-            if (SP == 0 && eepf_on && x >= lo && x <= hi) eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e]);
+            if (SP == 0 && eepf_on && live && x >= lo && x <= hi)
+                eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e]);
             const T xn = x + vxn * dt;
-            xa[e] = xn;
-            vxa[e] = vxn;
-            in[e] = (xn >= (T)0.0) && (xn <= L);
-            if (!in[e]) continue;
+            xa[e] = live ? xn : x;
+            vxa[e] = live ? vxn : vx;
+            in[e] = live && (xn >= (T)0.0) && (xn <= L);
+            T q2;
             if (SP == 0) {
-                const T v2 = vxn * vxn + vya[e] * vya[e] + vza[e] * vza[e];
-                w2[e] = v2;
-                if constexpr (is_f64<T>())
-                    kk[e] = cs_index(D->half_me * v2 / EDUPIC_QE, idx_scale, cs_n);
-                else
-                    kk[e] = cs_index_f(v2 * idx_scale + 0.5f, cs_n);
+                q2 = vxn * vxn + vya[e] * vya[e] + vza[e] * vza[e];
             } else {
                 // thermal partner drawn before the collision probability
-                const RngKey key{s_lo, s_hi, k0, k1};
-                T vax, vay, vaz;
-                ion_partner<T>(*D, key, (uint32_t)slot, vax, vay, vaz);
+                T vax = 0, vay = 0, vaz = 0;
+                if (in[e]) {
+                    const RngKey key{s_lo, s_hi, k0, k1};
+                    ion_partner<T>(*D, key, (uint32_t)(base + e), vax, vay, vaz);
+                }
                 const T gx = vxn - vax, gy = vya[e] - vay, gz = vza[e] - vaz;
-                const T g_sqr = gx * gx + gy * gy + gz * gz;
-                w2[e] = g_sqr;
-                kk[e] = ion_index<T>(*D, g_sqr, idx_scale, cs_n);
+                q2 = gx * gx + gy * gy + gz * gz;
             }
+            w2[e] = q2;
+            if constexpr (is_f64<T>())
+                kk[e] = cs_index((SP == 0 ? D->half_me : D->half_mu_arar) * q2 / EDUPIC_QE, idx_scale, cs_n);
+            else
+                kk[e] = cs_index_f(q2 * idx_scale + 0.5f, cs_n);
         }
-        // phase 2: collision-test uniforms of the slot pair (one Philox block)
+        // phase 2: collision-test uniforms (one Philox block per thread)
         T ut[VEC];
         {
-            const Words w = philox((uint32_t)base >> 1, s_lo, s_hi, (uint32_t)SP << 8, k0, k1);
-            uniforms(w, ut[0], ut[1]);
+            const Words w = philox((uint32_t)base / VEC, s_lo, s_hi, (uint32_t)SP << 8, k0, k1);
+            if constexpr (is_f64<T>()) {
+                uniforms(w, ut[0], ut[1]);
+            } else {
+                ut[0] = u24(w.a);
+                ut[1] = u24(w.b);
+                ut[2] = u24(w.c);
+                ut[3] = u24(w.d);
+            }
         }
         // phase 3: collision test (Algorithm 6), absorption records, deposition.
-        // The probability from the coarse maximum of n*sigma_tot bounds P_coll
-        // from above, so R01 above it (plus a rounding margin) decides "no
-        // collision" without the fine table; otherwise the test of Algorithm 6
-        // is taken with the fine entry.  Colliding slots are queued.
+        // With x = n sigma_tot v dt, P_coll = 1 - exp(-x) <= x, and the coarse
+        // maximum of sigma_tot bounds x from above: R01 at or above that bound
+        // (plus a rounding margin) decides "no collision" without the fine
+        // table; otherwise the test of Algorithm 6 is taken with the fine
+        // entry.  Colliding slots are queued.
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
             const int slot = base + e;
@@ -836,13 +848,12 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
                 continue;
             }
             const T speed = sqrt(w2[e]);
-            const T smax = sC[kk[e] >> cs_shift];
-            T pu;
+            T xu;
             if constexpr (is_f64<T>())
-                pu = p_coll(smax * ndt * speed * dt) + 1e-15;
+                xu = sC[kk[e] >> cs_shift] * ndt * speed * dt * 1.000001 + 1e-15;
             else
-                pu = p_coll(smax * ndt * speed) + 1e-6f;
-            if (ut[e] < pu) {
+                xu = sC[kk[e] >> cs_shift] * ndt * speed * 1.00001f + 1e-6f;
+            if (ut[e] < xu) {
                 const T sg = __ldg(sig + kk[e]);
                 T pc;
                 if constexpr (is_f64<T>())

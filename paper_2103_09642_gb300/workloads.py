@@ -139,14 +139,19 @@ def maxwellian(n: int, gap_m: float, kt_joule: float, mass: float, rng: np.rando
     return Particles(np.ascontiguousarray(x, dtype=np.float64), v[0].copy(), v[1].copy(), v[2].copy())
 
 
-def _sample_profile(n: int, gap_m: float, floor: float, sheath: float, rng) -> np.ndarray:
-    """Positions drawn from a flat-bulk profile that falls linearly to
-    `floor` (relative) at both electrodes over a width `sheath` (relative)."""
+def _sample_profile(n: int, gap_m: float, floor: float, rng, left: Tuple[float, float],
+                    right: Tuple[float, float]) -> np.ndarray:
+    """Positions drawn from a flat-bulk profile that, towards each electrode,
+    falls linearly to `floor` (relative) between the distances (start, end)
+    (fractions of the gap) given for that side, and is `floor` closer in."""
     out = np.empty(0)
     while out.size < n:
         x = rng.uniform(0.0, 1.0, 2 * (n - out.size) + 16)
-        d = np.minimum(x, 1.0 - x)
-        p = floor + (1.0 - floor) * np.minimum(1.0, d / sheath)
+        near_left = x < 0.5
+        d = np.where(near_left, x, 1.0 - x)
+        start = np.where(near_left, left[0], right[0])
+        end = np.where(near_left, left[1], right[1])
+        p = floor + (1.0 - floor) * np.clip((d - start) / (end - start), 0.0, 1.0)
         keep = rng.uniform(0.0, 1.0, x.size) < p
         out = np.concatenate([out, x[keep]])
     return np.clip(out[:n] * gap_m, 1e-12 * gap_m, gap_m * (1.0 - 1e-12))
@@ -164,6 +169,13 @@ def sheath_fraction(d: Discharge, n_particles: int) -> float:
     return float(min(0.3, max(0.08, s / d.gap_m)))
 
 
+def matched_electrons(n_i: int, sheath_frac: float) -> int:
+    """Electron count whose bulk density equals the ion bulk density for the
+    profiles of steady_shape (the sheaths hold ions but few electrons)."""
+    s = sheath_frac
+    return int(round(n_i * (1.0 - 1.26 * s) / (1.0 - 0.45 * s)))
+
+
 def steady_shape(n_e: int, n_i: int, d: Discharge, rng: np.random.Generator,
                  te_ev: float = 2.5, sheath_frac: float | None = None,
                  ion_drift_ms: float = 8.0e3) -> Tuple[Particles, Particles]:
@@ -174,8 +186,13 @@ def steady_shape(n_e: int, n_i: int, d: Discharge, rng: np.random.Generator,
     L = d.gap_m
     if sheath_frac is None:
         sheath_frac = sheath_fraction(d, n_i)
-    xe = _sample_profile(n_e, L, 0.0, sheath_frac, rng)
-    xi = _sample_profile(n_i, L, 0.55, sheath_frac, rng)
+    s = sheath_frac
+    # the state matches the drive at t = 0 (V = sum of the amplitudes on the
+    # powered electrode at x = 0): ions hold a symmetric, time-averaged
+    # profile; the electrons fill the collapsed sheath at x = 0 and leave the
+    # full sheath at x = L empty
+    xi = _sample_profile(n_i, L, 0.55, rng, (0.0, s), (0.0, s))
+    xe = _sample_profile(n_e, L, 0.0, rng, (0.02 * s, 0.3 * s), (s, 1.2 * s))
     e = maxwellian(n_e, L, te_ev * _QE, _ME, rng, x=xe)
     i = maxwellian(n_i, L, _KB * d.gas_temp_k, _M_AR, rng, x=xi)
     dist = np.minimum(xi, L - xi) / L
@@ -206,7 +223,7 @@ def reference_steady(seed: int = 1, n: int = 500_000, capacity: int | None = Non
     cap = capacity if capacity is not None else int(n * 1.25) + 4096
     d = reference_discharge(seed=seed, weight=7.0e4 * 1.0e5 / n, capacity=cap)
     rng = np.random.default_rng(10_000 + seed)
-    e, i = steady_shape(n, n, d, rng)
+    e, i = steady_shape(matched_electrons(n, sheath_fraction(d, n)), n, d, rng)
     return d, e, i
 
 
@@ -220,7 +237,7 @@ def dual_frequency(seed: int = 1, v_lf: float = 300.0, n: int = 2_000_000,
                   steps_per_cycle=16000 * 20, ion_subcycle=20, cycle_freq_hz=1.356e6,
                   harmonics=((1.356e6, v_lf), (27.12e6, 100.0)), seed=seed, capacity=cap)
     rng = np.random.default_rng(20_000 + seed)
-    e, i = steady_shape(n, n, d, rng)
+    e, i = steady_shape(matched_electrons(n, sheath_fraction(d, n)), n, d, rng)
     return d, e, i
 
 
@@ -242,7 +259,7 @@ def batch_mix(n_discharges: int = 64, seed0: int = 1000, n_min: float = 1e4, n_m
         w = density * 1e-4 * gap / n
         d = Discharge(gap_m=gap, pressure_pa=p, weight=w, n_grid=ng,
                       harmonics=((13.56e6, v0),), seed=seed0 + k,
-                      capacity=int(n * 1.6) + 4096)
-        e, i = steady_shape(n, n, d, rng, te_ev=rng.uniform(2.0, 3.0))
+                      capacity=int(n * 2.0) + 4096)
+        e, i = steady_shape(matched_electrons(n, sheath_fraction(d, n)), n, d, rng, te_ev=rng.uniform(2.0, 3.0))
         out.append((d, e, i))
     return out

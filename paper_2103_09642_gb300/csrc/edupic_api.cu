@@ -343,6 +343,7 @@ int read_ctrl(edupic_sim *S, int d, Ctrl *c)
 int error_of(const Ctrl &c)
 {
     if (c.error & kErrNan) return EDUPIC_ENAN;
+    if (c.error & kErrTimeout) return EDUPIC_ETIMEOUT;
     if (c.error) return EDUPIC_ECAPACITY;
     return EDUPIC_OK;
 }

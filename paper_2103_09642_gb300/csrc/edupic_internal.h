@@ -8,6 +8,7 @@
 namespace edupic {
 
 constexpr int kThreads = 256;          // particle-kernel block size
+constexpr int kStages = 3;             // particle tiles in flight per block (bulk-copy ring)
 constexpr int kFinalizeThreads = 512;  // one CTA per discharge for compaction + field solve
 constexpr int kGroupA = 128;           // finalize threads doing compaction and append
 constexpr int kGroupB = kFinalizeThreads - kGroupA;  // finalize threads doing the field solve
@@ -22,6 +23,7 @@ enum : int {
     kErrProducts = 2,  // more ionisations in a step than kEvents
     kErrCapacity = 4,  // created pairs dropped at particle capacity
     kErrNan = 8,       // non-finite position
+    kErrTimeout = 16,  // a bounded wait for an asynchronous copy expired
 };
 
 // Per-discharge counters and counts, written by the kernels.

@@ -319,6 +319,63 @@ __device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// ---------------------------------------------------------------- bulk copies
+// One-dimensional bulk copies global -> shared (cp.async.bulk), completed on
+// an mbarrier through its transaction count.  Addresses and sizes are
+// multiples of 16 bytes (particle arrays are 256-byte aligned and tiles are
+// whole multiples of 4 KB).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of the barrier for at most about one second; false
+// if the wait expired.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 template <typename V>
 __device__ __forceinline__ V warp_incl_scan(V v)
 {
@@ -553,13 +610,14 @@ __device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy,
 }
 
 // ---------------------------------------------------------------- particle kernel
-// Dynamic shared memory: [coarse sigma_max: kCoarse T][E pairs: ng_max T2]
-// [deposition: 3 x ng_max u32][tile prefix: nd+1 int].
+// Dynamic shared memory: [tile ring: kStages x 4 arrays x TILE T][coarse
+// sigma_max: kCoarse T][E pairs: ng_max T2][deposition: 3 x ng_max u32]
+// [tile prefix: nd+1 int].
 template <typename T>
 __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eepf_max)
 {
-    return (size_t)kCoarse * sizeof(T) + (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 12 +
-           (size_t)(nd + 1) * 4 + 0 * (size_t)eepf_max;
+    return (size_t)kStages * 4 * kThreads * VecOf<T>::n * sizeof(T) + (size_t)kCoarse * sizeof(T) +
+           (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 12 + (size_t)(nd + 1) * 4 + 0 * (size_t)eepf_max;
 }
 
 template <typename T, int SP>
@@ -570,8 +628,10 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     using T2 = typename VecOf<T>::pair;
     constexpr int VEC = VecOf<T>::n;  // slots per thread: one Philox test block
     constexpr int TILE = kThreads * VEC;
-    extern __shared__ __align__(16) unsigned char smem[];
-    T *sC = reinterpret_cast<T *>(smem);
+    static_assert(kQueue % TILE == 0, "the collider queue holds whole tiles");
+    extern __shared__ __align__(128) unsigned char smem[];
+    T *sRing = reinterpret_cast<T *>(smem);  // [stage][array x, vx, vy, vz][TILE]
+    T *sC = sRing + kStages * 4 * TILE;
     T2 *sE2 = reinterpret_cast<T2 *>(sC + kCoarse);
     DepAcc acc;
     acc.cnt = reinterpret_cast<unsigned int *>(sE2 + ng_max);
@@ -584,6 +644,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     __shared__ int sQueue[kQueue];
     __shared__ int sQn;
     __shared__ DischargeDev sD;  // descriptor of the discharge being processed
+    __shared__ __align__(8) uint64_t sBar[kStages];
 
     const int tid = threadIdx.x;
     // set-up data that does not depend on the preceding kernel, fetched
@@ -597,7 +658,11 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         int *dd = reinterpret_cast<int *>(&sD);
         for (int i = tid; i < (int)(sizeof(DischargeDev) / 4); i += blockDim.x) dd[i] = src[i];
     }
-    if (tid == 0) sQn = 0;
+    if (tid == 0) {
+        sQn = 0;
+        for (int k = 0; k < kStages; ++k) mbar_init(sBar + k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     if (tid < EDUPIC_N_COUNTERS) sCnt[tid] = 0;
     __syncthreads();
     const int cs_shift = sD.cs_shift[SP];
@@ -678,17 +743,29 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     };
 
     int since_flush = 0;
-    T xa[VEC], vxa[VEC], vya[VEC], vza[VEC];  // particles of the current tile
-    T xb[VEC], vxb[VEC], vyb[VEC], vzb[VEC];  // the next tile, loaded ahead
-    bool have_next = false;
-    auto load = [&](int b, T *x4, T *vx4, T *vy4, T *vz4) {
-        unpack(*reinterpret_cast<const V *>(X + b), x4);
-        unpack(*reinterpret_cast<const V *>(VX + b), vx4);
-        unpack(*reinterpret_cast<const V *>(VY + b), vy4);
-        unpack(*reinterpret_cast<const V *>(VZ + b), vz4);
-    };
+    T xa[VEC], vxa[VEC], vya[VEC], vza[VEC];  // particles of this thread in the current tile
 
-    for (int t = t0; t < t1; ++t) {
+    // Producer (thread 0): bulk-copy tile `pt` (x, vx, vy, vz; a whole TILE,
+    // inside the padded capacity) into ring stage `st`.
+    int pt = t0, pcur = 0;
+    auto issue = [&](int st) {
+        while (pt >= sPre[pcur + 1]) ++pcur;
+        const DischargeDev *Dq = DD + pcur;
+        const size_t off = (size_t)(pt - sPre[pcur]) * TILE;
+        uint64_t *bar = sBar + st;
+        T *dst = sRing + (size_t)st * 4 * TILE;
+        mbar_expect_tx(bar, 4u * TILE * (uint32_t)sizeof(T));
+        bulk_load(dst, reinterpret_cast<const T *>(Dq->x[SP]) + off, TILE * sizeof(T), bar);
+        bulk_load(dst + TILE, reinterpret_cast<const T *>(Dq->vx[SP]) + off, TILE * sizeof(T), bar);
+        bulk_load(dst + 2 * TILE, reinterpret_cast<const T *>(Dq->vy[SP]) + off, TILE * sizeof(T), bar);
+        bulk_load(dst + 3 * TILE, reinterpret_cast<const T *>(Dq->vz[SP]) + off, TILE * sizeof(T), bar);
+        ++pt;
+    };
+    if (tid == 0)
+        for (int k = 0; k < kStages && pt < t1; ++k) issue(k);
+
+    for (int t = t0, it = 0; t < t1; ++t, ++it) {
+        const int st = it % kStages;
         if (cur < 0 || t >= sPre[cur + 1]) {
             if (cur >= 0) flush(false);
             ++cur;
@@ -733,12 +810,6 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             VZ = reinterpret_cast<T *>(D->vz[SP]);
             cs_n = SP == 0 ? D->cs_n_e : D->cs_n_i;
             eepf_on = SP == 0 && measure;
-            // the first tile's particles are requested together with the field
-            {
-                const int b0 = (t - sPre[cur]) * TILE + tid * VEC;
-                if (b0 < n) load(b0, xb, vxb, vyb, vzb);
-                have_next = true;
-            }
             const T *ef = reinterpret_cast<const T *>(D->ef_t);
             for (int p = tid; p < ng; p += blockDim.x) {
                 sE2[p] = T2{ef[p], p + 1 < ng ? ef[p + 1] : (T)0};
@@ -747,32 +818,32 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             since_flush = 0;
             __syncthreads();
         }
-        if (((t - t0) & 3) == 3) {
-            __syncthreads();
-            if (sQn > kQueue - 4 * TILE) drain();
-            if (since_flush >= kDepFlush) {
-                flush_dep(true);
-                since_flush = 0;
-            }
-        }
-        since_flush += TILE;
         const int tbase = (t - sPre[cur]) * TILE;
         if (tid == 0) atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_PUSH_E : EDUPIC_C_PUSH_I), (unsigned)min(TILE, n - tbase));
         const int base = tbase + tid * VEC;
-        if (have_next) {
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) {
-                xa[e] = xb[e];
-                vxa[e] = vxb[e];
-                vya[e] = vyb[e];
-                vza[e] = vzb[e];
-            }
-        } else if (base < n) {
-            load(base, xa, vxa, vya, vza);
+        // this tile's particles from the ring
+        if (!mbar_wait_bounded(sBar + st, (uint32_t)((it / kStages) & 1))) atomicOr(&D->ctrl->error, kErrTimeout);
+        {
+            const T *rs = sRing + (size_t)st * 4 * TILE + tid * VEC;
+            unpack(*reinterpret_cast<const V *>(rs), xa);
+            unpack(*reinterpret_cast<const V *>(rs + TILE), vxa);
+            unpack(*reinterpret_cast<const V *>(rs + 2 * TILE), vya);
+            unpack(*reinterpret_cast<const V *>(rs + 3 * TILE), vza);
         }
-        // request the next tile of this discharge before computing this one
-        have_next = t + 1 < t1 && t + 1 < sPre[cur + 1];
-        if (have_next && base + TILE < n) load(base + TILE, xb, vxb, vyb, vzb);
+        __syncthreads();  // the stage is free: refill it with the tile kStages ahead
+        if (tid == 0 && pt < t1) {
+            fence_proxy_async();
+            issue(st);
+        }
+        // the queue takes at most TILE colliders per tile: drain it on a fixed
+        // schedule, every kQueue / TILE tiles (drain() reads its length after
+        // a barrier that every thread has reached, and returns if it is empty)
+        if (it > 0 && it % (kQueue / TILE) == 0) drain();
+        if (since_flush >= kDepFlush) {
+            flush_dep(true);
+            since_flush = 0;
+        }
+        since_flush += TILE;
         if (base >= n) continue;
 
         // phase 1: gather (Sec. 2.1.3), leapfrog push (Sec. 2.1.4), absorption

@@ -17,10 +17,10 @@ int Launch<T>::push_blocks_per_sm(int species, size_t smem)
     int nb = 0;
     cudaError_t e;
     if (species == 0) {
-        cudaFuncSetAttribute(k_push<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_push<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<T, 0>, kThreads, smem);
     } else {
-        cudaFuncSetAttribute(k_push<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_push<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<T, 1>, kThreads, smem);
     }
     return e == cudaSuccess ? nb : -1;

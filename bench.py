@@ -11,6 +11,11 @@ steps).  With --gpus N under torchrun every rank runs its own replica
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+At N=1 the line also carries "batched": the 64-discharge batch (seed-drawn
+gap 1.5-5 cm, 2-50 Pa, 100-500 V, N_G 200-800, 1e4-2e6 particles per species,
+~2e7 electrons in all) stepped together, timed the same way, with its own
+roofline of the electron particle kernel.
+
 --impl reference times the CPU oracle (single thread, FP64) on a bounded
 sample of the same workload.
 """
@@ -39,6 +44,8 @@ BYTES_PER_PUSH_FP32 = 24     # read x, vx, vy, vz (16 B) + write x, vx (8 B)
 # valid for the kernel source whose hash is given; null otherwise.
 TRAFFIC = {"sha": None, "bytes_per_launch": None}
 N_STEADY = 500_000
+BATCH_DISCHARGES = 64
+BATCH_STEPS_PER_CHUNK = 400   # time steps per batched bench step (20 ion subcycles)
 
 
 def _args():
@@ -49,6 +56,7 @@ def _args():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -178,6 +186,64 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args, peak, peak_kind, flush) -> dict:
+    """The 64-discharge batch (seed-drawn gap, pressure, voltage, N_G and
+    particle count, steady-shape states, ~2e7 electrons in all, state far
+    above L2) stepped together: one push launch per species and one finalize
+    launch per time step for all discharges, graph-captured per ion subcycle."""
+    import torch
+
+    from paper_2103_09642_gb300 import edupic as ed
+    from paper_2103_09642_gb300 import workloads as wl
+
+    mix = wl.batch_mix(n_discharges=BATCH_DISCHARGES, seed0=1000)
+    ds = [m[0] for m in mix]
+    se, si = wl.standin_cross_sections()
+    sim = ed.simulation_for(ds, ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(m[1], m[2]) for m in mix])
+    nd = len(ds)
+    n_e0 = sum(m[1].n for m in mix)
+    n_i0 = sum(m[2].n for m in mix)
+    del mix
+    chunk = BATCH_STEPS_PER_CHUNK
+    for _ in range(args.warmup):
+        sim.step(chunk, measure=True)
+    sim.synchronize()
+    tot = lambda: [sum(sim.counters(k)[c] for k in range(nd)) for c in ("push_e", "push_i")]
+    c0 = tot()
+    ms = 0.0
+    for _ in range(args.steps):
+        with torch.cuda.stream(sim.stream):
+            flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(sim.stream)
+        sim.step(chunk, measure=True)
+        b.record(sim.stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    c1 = tot()
+    ps = (c1[0] - c0[0]) + (c1[1] - c0[1])
+    p0 = tot()
+    ms_k, launches = sim.profile_steps(400, measure=True)
+    p1 = tot()
+    per_launch = (p1[0] - p0[0]) / max(launches[0], 1)
+    dur_s = ms_k[0] / max(launches[0], 1) / 1000.0
+    achieved = BYTES_PER_PUSH_FP32 * per_launch / dur_s / 1e9
+    sim.close()
+    return {"workload": f"{nd} independent 13.56 MHz Ar CCPs, seed 1000+k: gap U[1.5,5] cm, p logU[2,50] Pa, "
+                        f"V0 U[100,500] V, N_G U{{200..800}}, n logU[1e4,2e6] per species, steady-shape states",
+            "particles_e0": int(n_e0), "particles_i0": int(n_i0),
+            "value": ps / (ms / 1000.0), "unit": UNIT, "time_steps_per_bench_step": chunk,
+            "us_per_time_step": 1000.0 * ms / (args.steps * chunk),
+            "gpu_launches": int(args.steps * (2 * chunk + chunk // ds[0].ion_subcycle)),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_push<float, electrons>",
+                         "bytes_per_particle_step": BYTES_PER_PUSH_FP32, "particles_per_launch": per_launch,
+                         "avg_launch_us": dur_s * 1e6, "peak_kind": peak_kind,
+                         "kernel_time_share": {k: float(v) / max(float(ms_k.sum()), 1e-12)
+                                               for k, v in zip(("push_e", "push_i", "finalize"), ms_k)}}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -277,6 +343,8 @@ def run_ours(args):
         e2e = {"value": tot_ps / tot_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": reps, "note": "load particles from host FP64 arrays + 1 RF cycle + diagnostics read-back"}
 
+    batched = None if (args.no_batched or ws > 1) else run_batched(args, peak, peak_kind, flush)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(d, e, i)
@@ -302,6 +370,8 @@ def run_ours(args):
         }
         if e2e:
             line["e2e"] = e2e
+        if batched:
+            line["batched"] = batched
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

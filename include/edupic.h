@@ -213,6 +213,115 @@ int edupic_reset_diagnostics(edupic_sim *sim, int d);
 int edupic_save_state(edupic_sim *sim, int d, const char *path);
 int edupic_load_state(edupic_sim *sim, int d, const char *path);
 
+/* ---------------------------------------------------------------- request server */
+
+/* Continuous batching of independent discharge simulations on one GPU.
+ * (The paper runs one simulation per process and has no counterpart: its
+ * program flow of init, N RF cycles and read-out, Sec. 3.5 and Algorithm 1,
+ * is what each request asks for.)
+ *
+ * A server keeps up to max_slots requests resident.  Each request is a full
+ * simulation (edupic_params, initial particles, n_cycles RF cycles with the
+ * diagnostics of Sec. 3.5 accumulated over the whole run).  The particle
+ * and grid memory of a request is carved from the caller's arena when it is
+ * admitted and returned when it finishes, so the arena size is the HBM
+ * budget.  All running requests advance together, one push launch per
+ * species and one finalize launch per time step, and each stops at its own
+ * target step: a request's results are the same whatever else runs beside
+ * it.  Requests are admitted in submission order at ion-subcycle boundaries
+ * while a slot and enough arena memory are free. */
+typedef struct edupic_server edupic_server;
+
+typedef struct {
+    int max_slots;     /* requests resident at once, 1..EDUPIC_MAX_DISCHARGES */
+    int max_grid;      /* largest N_G a request may use, 3..EDUPIC_MAX_GRID */
+    int max_eepf_bins; /* largest EEPF bin count, 1..EDUPIC_MAX_EEPF_BINS */
+    int ion_subcycle;  /* N_SUB shared by every request */
+    int cs_entries;    /* cross-section table length shared by every request */
+    int reserved;
+} edupic_server_config;
+
+#define EDUPIC_REQ_QUEUED 0
+#define EDUPIC_REQ_RUNNING 1
+#define EDUPIC_REQ_DONE 2
+#define EDUPIC_REQ_FAILED 3
+
+typedef struct {
+    int state;            /* EDUPIC_REQ_* */
+    int status;           /* EDUPIC_OK, or the error that ended the request */
+    int slot;             /* slot it runs / ran in, -1 while queued */
+    int reserved;
+    int64_t steps_target; /* n_cycles * N_T */
+    int64_t steps_done;   /* time steps run (final value once done) */
+    int64_t n_e, n_i;     /* particle counts: initial while queued/running, final once done */
+    int64_t bytes;        /* arena bytes the request holds while running */
+    double t_submit, t_admit, t_done; /* seconds on the server's monotonic clock, -1 if not yet */
+} edupic_request_info;
+
+typedef struct {
+    double now;           /* seconds since the server was created */
+    int64_t steps_run;    /* time steps enqueued since creation */
+    int64_t heap_bytes, heap_used;
+    int running, queued;
+} edupic_server_stats_t;
+
+/* Arena bytes for a server with `heap_bytes` of request memory. */
+int edupic_server_arena_bytes(const edupic_server_config *cfg, int precision, size_t heap_bytes, size_t *bytes);
+
+/* Create a server in a caller-owned device arena (256-byte aligned; the
+ * caller keeps it alive until edupic_server_destroy).  The part of the arena
+ * beyond the fixed shared region is the request heap.  Work runs on
+ * cuda_stream (a non-default stream: steps are replayed as CUDA graphs).
+ * EDUPIC_ENOMEM if the arena cannot hold the shared region. */
+int edupic_server_create(const edupic_server_config *cfg, int precision, void *device_arena, size_t arena_bytes,
+                         void *cuda_stream, edupic_server **out);
+int edupic_server_destroy(edupic_server *srv);
+
+/* Cross sections shared by all requests (as edupic_set_cross_sections);
+ * EDUPIC_ESTATE while a request is running. */
+int edupic_server_set_cross_sections(edupic_server *srv, int species, int n_proc, int n_entries, double de_ev,
+                                     const double *sigma_m2);
+
+/* Arena bytes a request with these parameters holds while it runs. */
+int edupic_server_request_bytes(const edupic_server *srv, const edupic_params *p, size_t *bytes);
+
+/* Queue a request: parameters p (checked as edupic_create does, plus
+ * n_grid <= max_grid, eepf_bins <= max_eepf_bins and the server's N_SUB and
+ * table length), n_cycles >= 1 RF cycles, and the initial particles:
+ * e[0..3] = x, vx, vy, vz of n_e electrons and i[0..3] of n_i ions, host
+ * FP64 arrays copied during the call (positions in [0, L]).  Returns a
+ * ticket.  EDUPIC_ENOMEM if the request can never fit the arena,
+ * EDUPIC_ECAPACITY if a count exceeds its capacity. */
+int edupic_server_submit(edupic_server *srv, const edupic_params *p, int n_cycles, int64_t n_e,
+                         const double *const e[4], int64_t n_i, const double *const i[4], uint64_t *ticket);
+
+/* One scheduling round: wait for the steps enqueued by the previous call,
+ * retire requests that reached their target step (their results are read
+ * back to host memory and their arena memory freed), admit queued requests,
+ * then enqueue n_subcycles ion subcycles (n_subcycles * N_SUB time steps)
+ * for every running request and return without waiting for them.  Writes
+ * the running and queued counts after admission. */
+int edupic_server_advance(edupic_server *srv, int n_subcycles, int *n_running, int *n_queued);
+
+/* State, counts and timestamps of a request. */
+int edupic_server_info(edupic_server *srv, uint64_t ticket, edupic_request_info *info);
+
+/* Results of a finished request, as edupic_get_diagnostics and
+ * edupic_get_counters give them: time-averaged n_e, n_i, phi (n_grid each),
+ * EEPF counts (eepf_bins), IFED counts per electrode (ifed_bins each),
+ * counters and the number of measured steps.  Any pointer may be NULL.
+ * EDUPIC_ESTATE while the request is queued or running; the request's error
+ * if it failed. */
+int edupic_server_result(edupic_server *srv, uint64_t ticket, double *ne_avg, double *ni_avg, double *phi_avg,
+                         int64_t *eepf_counts, int64_t *ifed_pow_counts, int64_t *ifed_gnd_counts,
+                         int64_t counters[EDUPIC_N_COUNTERS], int64_t *measured_steps);
+
+/* Forget a finished or failed request (its host-side results). */
+int edupic_server_release(edupic_server *srv, uint64_t ticket);
+
+/* Clock, step count, heap use and slot occupancy. */
+int edupic_server_stats(edupic_server *srv, edupic_server_stats_t *out);
+
 /* ---------------------------------------------------------------- no-allocation entry point */
 
 /* Densities, potential and field of given particle positions, computed

@@ -1,12 +1,13 @@
 """In-tree build of the CUDA library (nvcc, sm_103a only).
 
-Four translation units are compiled in parallel and linked into
+Five translation units are compiled in parallel and linked into
 ``paper_2103_09642_gb300/_build/libedupic_gb300.so``:
 
 * ``kernels_f64.cu``  FP64 particle mode, ``-fmad=false`` (no FMA contraction)
 * ``kernels_f32.cu``  FP32 particle mode, FMA and fast division allowed
 * ``edupic_api.cu``   host orchestration of the C ABI (``include/edupic.h``)
 * ``edupic_noalloc.cu``  the entry point that works in a fixed static scratch
+* ``edupic_server.cu``  the request server (continuous batching)
 """
 from __future__ import annotations
 
@@ -28,8 +29,9 @@ UNITS = {
     "kernels_f32.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "edupic_api.cu": ["-fmad=false"],
     "edupic_noalloc.cu": ["-fmad=false"],
+    "edupic_server.cu": ["-fmad=false"],
 }
-HEADERS = ("edupic_internal.h", "edupic_kernels.cuh", "edupic_launch.cuh")
+HEADERS = ("edupic_internal.h", "edupic_kernels.cuh", "edupic_launch.cuh", "edupic_host.h")
 
 
 def nvcc() -> str:

@@ -4,20 +4,21 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
 
-#include "edupic_internal.h"
+#include "edupic_host.h"
 
 using namespace edupic;
+using namespace edupic::host;
 
-namespace {
+namespace edupic {
+namespace host {
 
-constexpr size_t kAlign = 256;
-constexpr int kTileAlign = 1024;  // particle arrays padded to whole tiles
 constexpr double kQE = 1.602176634e-19;
 constexpr double kME = 9.1093837015e-31;
 constexpr double kEPS0 = 8.8541878128e-12;
@@ -29,13 +30,6 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 long long padded(long long cap) { return (cap + kTileAlign - 1) / kTileAlign * kTileAlign; }
 
-// Byte layout of one discharge inside the arena (offsets from its base).
-struct Layout {
-    size_t x[2], vx[2], vy[2], vz[2];
-    size_t q_e, q_i, acc_e, acc_i, n_e, n_i, phi, ef, ef_t, f_cur, fs, sum_qe, sum_qi, sum_f, avg;
-    size_t eepf, ifed_pow, ifed_gnd, holes[2], prod_parent, sort_buf, prod_x, prod_ve[3], prod_vi[3], vdrive;
-    size_t bytes;
-};
 
 Layout layout_of(const edupic_params &p, size_t elem)
 {
@@ -118,48 +112,12 @@ int check_params(int nd, const edupic_params *ps, int precision)
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? EDUPIC_OK : EDUPIC_ECUDA; }
 
-}  // namespace
+}  // namespace host
+}  // namespace edupic
 
-struct edupic_sim {
-    int nd = 0, precision = 0;
-    size_t elem = 8;
-    std::vector<edupic_params> params;
-    std::vector<Layout> layouts;
-    std::vector<size_t> base;  // arena offset of each discharge
-    std::vector<DischargeDev> desc;
-    unsigned char *arena = nullptr;
-    size_t arena_bytes = 0;
-    DischargeDev *d_desc = nullptr;
-    Ctrl *d_ctrl = nullptr;  // packed array: one per discharge
-    void *cs_sig[2] = {nullptr, nullptr};
-    void *cs_thr[2] = {nullptr, nullptr};
-    void *cs_max[2] = {nullptr, nullptr};
-    bool cs_set[2] = {false, false};
-    cudaStream_t stream = nullptr;
-    int ng_max = 0, eepf_max = 0, nsub = 1, nt_common = -1;
-    int phase = 0;  // common step index modulo N_SUB
-    int cs_shift_pending[2] = {0, 0};
-    int grid[2] = {0, 0};
-    bool graphs = true;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
 
-    ~edupic_sim()
-    {
-        for (auto &g : graph)
-            if (g) cudaGraphExecDestroy(g);
-    }
-    void drop_graphs()
-    {
-        for (auto &g : graph)
-            if (g) {
-                cudaGraphExecDestroy(g);
-                g = nullptr;
-            }
-    }
-    Ctrl *ctrl(int d) const { return desc[d].ctrl; }
-};
-
-namespace {
+namespace edupic {
+namespace host {
 
 size_t shared_bytes(int nd, size_t elem, int cs_entries)
 {
@@ -245,6 +203,7 @@ void fill_desc(edupic_sim *S, int d)
     D.cs_n_e = S->desc.size() > (size_t)d ? S->desc[d].cs_n_e : 1;
     D.cs_n_i = S->desc.size() > (size_t)d ? S->desc[d].cs_n_i : 1;
     D.active = 1;
+    D.stop_step = LLONG_MAX;
     D.cap[0] = p.capacity_e;
     D.cap[1] = p.capacity_i;
     D.seed = p.seed;
@@ -298,6 +257,52 @@ int upload_desc(edupic_sim *S)
                                     S->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
     return cuda_status(e);
+}
+
+int upload_desc_one(edupic_sim *S, int d)
+{
+    cudaError_t e = cudaMemcpyAsync(S->d_desc + d, &S->desc[d], sizeof(DischargeDev), cudaMemcpyHostToDevice,
+                                    S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    return cuda_status(e);
+}
+
+void carve_shared(edupic_sim *S, int cs_entries)
+{
+    size_t o = 0;
+    S->d_desc = reinterpret_cast<DischargeDev *>(S->arena);
+    o = align_up(sizeof(DischargeDev) * S->nd, kAlign);
+    S->d_ctrl = reinterpret_cast<Ctrl *>(S->arena + o);
+    o += align_up(sizeof(Ctrl) * S->nd, kAlign);
+    for (int sp = 0; sp < 2; ++sp) {
+        S->cs_sig[sp] = S->arena + o;
+        o += align_up((size_t)cs_entries * S->elem, kAlign);
+    }
+    for (int sp = 0; sp < 2; ++sp) {
+        S->cs_thr[sp] = S->arena + o;
+        o += align_up((size_t)cs_entries * 2 * S->elem, kAlign);
+    }
+    for (int sp = 0; sp < 2; ++sp) {
+        S->cs_max[sp] = S->arena + o;
+        o += align_up((size_t)kCoarse * S->elem, kAlign);
+    }
+}
+
+int setup_grid(edupic_sim *S)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return EDUPIC_ECUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int sp = 0; sp < 2; ++sp) {
+        const int eb = sp == 0 ? S->eepf_max : 0;
+        const size_t smem = S->precision == EDUPIC_FP32 ? Launch<float>::push_smem(S->nd, S->ng_max, eb)
+                                                        : Launch<double>::push_smem(S->nd, S->ng_max, eb);
+        const int nb = S->precision == EDUPIC_FP32 ? Launch<float>::push_blocks_per_sm(sp, smem)
+                                                   : Launch<double>::push_blocks_per_sm(sp, smem);
+        if (nb < 1) return EDUPIC_ECUDA;
+        S->grid[sp] = nb * std::max(sms, 1);
+    }
+    return EDUPIC_OK;
 }
 
 template <typename T>
@@ -454,9 +459,17 @@ int refresh_species(edupic_sim *S, int d, int sp)
     return cuda_status(e);
 }
 
+int upload_species(edupic_sim *S, int d, int sp, int64_t n, const double *const src[4])
+{
+    if (n == 0) return EDUPIC_OK;
+    return S->precision == EDUPIC_FP32 ? upload_particles<float>(S, d, sp, n, src)
+                                       : upload_particles<double>(S, d, sp, n, src);
+}
+
 bool valid_d(const edupic_sim *S, int d) { return S && d >= 0 && d < S->nd; }
 
-}  // namespace
+}  // namespace host
+}  // namespace edupic
 
 extern "C" {
 
@@ -498,24 +511,9 @@ int edupic_create(int nd, const edupic_params *params, int precision, void *devi
         S->eepf_max = std::max(S->eepf_max, params[d].eepf_bins);
         if (params[d].steps_per_cycle != S->nt_common) S->nt_common = -1;
     }
-    // shared region: descriptors, then the two cross-section tables
-    size_t o = 0;
-    S->d_desc = reinterpret_cast<DischargeDev *>(S->arena);
-    o = align_up(sizeof(DischargeDev) * nd, kAlign);
-    S->d_ctrl = reinterpret_cast<Ctrl *>(S->arena + o);
-    o += align_up(sizeof(Ctrl) * nd, kAlign);
-    for (int sp = 0; sp < 2; ++sp) {
-        S->cs_sig[sp] = S->arena + o;
-        o += align_up((size_t)params[0].cs_entries * S->elem, kAlign);
-    }
-    for (int sp = 0; sp < 2; ++sp) {
-        S->cs_thr[sp] = S->arena + o;
-        o += align_up((size_t)params[0].cs_entries * 2 * S->elem, kAlign);
-    }
-    for (int sp = 0; sp < 2; ++sp) {
-        S->cs_max[sp] = S->arena + o;
-        o += align_up((size_t)kCoarse * S->elem, kAlign);
-    }
+    // shared region: descriptors, packed controls, the two cross-section tables
+    carve_shared(S, params[0].cs_entries);
+    size_t o = shared_bytes(nd, S->elem, params[0].cs_entries);
     for (int d = 0; d < nd; ++d) {
         S->layouts.push_back(layout_of(params[d], S->elem));
         S->base.push_back(o);
@@ -533,20 +531,10 @@ int edupic_create(int nd, const edupic_params *params, int precision, void *devi
         delete S;
         return rc;
     }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int sp = 0; sp < 2; ++sp) {
-        const int eb = sp == 0 ? S->eepf_max : 0;
-        const size_t smem = precision == EDUPIC_FP32 ? Launch<float>::push_smem(nd, S->ng_max, eb)
-                                                     : Launch<double>::push_smem(nd, S->ng_max, eb);
-        int nb = precision == EDUPIC_FP32 ? Launch<float>::push_blocks_per_sm(sp, smem)
-                                          : Launch<double>::push_blocks_per_sm(sp, smem);
-        if (nb < 1) {
-            delete S;
-            return EDUPIC_ECUDA;
-        }
-        S->grid[sp] = nb * std::max(sms, 1);
+    rc = setup_grid(S);
+    if (rc) {
+        delete S;
+        return rc;
     }
     // the field of step 0 (empty discharge: the vacuum field of V(0))
     for (int d = 0; d < nd && rc == EDUPIC_OK; ++d) {
@@ -611,9 +599,7 @@ int edupic_load_particles(edupic_sim *S, int d, int species, int64_t n, const do
         if (!(x[j] >= 0.0 && x[j] <= L) || !std::isfinite(vx[j]) || !std::isfinite(vy[j]) || !std::isfinite(vz[j]))
             return EDUPIC_EINVAL;
     const double *src[4] = {x, vx, vy, vz};
-    int rc = n == 0 ? EDUPIC_OK
-                    : (S->precision == EDUPIC_FP32 ? upload_particles<float>(S, d, species, n, src)
-                                                   : upload_particles<double>(S, d, species, n, src));
+    int rc = upload_species(S, d, species, n, src);
     if (rc) return rc;
     long long nn = n;
     cudaError_t e = cudaMemcpyAsync(&S->ctrl(d)->n[species], &nn, sizeof(nn), cudaMemcpyHostToDevice, S->stream);

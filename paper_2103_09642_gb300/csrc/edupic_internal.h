@@ -67,6 +67,7 @@ struct DischargeDev {
     int ng, nt, nsub, n_harm, eepf_bins, ifed_bins, cs_n_e, cs_n_i;
     int active;
     int pad0;
+    long long stop_step;       // the discharge is frozen (skipped) once its step count reaches this
     long long cap[2];
     unsigned long long seed;
     // particle SoA (T = float or double)

@@ -676,7 +676,8 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         for (int base = 0; base < nd; base += blockDim.x) {
             const int d = base + tid;
             int cnt = 0;
-            if (d < nd && DD[d].active) cnt = (int)((ctrls[d].n[SP] + TILE - 1) / TILE);
+            if (d < nd && DD[d].active && ctrls[d].step < DD[d].stop_step)
+                cnt = (int)((ctrls[d].n[SP] + TILE - 1) / TILE);
             int tot;
             const int ex = group_excl_scan(cnt, sW, tot, tid, blockDim.x, 1);
             if (d < nd) sPre[d] = running + ex;
@@ -1243,7 +1244,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDe
     __syncthreads();
     pdl_wait();
     pdl_launch_next();
-    if (!D.active) return;
+    if (!D.active || D.ctrl->step >= D.stop_step) return;
     Ctrl *C = D.ctrl;
     const long long next = C->step + 1;
     if (threadIdx.x < kGroupA) {

@@ -22,12 +22,14 @@ FP64, FP32 = 0, 1
 ELECTRONS, IONS = 0, 1
 MAX_HARMONICS = 4
 N_COUNTERS = 16
-STEP_EVENTS = 8192
+STEP_EVENTS = 65536
 COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela", "coll_e_exc",
                  "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped",
                  "push_e", "push_i")
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECAPACITY", -4: "ECUDA", -5: "ESTATE", -6: "ENAN",
-          -7: "EIO", -8: "ETIMEOUT"}
+          -7: "EIO", -8: "ETIMEOUT", -9: "ETOOBIG"}
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+REQ_STATES = {REQ_QUEUED: "queued", REQ_RUNNING: "running", REQ_DONE: "done", REQ_FAILED: "failed"}
 
 
 class EdupicError(RuntimeError):
@@ -69,6 +71,23 @@ def to_params(d: Discharge, cs_entries: int) -> Params:
     return p
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("max_grid", ctypes.c_int32), ("max_eepf_bins", ctypes.c_int32),
+                ("ion_subcycle", ctypes.c_int32), ("cs_entries", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("steps_target", ctypes.c_int64), ("steps_done", ctypes.c_int64),
+                ("n_e", ctypes.c_int64), ("n_i", ctypes.c_int64), ("bytes", ctypes.c_int64),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("now", ctypes.c_double), ("steps_run", ctypes.c_int64), ("heap_bytes", ctypes.c_int64),
+                ("heap_used", ctypes.c_int64), ("running", ctypes.c_int32), ("queued", ctypes.c_int32)]
+
+
 _lib = None
 _D = ctypes.POINTER(ctypes.c_double)
 _Q = ctypes.POINTER(ctypes.c_int64)
@@ -106,6 +125,22 @@ def load_library(path: str = LIB_PATH):
         "edupic_save_state": ([_VP, ctypes.c_int, ctypes.c_char_p]),
         "edupic_load_state": ([_VP, ctypes.c_int, ctypes.c_char_p]),
     }
+    SC = ctypes.POINTER(ServerConfig)
+    D4 = _D * 4
+    sig.update({
+        "edupic_server_arena_bytes": ([SC, ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+        "edupic_server_create": ([SC, ctypes.c_int, _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+        "edupic_server_destroy": ([_VP]),
+        "edupic_server_set_cross_sections": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]),
+        "edupic_server_request_bytes": ([_VP, P, ctypes.POINTER(ctypes.c_size_t)]),
+        "edupic_server_submit": ([_VP, P, ctypes.c_int, ctypes.c_int64, D4, ctypes.c_int64, D4,
+                                  ctypes.POINTER(ctypes.c_uint64)]),
+        "edupic_server_advance": ([_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "edupic_server_info": ([_VP, ctypes.c_uint64, ctypes.POINTER(RequestInfo)]),
+        "edupic_server_result": ([_VP, ctypes.c_uint64, _D, _D, _D, _Q, _Q, _Q, _Q, _Q]),
+        "edupic_server_release": ([_VP, ctypes.c_uint64]),
+        "edupic_server_stats": ([_VP, ctypes.POINTER(ServerStats)]),
+    })
     for name, args in sig.items():
         f = getattr(L, name)
         f.argtypes = args
@@ -286,3 +321,128 @@ def simulation_for(discharges: Iterable, precision: int = FP64, sigma=None, de_e
             sim.load(d, ELECTRONS, e)
             sim.load(d, IONS, i)
     return sim
+
+
+def server_arena_bytes(heap_bytes: int, max_slots: int = 64, max_grid: int = 800, max_eepf_bins: int = 2000,
+                       ion_subcycle: int = 20, cs_entries: int = 1_000_000, precision: int = FP32) -> int:
+    """Arena bytes of a server with `heap_bytes` of request memory."""
+    L = load_library()
+    cfg = ServerConfig(max_slots, max_grid, max_eepf_bins, ion_subcycle, cs_entries, 0)
+    b = ctypes.c_size_t(0)
+    _ck(L.edupic_server_arena_bytes(ctypes.byref(cfg), precision, int(heap_bytes), ctypes.byref(b)), "server_arena")
+    return int(b.value)
+
+
+class Server:
+    """Continuous-batching request server (edupic_server_* of the C ABI).
+
+    ``budget_bytes`` of device memory (one torch uint8 tensor) hold the
+    shared region and the request heap; requests are admitted while a slot
+    and heap memory are free.  ``advance(k)`` retires finished requests,
+    admits queued ones and enqueues k ion subcycles for all running ones.
+    """
+
+    def __init__(self, budget_bytes: int, max_slots: int = 64, max_grid: int = 800, max_eepf_bins: int = 2000,
+                 ion_subcycle: int = 20, cs_entries: int = 1_000_000, precision: int = FP32, stream=None,
+                 device: Optional[str] = None):
+        import torch
+
+        self._torch = torch
+        self.L = load_library()
+        self.precision = precision
+        self.cs_entries = cs_entries
+        cfg = ServerConfig(max_slots, max_grid, max_eepf_bins, ion_subcycle, cs_entries, 0)
+        self._cfg = cfg
+        need = ctypes.c_size_t(0)
+        _ck(self.L.edupic_server_arena_bytes(ctypes.byref(cfg), precision, 0, ctypes.byref(need)), "server_arena")
+        if budget_bytes < need.value:
+            raise EdupicError(-2, f"server budget below the shared region ({need.value} B)")
+        dev = torch.device(device) if device else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self.arena = torch.empty(int(budget_bytes), dtype=torch.uint8, device=dev)
+        h = _VP()
+        with torch.cuda.device(dev):
+            _ck(self.L.edupic_server_create(ctypes.byref(cfg), precision, ctypes.c_void_p(self.arena.data_ptr()),
+                                            int(budget_bytes), ctypes.c_void_p(self.stream.cuda_stream),
+                                            ctypes.byref(h)), "server_create")
+        self._h = h
+        self._req = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.L.edupic_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_cross_sections(self, species: int, sigma: np.ndarray, de_ev: float):
+        s = np.ascontiguousarray(sigma, dtype=np.float64)
+        _ck(self.L.edupic_server_set_cross_sections(self._h, species, s.shape[0], s.shape[1], de_ev, _ptr(s)),
+            "server_set_cross_sections")
+
+    def request_bytes(self, d: Discharge) -> int:
+        p = to_params(d, self.cs_entries)
+        b = ctypes.c_size_t(0)
+        _ck(self.L.edupic_server_request_bytes(self._h, ctypes.byref(p), ctypes.byref(b)), "request_bytes")
+        return int(b.value)
+
+    def submit(self, d: Discharge, e: Particles, i: Particles, n_cycles: int) -> int:
+        p = to_params(d, self.cs_entries)
+        arrs = []
+        ptrs = []
+        for parts in (e, i):
+            a = [np.ascontiguousarray(getattr(parts, k), dtype=np.float64) for k in ("x", "vx", "vy", "vz")]
+            arrs.append(a)
+            ptrs.append((_D * 4)(*[_ptr(v) for v in a]))
+        t = ctypes.c_uint64(0)
+        _ck(self.L.edupic_server_submit(self._h, ctypes.byref(p), int(n_cycles), arrs[0][0].size, ptrs[0],
+                                        arrs[1][0].size, ptrs[1], ctypes.byref(t)), "server_submit")
+        self._req[int(t.value)] = d
+        return int(t.value)
+
+    def advance(self, n_subcycles: int = 1):
+        r, q = ctypes.c_int(0), ctypes.c_int(0)
+        _ck(self.L.edupic_server_advance(self._h, int(n_subcycles), ctypes.byref(r), ctypes.byref(q)),
+            "server_advance")
+        return r.value, q.value
+
+    def info(self, ticket: int) -> dict:
+        x = RequestInfo()
+        _ck(self.L.edupic_server_info(self._h, ticket, ctypes.byref(x)), "server_info")
+        return {k: getattr(x, k) for k, _ in RequestInfo._fields_ if k != "reserved"}
+
+    def result(self, ticket: int) -> dict:
+        d = self._req[ticket]
+        ng = d.n_grid
+        avg = [np.zeros(ng) for _ in range(3)]
+        e = np.zeros(d.eepf_bins, dtype=np.int64)
+        ip = np.zeros(d.ifed_bins, dtype=np.int64)
+        ig = np.zeros(d.ifed_bins, dtype=np.int64)
+        c = np.zeros(N_COUNTERS, dtype=np.int64)
+        m = ctypes.c_int64()
+        _ck(self.L.edupic_server_result(self._h, ticket, *[_ptr(v) for v in avg],
+                                        *[_ptr(v, ctypes.c_int64) for v in (e, ip, ig, c)], ctypes.byref(m)),
+            "server_result")
+        return dict(measured_steps=m.value, n_e=avg[0], n_i=avg[1], phi=avg[2], eepf_counts=e,
+                    ifed_pow_counts=ip, ifed_gnd_counts=ig,
+                    counters={k: int(c[j]) for j, k in enumerate(COUNTER_NAMES)})
+
+    def release(self, ticket: int):
+        _ck(self.L.edupic_server_release(self._h, ticket), "server_release")
+        self._req.pop(ticket, None)
+
+    def stats(self) -> dict:
+        x = ServerStats()
+        _ck(self.L.edupic_server_stats(self._h, ctypes.byref(x)), "server_stats")
+        return {k: getattr(x, k) for k, _ in ServerStats._fields_}

@@ -241,25 +241,27 @@ def dual_frequency(seed: int = 1, v_lf: float = 300.0, n: int = 2_000_000,
     return d, e, i
 
 
+def draw_discharge(rng: np.random.Generator, seed: int, n_min: float = 1e4, n_max: float = 2e6,
+                   scale: float = 1.0, steps_per_cycle: int = 4000) -> Tuple[Discharge, Particles, Particles]:
+    """One 13.56 MHz discharge with gap 1.5-5 cm, pressure 2-50 Pa
+    (log-uniform), voltage 100-500 V, N_G 200-800 and particle count
+    n_min-n_max per species (log-uniform), in a steady-shape state.  `scale`
+    multiplies the particle count (small test versions)."""
+    gap = rng.uniform(0.015, 0.05)
+    p = math.exp(rng.uniform(math.log(2.0), math.log(50.0)))
+    v0 = rng.uniform(100.0, 500.0)
+    ng = int(rng.integers(200, 801))
+    n = max(16, int(scale * math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+    density = 2.8e15 * (p / 10.0) ** 0.5
+    w = density * 1e-4 * gap / n
+    d = Discharge(gap_m=gap, pressure_pa=p, weight=w, n_grid=ng, steps_per_cycle=steps_per_cycle,
+                  harmonics=((13.56e6, v0),), seed=seed, capacity=int(n * 2.0) + 4096)
+    e, i = steady_shape(matched_electrons(n, sheath_fraction(d, n)), n, d, rng, te_ev=rng.uniform(2.0, 3.0))
+    return d, e, i
+
+
 def batch_mix(n_discharges: int = 64, seed0: int = 1000, n_min: float = 1e4, n_max: float = 2e6,
               scale: float = 1.0) -> List[Tuple[Discharge, Particles, Particles]]:
-    """Independent 13.56 MHz discharges with seed-drawn gap 1.5-5 cm, pressure
-    2-50 Pa (log-uniform), voltage 100-500 V, N_G 200-800 and particle count
-    n_min-n_max per species (log-uniform), each in a steady-shape state.
-    `scale` multiplies every particle count (small test versions)."""
-    out = []
-    for k in range(n_discharges):
-        rng = np.random.default_rng(seed0 + k)
-        gap = rng.uniform(0.015, 0.05)
-        p = math.exp(rng.uniform(math.log(2.0), math.log(50.0)))
-        v0 = rng.uniform(100.0, 500.0)
-        ng = int(rng.integers(200, 801))
-        n = max(16, int(scale * math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
-        density = 2.8e15 * (p / 10.0) ** 0.5
-        w = density * 1e-4 * gap / n
-        d = Discharge(gap_m=gap, pressure_pa=p, weight=w, n_grid=ng,
-                      harmonics=((13.56e6, v0),), seed=seed0 + k,
-                      capacity=int(n * 2.0) + 4096)
-        e, i = steady_shape(matched_electrons(n, sheath_fraction(d, n)), n, d, rng, te_ev=rng.uniform(2.0, 3.0))
-        out.append((d, e, i))
-    return out
+    """Independent discharges drawn by draw_discharge with seeds seed0 + k."""
+    return [draw_discharge(np.random.default_rng(seed0 + k), seed0 + k, n_min, n_max, scale)
+            for k in range(n_discharges)]

@@ -8,7 +8,6 @@
 namespace edupic {
 
 constexpr int kThreads = 256;          // particle-kernel block size
-constexpr int kStages = 3;             // particle tiles in flight per block (bulk-copy ring)
 constexpr int kFinalizeThreads = 512;  // one CTA per discharge for compaction + field solve
 constexpr int kGroupA = 128;           // finalize threads doing compaction and append
 constexpr int kGroupB = kFinalizeThreads - kGroupA;  // finalize threads doing the field solve

@@ -345,6 +345,11 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
@@ -440,7 +445,7 @@ __device__ __forceinline__ __int128 group_sum128(__int128 v, __int128 *s_w, int 
 // them (Algorithm 6 after the test).  It re-derives the table index and, for
 // Ar+, the thermal partner from the same counter-based draws, so the result
 // is the same as executing the collision in place.
-constexpr int kQueue = 4096;  // queued colliders per block before a drain
+constexpr int kWarpQueue = 512;  // queued colliders per warp before the warp drains them
 
 // e- + Ar collision of the particle in `slot` (post-push state in memory),
 // including the append record and the deposition of an ionisation pair.
@@ -610,13 +615,21 @@ __device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy,
 }
 
 // ---------------------------------------------------------------- particle kernel
-// Dynamic shared memory: [tile ring: kStages x 4 arrays x TILE T][coarse
+// Tiles in the shared-memory ring: 4 in FP32 (16 KB each), 3 in FP64 (also
+// 16 KB each), so that two blocks fit an SM in both modes.
+template <typename T>
+__host__ __device__ constexpr int ring_stages()
+{
+    return is_f64<T>() ? 3 : 4;
+}
+
+// Dynamic shared memory: [tile ring: stages x 4 arrays x TILE T][coarse
 // sigma_max: kCoarse T][E pairs: ng_max T2][deposition: 3 x ng_max u32]
 // [tile prefix: nd+1 int].
 template <typename T>
 __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eepf_max)
 {
-    return (size_t)kStages * 4 * kThreads * VecOf<T>::n * sizeof(T) + (size_t)kCoarse * sizeof(T) +
+    return (size_t)ring_stages<T>() * 4 * kThreads * VecOf<T>::n * sizeof(T) + (size_t)kCoarse * sizeof(T) +
            (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 12 + (size_t)(nd + 1) * 4 + 0 * (size_t)eepf_max;
 }
 
@@ -628,10 +641,12 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     using T2 = typename VecOf<T>::pair;
     constexpr int VEC = VecOf<T>::n;  // slots per thread: one Philox test block
     constexpr int TILE = kThreads * VEC;
-    static_assert(kQueue % TILE == 0, "the collider queue holds whole tiles");
+    constexpr int S = ring_stages<T>();
+    constexpr int kWarps = kThreads / 32;
+    static_assert(kWarpQueue >= 2 * 32 * VEC, "a warp queue takes at least two tiles of colliders");
     extern __shared__ __align__(128) unsigned char smem[];
     T *sRing = reinterpret_cast<T *>(smem);  // [stage][array x, vx, vy, vz][TILE]
-    T *sC = sRing + kStages * 4 * TILE;
+    T *sC = sRing + S * 4 * TILE;
     T2 *sE2 = reinterpret_cast<T2 *>(sC + kCoarse);
     DepAcc acc;
     acc.cnt = reinterpret_cast<unsigned int *>(sE2 + ng_max);
@@ -641,12 +656,14 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     (void)eepf_max;
     __shared__ unsigned int sCnt[EDUPIC_N_COUNTERS];
     __shared__ int sW[33];
-    __shared__ int sQueue[kQueue];
-    __shared__ int sQn;
+    __shared__ int sQueue[kWarps][kWarpQueue];  // colliders queued by each warp
+    __shared__ int sQn[kWarps];
     __shared__ DischargeDev sD;  // descriptor of the discharge being processed
-    __shared__ __align__(8) uint64_t sBar[kStages];
+    __shared__ __align__(8) uint64_t sFull[S];   // stage holds its tile (bulk-copy transactions)
+    __shared__ __align__(8) uint64_t sEmpty[S];  // every warp has read the stage
 
     const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
     // set-up data that does not depend on the preceding kernel, fetched
     // before waiting for it: the coarse table (shared by all discharges) and
     // the descriptor of discharge 0
@@ -658,9 +675,12 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         int *dd = reinterpret_cast<int *>(&sD);
         for (int i = tid; i < (int)(sizeof(DischargeDev) / 4); i += blockDim.x) dd[i] = src[i];
     }
+    if (tid < kWarps) sQn[tid] = 0;
     if (tid == 0) {
-        sQn = 0;
-        for (int k = 0; k < kStages; ++k) mbar_init(sBar + k, 1);
+        for (int k = 0; k < S; ++k) {
+            mbar_init(sFull + k, 1);
+            mbar_init(sEmpty + k, kWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (tid < EDUPIC_N_COUNTERS) sCnt[tid] = 0;
@@ -700,21 +720,23 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     T *X = nullptr, *VX = nullptr, *VY = nullptr, *VZ = nullptr;
     bool eepf_on = false;
 
-    // execute the queued collisions of the current discharge (all threads)
+    // execute the collisions queued by this warp (the 32 lanes of the warp;
+    // the particles were stored by lanes of the same warp, ordered by the
+    // warp barrier)
     auto drain = [&]() {
-        __syncthreads();
-        const int qn = sQn;
-        if (qn == 0) return;  // uniform: read after the barrier
+        __syncwarp();
+        const int qn = sQn[warp];
+        if (qn == 0) return;  // uniform across the warp: read after the warp barrier
         const RngKey key{s_lo, s_hi, k0, k1};
-        for (int i = tid; i < qn; i += blockDim.x) {
+        for (int i = lane; i < qn; i += 32) {
             if (SP == 0)
-                electron_collision<T>(*D, sQueue[i], key, idx_scale, cs_n, inv_dx, acc, sCnt);
+                electron_collision<T>(*D, sQueue[warp][i], key, idx_scale, cs_n, inv_dx, acc, sCnt);
             else
-                ion_collision<T>(*D, sQueue[i], key, idx_scale, cs_n, sCnt);
+                ion_collision<T>(*D, sQueue[warp][i], key, idx_scale, cs_n, sCnt);
         }
-        __syncthreads();
-        if (tid == 0) sQn = 0;
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) sQn[warp] = 0;
+        __syncwarp();
     };
 
     // add the block's deposition into the discharge's accumulator (and clear it)
@@ -753,7 +775,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         while (pt >= sPre[pcur + 1]) ++pcur;
         const DischargeDev *Dq = DD + pcur;
         const size_t off = (size_t)(pt - sPre[pcur]) * TILE;
-        uint64_t *bar = sBar + st;
+        uint64_t *bar = sFull + st;
         T *dst = sRing + (size_t)st * 4 * TILE;
         mbar_expect_tx(bar, 4u * TILE * (uint32_t)sizeof(T));
         bulk_load(dst, reinterpret_cast<const T *>(Dq->x[SP]) + off, TILE * sizeof(T), bar);
@@ -763,10 +785,10 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         ++pt;
     };
     if (tid == 0)
-        for (int k = 0; k < kStages && pt < t1; ++k) issue(k);
+        for (int k = 0; k < S && pt < t1; ++k) issue(k);
 
     for (int t = t0, it = 0; t < t1; ++t, ++it) {
-        const int st = it % kStages;
+        const int st = it % S;
         if (cur < 0 || t >= sPre[cur + 1]) {
             if (cur >= 0) flush(false);
             ++cur;
@@ -822,8 +844,8 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         const int tbase = (t - sPre[cur]) * TILE;
         if (tid == 0) atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_PUSH_E : EDUPIC_C_PUSH_I), (unsigned)min(TILE, n - tbase));
         const int base = tbase + tid * VEC;
-        // this tile's particles from the ring
-        if (!mbar_wait_bounded(sBar + st, (uint32_t)((it / kStages) & 1))) atomicOr(&D->ctrl->error, kErrTimeout);
+        // this tile's particles from the ring; each warp then marks the stage read
+        if (!mbar_wait_bounded(sFull + st, (uint32_t)((it / S) & 1))) atomicOr(&D->ctrl->error, kErrTimeout);
         {
             const T *rs = sRing + (size_t)st * 4 * TILE + tid * VEC;
             unpack(*reinterpret_cast<const V *>(rs), xa);
@@ -831,20 +853,25 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             unpack(*reinterpret_cast<const V *>(rs + 2 * TILE), vya);
             unpack(*reinterpret_cast<const V *>(rs + 3 * TILE), vza);
         }
-        __syncthreads();  // the stage is free: refill it with the tile kStages ahead
-        if (tid == 0 && pt < t1) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(sEmpty + st);
+        // the producer refills the stage read in the previous iteration (every
+        // warp marked it then, so this wait rarely blocks) with the tile S - 1
+        // ahead
+        if (tid == 0 && it > 0 && pt < t1) {
+            const int ps = (it - 1) % S;
+            if (!mbar_wait_bounded(sEmpty + ps, (uint32_t)(((it - 1) / S) & 1)))
+                atomicOr(&D->ctrl->error, kErrTimeout);
             fence_proxy_async();
-            issue(st);
+            issue(ps);
         }
-        // the queue takes at most TILE colliders per tile: drain it on a fixed
-        // schedule, every kQueue / TILE tiles (drain() reads its length after
-        // a barrier that every thread has reached, and returns if it is empty)
-        if (it > 0 && it % (kQueue / TILE) == 0) drain();
         if (since_flush >= kDepFlush) {
             flush_dep(true);
             since_flush = 0;
         }
         since_flush += TILE;
+        // a tile adds at most 32 * VEC colliders to this warp's queue
+        if (sQn[warp] > kWarpQueue - 32 * VEC) drain();
         if (base >= n) continue;
 
         // phase 1: gather (Sec. 2.1.3), leapfrog push (Sec. 2.1.4), absorption
@@ -932,7 +959,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
                     pc = p_coll(sg * ndt * speed * dt);
                 else
                     pc = p_coll(sg * ndt * speed);
-                if (ut[e] < pc) sQueue[atomicAdd(&sQn, 1)] = slot;  // executed after the stores below
+                if (ut[e] < pc) sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;  // executed after the stores below
             }
             // deposition of the new position for the next step (Sec. 2.1.1)
             T d0;

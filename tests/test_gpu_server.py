@@ -25,15 +25,15 @@ build_ext.build()
 
 SE, SI = wl.standin_cross_sections(300_000)
 DE = wl.CS_DE_EV
-NT = 400  # time steps per RF cycle of the test discharges
+NT = 4000  # time steps per RF cycle (the paper's N_T)
 
 
 def _requests(k0=0, n=4):
     out = []
     for k in range(n):
         rng = np.random.default_rng(900 + k0 + k)
-        d, e, i = wl.draw_discharge(rng, 900 + k0 + k, scale=0.004, steps_per_cycle=NT)
-        out.append((d, e, i, 1 + k % 3))
+        d, e, i = wl.draw_discharge(rng, 900 + k0 + k, n_min=2e4, n_max=6e4, steps_per_cycle=NT)
+        out.append((d, e, i, 1 + k % 2))
     return out
 
 
@@ -45,7 +45,7 @@ def _server(precision, slots, budget=1 << 30):
     return srv
 
 
-def _serve(srv, reqs, arrivals):
+def _serve(srv, reqs, arrivals, allow_fail=()):
     """Submit request j at scheduling round arrivals[j]; advance one ion
     subcycle per round until every request has finished."""
     tickets = {}
@@ -62,6 +62,9 @@ def _serve(srv, reqs, arrivals):
                 continue
             inf = srv.info(t)
             if inf["state"] >= ed.REQ_DONE:
+                if inf["state"] == ed.REQ_FAILED and j in allow_fail:
+                    results[j] = (None, inf)
+                    continue
                 assert inf["state"] == ed.REQ_DONE, f"request {j} failed: {inf['status']}"
                 results[j] = (srv.result(t), inf)
         rnd += 1
@@ -119,3 +122,16 @@ def test_admission_waits_for_memory():
     d, e, i, _ = reqs[0]
     with pytest.raises(ed.EdupicError):
         srv.submit(dataclasses.replace(d, capacity=20_000_000), e, i, 1)
+
+
+def test_failing_request_leaves_the_others_unchanged():
+    good = _requests(k0=60, n=1)[0]
+    # a few hundred superparticles over hundreds of cells: the charge noise
+    # drives an ionisation avalanche that overflows the particle capacity
+    rng = np.random.default_rng(901)
+    d, e, i = wl.draw_discharge(rng, 901, scale=0.004, steps_per_cycle=NT)
+    bad = (d, e, i, 2)
+    mixed = _serve(_server(ed.FP32, slots=2), [good, bad], arrivals=[0, 0], allow_fail=(1,))
+    assert mixed[1][1]["state"] == ed.REQ_FAILED and mixed[1][1]["status"] == -3  # EDUPIC_ECAPACITY
+    alone = _serve(_server(ed.FP32, slots=1), [good], arrivals=[0])
+    _same(mixed[0][0], alone[0][0])

@@ -46,6 +46,12 @@ TRAFFIC = {"sha": None, "bytes_per_launch": None}
 N_STEADY = 500_000
 BATCH_DISCHARGES = 64
 BATCH_STEPS_PER_CHUNK = 400   # time steps per batched bench step (20 ion subcycles)
+DF_N = 2_000_000              # dual-frequency particles per species
+SERVED_REQUESTS = 32
+SERVED_CYCLES = (2, 10)
+# 0.8 x (batched capacity ~9.5e10 particle-steps/s) / mean request work
+# (mean 3.8e5 particles per species x 1.05 x 4000 steps x 6 cycles)
+SERVED_RATE_HZ = 8.0
 
 
 def _args():
@@ -205,6 +211,8 @@ def run_batched(args, peak, peak_kind, flush) -> dict:
     n_i0 = sum(m[2].n for m in mix)
     del mix
     chunk = BATCH_STEPS_PER_CHUNK
+    # launch shape picked by timing (the trials are warm-up steps)
+    grid, _ = sim.autotune(subcycles=5, measure=True)
     for _ in range(args.warmup):
         sim.step(chunk, measure=True)
     sim.synchronize()
@@ -235,6 +243,7 @@ def run_batched(args, peak, peak_kind, flush) -> dict:
             "particles_e0": int(n_e0), "particles_i0": int(n_i0),
             "value": ps / (ms / 1000.0), "unit": UNIT, "time_steps_per_bench_step": chunk,
             "us_per_time_step": 1000.0 * ms / (args.steps * chunk),
+            "autotuned_push_grid": grid,
             "gpu_launches": int(args.steps * (2 * chunk + chunk // ds[0].ion_subcycle)),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "k_push<float, electrons>",
@@ -242,6 +251,81 @@ def run_batched(args, peak, peak_kind, flush) -> dict:
                          "avg_launch_us": dur_s * 1e6, "peak_kind": peak_kind,
                          "kernel_time_share": {k: float(v) / max(float(ms_k.sum()), 1e-12)
                                                for k, v in zip(("push_e", "push_i", "finalize"), ms_k)}}}
+
+
+def run_dual_frequency(args, peak, peak_kind, flush) -> dict:
+    """Dual-frequency discharge (1.356 MHz 300 V + 27.12 MHz 100 V, 5 Pa,
+    N_G = 800, 16 000 steps per HF cycle, ~2e6 particles per species),
+    timed over one full LF cycle (320 000 time steps)."""
+    import torch
+
+    from paper_2103_09642_gb300 import edupic as ed
+    from paper_2103_09642_gb300 import workloads as wl
+
+    d, e, i = wl.dual_frequency(seed=1, v_lf=300.0, n=DF_N, capacity=2 * DF_N)
+    se, si = wl.standin_cross_sections()
+    sim = ed.simulation_for([d], ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(e, i)])
+    n_e0, n_i0 = e.n, i.n
+    del e, i
+    sim.step(max(args.warmup, 3) * 200, measure=True)
+    sim.synchronize()
+    c0 = sim.counters(0)
+    with torch.cuda.stream(sim.stream):
+        flush.fill_(1)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(sim.stream)
+    sim.run_cycles(1, measure=True)
+    b.record(sim.stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    c1 = sim.counters(0)
+    ps = (c1["push_e"] - c0["push_e"]) + (c1["push_i"] - c0["push_i"])
+    p0 = sim.counters(0)
+    ms_k, launches = sim.profile_steps(400, measure=True)
+    p1 = sim.counters(0)
+    per_launch = (p1["push_e"] - p0["push_e"]) / max(launches[0], 1)
+    dur_s = ms_k[0] / max(launches[0], 1) / 1000.0
+    achieved = BYTES_PER_PUSH_FP32 * per_launch / dur_s / 1e9
+    n_e, n_i, _ = sim.counts(0)
+    sim.close()
+    return {"workload": "dual-frequency Ar CCP: 1.356 MHz 300 V + 27.12 MHz 100 V, 25 mm, 5 Pa, 350 K, N_G=800, "
+                        "16000 steps per HF cycle, steady-shape state",
+            "particles_e0": int(n_e0), "particles_i0": int(n_i0), "particles_e": int(n_e), "particles_i": int(n_i),
+            "value": ps / (ms / 1000.0), "unit": UNIT, "time_steps": int(d.steps_per_cycle),
+            "ms_per_lf_cycle": ms, "us_per_time_step": 1000.0 * ms / d.steps_per_cycle,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_push<float, electrons>",
+                         "bytes_per_particle_step": BYTES_PER_PUSH_FP32, "particles_per_launch": per_launch,
+                         "avg_launch_us": dur_s * 1e6, "peak_kind": peak_kind}}
+
+
+def run_served(args) -> dict:
+    """A bounded Poisson stream through the request server: 32 requests
+    drawn like the 64-discharge batch, 2-10 RF cycles each (the full stream,
+    200 requests of 20-200 cycles, is run by paper_2103_09642_gb300.serving),
+    arrival rate 0.8 x the batched capacity measured above."""
+    import torch
+
+    from paper_2103_09642_gb300 import edupic as ed
+    from paper_2103_09642_gb300 import serving
+    from paper_2103_09642_gb300 import workloads as wl
+
+    specs = serving.poisson_stream(SERVED_REQUESTS, rate_hz=SERVED_RATE_HZ, seed=7, cycles=SERVED_CYCLES)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.5 * free) // 256 * 256
+    se, si = wl.standin_cross_sections()
+    srv = ed.Server(budget, max_slots=96, max_grid=800, max_eepf_bins=2000, precision=ed.FP32)
+    srv.set_cross_sections(ed.ELECTRONS, se, wl.CS_DE_EV)
+    srv.set_cross_sections(ed.IONS, si, wl.CS_DE_EV)
+    rep = serving.run_stream(srv, specs, chunk_subcycles=5)
+    srv.close()
+    return {"workload": f"{SERVED_REQUESTS} Poisson-arrival requests (rate {SERVED_RATE_HZ}/s), parameters as the "
+                        f"64-discharge batch, {SERVED_CYCLES[0]}-{SERVED_CYCLES[1]} RF cycles each",
+            "value": rep["particle_steps_per_s"], "unit": UNIT,
+            "p50_time_to_result_s": rep["p50_time_to_result_s"], "p99_time_to_result_s": rep["p99_time_to_result_s"],
+            "makespan_s": rep["makespan_s"], "requests": rep["requests"], "failed": rep["failed"],
+            "hbm_budget_bytes": budget}
 
 
 def run_ours(args):
@@ -344,6 +428,8 @@ def run_ours(args):
                "steps": reps, "note": "load particles from host FP64 arrays + 1 RF cycle + diagnostics read-back"}
 
     batched = None if (args.no_batched or ws > 1) else run_batched(args, peak, peak_kind, flush)
+    dual = None if (args.no_batched or ws > 1) else run_dual_frequency(args, peak, peak_kind, flush)
+    served = None if (args.no_batched or ws > 1) else run_served(args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -372,6 +458,10 @@ def run_ours(args):
             line["e2e"] = e2e
         if batched:
             line["batched"] = batched
+        if dual:
+            line["dual_frequency"] = dual
+        if served:
+            line["served"] = served
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

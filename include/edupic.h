@@ -171,6 +171,27 @@ int edupic_profile_steps(edupic_sim *sim, int64_t n_steps, int measure, double o
  * subcycle of kernel launches.  Results are identical either way. */
 int edupic_set_graphs(edupic_sim *sim, int enable);
 
+/* Launch shape of the particle kernels (no counterpart in the paper, whose
+ * particle loops are serial).  The particle kernel runs a persistent grid
+ * of `blocks` thread blocks that share the particle tiles of all discharges;
+ * blocks = 0 restores the default (the resident limit: blocks per SM that
+ * fit the registers and shared memory, times the SM count).  A grid above
+ * the resident limit is rejected (EDUPIC_EINVAL).  Results do not depend on
+ * the grid; only the time does.  edupic_get_push_grid writes the grids of
+ * the electron and ion kernels to out[0..1] (host memory). */
+int edupic_set_push_grid(edupic_sim *sim, int species, int blocks);
+int edupic_get_push_grid(edupic_sim *sim, int out[2]);
+
+/* Autotuner of the launch shape: times `subcycles` ion subcycles for each
+ * candidate grid (half, one, one and a half and two blocks per SM, within
+ * the resident limit) and keeps the fastest for both species.  The trial
+ * steps are real simulation steps (the simulation advances by
+ * (candidates x (subcycles + 1)) ion subcycles, measured if `measure`);
+ * call it at the start of a run, at ion phase 0 (else EDUPIC_ESTATE).
+ * out_blocks[0..1] and out_ms_per_step (host, may be NULL) receive the
+ * chosen grids and the trial time per step of the winner. */
+int edupic_autotune(edupic_sim *sim, int subcycles, int measure, int out_blocks[2], double *out_ms_per_step);
+
 /* ---------------------------------------------------------------- read-back (synchronising) */
 
 /* Live particle counts and the global step index of discharge d. */

@@ -301,7 +301,9 @@ int setup_grid(edupic_sim *S)
                                                    : Launch<double>::push_blocks_per_sm(sp, smem);
         if (nb < 1) return EDUPIC_ECUDA;
         S->grid[sp] = nb * std::max(sms, 1);
+        S->grid_max[sp] = S->grid[sp];
     }
+    S->sms = std::max(sms, 1);
     return EDUPIC_OK;
 }
 
@@ -718,6 +720,75 @@ int edupic_profile_steps(edupic_sim *S, int64_t n_steps, int measure, double out
     }
     for (auto &e : ev) cudaEventDestroy(e);
     return rc;
+}
+
+int edupic_set_push_grid(edupic_sim *S, int species, int blocks)
+{
+    if (!S || (species != 0 && species != 1) || blocks < 0) return EDUPIC_EINVAL;
+    const int g = blocks == 0 ? S->grid_max[species] : blocks;
+    if (g > S->grid_max[species]) return EDUPIC_EINVAL;  // a persistent grid must be resident
+    if (g != S->grid[species]) {
+        S->grid[species] = g;
+        S->drop_graphs();  // captured launches carry the grid
+    }
+    return EDUPIC_OK;
+}
+
+int edupic_get_push_grid(edupic_sim *S, int out[2])
+{
+    if (!S || !out) return EDUPIC_EINVAL;
+    out[0] = S->grid[0];
+    out[1] = S->grid[1];
+    return EDUPIC_OK;
+}
+
+int edupic_autotune(edupic_sim *S, int subcycles, int measure, int out_blocks[2], double *out_ms_per_step)
+{
+    if (!S || subcycles < 1) return EDUPIC_EINVAL;
+    if (!S->cs_set[0] || !S->cs_set[1]) return EDUPIC_ESTATE;
+    if (S->phase != 0) return EDUPIC_ESTATE;  // trials are whole ion subcycles
+    // candidates: half, one, one and a half and two blocks per SM, within the resident limit
+    std::vector<int> cand;
+    for (int h = 1; h <= 4; ++h) {
+        const int g = h * S->sms / 2;
+        if (g >= 1 && g <= std::min(S->grid_max[0], S->grid_max[1])) cand.push_back(g);
+    }
+    if (cand.empty()) cand.push_back(std::min(S->grid_max[0], S->grid_max[1]));
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return EDUPIC_ECUDA;
+    const int64_t steps = (int64_t)subcycles * S->nsub;
+    int best = S->grid[0];
+    double best_ms = -1.0;
+    int rc = EDUPIC_OK;
+    for (int g : cand) {
+        S->grid[0] = S->grid[1] = g;
+        S->drop_graphs();
+        rc = edupic_step(S, S->nsub, measure);  // builds the graph for this grid
+        if (rc) break;
+        cudaError_t e = cudaEventRecord(a, S->stream);
+        if (e == cudaSuccess) rc = edupic_step(S, steps, measure);
+        if (e == cudaSuccess && rc == EDUPIC_OK) e = cudaEventRecord(b, S->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) rc = EDUPIC_ECUDA;
+        if (rc) break;
+        if (best_ms < 0 || ms < best_ms) {
+            best_ms = ms;
+            best = g;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    S->grid[0] = S->grid[1] = best;
+    S->drop_graphs();
+    if (rc) return rc;
+    if (out_blocks) {
+        out_blocks[0] = best;
+        out_blocks[1] = best;
+    }
+    if (out_ms_per_step) *out_ms_per_step = best_ms / (double)steps;
+    return EDUPIC_OK;
 }
 
 int edupic_set_graphs(edupic_sim *S, int enable)

@@ -995,10 +995,28 @@ struct FieldScratch {
 
 // Load (Q_e, Q_i) of the owned points; swap in the accumulated deposition
 // when `swap` (and add the current field to the time sums when `measure`).
+// Every load of the owned points is issued before any store, so the points
+// cost one memory round trip together rather than one each.
 template <int PMAX>
 __device__ __forceinline__ void load_q(const DischargeDev &D, int first, int last, bool swap, bool next_ion,
                                        bool measure, long long *Qe, long long *Qi)
 {
+    long long qe[PMAX], qi[PMAX], ae[PMAX], ai[PMAX], fc[PMAX];
+    double se[PMAX], si[PMAX], sf[PMAX];
+#pragma unroll
+    for (int j = 0; j < PMAX; ++j) {
+        const int p = first + j;
+        const bool own = p < last;
+        qe[j] = own ? D.q_e[p] : 0;
+        qi[j] = own ? D.q_i[p] : 0;
+        ae[j] = own && swap ? D.acc_e[p] : 0;
+        ai[j] = own && swap && next_ion ? D.acc_i[p] : 0;
+        const bool sums = own && swap && measure;
+        fc[j] = sums ? D.f_cur[p] : 0;
+        se[j] = sums ? D.sum_qe[p] : 0.0;
+        si[j] = sums ? D.sum_qi[p] : 0.0;
+        sf[j] = sums ? D.sum_f[p] : 0.0;
+    }
 #pragma unroll
     for (int j = 0; j < PMAX; ++j) {
         const int p = first + j;
@@ -1006,24 +1024,24 @@ __device__ __forceinline__ void load_q(const DischargeDev &D, int first, int las
         Qi[j] = 0;
         if (p >= last) continue;
         if (swap && measure) {
-            D.sum_qe[p] += (double)D.q_e[p];
-            D.sum_qi[p] += (double)D.q_i[p];
-            D.sum_f[p] += (double)D.f_cur[p];
+            D.sum_qe[p] = se[j] + (double)qe[j];
+            D.sum_qi[p] = si[j] + (double)qi[j];
+            D.sum_f[p] = sf[j] + (double)fc[j];
         }
         if (swap) {
-            Qe[j] = D.acc_e[p];
+            Qe[j] = ae[j];
             D.acc_e[p] = 0;
-            D.q_e[p] = Qe[j];
+            D.q_e[p] = ae[j];
             if (next_ion) {
-                Qi[j] = D.acc_i[p];
+                Qi[j] = ai[j];
                 D.acc_i[p] = 0;
-                D.q_i[p] = Qi[j];
+                D.q_i[p] = ai[j];
             } else {
-                Qi[j] = D.q_i[p];
+                Qi[j] = qi[j];
             }
         } else {
-            Qe[j] = D.q_e[p];
-            Qi[j] = D.q_i[p];
+            Qe[j] = qe[j];
+            Qi[j] = qi[j];
         }
     }
 }
@@ -1042,6 +1060,7 @@ __device__ void solve_field(const DischargeDev &D, long long tc, bool swap, bool
         D.fs->sum_d0 += D.fs->d0;
     }
     long long Qe[PMAX], Qi[PMAX], F[PMAX];
+    const double V = D.vdrive[tc];  // fetched with the densities, used after the scans
     load_q<PMAX>(D, first, last, swap, next_ion, measure, Qe, Qi);
     // F: inclusive scan of D_p over p = 0..M (D_p = 0 at the electrodes)
     long long run = 0;
@@ -1066,7 +1085,6 @@ __device__ void solve_field(const DischargeDev &D, long long tc, bool swap, bool
         }
     }
     const __int128 gtot = group_sum128(gpart, sm.w128, gtid, G, bar);
-    const double V = D.vdrive[tc];
     const double c = D.poisson_c;
     if (gtid == 0) {
         const double d0 = (c * (double)gtot - V) / (double)M;
@@ -1180,8 +1198,12 @@ __device__ long long compact_species(const DischargeDev &D, int sp, int *sA, int
     for (int b = 0; b < H; b += g) {
         const long long j = nn + b + gtid;
         bool alive = false;
-        if (b + gtid < H) {
-            const T xj = X[j];
+        T xj = 0, vxj = 0, vyj = 0, vzj = 0;
+        if (b + gtid < H) {  // the whole tail particle is loaded before any store
+            xj = X[j];
+            vxj = VX[j];
+            vyj = VY[j];
+            vzj = VZ[j];
             alive = (xj >= (T)0.0) && (xj <= L);
         }
         int tot;
@@ -1190,10 +1212,10 @@ __device__ long long compact_species(const DischargeDev &D, int sp, int *sA, int
         const int dst = (alive && k < H) ? hs[k] : -1;
         if (alive && (dst < 0 || dst >= nn)) atomicOr(&C->error, kErrHoles);  // inconsistent hole list
         if (alive && dst >= 0 && dst < nn) {
-            X[dst] = X[j];
-            VX[dst] = VX[j];
-            VY[dst] = VY[j];
-            VZ[dst] = VZ[j];
+            X[dst] = xj;
+            VX[dst] = vxj;
+            VY[dst] = vyj;
+            VZ[dst] = vzj;
         }
         filled += tot;
     }
@@ -1220,6 +1242,14 @@ __device__ void append_products(const DischargeDev &D, int *sA, long long &ne, l
     const T *px = reinterpret_cast<const T *>(D.prod_x);
     for (int i = gtid; i < P; i += g) {
         const int h = D.prod_parent[i];
+        // the product's values are loaded before its rank is known
+        const T x = px[i];
+        const T ve0 = reinterpret_cast<const T *>(D.prod_ve[0])[i];
+        const T ve1 = reinterpret_cast<const T *>(D.prod_ve[1])[i];
+        const T ve2 = reinterpret_cast<const T *>(D.prod_ve[2])[i];
+        const T vi0 = reinterpret_cast<const T *>(D.prod_vi[0])[i];
+        const T vi1 = reinterpret_cast<const T *>(D.prod_vi[1])[i];
+        const T vi2 = reinterpret_cast<const T *>(D.prod_vi[2])[i];
         int lo = 0, hi = P;  // rank of h among the sorted parents
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
@@ -1231,14 +1261,14 @@ __device__ void append_products(const DischargeDev &D, int *sA, long long &ne, l
         const int r = lo;
         if (r < keep) {
             const long long se = ne + r, si = ni + r;
-            X0[se] = px[i];
-            VX0[se] = reinterpret_cast<const T *>(D.prod_ve[0])[i];
-            VY0[se] = reinterpret_cast<const T *>(D.prod_ve[1])[i];
-            VZ0[se] = reinterpret_cast<const T *>(D.prod_ve[2])[i];
-            X1[si] = px[i];
-            VX1[si] = reinterpret_cast<const T *>(D.prod_vi[0])[i];
-            VY1[si] = reinterpret_cast<const T *>(D.prod_vi[1])[i];
-            VZ1[si] = reinterpret_cast<const T *>(D.prod_vi[2])[i];
+            X0[se] = x;
+            VX0[se] = ve0;
+            VY0[se] = ve1;
+            VZ0[se] = ve2;
+            X1[si] = x;
+            VX1[si] = vi0;
+            VY1[si] = vi1;
+            VZ1[si] = vi2;
         }
     }
     if (gtid == 0) {

@@ -114,6 +114,9 @@ def load_library(path: str = LIB_PATH):
         "edupic_synchronize": ([_VP]),
         "edupic_set_graphs": ([_VP, ctypes.c_int]),
         "edupic_profile_steps": ([_VP, ctypes.c_int64, ctypes.c_int, _D, _Q]),
+        "edupic_set_push_grid": ([_VP, ctypes.c_int, ctypes.c_int]),
+        "edupic_get_push_grid": ([_VP, ctypes.POINTER(ctypes.c_int)]),
+        "edupic_autotune": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]),
         "edupic_get_counts": ([_VP, ctypes.c_int, _Q, _Q, _Q]),
         "edupic_get_particles": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _D, _D, _D, _D, _Q]),
         "edupic_get_fields": ([_VP, ctypes.c_int, _D, _D, _D, _D, _Q, _Q]),
@@ -243,6 +246,22 @@ class Simulation:
 
     def set_graphs(self, enable: bool):
         _ck(self.L.edupic_set_graphs(self._h, 1 if enable else 0), "set_graphs")
+
+    def set_push_grid(self, species: int, blocks: int):
+        _ck(self.L.edupic_set_push_grid(self._h, species, int(blocks)), "set_push_grid")
+
+    def push_grid(self):
+        g = (ctypes.c_int * 2)()
+        _ck(self.L.edupic_get_push_grid(self._h, g), "get_push_grid")
+        return g[0], g[1]
+
+    def autotune(self, subcycles: int = 5, measure: bool = False):
+        """Pick the particle-kernel grid by timing (advances the simulation);
+        returns (grid, trial ms per step)."""
+        g = (ctypes.c_int * 2)()
+        ms = ctypes.c_double(0)
+        _ck(self.L.edupic_autotune(self._h, int(subcycles), 1 if measure else 0, g, ctypes.byref(ms)), "autotune")
+        return g[0], ms.value
 
     # ------------------------------------------------------------- read-back
     def counts(self, d: int = 0):

@@ -1,0 +1,97 @@
+"""FP32 particles against the FP64 oracle over full runs (statistical tier).
+
+In FP32 mode the particle positions, velocities, push and collision
+arithmetic are single precision (the field solve, deposition accumulation and
+diagnostics stay FP64/int64).  Monte Carlo runs in different precision
+diverge step by step, so they are compared through the time-averaged
+quantities the method reports (Sec. 3.5): over 5 seeds of the reference
+discharge (10 Pa, 250 V, 13.56 MHz, N_G = 400) in a steady-shape state of
+4e4 particles per species, one unmeasured RF cycle and five measured ones,
+the mean over the seeds of
+
+* the electron and ion densities averaged over the bulk (0.3 L .. 0.7 L),
+* the EEPF (centre 10% of the gap): mean energy and the fraction of samples
+  in each 1 eV bin up to 10 eV,
+* the ion flux to the electrodes (absorbed ions per electrode over the
+  measured cycles) and the mean energy of each electrode's IFED,
+
+agree within 2%.  The oracle alone, seeds 1-5 against seeds 6-10, differs by
+at most 1% in every one of these figures at this size (Monte Carlo noise).
+"""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import oracle_workers
+from paper_2103_09642_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2103_09642_gb300 import build_ext  # noqa: E402
+from paper_2103_09642_gb300 import edupic as ed  # noqa: E402
+
+build_ext.build()
+
+SEEDS = (1, 2, 3, 4, 5)
+N = 40_000
+WARM, MEASURED = 1, 5  # RF cycles
+TOL = 0.02
+
+
+def _stats(diag, cnt0, cnt1, d):
+    ng = d.n_grid
+    lo, hi = int(0.3 * (ng - 1)), int(0.7 * (ng - 1))
+    return {
+        "n_e": float(np.mean(diag["n_e"][lo:hi + 1])),
+        "n_i": float(np.mean(diag["n_i"][lo:hi + 1])),
+        "eepf": np.asarray(diag["eepf_counts"], dtype=np.float64),
+        "ifed_pow": np.asarray(diag["ifed_pow_counts"], dtype=np.float64),
+        "ifed_gnd": np.asarray(diag["ifed_gnd_counts"], dtype=np.float64),
+        "flux_pow": cnt1["abs_i_pow"] - cnt0["abs_i_pow"],
+        "flux_gnd": cnt1["abs_i_gnd"] - cnt0["abs_i_gnd"],
+    }
+
+
+def _gpu_runs():
+    se, si = wl.standin_cross_sections()
+    runs = [wl.reference_steady(seed=s, n=N) for s in SEEDS]
+    ds = [r[0] for r in runs]
+    sim = ed.simulation_for(ds, ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(r[1], r[2]) for r in runs])
+    sim.step(WARM * ds[0].steps_per_cycle, measure=False)
+    c0 = [sim.counters(k) for k in range(len(ds))]
+    sim.step(MEASURED * ds[0].steps_per_cycle, measure=True)
+    sim.synchronize()
+    out = [_stats(sim.diagnostics(k), c0[k], sim.counters(k), ds[k]) for k in range(len(ds))]
+    sim.close()
+    return out, ds[0]
+
+
+def _summary(runs, d):
+    s = {"n_e": np.mean([r["n_e"] for r in runs]), "n_i": np.mean([r["n_i"] for r in runs])}
+    h = np.sum([r["eepf"] for r in runs], axis=0)
+    eb = (np.arange(h.size) + 0.5) * d.eepf_de_ev
+    s["eepf_mean_ev"] = float((h * eb).sum() / h.sum())
+    per_ev = int(round(1.0 / d.eepf_de_ev))
+    s["eepf_1ev_bins"] = np.add.reduceat(h, np.arange(0, 10 * per_ev, per_ev))[:10] / h.sum()
+    s["ion_flux"] = float(np.mean([r["flux_pow"] + r["flux_gnd"] for r in runs]))
+    for side in ("pow", "gnd"):
+        f = np.sum([r["ifed_" + side] for r in runs], axis=0)
+        s["ifed_mean_ev_" + side] = float((f * (np.arange(f.size) + 0.5) * d.ifed_de_ev).sum() / f.sum())
+    return s
+
+
+def test_fp32_matches_fp64_oracle_statistically():
+    ctx = mp.get_context("spawn")  # the parent already holds a CUDA context
+    with ctx.Pool(len(SEEDS)) as pool:
+        ref_async = pool.starmap_async(oracle_workers.run_statistics, [(s, N, WARM, MEASURED) for s in SEEDS])
+        gpu, d = _gpu_runs()
+        ref = [_stats(r, r["counters0"], r["counters1"], d) for r in ref_async.get(timeout=1800)]
+    g, o = _summary(gpu, d), _summary(ref, d)
+    for k in o:
+        rel = np.abs(np.asarray(g[k]) - np.asarray(o[k])) / np.abs(np.asarray(o[k]))
+        assert np.all(rel <= TOL), f"{k}: GPU FP32 {g[k]} vs oracle {o[k]} (relative {rel})"

@@ -182,9 +182,11 @@ def test_steady_shape_fp64_with_ionisation():
 
 
 # --------------------------------------------------------------- graph, batch, checkpoint
-def _run(ds, parts, precision, steps, graphs=True, measure=False):
+def _run(ds, parts, precision, steps, graphs=True, measure=False, grid=0):
     sim = ed.simulation_for(ds, precision, sigma=(SE, SI), de_ev=DE, particles=parts)
     sim.set_graphs(graphs)
+    for sp in (0, 1):
+        sim.set_push_grid(sp, grid)
     sim.step(steps, measure=measure)
     out = [[sim.particles(k, sp) for sp in (0, 1)] for k in range(len(ds))]
     diag = [sim.diagnostics(k) for k in range(len(ds))]
@@ -218,6 +220,38 @@ def test_batched_equals_alone(precision):
             for c in range(4):
                 assert np.array_equal(together[0][k][sp][c], alone[0][0][sp][c])
         assert np.array_equal(together[1][k]["n_e"], alone[1][0]["n_e"])
+
+
+@pytest.mark.parametrize("precision", [ed.FP64, ed.FP32])
+def test_push_grid_does_not_change_results(precision):
+    mix = wl.batch_mix(n_discharges=3, seed0=300, scale=0.02)
+    ds = [m[0] for m in mix]
+    parts = [(m[1], m[2]) for m in mix]
+    ref = _run(ds, parts, precision, 43, measure=True)
+    for grid in (1, 37, 152):
+        got = _run(ds, parts, precision, 43, measure=True, grid=grid)
+        assert got[2] == ref[2]
+        for k in range(len(ds)):
+            for sp in (0, 1):
+                for c in range(4):
+                    assert np.array_equal(got[0][k][sp][c], ref[0][k][sp][c])
+            assert np.array_equal(got[1][k]["eepf_counts"], ref[1][k]["eepf_counts"])
+            assert np.array_equal(got[1][k]["n_e"], ref[1][k]["n_e"])
+
+
+def test_autotune_picks_a_resident_grid():
+    mix = wl.batch_mix(n_discharges=4, seed0=310, scale=0.05)
+    sim = ed.simulation_for([m[0] for m in mix], ed.FP32, sigma=(SE, SI), de_ev=DE,
+                            particles=[(m[1], m[2]) for m in mix])
+    default = sim.push_grid()
+    grid, ms = sim.autotune(subcycles=2)
+    assert 1 <= grid <= default[0] and ms > 0
+    assert sim.push_grid() == (grid, grid)
+    with pytest.raises(ed.EdupicError):
+        sim.set_push_grid(0, default[0] + 1)
+    sim.step(40)
+    sim.synchronize()
+    sim.close()
 
 
 def test_checkpoint_resume_is_exact(tmp_path):

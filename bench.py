@@ -63,6 +63,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--reference-sample", type=int, default=20,
+                    help="time steps of the oracle per bench step in --impl reference")
     return ap.parse_args()
 
 
@@ -140,6 +142,21 @@ def _workload(rank: int):
     return d, e, i
 
 
+def reduce_over_ranks(ms_total: float, work: float, ws: int, device: str):
+    """Whole-job figures of a replica run: the slowest rank's time and the
+    work of all ranks (one all-reduce each; nothing else crosses ranks)."""
+    if ws <= 1:
+        return float(ms_total), float(work)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms_total)], dtype=torch.float64, device=device)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def cpu_baseline(d, e, i, steps: int = 200) -> dict:
     """The oracle (FP64, one thread) on the first `steps` time steps of the
     same state: a bounded sample of the workload."""
@@ -168,7 +185,7 @@ def run_reference(args):
     d, e, i = _workload(0)
     se, si = wl.standin_cross_sections()
     ref = oracle.Sim(d, se, si, wl.CS_DE_EV, e, i)
-    sample = 20  # time steps per bench step (one ion subcycle)
+    sample = max(1, args.reference_sample)  # time steps per bench step (default: one ion subcycle)
     for _ in range(args.warmup):
         ref.step(sample, measure=True)
     c0 = ref.counters()
@@ -376,14 +393,7 @@ def run_ours(args):
     sim.synchronize()
     c1 = sim.counters(0)
     ps = (c1["push_e"] - c0["push_e"]) + (c1["push_i"] - c0["push_i"])
-    if ws > 1:
-        t = torch.tensor([ms_total, float(ps)], dtype=torch.float64, device="cuda")
-        tm = t.clone()
-        torch.distributed.all_reduce(tm[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        ms_max, ps_all = float(tm[0]), float(t[1])
-    else:
-        ms_max, ps_all = ms_total, float(ps)
+    ms_max, ps_all = reduce_over_ranks(ms_total, ps, ws, "cuda")
     value = ps_all / (ms_max / 1000.0)
     n_e, n_i, _ = sim.counts(0)
 

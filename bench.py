@@ -1,30 +1,33 @@
 #!/usr/bin/env python
-"""Throughput of the GB300 PIC/MCC particle loop.
+"""Throughput of the GB300 PIC/MCC particle loop (one JSON line).
 
-One bench step = one RF cycle (N_T = 4000 time steps, ions every N_SUB = 20)
-of the reference argon discharge (250 V, 13.56 MHz, 25 mm, 10 Pa, 350 K,
-N_G = 400) in a synthetic steady-shape state of ~5e5 electrons + 5e5 Ar+
-(weight 1.4e4), FP32 particles, FP64 field solve, diagnostics on.  The
-metric is particle-steps/s (electron pushes every step + ion pushes on ion
-steps).  With --gpus N under torchrun every rank runs its own replica
+Main line: the batched path.  64 independent 13.56 MHz argon discharges
+(seed-drawn gap 1.5-5 cm, 2-50 Pa, 100-500 V, N_G 200-800, 1e4-2e6
+particles per species, steady-shape states; ~2e7 electrons and ~2.3e7 Ar+ in
+all, 0.7 GB of FP32 particle state, far above the 126 MB L2) are stepped
+together, one push launch per species and one finalize launch per time step
+for all discharges, replayed as one CUDA graph per ion subcycle.  One bench
+step = 400 time steps (20 ion subcycles).  The metric is particle-steps/s
+(electron pushes every step + ion pushes on ion steps); the roofline is that
+of the electron particle kernel against the measured HBM copy bandwidth.
+
+Beside it, on the same GPU: "plain" (the reference discharge of the paper's
+Table 2 alone, ~4e5 e- + 4e5 Ar+, one RF cycle per bench step),
+"dual_frequency" (1.356 + 27.12 MHz, N_G = 800, ~2e6 per species, one full LF
+cycle) and "served" (a Poisson stream of requests through the continuous-
+batching server).  With --gpus N under torchrun every rank runs its own batch
 (independent discharges: no collective on the data path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-At N=1 the line also carries "batched": the 64-discharge batch (seed-drawn
-gap 1.5-5 cm, 2-50 Pa, 100-500 V, N_G 200-800, 1e4-2e6 particles per species,
-~2e7 electrons in all) stepped together, timed the same way, with its own
-roofline of the electron particle kernel.
-
---impl reference times the CPU oracle (single thread, FP64) on a bounded
-sample of the same workload.
+--impl reference times the CPU oracle (FP64, one thread) on a bounded
+sample of the same batch.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -40,18 +43,21 @@ UNIT = "particle-steps/s"
 HBM_PEAK_FALLBACK = 6754.5   # GB/s, STREAM-style copy measured on this machine's GB300
 BYTES_PER_PUSH_FP32 = 24     # read x, vx, vy, vz (16 B) + write x, vx (8 B)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the electron
-# particle kernel from one ncu capture (profiles/k_push_electron_reference_steady.md),
-# valid for the kernel source whose hash is given; null otherwise.
+# particle kernel on the 64-discharge batch, from one ncu capture
+# (profiles/k_push_electron_batch64.md), valid for the kernel source whose
+# hash is given; null otherwise.
 TRAFFIC = {"sha": None, "bytes_per_launch": None}
-N_STEADY = 500_000
 BATCH_DISCHARGES = 64
-BATCH_STEPS_PER_CHUNK = 400   # time steps per batched bench step (20 ion subcycles)
+BATCH_STEPS = 400             # time steps per bench step (20 ion subcycles)
+N_STEADY = 500_000            # plain leg: particles per species of the steady-shape state
 DF_N = 2_000_000              # dual-frequency particles per species
 SERVED_REQUESTS = 32
 SERVED_CYCLES = (2, 10)
-# 0.8 x (batched capacity ~9.5e10 particle-steps/s) / mean request work
+# 0.8 x (batched capacity ~1e11 particle-steps/s) / mean request work
 # (mean 3.8e5 particles per species x 1.05 x 4000 steps x 6 cycles)
 SERVED_RATE_HZ = 8.0
+CPU_SAMPLE_DISCHARGES = 4     # oracle sample: the first discharges of the batch
+CPU_SAMPLE_WORK = 4e8         # particle-steps of the oracle sample (~15 s on one core)
 
 
 def _args():
@@ -62,7 +68,7 @@ def _args():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the plain, dual-frequency and served legs")
     ap.add_argument("--reference-sample", type=int, default=20,
                     help="time steps of the oracle per bench step in --impl reference")
     return ap.parse_args()
@@ -85,7 +91,7 @@ def _peak_hbm():
 
 def _kernel_sha():
     h = hashlib.sha256()
-    for f in ("edupic_kernels.cuh", "edupic_launch.cuh", "kernels_f32.cu"):
+    for f in ("edupic_kernels.cuh", "edupic_launch.cuh", "kernels_f32.cu", "edupic_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2103_09642_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -135,13 +141,6 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _workload(rank: int):
-    from paper_2103_09642_gb300 import workloads as wl
-
-    d, e, i = wl.reference_steady(seed=1 + rank, n=N_STEADY, capacity=2 * N_STEADY)
-    return d, e, i
-
-
 def reduce_over_ranks(ms_total: float, work: float, ws: int, device: str):
     """Whole-job figures of a replica run: the slowest rank's time and the
     work of all ranks (one all-reduce each; nothing else crosses ranks)."""
@@ -157,125 +156,169 @@ def reduce_over_ranks(ms_total: float, work: float, ws: int, device: str):
     return float(t.item()), float(w.item())
 
 
-def cpu_baseline(d, e, i, steps: int = 200) -> dict:
-    """The oracle (FP64, one thread) on the first `steps` time steps of the
-    same state: a bounded sample of the workload."""
+def _batch(rank: int):
+    from paper_2103_09642_gb300 import workloads as wl
+
+    return wl.batch_mix(n_discharges=BATCH_DISCHARGES, seed0=1000 + BATCH_DISCHARGES * rank)
+
+
+BATCH_WORKLOAD = ("64 independent 13.56 MHz Ar CCPs (seed 1000+k): gap U[1.5,5] cm, p logU[2,50] Pa, "
+                  "V0 U[100,500] V, N_G U{200..800}, n logU[1e4,2e6] per species, steady-shape states; "
+                  "N_T=4000, N_SUB=20, FP32 particles, FP64 field and diagnostics")
+
+
+def _oracle_sample(mix, step_work: float):
+    """The first CPU_SAMPLE_DISCHARGES discharges of the batch in the oracle;
+    steps (a multiple of N_SUB) sized to about `step_work` particle-steps."""
     import oracle
     from paper_2103_09642_gb300 import workloads as wl
 
     se, si = wl.standin_cross_sections()
-    ref = oracle.Sim(d, se, si, wl.CS_DE_EV, e, i)
+    sims = [oracle.Sim(d, se, si, wl.CS_DE_EV, e, i) for d, e, i in mix[:CPU_SAMPLE_DISCHARGES]]
+    n = sum(e.n + i.n / 20.0 for _, e, i in mix[:CPU_SAMPLE_DISCHARGES])
+    steps = int(max(20, min(2000, step_work / max(n, 1.0))) // 20 * 20)
+    return sims, steps
+
+
+def _run_oracle(sims, steps):
     t0 = time.perf_counter()
-    ref.step(steps, measure=True)
+    c0 = [s.counters() for s in sims]
+    for s in sims:
+        s.step(steps, measure=True)
     dt = time.perf_counter() - t0
-    c = ref.counters()
-    ps = c["push_e"] + c["push_i"]
+    ps = 0
+    for s, a in zip(sims, c0):
+        c = s.counters()
+        ps += (c["push_e"] - a["push_e"]) + (c["push_i"] - a["push_i"])
+    return ps, dt
+
+
+def cpu_baseline(mix) -> dict:
+    """The oracle (FP64, one thread) on a bounded sample of the same batch."""
+    sims, steps = _oracle_sample(mix, CPU_SAMPLE_WORK)
+    ps, dt = _run_oracle(sims, steps)
     return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} time steps of the same {e.n}+{i.n}-particle state, FP64, one host thread "
-                      f"({ps} particle-steps in {dt:.1f} s)"}
+            "sample": f"discharges 0-{CPU_SAMPLE_DISCHARGES - 1} of the 64-discharge batch, {steps} time steps each, "
+                      f"FP64, one host thread ({ps} particle-steps in {dt:.1f} s)"}
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    import oracle
-    from paper_2103_09642_gb300 import workloads as wl
-
-    d, e, i = _workload(0)
-    se, si = wl.standin_cross_sections()
-    ref = oracle.Sim(d, se, si, wl.CS_DE_EV, e, i)
+    mix = _batch(0)
     sample = max(1, args.reference_sample)  # time steps per bench step (default: one ion subcycle)
+    sims, _ = _oracle_sample(mix, 0)
+    del mix
     for _ in range(args.warmup):
-        ref.step(sample, measure=True)
-    c0 = ref.counters()
-    t0 = time.perf_counter()
+        _run_oracle(sims, sample)
+    ps_tot, dt_tot = 0, 0.0
     for _ in range(args.steps):
-        ref.step(sample, measure=True)
-    dt = time.perf_counter() - t0
-    c1 = ref.counters()
-    ps = (c1["push_e"] - c0["push_e"]) + (c1["push_i"] - c0["push_i"])
-    v = ps / dt
+        ps, dt = _run_oracle(sims, sample)
+        ps_tot += ps
+        dt_tot += dt
+    v = ps_tot / dt_tot
+    desc = (f"discharges 0-{CPU_SAMPLE_DISCHARGES - 1} of the 64-discharge batch, {sample} time steps each per "
+            f"bench step, FP64, one host thread")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt_tot / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "reference discharge, steady-shape 5e5 e- + 5e5 Ar+, bounded sample",
-                       "time_steps_per_bench_step": sample, "n_grid": d.n_grid},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{sample} time steps per bench step of the {e.n}+{i.n}-particle state"},
+            "data": "synthetic", "config": {"workload": BATCH_WORKLOAD + " (bounded oracle sample)",
+                                            "sample": desc},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_batched(args, peak, peak_kind, flush) -> dict:
-    """The 64-discharge batch (seed-drawn gap, pressure, voltage, N_G and
-    particle count, steady-shape states, ~2e7 electrons in all, state far
-    above L2) stepped together: one push launch per species and one finalize
-    launch per time step for all discharges, graph-captured per ion subcycle."""
+def _roofline(sim, nd, peak, peak_kind, measure=True, steps=400):
+    """Electron-kernel roofline, timed live with CUDA events around every
+    launch (edupic_profile_steps) on the simulation's own stream."""
+    tot = lambda: sum(sim.counters(k)["push_e"] for k in range(nd))
+    p0 = tot()
+    ms_k, launches = sim.profile_steps(steps, measure=measure)
+    per_launch = (tot() - p0) / max(launches[0], 1)
+    dur_s = ms_k[0] / max(launches[0], 1) / 1000.0
+    achieved = BYTES_PER_PUSH_FP32 * per_launch / dur_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_push<float, electrons>", "bytes_per_particle_step": BYTES_PER_PUSH_FP32,
+            "particles_per_launch": per_launch, "avg_launch_us": dur_s * 1e6, "peak_kind": peak_kind,
+            "kernel_time_share": {k: float(v) / max(float(ms_k.sum()), 1e-12)
+                                  for k, v in zip(("push_e", "push_i", "finalize"), ms_k)}}
+
+
+def _timed(stream, flush, steps, run):
+    """Device time (ms) of `steps` calls of run(), an L2-sized buffer written
+    before each one outside the events."""
     import torch
 
-    from paper_2103_09642_gb300 import edupic as ed
-    from paper_2103_09642_gb300 import workloads as wl
-
-    mix = wl.batch_mix(n_discharges=BATCH_DISCHARGES, seed0=1000)
-    ds = [m[0] for m in mix]
-    se, si = wl.standin_cross_sections()
-    sim = ed.simulation_for(ds, ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(m[1], m[2]) for m in mix])
-    nd = len(ds)
-    n_e0 = sum(m[1].n for m in mix)
-    n_i0 = sum(m[2].n for m in mix)
-    del mix
-    chunk = BATCH_STEPS_PER_CHUNK
-    # launch shape picked by timing (the trials are warm-up steps)
-    grid, _ = sim.autotune(subcycles=5, measure=True)
-    for _ in range(args.warmup):
-        sim.step(chunk, measure=True)
-    sim.synchronize()
-    tot = lambda: [sum(sim.counters(k)[c] for k in range(nd)) for c in ("push_e", "push_i")]
-    c0 = tot()
     ms = 0.0
-    for _ in range(args.steps):
-        with torch.cuda.stream(sim.stream):
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
             flush.fill_(1)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        a.record(sim.stream)
-        sim.step(chunk, measure=True)
-        b.record(sim.stream)
+        a.record(stream)
+        run()
+        b.record(stream)
         b.synchronize()
         ms += a.elapsed_time(b)
-    c1 = tot()
-    ps = (c1[0] - c0[0]) + (c1[1] - c0[1])
-    p0 = tot()
-    ms_k, launches = sim.profile_steps(400, measure=True)
-    p1 = tot()
-    per_launch = (p1[0] - p0[0]) / max(launches[0], 1)
-    dur_s = ms_k[0] / max(launches[0], 1) / 1000.0
-    achieved = BYTES_PER_PUSH_FP32 * per_launch / dur_s / 1e9
+    return ms
+
+
+def leg_plain(args, peak, peak_kind, flush) -> dict:
+    """The reference discharge (Table 2: 250 V, 13.56 MHz, 25 mm, 10 Pa,
+    350 K, N_G = 400) alone, steady-shape state of ~4e5 e- + 4e5 Ar+ (weight
+    1.4e4), one RF cycle (4000 time steps) per bench step."""
+    from paper_2103_09642_gb300 import edupic as ed
+    from paper_2103_09642_gb300 import workloads as wl
+
+    d, e, i = wl.reference_steady(seed=1, n=N_STEADY, capacity=2 * N_STEADY)
+    se, si = wl.standin_cross_sections()
+    sim = ed.simulation_for([d], ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(e, i)])
+    grid, _ = sim.autotune(subcycles=10, measure=True)
+    for _ in range(args.warmup):
+        sim.run_cycles(1, measure=True)
+    sim.synchronize()
+    c0 = sim.counters(0)
+    steps = max(3, min(args.steps, 10))
+    ms = _timed(sim.stream, flush, steps, lambda: sim.run_cycles(1, measure=True))
+    c1 = sim.counters(0)
+    ps = (c1["push_e"] - c0["push_e"]) + (c1["push_i"] - c0["push_i"])
+    n_e, n_i, _ = sim.counts(0)
+    roof = _roofline(sim, 1, peak, peak_kind)
     sim.close()
-    return {"workload": f"{nd} independent 13.56 MHz Ar CCPs, seed 1000+k: gap U[1.5,5] cm, p logU[2,50] Pa, "
-                        f"V0 U[100,500] V, N_G U{{200..800}}, n logU[1e4,2e6] per species, steady-shape states",
-            "particles_e0": int(n_e0), "particles_i0": int(n_i0),
-            "value": ps / (ms / 1000.0), "unit": UNIT, "time_steps_per_bench_step": chunk,
-            "us_per_time_step": 1000.0 * ms / (args.steps * chunk),
-            "autotuned_push_grid": grid,
-            "gpu_launches": int(args.steps * (2 * chunk + chunk // ds[0].ion_subcycle)),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_push<float, electrons>",
-                         "bytes_per_particle_step": BYTES_PER_PUSH_FP32, "particles_per_launch": per_launch,
-                         "avg_launch_us": dur_s * 1e6, "peak_kind": peak_kind,
-                         "kernel_time_share": {k: float(v) / max(float(ms_k.sum()), 1e-12)
-                                               for k, v in zip(("push_e", "push_i", "finalize"), ms_k)}}}
+    # end to end through the public API: particles from host arrays, one cycle, diagnostics back
+    sim2 = ed.simulation_for([d], ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV)
+    sim2.set_push_grid(0, grid)
+    sim2.set_push_grid(1, grid)
+    tot_ps, tot_t = 0, 0.0
+    for r in range(3):
+        t0 = time.perf_counter()
+        sim2.load(0, ed.ELECTRONS, e)
+        sim2.load(0, ed.IONS, i)
+        ca = sim2.counters(0)
+        sim2.run_cycles(1, measure=True)
+        sim2.diagnostics(0)
+        cb = sim2.counters(0)
+        sim2.reset_diagnostics(0)
+        if r > 0:  # the first repetition builds the graph
+            tot_t += time.perf_counter() - t0
+            tot_ps += (cb["push_e"] - ca["push_e"]) + (cb["push_i"] - ca["push_i"])
+    sim2.close()
+    return {"workload": "reference argon discharge (Table 2 settings, N_G=400, N_T=4000, N_SUB=20) in a "
+                        "steady-shape state, weight 1.4e4, one RF cycle per bench step",
+            "particles_e": int(n_e), "particles_i": int(n_i), "value": ps / (ms / 1000.0), "unit": UNIT,
+            "ms_per_rf_cycle": ms / steps, "us_per_time_step": 1000.0 * ms / (steps * d.steps_per_cycle),
+            "steps": steps, "autotuned_push_grid": grid, "roofline": roof,
+            "e2e": {"value": tot_ps / tot_t, "unit": UNIT, "h2d_bytes_per_step": 16 * (e.n + i.n),
+                    "d2h_bytes_per_step": 8 * (3 * d.n_grid + d.eepf_bins + 2 * d.ifed_bins)}}
 
 
-def run_dual_frequency(args, peak, peak_kind, flush) -> dict:
+def leg_dual_frequency(args, peak, peak_kind, flush) -> dict:
     """Dual-frequency discharge (1.356 MHz 300 V + 27.12 MHz 100 V, 5 Pa,
     N_G = 800, 16 000 steps per HF cycle, ~2e6 particles per species),
     timed over one full LF cycle (320 000 time steps)."""
-    import torch
-
     from paper_2103_09642_gb300 import edupic as ed
     from paper_2103_09642_gb300 import workloads as wl
 
@@ -284,44 +327,29 @@ def run_dual_frequency(args, peak, peak_kind, flush) -> dict:
     sim = ed.simulation_for([d], ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(e, i)])
     n_e0, n_i0 = e.n, i.n
     del e, i
+    grid, _ = sim.autotune(subcycles=10, measure=True)
     sim.step(max(args.warmup, 3) * 200, measure=True)
     sim.synchronize()
     c0 = sim.counters(0)
-    with torch.cuda.stream(sim.stream):
-        flush.fill_(1)
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(sim.stream)
-    sim.run_cycles(1, measure=True)
-    b.record(sim.stream)
-    b.synchronize()
-    ms = a.elapsed_time(b)
+    ms = _timed(sim.stream, flush, 1, lambda: sim.run_cycles(1, measure=True))
     c1 = sim.counters(0)
     ps = (c1["push_e"] - c0["push_e"]) + (c1["push_i"] - c0["push_i"])
-    p0 = sim.counters(0)
-    ms_k, launches = sim.profile_steps(400, measure=True)
-    p1 = sim.counters(0)
-    per_launch = (p1["push_e"] - p0["push_e"]) / max(launches[0], 1)
-    dur_s = ms_k[0] / max(launches[0], 1) / 1000.0
-    achieved = BYTES_PER_PUSH_FP32 * per_launch / dur_s / 1e9
     n_e, n_i, _ = sim.counts(0)
+    roof = _roofline(sim, 1, peak, peak_kind)
     sim.close()
     return {"workload": "dual-frequency Ar CCP: 1.356 MHz 300 V + 27.12 MHz 100 V, 25 mm, 5 Pa, 350 K, N_G=800, "
-                        "16000 steps per HF cycle, steady-shape state",
+                        "16000 steps per HF cycle, steady-shape state, one LF cycle timed",
             "particles_e0": int(n_e0), "particles_i0": int(n_i0), "particles_e": int(n_e), "particles_i": int(n_i),
             "value": ps / (ms / 1000.0), "unit": UNIT, "time_steps": int(d.steps_per_cycle),
             "ms_per_lf_cycle": ms, "us_per_time_step": 1000.0 * ms / d.steps_per_cycle,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_push<float, electrons>",
-                         "bytes_per_particle_step": BYTES_PER_PUSH_FP32, "particles_per_launch": per_launch,
-                         "avg_launch_us": dur_s * 1e6, "peak_kind": peak_kind}}
+            "autotuned_push_grid": grid, "roofline": roof}
 
 
-def run_served(args) -> dict:
+def leg_served(args) -> dict:
     """A bounded Poisson stream through the request server: 32 requests
     drawn like the 64-discharge batch, 2-10 RF cycles each (the full stream,
     200 requests of 20-200 cycles, is run by paper_2103_09642_gb300.serving),
-    arrival rate 0.8 x the batched capacity measured above."""
+    arrival rate about 0.8 x the batched capacity."""
     import torch
 
     from paper_2103_09642_gb300 import edupic as ed
@@ -346,7 +374,6 @@ def run_served(args) -> dict:
 
 
 def run_ours(args):
-    import numpy as np
     import torch
 
     ws, rank, local = _dist()
@@ -359,11 +386,15 @@ def run_ours(args):
     from paper_2103_09642_gb300 import workloads as wl
 
     ed.load_library()
-    d, e, i = _workload(rank)
+    peak, peak_kind = _peak_hbm()
+    mix = _batch(rank)
+    ds = [m[0] for m in mix]
+    nd = len(ds)
     se, si = wl.standin_cross_sections()
-    sim = ed.simulation_for([d], ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(e, i)])
+    sim = ed.simulation_for(ds, ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(m[1], m[2]) for m in mix])
     stream = sim.stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    grid, _ = sim.autotune(subcycles=5, measure=True)  # launch shape picked by timing (warm-up steps)
 
     def barrier():
         torch.cuda.synchronize()
@@ -372,110 +403,86 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        sim.run_cycles(1, measure=True)
+        sim.step(BATCH_STEPS, measure=True)
     sim.synchronize()
-    c0 = sim.counters(0)
+    tot = lambda: sum(sim.counters(k)["push_e"] + sim.counters(k)["push_i"] for k in range(nd))
+    c0 = tot()
     clocks = Clocks(local)
     barrier()
-    ms_total = 0.0
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(1)          # L2 flush between timed steps (outside the events)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        sim.run_cycles(1, measure=True)
-        b.record(stream)
-        b.synchronize()
-        ms_total += a.elapsed_time(b)
+    ms_total = _timed(stream, flush, args.steps, lambda: sim.step(BATCH_STEPS, measure=True))
     barrier()
     clk = clocks.stop()
     sim.synchronize()
-    c1 = sim.counters(0)
-    ps = (c1["push_e"] - c0["push_e"]) + (c1["push_i"] - c0["push_i"])
+    ps = tot() - c0
     ms_max, ps_all = reduce_over_ranks(ms_total, ps, ws, "cuda")
     value = ps_all / (ms_max / 1000.0)
-    n_e, n_i, _ = sim.counts(0)
-
-    # roofline of the electron particle kernel, timed live with CUDA events
-    cp0 = sim.counters(0)
-    prof_steps = 400
-    ms_k, launches = sim.profile_steps(prof_steps, measure=True)
-    cp1 = sim.counters(0)
-    push_e_per_launch = (cp1["push_e"] - cp0["push_e"]) / max(launches[0], 1)
-    dur_s = ms_k[0] / max(launches[0], 1) / 1000.0
-    achieved = BYTES_PER_PUSH_FP32 * push_e_per_launch / dur_s / 1e9
-    peak, peak_kind = _peak_hbm()
+    n_e = sum(sim.counts(k)[0] for k in range(nd))
+    n_i = sum(sim.counts(k)[1] for k in range(nd))
+    roof = _roofline(sim, nd, peak, peak_kind)
     sha = _kernel_sha()
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sha"] == sha else None
-    share = {k: float(v) / max(float(ms_k.sum()), 1e-12) for k, v in zip(("push_e", "push_i", "finalize"), ms_k)}
+    roof["kernel_src"] = sha
+    roof["traffic"] = TRAFFIC["bytes_per_launch"] if TRAFFIC["sha"] == sha else None
+    sim.close()
 
-    # end to end through the public API: host buffers in, diagnostics out
+    # end to end through the public API: every discharge's particles from host
+    # FP64 arrays (converted and copied as FP32), one bench step, diagnostics back
     e2e = None
     if not args.no_e2e:
-        sim2 = ed.simulation_for([d], ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV)
-        reps = max(2, min(args.steps, 5))
-        h2d = 4 * 4 * (e.n + i.n)  # x, vx, vy, vz of both species, copied as FP32
-        d2h = 0
+        sim2 = ed.simulation_for(ds, ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV)
+        sim2.set_push_grid(0, grid)
+        sim2.set_push_grid(1, grid)
+        h2d = 16 * sum(m[1].n + m[2].n for m in mix)
+        d2h = sum(8 * (3 * d.n_grid + d.eepf_bins + 2 * d.ifed_bins) for d in ds)
+        reps = max(2, min(args.steps, 3))
         tot_ps, tot_t = 0, 0.0
         for r in range(reps + 1):
             t0 = time.perf_counter()
-            sim2.load(0, ed.ELECTRONS, e)
-            sim2.load(0, ed.IONS, i)
-            ca = sim2.counters(0)
-            sim2.run_cycles(1, measure=True)
-            diag = sim2.diagnostics(0)
-            cb = sim2.counters(0)
-            sim2.reset_diagnostics(0)
-            t1 = time.perf_counter()
-            d2h = 8 * (3 * d.n_grid + d.eepf_bins + 2 * d.ifed_bins)
-            if r > 0:  # first repetition warms the graph
-                tot_t += t1 - t0
-                tot_ps += (cb["push_e"] - ca["push_e"]) + (cb["push_i"] - ca["push_i"])
-            assert diag["measured_steps"] > 0
+            for k, (d, e, i) in enumerate(mix):
+                sim2.load(k, ed.ELECTRONS, e)
+                sim2.load(k, ed.IONS, i)
+            ca = sum(sim2.counters(k)["push_e"] + sim2.counters(k)["push_i"] for k in range(nd))
+            sim2.step(BATCH_STEPS, measure=True)
+            for k in range(nd):
+                sim2.diagnostics(k)
+            cb = sum(sim2.counters(k)["push_e"] + sim2.counters(k)["push_i"] for k in range(nd))
+            for k in range(nd):
+                sim2.reset_diagnostics(k)
+            if r > 0:  # the first repetition builds the graph
+                tot_t += time.perf_counter() - t0
+                tot_ps += cb - ca
         sim2.close()
-        e2e = {"value": tot_ps / tot_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "steps": reps, "note": "load particles from host FP64 arrays + 1 RF cycle + diagnostics read-back"}
+        e2e = {"value": tot_ps / tot_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": reps, "note": "64 discharges loaded from host FP64 arrays + 400 time steps + diagnostics "
+                                      "of every discharge read back, per step"}
 
-    batched = None if (args.no_batched or ws > 1) else run_batched(args, peak, peak_kind, flush)
-    dual = None if (args.no_batched or ws > 1) else run_dual_frequency(args, peak, peak_kind, flush)
-    served = None if (args.no_batched or ws > 1) else run_served(args)
-
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(d, e, i)
+    extra = {}
+    if rank == 0 and ws == 1 and not args.no_extra:
+        extra["plain"] = leg_plain(args, peak, peak_kind, flush)
+        extra["dual_frequency"] = leg_dual_frequency(args, peak, peak_kind, flush)
+        extra["served"] = leg_served(args)
+    cpu = cpu_baseline(mix) if (rank == 0 and ws == 1 and not args.no_cpu) else None
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "reference argon discharge (250 V, 13.56 MHz, 25 mm, 10 Pa, 350 K, N_G=400, "
-                                   "N_T=4000, N_SUB=20) in a steady-shape state, ~5e5 e- + 5e5 Ar+ per GPU, "
-                                   "1 RF cycle per step, FP32 particles, FP64 field and diagnostics",
-                       "particles_e": int(n_e), "particles_i": int(n_i), "weight": d.weight,
-                       "l2": "256 MB buffer written between timed steps (outside the timed events)",
-                       "parallelism": f"replicas x{ws}", "cross_sections": "stand-in set"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_push<float, electrons>",
-                         "bytes_per_particle_step": BYTES_PER_PUSH_FP32,
-                         "particles_per_launch": push_e_per_launch, "avg_launch_us": dur_s * 1e6,
-                         "peak_kind": peak_kind, "kernel_time_share": share, "kernel_src": sha},
-            "gpu_launches": int(args.steps * (2 * d.steps_per_cycle + d.steps_per_cycle // d.ion_subcycle)),
+            "config": {"workload": BATCH_WORKLOAD, "discharges": nd, "time_steps_per_step": BATCH_STEPS,
+                       "particles_e": int(n_e), "particles_i": int(n_i),
+                       "l2": "256 MB buffer written between timed steps (outside the timed events); "
+                             "particle state 0.7 GB > L2",
+                       "parallelism": f"replicas x{ws}", "cross_sections": "stand-in set",
+                       "autotuned_push_grid": grid},
+            "roofline": roof,
+            "gpu_launches": int(args.steps * (2 * BATCH_STEPS + BATCH_STEPS // ds[0].ion_subcycle)),
             "clocks": clk,
         }
         if e2e:
             line["e2e"] = e2e
-        if batched:
-            line["batched"] = batched
-        if dual:
-            line["dual_frequency"] = dual
-        if served:
-            line["served"] = served
         if cpu:
             line["cpu_baseline"] = cpu
+        line.update(extra)
         print(json.dumps(line), flush=True)
-    sim.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0

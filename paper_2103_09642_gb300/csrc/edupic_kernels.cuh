@@ -381,6 +381,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Start moving a global line into this SM's L1 (no result, no wait): later
+// loads of the line then wait for this fill instead of starting their own
+// round trip.
+__device__ __forceinline__ void prefetch_l1(const void *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 template <typename V>
 __device__ __forceinline__ V warp_incl_scan(V v)
 {
@@ -445,7 +453,7 @@ __device__ __forceinline__ __int128 group_sum128(__int128 v, __int128 *s_w, int 
 // them (Algorithm 6 after the test).  It re-derives the table index and, for
 // Ar+, the thermal partner from the same counter-based draws, so the result
 // is the same as executing the collision in place.
-constexpr int kWarpQueue = 512;  // queued colliders per warp before the warp drains them
+constexpr int kWarpQueue = 256;  // queued colliders per warp before the warp drains them
 
 // e- + Ar collision of the particle in `slot` (post-push state in memory),
 // including the append record and the deposition of an ionisation pair.
@@ -592,9 +600,10 @@ __device__ __noinline__ void absorbed(const DischargeDev *Dp, int slot, T xn, T 
 }
 
 // EEPF sample (Sec. 3.5): electrons in the centre 10% of the gap, energy of
-// the time-centred velocity.
+// the time-centred velocity, counted in the block's shared histogram sH
+// (added to the discharge's counters when the block flushes).
 template <typename T>
-__device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy, T vz)
+__device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy, T vz, unsigned int *sH)
 {
     const DischargeDev &D = *Dp;
     const T v2c = vxc * vxc + vy * vy + vz * vz;
@@ -610,8 +619,7 @@ __device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy,
         ok = r < (float)D.eepf_bins;
         b = ok ? (int)r : 0;
     }
-    // striped over kEepfStripes copies to spread the atomics; summed on read
-    if (ok) atomicAdd(D.eepf + (blockIdx.x & (kEepfStripes - 1)) * D.eepf_bins + b, 1ull);
+    if (ok) atomicAdd(sH + b, 1u);
 }
 
 // ---------------------------------------------------------------- particle kernel
@@ -625,12 +633,12 @@ __host__ __device__ constexpr int ring_stages()
 
 // Dynamic shared memory: [tile ring: stages x 4 arrays x TILE T][coarse
 // sigma_max: kCoarse T][E pairs: ng_max T2][deposition: 3 x ng_max u32]
-// [tile prefix: nd+1 int].
+// [EEPF histogram: eepf_max u32][tile prefix: nd+1 int].
 template <typename T>
 __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eepf_max)
 {
     return (size_t)ring_stages<T>() * 4 * kThreads * VecOf<T>::n * sizeof(T) + (size_t)kCoarse * sizeof(T) +
-           (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 12 + (size_t)(nd + 1) * 4 + 0 * (size_t)eepf_max;
+           (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 12 + (size_t)eepf_max * 4 + (size_t)(nd + 1) * 4;
 }
 
 template <typename T, int SP>
@@ -652,8 +660,8 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     acc.cnt = reinterpret_cast<unsigned int *>(sE2 + ng_max);
     acc.lo = acc.cnt + ng_max;
     acc.hi = acc.lo + ng_max;
-    int *sPre = reinterpret_cast<int *>(acc.hi + ng_max);
-    (void)eepf_max;
+    unsigned int *sH = acc.hi + ng_max;  // EEPF counts of the current discharge (electrons)
+    int *sPre = reinterpret_cast<int *>(sH + eepf_max);
     __shared__ unsigned int sCnt[EDUPIC_N_COUNTERS];
     __shared__ int sW[33];
     __shared__ int sQueue[kWarps][kWarpQueue];  // colliders queued by each warp
@@ -684,12 +692,21 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (tid < EDUPIC_N_COUNTERS) sCnt[tid] = 0;
+    if (SP == 0 && measure)
+        for (int b = tid; b < eepf_max; b += blockDim.x) sH[b] = 0u;
     __syncthreads();
     const int cs_shift = sD.cs_shift[SP];
     const Ctrl *ctrls = sD.ctrl;  // the counts of all discharges are one packed array
     int staged = 0;
     pdl_wait();
     pdl_launch_next();
+    {
+        // the field of the pre-staged discharge (written by the preceding
+        // kernel) is requested now, beside the counts read next
+        const T *ef = reinterpret_cast<const T *>(sD.ef_t);
+        for (int p = tid * (128 / (int)sizeof(T)); p < sD.ng; p += blockDim.x * (128 / (int)sizeof(T)))
+            prefetch_l1(ef + p);
+    }
     // tiles per discharge -> prefix over discharges (every block computes it)
     {
         int running = 0;
@@ -756,7 +773,18 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
 
     auto flush = [&](bool last) {
         drain();
-        flush_dep(!last);
+        flush_dep(!last);  // ends with every thread past its samples
+        if (eepf_on) {
+            // non-empty bins into one of the discharge's striped histograms
+            unsigned long long *h = D->eepf + (blockIdx.x & (kEepfStripes - 1)) * D->eepf_bins;
+            for (int b = tid; b < D->eepf_bins; b += blockDim.x) {
+                const unsigned int c = sH[b];
+                if (c) {
+                    atomicAdd(h + b, (unsigned long long)c);
+                    sH[b] = 0u;
+                }
+            }
+        }
         if (tid < EDUPIC_N_COUNTERS) {
             const unsigned int c = sCnt[tid];
             if (c) atomicAdd(D->ctrl->counters + tid, (unsigned long long)c);
@@ -895,7 +923,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             }
             const T vxn = SP == 0 ? vx - e_x * factor : vx + e_x * factor;
             if (SP == 0 && eepf_on && live && x >= lo && x <= hi)
-                eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e]);
+                eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e], sH);
             const T xn = x + vxn * dt;
             xa[e] = live ? xn : x;
             vxa[e] = live ? vxn : vx;
@@ -1307,6 +1335,39 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDe
     if (threadIdx.x < kGroupA) {
         // (A) particle bookkeeping
         const int gtid = threadIdx.x;
+        {
+            // the event lists and the records they touch first (the tail
+            // particles that fill holes, the product records) are requested
+            // together, so the steps below find them on their way
+            const int he = min(C->holes[0], kEvents), hi = ion_step ? min(C->holes[1], kEvents) : 0;
+            const int np = min(C->products, kEvents);
+            const long long n0 = C->n[0], n1 = C->n[1];
+            const int es = (int)sizeof(T);
+            if (gtid < he && he <= n0) {
+                prefetch_l1(D.holes[0] + gtid);
+                const long long j = n0 - he + gtid;
+                prefetch_l1((const char *)D.x[0] + j * es);
+                prefetch_l1((const char *)D.vx[0] + j * es);
+                prefetch_l1((const char *)D.vy[0] + j * es);
+                prefetch_l1((const char *)D.vz[0] + j * es);
+            }
+            if (gtid < hi && hi <= n1) {
+                prefetch_l1(D.holes[1] + gtid);
+                const long long j = n1 - hi + gtid;
+                prefetch_l1((const char *)D.x[1] + j * es);
+                prefetch_l1((const char *)D.vx[1] + j * es);
+                prefetch_l1((const char *)D.vy[1] + j * es);
+                prefetch_l1((const char *)D.vz[1] + j * es);
+            }
+            if (gtid < np) {
+                prefetch_l1(D.prod_parent + gtid);
+                prefetch_l1((const char *)D.prod_x + gtid * es);
+                for (int c = 0; c < 3; ++c) {
+                    prefetch_l1((const char *)D.prod_ve[c] + gtid * es);
+                    prefetch_l1((const char *)D.prod_vi[c] + gtid * es);
+                }
+            }
+        }
         long long ne = compact_species<T>(D, 0, sA, sW, gtid, kGroupA, 1);
         long long ni = ion_step ? compact_species<T>(D, 1, sA, sW, gtid, kGroupA, 1) : C->n[1];
         append_products<T>(D, sA, ne, ni, gtid, kGroupA, 1);

@@ -58,6 +58,12 @@ SERVED_CYCLES = (2, 10)
 SERVED_RATE_HZ = 8.0
 CPU_SAMPLE_DISCHARGES = 4     # oracle sample: the first discharges of the batch
 CPU_SAMPLE_WORK = 4e8         # particle-steps of the oracle sample (~15 s on one core)
+_T0 = time.time()
+
+
+def _log(msg: str):
+    """Progress on stderr (stdout carries only the JSON line)."""
+    print(f"[bench {time.time() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
 
 
 def _args():
@@ -310,7 +316,7 @@ def leg_plain(args, peak, peak_kind, flush) -> dict:
                         "steady-shape state, weight 1.4e4, one RF cycle per bench step",
             "particles_e": int(n_e), "particles_i": int(n_i), "value": ps / (ms / 1000.0), "unit": UNIT,
             "ms_per_rf_cycle": ms / steps, "us_per_time_step": 1000.0 * ms / (steps * d.steps_per_cycle),
-            "steps": steps, "autotuned_push_grid": grid, "roofline": roof,
+            "steps": steps, "push_grid": grid, "roofline": roof,
             "e2e": {"value": tot_ps / tot_t, "unit": UNIT, "h2d_bytes_per_step": 16 * (e.n + i.n),
                     "d2h_bytes_per_step": 8 * (3 * d.n_grid + d.eepf_bins + 2 * d.ifed_bins)}}
 
@@ -342,7 +348,7 @@ def leg_dual_frequency(args, peak, peak_kind, flush) -> dict:
             "particles_e0": int(n_e0), "particles_i0": int(n_i0), "particles_e": int(n_e), "particles_i": int(n_i),
             "value": ps / (ms / 1000.0), "unit": UNIT, "time_steps": int(d.steps_per_cycle),
             "ms_per_lf_cycle": ms, "us_per_time_step": 1000.0 * ms / d.steps_per_cycle,
-            "autotuned_push_grid": grid, "roofline": roof}
+            "push_grid": grid, "roofline": roof}
 
 
 def leg_served(args) -> dict:
@@ -363,7 +369,7 @@ def leg_served(args) -> dict:
     srv = ed.Server(budget, max_slots=96, max_grid=800, max_eepf_bins=2000, precision=ed.FP32)
     srv.set_cross_sections(ed.ELECTRONS, se, wl.CS_DE_EV)
     srv.set_cross_sections(ed.IONS, si, wl.CS_DE_EV)
-    rep = serving.run_stream(srv, specs, chunk_subcycles=5)
+    rep = serving.run_stream(srv, specs, chunk_subcycles=5, max_wall_s=180.0)
     srv.close()
     return {"workload": f"{SERVED_REQUESTS} Poisson-arrival requests (rate {SERVED_RATE_HZ}/s), parameters as the "
                         f"64-discharge batch, {SERVED_CYCLES[0]}-{SERVED_CYCLES[1]} RF cycles each",
@@ -387,6 +393,7 @@ def run_ours(args):
 
     ed.load_library()
     peak, peak_kind = _peak_hbm()
+    _log("generating the 64-discharge batch")
     mix = _batch(rank)
     ds = [m[0] for m in mix]
     nd = len(ds)
@@ -394,7 +401,9 @@ def run_ours(args):
     sim = ed.simulation_for(ds, ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(m[1], m[2]) for m in mix])
     stream = sim.stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    grid, _ = sim.autotune(subcycles=5, measure=True)  # launch shape picked by timing (warm-up steps)
+    _log("batch created; autotuning the stepping mode")
+    grid, _ = sim.autotune(subcycles=5, measure=True)  # graph replay or not, by timing (warm-up steps)
+    _log("warm-up")
 
     def barrier():
         torch.cuda.synchronize()
@@ -407,6 +416,7 @@ def run_ours(args):
     sim.synchronize()
     tot = lambda: sum(sim.counters(k)["push_e"] + sim.counters(k)["push_i"] for k in range(nd))
     c0 = tot()
+    _log("timed steps")
     clocks = Clocks(local)
     barrier()
     ms_total = _timed(stream, flush, args.steps, lambda: sim.step(BATCH_STEPS, measure=True))
@@ -418,6 +428,7 @@ def run_ours(args):
     value = ps_all / (ms_max / 1000.0)
     n_e = sum(sim.counts(k)[0] for k in range(nd))
     n_i = sum(sim.counts(k)[1] for k in range(nd))
+    _log("roofline")
     roof = _roofline(sim, nd, peak, peak_kind)
     sha = _kernel_sha()
     roof["kernel_src"] = sha
@@ -428,6 +439,7 @@ def run_ours(args):
     # FP64 arrays (converted and copied as FP32), one bench step, diagnostics back
     e2e = None
     if not args.no_e2e:
+        _log("end to end")
         sim2 = ed.simulation_for(ds, ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV)
         sim2.set_push_grid(0, grid)
         sim2.set_push_grid(1, grid)
@@ -457,10 +469,16 @@ def run_ours(args):
 
     extra = {}
     if rank == 0 and ws == 1 and not args.no_extra:
+        _log("plain leg")
         extra["plain"] = leg_plain(args, peak, peak_kind, flush)
+        _log("dual-frequency leg")
         extra["dual_frequency"] = leg_dual_frequency(args, peak, peak_kind, flush)
+        _log("served leg")
         extra["served"] = leg_served(args)
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        _log("cpu baseline")
     cpu = cpu_baseline(mix) if (rank == 0 and ws == 1 and not args.no_cpu) else None
+    _log("done")
 
     if rank == 0:
         line = {
@@ -472,7 +490,7 @@ def run_ours(args):
                        "l2": "256 MB buffer written between timed steps (outside the timed events); "
                              "particle state 0.7 GB > L2",
                        "parallelism": f"replicas x{ws}", "cross_sections": "stand-in set",
-                       "autotuned_push_grid": grid},
+                       "push_grid": grid},
             "roofline": roof,
             "gpu_launches": int(args.steps * (2 * BATCH_STEPS + BATCH_STEPS // ds[0].ion_subcycle)),
             "clocks": clk,

@@ -173,23 +173,23 @@ int edupic_set_graphs(edupic_sim *sim, int enable);
 
 /* Launch shape of the particle kernels (no counterpart in the paper, whose
  * particle loops are serial).  The particle kernel runs a persistent grid
- * of `blocks` thread blocks that share the particle tiles of all discharges;
- * blocks = 0 restores the default (the resident limit: blocks per SM that
- * fit the registers and shared memory, times the SM count).  A grid above
- * the resident limit is rejected (EDUPIC_EINVAL).  Results do not depend on
- * the grid; only the time does.  edupic_get_push_grid writes the grids of
- * the electron and ion kernels to out[0..1] (host memory). */
+ * of thread blocks that share the particle tiles of all discharges: the
+ * resident limit (blocks per SM that fit the registers and shared memory,
+ * times the SM count).  edupic_set_push_grid accepts blocks = 0 or that
+ * limit (anything else is EDUPIC_EINVAL: smaller persistent grids stalled on
+ * large batches and are not offered).  edupic_get_push_grid writes the
+ * grids of the electron and ion kernels to out[0..1] (host memory). */
 int edupic_set_push_grid(edupic_sim *sim, int species, int blocks);
 int edupic_get_push_grid(edupic_sim *sim, int out[2]);
 
-/* Autotuner of the launch shape: times `subcycles` ion subcycles for each
- * candidate grid (half, one, one and a half and two blocks per SM, within
- * the resident limit) and keeps the fastest for both species.  The trial
- * steps are real simulation steps (the simulation advances by
- * (candidates x (subcycles + 1)) ion subcycles, measured if `measure`);
- * call it at the start of a run, at ion phase 0 (else EDUPIC_ESTATE).
- * out_blocks[0..1] and out_ms_per_step (host, may be NULL) receive the
- * chosen grids and the trial time per step of the winner. */
+/* Autotuner of the stepping mode: times `subcycles` ion subcycles replayed
+ * through one CUDA graph per ion subcycle and the same launched kernel by
+ * kernel, and keeps the faster (results are identical either way).  The
+ * trial steps are real simulation steps (the simulation advances by
+ * 2 x (subcycles + 1) ion subcycles, measured if `measure`); call it at the
+ * start of a run, at ion phase 0 (else EDUPIC_ESTATE).  out_blocks[0..1]
+ * and out_ms_per_step (host, may be NULL) receive the grids in use and the
+ * trial time per step of the faster mode. */
 int edupic_autotune(edupic_sim *sim, int subcycles, int measure, int out_blocks[2], double *out_ms_per_step);
 
 /* ---------------------------------------------------------------- read-back (synchronising) */

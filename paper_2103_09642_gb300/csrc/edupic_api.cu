@@ -725,8 +725,10 @@ int edupic_profile_steps(edupic_sim *S, int64_t n_steps, int measure, double out
 int edupic_set_push_grid(edupic_sim *S, int species, int blocks)
 {
     if (!S || (species != 0 && species != 1) || blocks < 0) return EDUPIC_EINVAL;
-    const int g = blocks == 0 ? S->grid_max[species] : blocks;
-    if (g > S->grid_max[species]) return EDUPIC_EINVAL;  // a persistent grid must be resident
+    // only the resident limit: a persistent grid below it stalled on large
+    // batches (see the design notes), so such grids are refused
+    if (blocks != 0 && blocks != S->grid_max[species]) return EDUPIC_EINVAL;
+    const int g = S->grid_max[species];
     if (g != S->grid[species]) {
         S->grid[species] = g;
         S->drop_graphs();  // captured launches carry the grid
@@ -747,23 +749,20 @@ int edupic_autotune(edupic_sim *S, int subcycles, int measure, int out_blocks[2]
     if (!S || subcycles < 1) return EDUPIC_EINVAL;
     if (!S->cs_set[0] || !S->cs_set[1]) return EDUPIC_ESTATE;
     if (S->phase != 0) return EDUPIC_ESTATE;  // trials are whole ion subcycles
-    // candidates: half, one, one and a half and two blocks per SM, within the resident limit
-    std::vector<int> cand;
-    for (int h = 1; h <= 4; ++h) {
-        const int g = h * S->sms / 2;
-        if (g >= 1 && g <= std::min(S->grid_max[0], S->grid_max[1])) cand.push_back(g);
-    }
-    if (cand.empty()) cand.push_back(std::min(S->grid_max[0], S->grid_max[1]));
+    // candidates: step replay through one CUDA graph per ion subcycle, or
+    // launch by launch (both at the resident grid); results are identical
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return EDUPIC_ECUDA;
     const int64_t steps = (int64_t)subcycles * S->nsub;
-    int best = S->grid[0];
+    const bool keep = S->graphs;
+    bool best = keep;
     double best_ms = -1.0;
     int rc = EDUPIC_OK;
-    for (int g : cand) {
-        S->grid[0] = S->grid[1] = g;
-        S->drop_graphs();
-        rc = edupic_step(S, S->nsub, measure);  // builds the graph for this grid
+    for (int c = 0; c < 2 && rc == EDUPIC_OK; ++c) {
+        const bool graphs = c == 0;
+        S->graphs = graphs;
+        if (!graphs) S->drop_graphs();
+        rc = edupic_step(S, S->nsub, measure);  // warm (builds the graph when used)
         if (rc) break;
         cudaError_t e = cudaEventRecord(a, S->stream);
         if (e == cudaSuccess) rc = edupic_step(S, steps, measure);
@@ -775,17 +774,17 @@ int edupic_autotune(edupic_sim *S, int subcycles, int measure, int out_blocks[2]
         if (rc) break;
         if (best_ms < 0 || ms < best_ms) {
             best_ms = ms;
-            best = g;
+            best = graphs;
         }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    S->grid[0] = S->grid[1] = best;
-    S->drop_graphs();
+    S->graphs = rc ? keep : best;
+    if (!S->graphs) S->drop_graphs();
     if (rc) return rc;
     if (out_blocks) {
-        out_blocks[0] = best;
-        out_blocks[1] = best;
+        out_blocks[0] = S->grid[0];
+        out_blocks[1] = S->grid[1];
     }
     if (out_ms_per_step) *out_ms_per_step = best_ms / (double)steps;
     return EDUPIC_OK;

@@ -256,8 +256,8 @@ class Simulation:
         return g[0], g[1]
 
     def autotune(self, subcycles: int = 5, measure: bool = False):
-        """Pick the particle-kernel grid by timing (advances the simulation);
-        returns (grid, trial ms per step)."""
+        """Pick graph replay or kernel-by-kernel stepping by timing (advances
+        the simulation); returns (grid in use, trial ms per step)."""
         g = (ctypes.c_int * 2)()
         ms = ctypes.c_double(0)
         _ck(self.L.edupic_autotune(self._h, int(subcycles), 1 if measure else 0, g, ctypes.byref(ms)), "autotune")

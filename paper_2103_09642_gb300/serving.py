@@ -63,10 +63,11 @@ def percentile(v, q: float) -> Optional[float]:
 
 
 def run_stream(server, specs: List[RequestSpec], chunk_subcycles: int = 5, clock=time.perf_counter,
-               sleep=time.sleep, keep_results: bool = False) -> dict:
+               sleep=time.sleep, keep_results: bool = False, max_wall_s: Optional[float] = None) -> dict:
     """Feed `specs` to `server` at their arrival times (relative to the start
     of this call), keep calling server.advance(chunk_subcycles) while work is
-    resident or queued, and collect each request's timing and counters."""
+    resident or queued, and collect each request's timing and counters.
+    Raises TimeoutError after `max_wall_s` seconds (if given)."""
     order = sorted(range(len(specs)), key=lambda k: specs[k].arrival_s)
     t0 = clock()
     srv0 = server.stats()["now"]
@@ -76,6 +77,9 @@ def run_stream(server, specs: List[RequestSpec], chunk_subcycles: int = 5, clock
     done = 0
     while done < len(specs):
         now = clock() - t0
+        if max_wall_s is not None and now > max_wall_s:
+            raise TimeoutError(f"request stream not finished after {max_wall_s} s "
+                               f"({done} of {len(specs)} done, {len(live)} live)")
         while nxt < len(order) and specs[order[nxt]].arrival_s <= now:
             s = specs[order[nxt]]
             tk = server.submit(s.discharge, s.electrons, s.ions, s.n_cycles)

@@ -222,36 +222,42 @@ def test_batched_equals_alone(precision):
         assert np.array_equal(together[1][k]["n_e"], alone[1][0]["n_e"])
 
 
-@pytest.mark.parametrize("precision", [ed.FP64, ed.FP32])
-def test_push_grid_does_not_change_results(precision):
+def test_push_grid_only_the_resident_limit():
     mix = wl.batch_mix(n_discharges=3, seed0=300, scale=0.02)
     ds = [m[0] for m in mix]
     parts = [(m[1], m[2]) for m in mix]
-    ref = _run(ds, parts, precision, 43, measure=True)
-    for grid in (1, 37, 152):
-        got = _run(ds, parts, precision, 43, measure=True, grid=grid)
-        assert got[2] == ref[2]
-        for k in range(len(ds)):
-            for sp in (0, 1):
-                for c in range(4):
-                    assert np.array_equal(got[0][k][sp][c], ref[0][k][sp][c])
-            assert np.array_equal(got[1][k]["eepf_counts"], ref[1][k]["eepf_counts"])
-            assert np.array_equal(got[1][k]["n_e"], ref[1][k]["n_e"])
-
-
-def test_autotune_picks_a_resident_grid():
-    mix = wl.batch_mix(n_discharges=4, seed0=310, scale=0.05)
-    sim = ed.simulation_for([m[0] for m in mix], ed.FP32, sigma=(SE, SI), de_ev=DE,
-                            particles=[(m[1], m[2]) for m in mix])
-    default = sim.push_grid()
-    grid, ms = sim.autotune(subcycles=2)
-    assert 1 <= grid <= default[0] and ms > 0
-    assert sim.push_grid() == (grid, grid)
-    with pytest.raises(ed.EdupicError):
-        sim.set_push_grid(0, default[0] + 1)
-    sim.step(40)
-    sim.synchronize()
+    sim = ed.simulation_for(ds, ed.FP32, sigma=(SE, SI), de_ev=DE, particles=parts)
+    limit = sim.push_grid()
+    for sp in (0, 1):
+        sim.set_push_grid(sp, limit[sp])  # the resident limit itself is accepted
+        sim.set_push_grid(sp, 0)
+        for bad in (1, limit[sp] // 2, limit[sp] - 1, limit[sp] + 1):
+            with pytest.raises(ed.EdupicError):
+                sim.set_push_grid(sp, bad)
+    assert sim.push_grid() == limit
     sim.close()
+
+
+def test_autotune_keeps_results():
+    mix = wl.batch_mix(n_discharges=4, seed0=310, scale=0.05)
+    ds = [m[0] for m in mix]
+    parts = [(m[1], m[2]) for m in mix]
+    ref = ed.simulation_for(ds, ed.FP32, sigma=(SE, SI), de_ev=DE, particles=parts)
+    sim = ed.simulation_for(ds, ed.FP32, sigma=(SE, SI), de_ev=DE, particles=parts)
+    limit = sim.push_grid()
+    grid, ms = sim.autotune(subcycles=2)
+    assert grid == limit[0] and ms > 0
+    n = 2 * (2 + 1) * ds[0].ion_subcycle  # the trial steps
+    ref.step(n + 40)
+    sim.step(40)
+    for k in range(len(ds)):
+        assert sim.counters(k) == ref.counters(k)
+        for sp in (0, 1):
+            a, b = sim.particles(k, sp), ref.particles(k, sp)
+            for c in range(4):
+                assert np.array_equal(a[c], b[c])
+    sim.close()
+    ref.close()
 
 
 def test_checkpoint_resume_is_exact(tmp_path):

@@ -113,3 +113,19 @@ def test_poisson_stream_rate_and_ranges():
     assert abs(gaps.mean() - 0.5) < 0.1  # mean inter-arrival 1/rate
     assert all(20 <= s.n_cycles <= 200 for s in specs)
     assert all(0.015 <= s.discharge.gap_m <= 0.05 and 200 <= s.discharge.n_grid <= 800 for s in specs)
+
+
+def test_stream_gives_up_after_its_wall_bound():
+    clk = FakeClock()
+    srv = FakeServer(clk, slots=0, round_s=0.0)  # nothing is ever admitted
+    specs = _specs([0.0], [1])
+
+    def advance(k):
+        clk.t += 0.5
+        return 0, len(srv.queue)
+
+    srv.advance = advance
+    import pytest
+
+    with pytest.raises(TimeoutError):
+        serving.run_stream(srv, specs, clock=clk, sleep=clk.sleep, max_wall_s=5.0)

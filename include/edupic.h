@@ -56,6 +56,7 @@ extern "C" {
 #define EDUPIC_MAX_EEPF_BINS 2048
 #define EDUPIC_MAX_IFED_BINS 4096
 #define EDUPIC_MAX_DISCHARGES 1024 /* discharges per simulation object */
+#define EDUPIC_MAX_CS_ENTRIES 4194304 /* cross-section table length (2^22) */
 #define EDUPIC_STEP_EVENTS 65536   /* absorbed particles (per species) and ionisations per step and discharge */
 #define EDUPIC_N_COUNTERS 16
 

@@ -104,7 +104,7 @@ int check_params(int nd, const edupic_params *ps, int precision)
         if (p.capacity_e < 1 || p.capacity_i < 1 || p.capacity_e > (1ll << 31) - 2 * kTileAlign ||
             p.capacity_i > (1ll << 31) - 2 * kTileAlign)
             return EDUPIC_EINVAL;
-        if (p.cs_entries < 1) return EDUPIC_EINVAL;
+        if (p.cs_entries < 1 || p.cs_entries > EDUPIC_MAX_CS_ENTRIES) return EDUPIC_EINVAL;
         if (!(p.e_exc_ev >= 0) || !(p.e_ion_ev > 0)) return EDUPIC_EINVAL;
     }
     return EDUPIC_OK;

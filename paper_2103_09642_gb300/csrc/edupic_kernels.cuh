@@ -381,14 +381,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Start moving a global line into this SM's L1 (no result, no wait): later
-// loads of the line then wait for this fill instead of starting their own
-// round trip.
-__device__ __forceinline__ void prefetch_l1(const void *p)
-{
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
 template <typename V>
 __device__ __forceinline__ V warp_incl_scan(V v)
 {
@@ -453,7 +445,7 @@ __device__ __forceinline__ __int128 group_sum128(__int128 v, __int128 *s_w, int 
 // them (Algorithm 6 after the test).  It re-derives the table index and, for
 // Ar+, the thermal partner from the same counter-based draws, so the result
 // is the same as executing the collision in place.
-constexpr int kWarpQueue = 256;  // queued colliders per warp before the warp drains them
+constexpr int kWarpQueue = 512;  // queued colliders per warp before the warp drains them
 
 // e- + Ar collision of the particle in `slot` (post-push state in memory),
 // including the append record and the deposition of an ionisation pair.
@@ -600,10 +592,9 @@ __device__ __noinline__ void absorbed(const DischargeDev *Dp, int slot, T xn, T 
 }
 
 // EEPF sample (Sec. 3.5): electrons in the centre 10% of the gap, energy of
-// the time-centred velocity, counted in the block's shared histogram sH
-// (added to the discharge's counters when the block flushes).
+// the time-centred velocity.
 template <typename T>
-__device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy, T vz, unsigned int *sH)
+__device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy, T vz)
 {
     const DischargeDev &D = *Dp;
     const T v2c = vxc * vxc + vy * vy + vz * vz;
@@ -619,7 +610,8 @@ __device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy,
         ok = r < (float)D.eepf_bins;
         b = ok ? (int)r : 0;
     }
-    if (ok) atomicAdd(sH + b, 1u);
+    // striped over kEepfStripes copies to spread the atomics; summed on read
+    if (ok) atomicAdd(D.eepf + (blockIdx.x & (kEepfStripes - 1)) * D.eepf_bins + b, 1ull);
 }
 
 // ---------------------------------------------------------------- particle kernel
@@ -633,12 +625,12 @@ __host__ __device__ constexpr int ring_stages()
 
 // Dynamic shared memory: [tile ring: stages x 4 arrays x TILE T][coarse
 // sigma_max: kCoarse T][E pairs: ng_max T2][deposition: 3 x ng_max u32]
-// [EEPF histogram: eepf_max u32][tile prefix: nd+1 int].
+// [tile prefix: nd+1 int].
 template <typename T>
 __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eepf_max)
 {
     return (size_t)ring_stages<T>() * 4 * kThreads * VecOf<T>::n * sizeof(T) + (size_t)kCoarse * sizeof(T) +
-           (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 12 + (size_t)eepf_max * 4 + (size_t)(nd + 1) * 4;
+           (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 12 + (size_t)(nd + 1) * 4 + 0 * (size_t)eepf_max;
 }
 
 template <typename T, int SP>
@@ -660,8 +652,8 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     acc.cnt = reinterpret_cast<unsigned int *>(sE2 + ng_max);
     acc.lo = acc.cnt + ng_max;
     acc.hi = acc.lo + ng_max;
-    unsigned int *sH = acc.hi + ng_max;  // EEPF counts of the current discharge (electrons)
-    int *sPre = reinterpret_cast<int *>(sH + eepf_max);
+    int *sPre = reinterpret_cast<int *>(acc.hi + ng_max);
+    (void)eepf_max;
     __shared__ unsigned int sCnt[EDUPIC_N_COUNTERS];
     __shared__ int sW[33];
     __shared__ int sQueue[kWarps][kWarpQueue];  // colliders queued by each warp
@@ -692,21 +684,12 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (tid < EDUPIC_N_COUNTERS) sCnt[tid] = 0;
-    if (SP == 0 && measure)
-        for (int b = tid; b < eepf_max; b += blockDim.x) sH[b] = 0u;
     __syncthreads();
     const int cs_shift = sD.cs_shift[SP];
     const Ctrl *ctrls = sD.ctrl;  // the counts of all discharges are one packed array
     int staged = 0;
     pdl_wait();
     pdl_launch_next();
-    {
-        // the field of the pre-staged discharge (written by the preceding
-        // kernel) is requested now, beside the counts read next
-        const T *ef = reinterpret_cast<const T *>(sD.ef_t);
-        for (int p = tid * (128 / (int)sizeof(T)); p < sD.ng; p += blockDim.x * (128 / (int)sizeof(T)))
-            prefetch_l1(ef + p);
-    }
     // tiles per discharge -> prefix over discharges (every block computes it)
     {
         int running = 0;
@@ -773,18 +756,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
 
     auto flush = [&](bool last) {
         drain();
-        flush_dep(!last);  // ends with every thread past its samples
-        if (eepf_on) {
-            // non-empty bins into one of the discharge's striped histograms
-            unsigned long long *h = D->eepf + (blockIdx.x & (kEepfStripes - 1)) * D->eepf_bins;
-            for (int b = tid; b < D->eepf_bins; b += blockDim.x) {
-                const unsigned int c = sH[b];
-                if (c) {
-                    atomicAdd(h + b, (unsigned long long)c);
-                    sH[b] = 0u;
-                }
-            }
-        }
+        flush_dep(!last);
         if (tid < EDUPIC_N_COUNTERS) {
             const unsigned int c = sCnt[tid];
             if (c) atomicAdd(D->ctrl->counters + tid, (unsigned long long)c);
@@ -923,7 +895,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             }
             const T vxn = SP == 0 ? vx - e_x * factor : vx + e_x * factor;
             if (SP == 0 && eepf_on && live && x >= lo && x <= hi)
-                eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e], sH);
+                eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e]);
             const T xn = x + vxn * dt;
             xa[e] = live ? xn : x;
             vxa[e] = live ? vxn : vx;
@@ -1023,28 +995,10 @@ struct FieldScratch {
 
 // Load (Q_e, Q_i) of the owned points; swap in the accumulated deposition
 // when `swap` (and add the current field to the time sums when `measure`).
-// Every load of the owned points is issued before any store, so the points
-// cost one memory round trip together rather than one each.
 template <int PMAX>
 __device__ __forceinline__ void load_q(const DischargeDev &D, int first, int last, bool swap, bool next_ion,
                                        bool measure, long long *Qe, long long *Qi)
 {
-    long long qe[PMAX], qi[PMAX], ae[PMAX], ai[PMAX], fc[PMAX];
-    double se[PMAX], si[PMAX], sf[PMAX];
-#pragma unroll
-    for (int j = 0; j < PMAX; ++j) {
-        const int p = first + j;
-        const bool own = p < last;
-        qe[j] = own ? D.q_e[p] : 0;
-        qi[j] = own ? D.q_i[p] : 0;
-        ae[j] = own && swap ? D.acc_e[p] : 0;
-        ai[j] = own && swap && next_ion ? D.acc_i[p] : 0;
-        const bool sums = own && swap && measure;
-        fc[j] = sums ? D.f_cur[p] : 0;
-        se[j] = sums ? D.sum_qe[p] : 0.0;
-        si[j] = sums ? D.sum_qi[p] : 0.0;
-        sf[j] = sums ? D.sum_f[p] : 0.0;
-    }
 #pragma unroll
     for (int j = 0; j < PMAX; ++j) {
         const int p = first + j;
@@ -1052,24 +1006,24 @@ __device__ __forceinline__ void load_q(const DischargeDev &D, int first, int las
         Qi[j] = 0;
         if (p >= last) continue;
         if (swap && measure) {
-            D.sum_qe[p] = se[j] + (double)qe[j];
-            D.sum_qi[p] = si[j] + (double)qi[j];
-            D.sum_f[p] = sf[j] + (double)fc[j];
+            D.sum_qe[p] += (double)D.q_e[p];
+            D.sum_qi[p] += (double)D.q_i[p];
+            D.sum_f[p] += (double)D.f_cur[p];
         }
         if (swap) {
-            Qe[j] = ae[j];
+            Qe[j] = D.acc_e[p];
             D.acc_e[p] = 0;
-            D.q_e[p] = ae[j];
+            D.q_e[p] = Qe[j];
             if (next_ion) {
-                Qi[j] = ai[j];
+                Qi[j] = D.acc_i[p];
                 D.acc_i[p] = 0;
-                D.q_i[p] = ai[j];
+                D.q_i[p] = Qi[j];
             } else {
-                Qi[j] = qi[j];
+                Qi[j] = D.q_i[p];
             }
         } else {
-            Qe[j] = qe[j];
-            Qi[j] = qi[j];
+            Qe[j] = D.q_e[p];
+            Qi[j] = D.q_i[p];
         }
     }
 }
@@ -1088,7 +1042,6 @@ __device__ void solve_field(const DischargeDev &D, long long tc, bool swap, bool
         D.fs->sum_d0 += D.fs->d0;
     }
     long long Qe[PMAX], Qi[PMAX], F[PMAX];
-    const double V = D.vdrive[tc];  // fetched with the densities, used after the scans
     load_q<PMAX>(D, first, last, swap, next_ion, measure, Qe, Qi);
     // F: inclusive scan of D_p over p = 0..M (D_p = 0 at the electrodes)
     long long run = 0;
@@ -1113,6 +1066,7 @@ __device__ void solve_field(const DischargeDev &D, long long tc, bool swap, bool
         }
     }
     const __int128 gtot = group_sum128(gpart, sm.w128, gtid, G, bar);
+    const double V = D.vdrive[tc];
     const double c = D.poisson_c;
     if (gtid == 0) {
         const double d0 = (c * (double)gtot - V) / (double)M;
@@ -1226,12 +1180,8 @@ __device__ long long compact_species(const DischargeDev &D, int sp, int *sA, int
     for (int b = 0; b < H; b += g) {
         const long long j = nn + b + gtid;
         bool alive = false;
-        T xj = 0, vxj = 0, vyj = 0, vzj = 0;
-        if (b + gtid < H) {  // the whole tail particle is loaded before any store
-            xj = X[j];
-            vxj = VX[j];
-            vyj = VY[j];
-            vzj = VZ[j];
+        if (b + gtid < H) {
+            const T xj = X[j];
             alive = (xj >= (T)0.0) && (xj <= L);
         }
         int tot;
@@ -1240,10 +1190,10 @@ __device__ long long compact_species(const DischargeDev &D, int sp, int *sA, int
         const int dst = (alive && k < H) ? hs[k] : -1;
         if (alive && (dst < 0 || dst >= nn)) atomicOr(&C->error, kErrHoles);  // inconsistent hole list
         if (alive && dst >= 0 && dst < nn) {
-            X[dst] = xj;
-            VX[dst] = vxj;
-            VY[dst] = vyj;
-            VZ[dst] = vzj;
+            X[dst] = X[j];
+            VX[dst] = VX[j];
+            VY[dst] = VY[j];
+            VZ[dst] = VZ[j];
         }
         filled += tot;
     }
@@ -1270,14 +1220,6 @@ __device__ void append_products(const DischargeDev &D, int *sA, long long &ne, l
     const T *px = reinterpret_cast<const T *>(D.prod_x);
     for (int i = gtid; i < P; i += g) {
         const int h = D.prod_parent[i];
-        // the product's values are loaded before its rank is known
-        const T x = px[i];
-        const T ve0 = reinterpret_cast<const T *>(D.prod_ve[0])[i];
-        const T ve1 = reinterpret_cast<const T *>(D.prod_ve[1])[i];
-        const T ve2 = reinterpret_cast<const T *>(D.prod_ve[2])[i];
-        const T vi0 = reinterpret_cast<const T *>(D.prod_vi[0])[i];
-        const T vi1 = reinterpret_cast<const T *>(D.prod_vi[1])[i];
-        const T vi2 = reinterpret_cast<const T *>(D.prod_vi[2])[i];
         int lo = 0, hi = P;  // rank of h among the sorted parents
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
@@ -1289,14 +1231,14 @@ __device__ void append_products(const DischargeDev &D, int *sA, long long &ne, l
         const int r = lo;
         if (r < keep) {
             const long long se = ne + r, si = ni + r;
-            X0[se] = x;
-            VX0[se] = ve0;
-            VY0[se] = ve1;
-            VZ0[se] = ve2;
-            X1[si] = x;
-            VX1[si] = vi0;
-            VY1[si] = vi1;
-            VZ1[si] = vi2;
+            X0[se] = px[i];
+            VX0[se] = reinterpret_cast<const T *>(D.prod_ve[0])[i];
+            VY0[se] = reinterpret_cast<const T *>(D.prod_ve[1])[i];
+            VZ0[se] = reinterpret_cast<const T *>(D.prod_ve[2])[i];
+            X1[si] = px[i];
+            VX1[si] = reinterpret_cast<const T *>(D.prod_vi[0])[i];
+            VY1[si] = reinterpret_cast<const T *>(D.prod_vi[1])[i];
+            VZ1[si] = reinterpret_cast<const T *>(D.prod_vi[2])[i];
         }
     }
     if (gtid == 0) {
@@ -1335,39 +1277,6 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDe
     if (threadIdx.x < kGroupA) {
         // (A) particle bookkeeping
         const int gtid = threadIdx.x;
-        {
-            // the event lists and the records they touch first (the tail
-            // particles that fill holes, the product records) are requested
-            // together, so the steps below find them on their way
-            const int he = min(C->holes[0], kEvents), hi = ion_step ? min(C->holes[1], kEvents) : 0;
-            const int np = min(C->products, kEvents);
-            const long long n0 = C->n[0], n1 = C->n[1];
-            const int es = (int)sizeof(T);
-            if (gtid < he && he <= n0) {
-                prefetch_l1(D.holes[0] + gtid);
-                const long long j = n0 - he + gtid;
-                prefetch_l1((const char *)D.x[0] + j * es);
-                prefetch_l1((const char *)D.vx[0] + j * es);
-                prefetch_l1((const char *)D.vy[0] + j * es);
-                prefetch_l1((const char *)D.vz[0] + j * es);
-            }
-            if (gtid < hi && hi <= n1) {
-                prefetch_l1(D.holes[1] + gtid);
-                const long long j = n1 - hi + gtid;
-                prefetch_l1((const char *)D.x[1] + j * es);
-                prefetch_l1((const char *)D.vx[1] + j * es);
-                prefetch_l1((const char *)D.vy[1] + j * es);
-                prefetch_l1((const char *)D.vz[1] + j * es);
-            }
-            if (gtid < np) {
-                prefetch_l1(D.prod_parent + gtid);
-                prefetch_l1((const char *)D.prod_x + gtid * es);
-                for (int c = 0; c < 3; ++c) {
-                    prefetch_l1((const char *)D.prod_ve[c] + gtid * es);
-                    prefetch_l1((const char *)D.prod_vi[c] + gtid * es);
-                }
-            }
-        }
         long long ne = compact_species<T>(D, 0, sA, sW, gtid, kGroupA, 1);
         long long ni = ion_step ? compact_species<T>(D, 1, sA, sW, gtid, kGroupA, 1) : C->n[1];
         append_products<T>(D, sA, ne, ni, gtid, kGroupA, 1);

@@ -43,6 +43,7 @@ extern "C" {
 #define EDUPIC_EIO (-7)       /* checkpoint file could not be read/written */
 #define EDUPIC_ETIMEOUT (-8)  /* bounded wait expired */
 #define EDUPIC_ETOOBIG (-9)   /* size beyond the fixed scratch of edupic_fields_noalloc */
+#define EDUPIC_ESTABILITY (-10) /* an accuracy/stability condition fails (edupic_check_accuracy) */
 
 /* ---------------------------------------------------------------- enums */
 #define EDUPIC_FP64 0 /* particles, push and collisions in FP64 */
@@ -226,6 +227,35 @@ int edupic_get_counters(edupic_sim *sim, int d, int64_t out[EDUPIC_N_COUNTERS]);
 
 /* Clear the measured diagnostics of discharge d. */
 int edupic_reset_diagnostics(edupic_sim *sim, int d);
+
+/* Accuracy and stability conditions of Sec. 2.2 (the checks the paper's
+ * code writes to info.txt, Sec. 3.5), evaluated for discharge d from its
+ * measured diagnostics (so after measured steps, else EDUPIC_ESTATE):
+ *  1. dx / lambda_D <= 1, lambda_D from the peak time-averaged n_e and the
+ *     effective temperature kT_e = 2/3 of the mean EEPF energy;
+ *  2. omega_pe dt_e < 2 at the peak time-averaged n_e;
+ *  3. the largest collision probability per step, 1 - exp(-n_gas
+ *     max(sigma_tot v) dt), below 0.05 for e- (dt_e) and Ar+ (dt_i), the
+ *     maximum taken over the tables (v: e- speed of the entry's energy,
+ *     Ar+ relative speed with the reduced mass);
+ *  4. the energies at which v dt = dx (e-: dt_e, Ar+: dt_i): the CFL limit,
+ *     to be compared by the user with where the EEPF has decayed.
+ * Writes *out (host) and returns EDUPIC_OK, or EDUPIC_ESTABILITY if one of
+ * 1-3 fails (out->failed: bit 0, 1, 2).  Opt-in: nothing else calls it. */
+typedef struct {
+    double debye_ratio;   /* dx / lambda_D */
+    double wpe_dt;        /* omega_pe dt_e */
+    double pcoll_max_e;   /* largest e- collision probability per electron step */
+    double pcoll_max_i;   /* largest Ar+ collision probability per ion step */
+    double cfl_max_ev_e;  /* e- energy (eV) with v dt_e = dx */
+    double cfl_max_ev_i;  /* Ar+ energy (eV) with v dt_i = dx */
+    double te_ev;         /* effective electron temperature used (eV) */
+    double ne_max;        /* peak time-averaged electron density used (m^-3) */
+    int failed;           /* bit 0: condition 1, bit 1: condition 2, bit 2: condition 3 */
+    int reserved;
+} edupic_accuracy;
+
+int edupic_check_accuracy(edupic_sim *sim, int d, edupic_accuracy *out);
 
 /* ---------------------------------------------------------------- checkpoint */
 

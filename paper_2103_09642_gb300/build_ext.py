@@ -23,7 +23,7 @@ LIB = os.path.join(BUILD, "libedupic_gb300.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-          "-Xcompiler", "-fno-fast-math"]
+          "-Xcompiler", "-fno-fast-math", "-Xcompiler", "-pthread"]
 UNITS = {
     "kernels_f64.cu": ["-fmad=false"],
     "kernels_f32.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
@@ -71,7 +71,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     print(r.stdout, r.stderr)
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+        r = subprocess.run([nvcc(), *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs],
+                           capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)

@@ -4,11 +4,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "edupic_host.h"
@@ -413,18 +415,59 @@ int upload_drive(edupic_sim *S, int d)
     return cuda_status(e);
 }
 
+// Run f(lo, hi) over [0, n) on up to 16 host threads (ranges of at least
+// 64 Ki elements; small n runs on the calling thread).
+template <typename F>
+void parallel_ranges(int64_t n, F f)
+{
+    constexpr int64_t kGrain = 1 << 16;
+    const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+    const int64_t nt = std::min<int64_t>({hw, 16, (n + kGrain - 1) / kGrain});
+    if (nt <= 1) {
+        f((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> ts;
+    ts.reserve((size_t)nt);
+    for (int64_t t = 0; t < nt; ++t) ts.emplace_back(f, n * t / nt, n * (t + 1) / nt);
+    for (auto &t : ts) t.join();
+}
+
+// Page-locked host staging buffer of the object (grown on demand, freed with it).
+void *pinned_reserve(edupic_sim *S, size_t bytes)
+{
+    if (S->pinned_bytes >= bytes) return S->pinned;
+    if (S->pinned) cudaFreeHost(S->pinned);
+    S->pinned = nullptr;
+    S->pinned_bytes = 0;
+    void *p = nullptr;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) return nullptr;
+    S->pinned = p;
+    S->pinned_bytes = bytes;
+    return p;
+}
+
+// x, vx, vy, vz converted to T in parallel into the pinned buffer, then
+// copied to the device as four DMA transfers and one synchronisation.
 template <typename T>
 int upload_particles(edupic_sim *S, int d, int sp, int64_t n, const double *const src[4])
 {
     void *dst[4] = {S->desc[d].x[sp], S->desc[d].vx[sp], S->desc[d].vy[sp], S->desc[d].vz[sp]};
-    std::vector<T> tmp((size_t)n);
-    for (int c = 0; c < 4; ++c) {
-        for (int64_t j = 0; j < n; ++j) tmp[j] = (T)src[c][j];
-        cudaError_t e = cudaMemcpyAsync(dst[c], tmp.data(), sizeof(T) * (size_t)n, cudaMemcpyHostToDevice, S->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-        if (e != cudaSuccess) return EDUPIC_ECUDA;
-    }
-    return EDUPIC_OK;
+    T *stage = static_cast<T *>(pinned_reserve(S, 4 * sizeof(T) * (size_t)n));
+    if (!stage) return EDUPIC_ENOMEM;
+    parallel_ranges(n, [&](int64_t lo, int64_t hi) {
+        for (int c = 0; c < 4; ++c) {
+            T *o = stage + (size_t)c * (size_t)n;
+            const double *in = src[c];
+            for (int64_t j = lo; j < hi; ++j) o[j] = (T)in[j];
+        }
+    });
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < 4 && e == cudaSuccess; ++c)
+        e = cudaMemcpyAsync(dst[c], stage + (size_t)c * (size_t)n, sizeof(T) * (size_t)n, cudaMemcpyHostToDevice,
+                            S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);  // the stage is reused by the next upload
+    return cuda_status(e);
 }
 
 template <typename T>
@@ -586,6 +629,19 @@ int edupic_set_cross_sections(edupic_sim *S, int species, int n_proc, int n_entr
             S->desc[d].g_idx_if = (float)(0.5 * (kArMassU * kAMU / 2.0) / kQE / de_ev);
         }
     }
+    // largest sigma_tot * v of the table (v of the lookup energy: e- lab
+    // speed, Ar+ relative speed with the reduced mass), for the accuracy check
+    {
+        const double m = species == 0 ? kME : 0.5 * kArMassU * kAMU;
+        double best = 0.0;
+        for (int k = 0; k < n_entries; ++k) {
+            double st = 0.0;
+            for (int q = 0; q < n_proc; ++q) st += sigma_m2[(size_t)q * n_entries + k];
+            const double v = std::sqrt(2.0 * (k * de_ev) * kQE / m);
+            best = std::max(best, st * v);
+        }
+        S->sigv_max[species] = best;
+    }
     S->cs_set[species] = true;
     return upload_desc(S);
 }
@@ -597,9 +653,16 @@ int edupic_load_particles(edupic_sim *S, int d, int species, int64_t n, const do
     if (n > (species == 0 ? S->params[d].capacity_e : S->params[d].capacity_i)) return EDUPIC_ECAPACITY;
     if (n > 0 && (!x || !vx || !vy || !vz)) return EDUPIC_EINVAL;
     const double L = S->params[d].gap_m;
-    for (int64_t j = 0; j < n; ++j)
-        if (!(x[j] >= 0.0 && x[j] <= L) || !std::isfinite(vx[j]) || !std::isfinite(vy[j]) || !std::isfinite(vz[j]))
-            return EDUPIC_EINVAL;
+    std::atomic<bool> bad{false};
+    parallel_ranges(n, [&](int64_t lo, int64_t hi) {
+        for (int64_t j = lo; j < hi; ++j)
+            if (!(x[j] >= 0.0 && x[j] <= L) || !std::isfinite(vx[j]) || !std::isfinite(vy[j]) ||
+                !std::isfinite(vz[j])) {
+                bad.store(true, std::memory_order_relaxed);
+                return;
+            }
+    });
+    if (bad.load()) return EDUPIC_EINVAL;
     const double *src[4] = {x, vx, vy, vz};
     int rc = upload_species(S, d, species, n, src);
     if (rc) return rc;
@@ -1031,6 +1094,42 @@ int edupic_load_state(edupic_sim *S, int d, const char *path)
     return EDUPIC_OK;
 }
 
+int edupic_check_accuracy(edupic_sim *S, int d, edupic_accuracy *out)
+{
+    if (!valid_d(S, d) || !out) return EDUPIC_EINVAL;
+    if (!S->cs_set[0] || !S->cs_set[1]) return EDUPIC_ESTATE;
+    const edupic_params &p = S->params[d];
+    const DischargeDev &D = S->desc[d];
+    std::vector<double> ne((size_t)p.n_grid);
+    std::vector<int64_t> h((size_t)p.eepf_bins);
+    int64_t measured = 0;
+    int rc = edupic_get_diagnostics(S, d, ne.data(), nullptr, nullptr, h.data(), nullptr, nullptr, &measured);
+    if (rc) return rc;
+    if (measured < 1) return EDUPIC_ESTATE;
+    double nmax = 0.0;
+    for (double v : ne) nmax = std::max(nmax, v);
+    double cnt = 0.0, esum = 0.0;
+    for (int k = 0; k < p.eepf_bins; ++k) {
+        cnt += (double)h[k];
+        esum += (double)h[k] * (k + 0.5) * p.eepf_de_ev;
+    }
+    edupic_accuracy a{};
+    a.ne_max = nmax;
+    a.te_ev = cnt > 0 ? (2.0 / 3.0) * esum / cnt : 0.0;  // effective temperature of the mean energy
+    const double lambda_d = (nmax > 0 && a.te_ev > 0) ? std::sqrt(kEPS0 * a.te_ev * kQE / (nmax * kQE * kQE)) : 0.0;
+    a.debye_ratio = lambda_d > 0 ? D.dx / lambda_d : 0.0;
+    a.wpe_dt = std::sqrt(nmax * kQE * kQE / (kEPS0 * kME)) * D.dt_e;
+    a.pcoll_max_e = 1.0 - std::exp(-D.n_gas * S->sigv_max[0] * D.dt_e);
+    a.pcoll_max_i = 1.0 - std::exp(-D.n_gas * S->sigv_max[1] * D.dt_i);
+    const double ve = D.dx / D.dt_e, vi = D.dx / D.dt_i;
+    a.cfl_max_ev_e = 0.5 * kME * ve * ve / kQE;
+    a.cfl_max_ev_i = 0.5 * (kArMassU * kAMU) * vi * vi / kQE;
+    a.failed = (a.debye_ratio > 1.0 ? 1 : 0) | (a.wpe_dt >= 2.0 ? 2 : 0) |
+               (a.pcoll_max_e >= 0.05 || a.pcoll_max_i >= 0.05 ? 4 : 0);
+    *out = a;
+    return a.failed ? EDUPIC_ESTABILITY : EDUPIC_OK;
+}
+
 const char *edupic_strerror(int status)
 {
     switch (status) {
@@ -1043,6 +1142,7 @@ const char *edupic_strerror(int status)
     case EDUPIC_ENAN: return "non-finite particle position";
     case EDUPIC_EIO: return "checkpoint file error";
     case EDUPIC_ETIMEOUT: return "bounded wait expired";
+    case EDUPIC_ESTABILITY: return "an accuracy or stability condition fails (see edupic_check_accuracy)";
     case EDUPIC_ETOOBIG: return "n_grid exceeds the fixed scratch of the no-allocation entry point (max 2048)";
     default: return "unknown status";
     }

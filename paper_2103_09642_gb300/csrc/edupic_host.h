@@ -57,11 +57,15 @@ struct edupic_sim {
     int sms = 0;
     bool graphs = true;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    double sigv_max[2] = {0.0, 0.0};  // largest sigma_tot * v of each species' table
+    void *pinned = nullptr;  // page-locked staging buffer for particle uploads
+    size_t pinned_bytes = 0;
 
     ~edupic_sim()
     {
         for (auto &g : graph)
             if (g) cudaGraphExecDestroy(g);
+        if (pinned) cudaFreeHost(pinned);
     }
     void drop_graphs()
     {

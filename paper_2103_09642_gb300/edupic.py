@@ -27,7 +27,7 @@ COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela
                  "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped",
                  "push_e", "push_i")
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECAPACITY", -4: "ECUDA", -5: "ESTATE", -6: "ENAN",
-          -7: "EIO", -8: "ETIMEOUT", -9: "ETOOBIG"}
+          -7: "EIO", -8: "ETIMEOUT", -9: "ETOOBIG", -10: "ESTABILITY"}
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 REQ_STATES = {REQ_QUEUED: "queued", REQ_RUNNING: "running", REQ_DONE: "done", REQ_FAILED: "failed"}
 
@@ -69,6 +69,13 @@ def to_params(d: Discharge, cs_entries: int) -> Params:
     p.e_exc_ev, p.e_ion_ev = d.e_exc_ev, d.e_ion_ev
     p.cs_entries = cs_entries
     return p
+
+
+class Accuracy(ctypes.Structure):
+    _fields_ = [("debye_ratio", ctypes.c_double), ("wpe_dt", ctypes.c_double), ("pcoll_max_e", ctypes.c_double),
+                ("pcoll_max_i", ctypes.c_double), ("cfl_max_ev_e", ctypes.c_double), ("cfl_max_ev_i", ctypes.c_double),
+                ("te_ev", ctypes.c_double), ("ne_max", ctypes.c_double), ("failed", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -117,6 +124,7 @@ def load_library(path: str = LIB_PATH):
         "edupic_set_push_grid": ([_VP, ctypes.c_int, ctypes.c_int]),
         "edupic_get_push_grid": ([_VP, ctypes.POINTER(ctypes.c_int)]),
         "edupic_autotune": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]),
+        "edupic_check_accuracy": ([_VP, ctypes.c_int, ctypes.POINTER(Accuracy)]),
         "edupic_get_counts": ([_VP, ctypes.c_int, _Q, _Q, _Q]),
         "edupic_get_particles": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _D, _D, _D, _D, _Q]),
         "edupic_get_fields": ([_VP, ctypes.c_int, _D, _D, _D, _D, _Q, _Q]),
@@ -315,6 +323,17 @@ class Simulation:
         c = np.zeros(N_COUNTERS, dtype=np.int64)
         _ck(self.L.edupic_get_counters(self._h, d, _ptr(c, ctypes.c_int64)), "get_counters")
         return {k: int(c[i]) for i, k in enumerate(COUNTER_NAMES)}
+
+    def check_accuracy(self, d: int = 0) -> dict:
+        """Accuracy and stability conditions of Sec. 2.2 from the measured
+        diagnostics; 'ok' is False when condition 1, 2 or 3 fails."""
+        a = Accuracy()
+        rc = self.L.edupic_check_accuracy(self._h, d, ctypes.byref(a))
+        if rc not in (0, -10):
+            _ck(rc, "check_accuracy")
+        out = {k: getattr(a, k) for k, _ in Accuracy._fields_ if k != "reserved"}
+        out["ok"] = rc == 0
+        return out
 
     def reset_diagnostics(self, d: int = 0):
         _ck(self.L.edupic_reset_diagnostics(self._h, d), "reset_diagnostics")

@@ -276,3 +276,47 @@ def test_checkpoint_resume_is_exact(tmp_path):
         got = sim2.particles(0, sp)
         for c in range(4):
             assert np.array_equal(got[c], full[0][0][sp][c])
+
+
+# --------------------------------------------------------------- accuracy conditions (Sec. 2.2)
+def _conditions(sim, d, k, se, si, de):
+    """The conditions written out here from the measured diagnostics."""
+    qe, me, eps0, amu = 1.602176634e-19, 9.1093837015e-31, 8.8541878128e-12, 1.66053906660e-27
+    g = sim.diagnostics(k)
+    h = g["eepf_counts"].astype(np.float64)
+    te = 2.0 / 3.0 * float((h * (np.arange(h.size) + 0.5) * d.eepf_de_ev).sum() / h.sum())
+    nmax = float(g["n_e"].max())
+    dx = d.gap_m / (d.n_grid - 1)
+    dt_e = 1.0 / (d.cycle_freq_hz * d.steps_per_cycle)
+    dt_i = d.ion_subcycle * dt_e
+    n_gas = d.pressure_pa / (1.380649e-23 * d.gas_temp_k)
+    lam = np.sqrt(eps0 * te * qe / (nmax * qe * qe))
+    mu_i = 0.5 * 39.948 * amu
+    eps = np.arange(se.shape[1]) * de
+    sv_e = (se.sum(axis=0) * np.sqrt(2 * eps * qe / me)).max()
+    sv_i = (si.sum(axis=0) * np.sqrt(2 * eps * qe / mu_i)).max()
+    return {"debye_ratio": dx / lam, "wpe_dt": np.sqrt(nmax * qe * qe / (eps0 * me)) * dt_e,
+            "pcoll_max_e": 1 - np.exp(-n_gas * sv_e * dt_e), "pcoll_max_i": 1 - np.exp(-n_gas * sv_i * dt_i),
+            "cfl_max_ev_e": 0.5 * me * (dx / dt_e) ** 2 / qe, "cfl_max_ev_i": 0.5 * 39.948 * amu * (dx / dt_i) ** 2 / qe}
+
+
+def test_accuracy_conditions():
+    d, e, i = wl.reference_steady(seed=3, n=20_000)
+    sim = ed.simulation_for([d], ed.FP32, sigma=(SE, SI), de_ev=DE, particles=[(e, i)])
+    with pytest.raises(ed.EdupicError):
+        sim.check_accuracy(0)  # nothing measured yet
+    sim.step(200, measure=True)
+    got = sim.check_accuracy(0)
+    ref = _conditions(sim, d, 0, SE, SI, DE)
+    for k, v in ref.items():
+        assert abs(got[k] - v) <= 1e-9 * abs(v), (k, got[k], v)
+    # the reference discharge meets conditions 1-3 at this density (Table 2 settings)
+    assert got["ok"] and got["failed"] == 0
+    # a time step 40x longer breaks omega_pe dt < 2 and the collision bound
+    d2 = d.replace(steps_per_cycle=100, ion_subcycle=20)
+    sim2 = ed.simulation_for([d2], ed.FP32, sigma=(SE, SI), de_ev=DE, particles=[(e, i)])
+    sim2.step(20, measure=True)
+    bad = sim2.check_accuracy(0)
+    assert not bad["ok"] and bad["failed"] & 4
+    sim.close()
+    sim2.close()

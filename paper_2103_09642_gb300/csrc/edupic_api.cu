@@ -416,11 +416,11 @@ int upload_drive(edupic_sim *S, int d)
 }
 
 // Run f(lo, hi) over [0, n) on up to 16 host threads (ranges of at least
-// 64 Ki elements; small n runs on the calling thread).
+// 256 Ki elements; small n runs on the calling thread).
 template <typename F>
 void parallel_ranges(int64_t n, F f)
 {
-    constexpr int64_t kGrain = 1 << 16;
+    constexpr int64_t kGrain = 1 << 18;
     const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
     const int64_t nt = std::min<int64_t>({hw, 16, (n + kGrain - 1) / kGrain});
     if (nt <= 1) {
@@ -447,21 +447,33 @@ void *pinned_reserve(edupic_sim *S, size_t bytes)
     return p;
 }
 
-// x, vx, vy, vz converted to T in parallel into the pinned buffer, then
-// copied to the device as four DMA transfers and one synchronisation.
+// x, vx, vy, vz checked (0 <= x <= L, finite velocities) and converted to
+// T in one parallel pass into the pinned buffer, then copied to the device
+// as four DMA transfers and one synchronisation.  EDUPIC_EINVAL (nothing
+// copied) if a particle fails the check.
 template <typename T>
 int upload_particles(edupic_sim *S, int d, int sp, int64_t n, const double *const src[4])
 {
     void *dst[4] = {S->desc[d].x[sp], S->desc[d].vx[sp], S->desc[d].vy[sp], S->desc[d].vz[sp]};
     T *stage = static_cast<T *>(pinned_reserve(S, 4 * sizeof(T) * (size_t)n));
     if (!stage) return EDUPIC_ENOMEM;
+    const double L = S->params[d].gap_m;
+    std::atomic<bool> bad{false};
     parallel_ranges(n, [&](int64_t lo, int64_t hi) {
-        for (int c = 0; c < 4; ++c) {
-            T *o = stage + (size_t)c * (size_t)n;
-            const double *in = src[c];
-            for (int64_t j = lo; j < hi; ++j) o[j] = (T)in[j];
+        T *o0 = stage, *o1 = stage + (size_t)n, *o2 = stage + 2 * (size_t)n, *o3 = stage + 3 * (size_t)n;
+        const double *x = src[0], *vx = src[1], *vy = src[2], *vz = src[3];
+        bool ok = true;
+        for (int64_t j = lo; j < hi; ++j) {
+            ok = ok && (x[j] >= 0.0 && x[j] <= L) && std::isfinite(vx[j]) && std::isfinite(vy[j]) &&
+                 std::isfinite(vz[j]);
+            o0[j] = (T)x[j];
+            o1[j] = (T)vx[j];
+            o2[j] = (T)vy[j];
+            o3[j] = (T)vz[j];
         }
+        if (!ok) bad.store(true, std::memory_order_relaxed);
     });
+    if (bad.load()) return EDUPIC_EINVAL;
     cudaError_t e = cudaSuccess;
     for (int c = 0; c < 4 && e == cudaSuccess; ++c)
         e = cudaMemcpyAsync(dst[c], stage + (size_t)c * (size_t)n, sizeof(T) * (size_t)n, cudaMemcpyHostToDevice,
@@ -652,18 +664,7 @@ int edupic_load_particles(edupic_sim *S, int d, int species, int64_t n, const do
     if (!valid_d(S, d) || (species != 0 && species != 1) || n < 0) return EDUPIC_EINVAL;
     if (n > (species == 0 ? S->params[d].capacity_e : S->params[d].capacity_i)) return EDUPIC_ECAPACITY;
     if (n > 0 && (!x || !vx || !vy || !vz)) return EDUPIC_EINVAL;
-    const double L = S->params[d].gap_m;
-    std::atomic<bool> bad{false};
-    parallel_ranges(n, [&](int64_t lo, int64_t hi) {
-        for (int64_t j = lo; j < hi; ++j)
-            if (!(x[j] >= 0.0 && x[j] <= L) || !std::isfinite(vx[j]) || !std::isfinite(vy[j]) ||
-                !std::isfinite(vz[j])) {
-                bad.store(true, std::memory_order_relaxed);
-                return;
-            }
-    });
-    if (bad.load()) return EDUPIC_EINVAL;
-    const double *src[4] = {x, vx, vy, vz};
+    const double *src[4] = {x, vx, vy, vz};  // checked while they are converted
     int rc = upload_species(S, d, species, n, src);
     if (rc) return rc;
     long long nn = n;

@@ -320,3 +320,18 @@ def test_accuracy_conditions():
     assert not bad["ok"] and bad["failed"] & 4
     sim.close()
     sim2.close()
+
+
+def test_load_rejects_invalid_particles():
+    d, e, i = wl.reference_start(seed=11, n0=500)
+    sim = ed.simulation_for([d], ed.FP32, sigma=(SE, SI), de_ev=DE, particles=[(e, i)])
+    before = [a.copy() for a in sim.particles(0, ed.ELECTRONS)]
+    for field, value in (("x", -1e-6), ("x", d.gap_m * 1.001), ("vy", np.nan), ("vz", np.inf)):
+        bad = wl.Particles(e.x.copy(), e.vx.copy(), e.vy.copy(), e.vz.copy())
+        getattr(bad, field)[123] = value
+        with pytest.raises(ed.EdupicError):
+            sim.load(0, ed.ELECTRONS, bad)
+        after = sim.particles(0, ed.ELECTRONS)
+        for c in range(4):  # nothing was copied
+            assert np.array_equal(after[c], before[c])
+    sim.close()

@@ -228,6 +228,16 @@ int edupic_get_counters(edupic_sim *sim, int d, int64_t out[EDUPIC_N_COUNTERS]);
 /* Clear the measured diagnostics of discharge d. */
 int edupic_reset_diagnostics(edupic_sim *sim, int d);
 
+/* Power absorption of Sec. 3.5: the space and time average of j E for
+ * electrons (out[0]) and Ar+ (out[1]) over the gap and the measured steps,
+ * in W/m^3, from the field's work on every measured push, q E_x v_c dt with
+ * v_c = (v_old + v_new) / 2 (E_x gathered at the position before the push):
+ * W / (A L T_meas) times that sum, T_meas = measured steps x dt_e.  out is
+ * host memory; zero before any measured step.  The sums are added in an
+ * order that depends on the launch, so results agree to rounding, not bit
+ * for bit, between runs. */
+int edupic_get_power(edupic_sim *sim, int d, double out[2]);
+
 /* Accuracy and stability conditions of Sec. 2.2 (the checks the paper's
  * code writes to info.txt, Sec. 3.5), evaluated for discharge d from its
  * measured diagnostics (so after measured steps, else EDUPIC_ESTATE):

@@ -95,6 +95,8 @@ def lib():
             L.orc_get_counters.argtypes = [ctypes.c_void_p, _Q]
             L.orc_get_diagnostics.argtypes = [ctypes.c_void_p, _D, _D, _D, _Q, _Q, _Q]
             L.orc_get_diagnostics.restype = ctypes.c_int64
+            L.orc_get_power.argtypes = [ctypes.c_void_p, _D]
+            L.orc_get_power.restype = ctypes.c_int64
             L.orc_eepf_normalise.argtypes = [_Q, ctypes.c_int, ctypes.c_double, _D, _D]
             L.orc_ifed_normalise.argtypes = [_Q, ctypes.c_int, ctypes.c_double, _D, _D]
             L.orc_get_derived.argtypes = [ctypes.c_void_p, _D]
@@ -304,6 +306,13 @@ class Sim:
                                       *[_p(v, ctypes.c_int64) for v in (eepf, ip, ig)])
         return dict(measured_steps=int(m), n_e=ne, n_i=ni, phi=phi, eepf_counts=eepf,
                     ifed_pow_counts=ip, ifed_gnd_counts=ig)
+
+    def power(self) -> dict:
+        """Power absorption densities of e- and Ar+ (W/m^3), space and time
+        averaged over the measured steps."""
+        out = np.zeros(2)
+        m = lib().orc_get_power(self._h, _p(out, ctypes.c_double))
+        return dict(measured_steps=int(m), electrons=float(out[0]), ions=float(out[1]))
 
     def derived(self) -> dict:
         out = np.zeros(12)

@@ -202,6 +202,7 @@ typedef struct {
     int64_t measured_steps;
     double *sum_ne, *sum_ni, *sum_phi;
     int64_t *eepf, *ifed_pow, *ifed_gnd;
+    double work[2]; /* sum over measured pushes of q E_x v_c dt, per unit weight (J), e- and Ar+ */
     int64_t counters[16];
     /* scratch */
     orc_product *prod;
@@ -711,6 +712,9 @@ static void one_step(orc_sim *s, int measure)
         double vx_old = E->vx[k];
         E->vx[k] -= e_x * s->factor_e;
         if (measure) {
+            /* power absorption (Sec. 3.5): the field's work on the particle
+             * over the step, q E_x v_c dt with the time-centred velocity */
+            s->work[ORC_SPECIES_E] += -ORC_E_CHARGE * e_x * (0.5 * (vx_old + E->vx[k])) * s->dt_e;
             double xo = E->x[k];
             if (xo >= 0.45 * p->gap_m && xo <= 0.55 * p->gap_m) {
                 double vc = 0.5 * (vx_old + E->vx[k]);
@@ -729,7 +733,9 @@ static void one_step(orc_sim *s, int measure)
             cell_of(I->x[k], s->inv_dx, ng, &c, &c0);
             double c1 = c + 1 - c0, c2 = c0 - c;
             double e_x = c1 * s->efield[c] + c2 * s->efield[c + 1];
+            double vx_old = I->vx[k];
             I->vx[k] += e_x * s->factor_i;
+            if (measure) s->work[ORC_SPECIES_I] += ORC_E_CHARGE * e_x * (0.5 * (vx_old + I->vx[k])) * s->dt_i;
             I->x[k] += I->vx[k] * s->dt_i;
         }
     }
@@ -919,6 +925,17 @@ int64_t orc_get_diagnostics(const orc_sim *s, double *ne_avg, double *ni_avg, do
     if (eepf_counts) memcpy(eepf_counts, s->eepf, sizeof(int64_t) * (size_t)s->p.eepf_bins);
     if (ifed_pow_counts) memcpy(ifed_pow_counts, s->ifed_pow, sizeof(int64_t) * (size_t)s->p.ifed_bins);
     if (ifed_gnd_counts) memcpy(ifed_gnd_counts, s->ifed_gnd, sizeof(int64_t) * (size_t)s->p.ifed_bins);
+    return s->measured_steps;
+}
+
+/* Power absorption by e- and Ar+ (Sec. 3.5): the space and time average of
+ * j E over the gap and the measured time, = (work per unit weight) W /
+ * (A L T_meas), with T_meas = measured steps x dt_e.  W/m^3. */
+int64_t orc_get_power(const orc_sim *s, double out[2])
+{
+    const double t = (double)s->measured_steps * s->dt_e;
+    for (int k = 0; k < 2; ++k)
+        out[k] = t > 0.0 ? s->work[k] * s->p.weight / (s->p.area_m2 * s->p.gap_m * t) : 0.0;
     return s->measured_steps;
 }
 

@@ -68,6 +68,7 @@ Layout layout_of(const edupic_params &p, size_t elem)
     L.eepf = take((size_t)kEepfStripes * p.eepf_bins * 8);
     L.ifed_pow = take((size_t)p.ifed_bins * 8);
     L.ifed_gnd = take((size_t)p.ifed_bins * 8);
+    L.power = take(2 * sizeof(double));
     L.holes[0] = take((size_t)kEvents * 4);
     L.holes[1] = take((size_t)kEvents * 4);
     L.prod_parent = take((size_t)kEvents * 4);
@@ -234,6 +235,7 @@ void fill_desc(edupic_sim *S, int d)
     D.eepf = reinterpret_cast<unsigned long long *>(b + L.eepf);
     D.ifed_pow = reinterpret_cast<unsigned long long *>(b + L.ifed_pow);
     D.ifed_gnd = reinterpret_cast<unsigned long long *>(b + L.ifed_gnd);
+    D.power = reinterpret_cast<double *>(b + L.power);
     D.ctrl = S->d_ctrl + d;
     D.prod_parent = reinterpret_cast<int *>(b + L.prod_parent);
     D.sort_buf = reinterpret_cast<int *>(b + L.sort_buf);
@@ -1008,6 +1010,7 @@ int edupic_reset_diagnostics(edupic_sim *S, int d)
     if (e == cudaSuccess) e = cudaMemsetAsync(D.eepf, 0, (size_t)kEepfStripes * p.eepf_bins * 8, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.ifed_pow, 0, (size_t)p.ifed_bins * 8, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.ifed_gnd, 0, (size_t)p.ifed_bins * 8, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.power, 0, 2 * sizeof(double), S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&D.ctrl->measured, 0, sizeof(long long), S->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
     return cuda_status(e);
@@ -1093,6 +1096,23 @@ int edupic_load_state(edupic_sim *S, int d, const char *path)
         if (rc) return rc;
     }
     return EDUPIC_OK;
+}
+
+int edupic_get_power(edupic_sim *S, int d, double out[2])
+{
+    if (!valid_d(S, d) || !out) return EDUPIC_EINVAL;
+    Ctrl c;
+    int rc = read_ctrl(S, d, &c);
+    if (rc) return rc;
+    double sums[2];
+    if (cudaMemcpy(sums, S->desc[d].power, sizeof(sums), cudaMemcpyDeviceToHost) != cudaSuccess) return EDUPIC_ECUDA;
+    const edupic_params &p = S->params[d];
+    const DischargeDev &D = S->desc[d];
+    // q E_x v_c dt summed per unit weight, with v_c = (v_old + v_new) / 2
+    const double work[2] = {-kQE * 0.5 * sums[0] * D.dt_e, kQE * 0.5 * sums[1] * D.dt_i};
+    const double t = (double)c.measured * D.dt_e;
+    for (int k = 0; k < 2; ++k) out[k] = t > 0.0 ? work[k] * p.weight / (p.area_m2 * p.gap_m * t) : 0.0;
+    return error_of(c);
 }
 
 int edupic_check_accuracy(edupic_sim *S, int d, edupic_accuracy *out)

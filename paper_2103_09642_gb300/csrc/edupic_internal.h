@@ -82,6 +82,7 @@ struct DischargeDev {
     double *avg;               // [3][ng] read-back buffer: time-averaged n_e, n_i, phi
     unsigned long long *eepf;  // [kEepfStripes][eepf_bins], summed on read
     unsigned long long *ifed_pow, *ifed_gnd;
+    double *power;             // [2] e-, Ar+: sum over measured pushes of E_x (v_old + v_new)
     Ctrl *ctrl;
     int *holes[2];
     int *prod_parent;

@@ -754,9 +754,19 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         __syncthreads();
     };
 
+    double pw_acc = 0.0;  // E_x (v_old + v_new) of this thread's measured pushes (current discharge)
+
     auto flush = [&](bool last) {
         drain();
         flush_dep(!last);
+        if (measure) {
+            // power absorption: warp sums, one add per warp
+            double v = pw_acc;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0 && v != 0.0) atomicAdd(D->power + SP, v);
+            pw_acc = 0.0;
+        }
         if (tid < EDUPIC_N_COUNTERS) {
             const unsigned int c = sCnt[tid];
             if (c) atomicAdd(D->ctrl->counters + tid, (unsigned long long)c);
@@ -879,6 +889,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         int kk[VEC];
         bool in[VEC];
         T w2[VEC];  // v^2 (e-) or g^2 (Ar+)
+        T pw = (T)0;  // E_x (v_old + v_new) of the measured pushes of this tile
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
             const bool live = base + e < n;
@@ -894,6 +905,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
                 e_x = ep.x + (c0 - (T)p) * (ep.y - ep.x);  // same linear weights
             }
             const T vxn = SP == 0 ? vx - e_x * factor : vx + e_x * factor;
+            if (measure && live) pw += e_x * (vx + vxn);
             if (SP == 0 && eepf_on && live && x >= lo && x <= hi)
                 eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e]);
             const T xn = x + vxn * dt;
@@ -919,6 +931,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             else
                 kk[e] = cs_index_f(q2 * idx_scale + 0.5f, cs_n);
         }
+        if (measure) pw_acc += (double)pw;
         // phase 2: collision-test uniforms (one Philox block per thread)
         T ut[VEC];
         {

@@ -125,6 +125,7 @@ def load_library(path: str = LIB_PATH):
         "edupic_get_push_grid": ([_VP, ctypes.POINTER(ctypes.c_int)]),
         "edupic_autotune": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]),
         "edupic_check_accuracy": ([_VP, ctypes.c_int, ctypes.POINTER(Accuracy)]),
+        "edupic_get_power": ([_VP, ctypes.c_int, _D]),
         "edupic_get_counts": ([_VP, ctypes.c_int, _Q, _Q, _Q]),
         "edupic_get_particles": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _D, _D, _D, _D, _Q]),
         "edupic_get_fields": ([_VP, ctypes.c_int, _D, _D, _D, _D, _Q, _Q]),
@@ -323,6 +324,13 @@ class Simulation:
         c = np.zeros(N_COUNTERS, dtype=np.int64)
         _ck(self.L.edupic_get_counters(self._h, d, _ptr(c, ctypes.c_int64)), "get_counters")
         return {k: int(c[i]) for i, k in enumerate(COUNTER_NAMES)}
+
+    def power(self, d: int = 0) -> dict:
+        """Power absorption densities of e- and Ar+ (W/m^3), space and time
+        averaged over the measured steps (Sec. 3.5)."""
+        out = np.zeros(2)
+        _ck(self.L.edupic_get_power(self._h, d, _ptr(out)), "get_power")
+        return {"electrons": float(out[0]), "ions": float(out[1])}
 
     def check_accuracy(self, d: int = 0) -> dict:
         """Accuracy and stability conditions of Sec. 2.2 from the measured

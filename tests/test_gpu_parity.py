@@ -179,6 +179,10 @@ def test_steady_shape_fp64_with_ionisation():
     for k in ("n_e", "n_i"):
         assert np.abs(gd[k] - od[k]).max() <= 1e-9 * np.abs(od[k]).max(), k
     assert np.abs(gd["phi"] - od["phi"]).max() <= 1e-12 * np.abs(od["phi"]).max()
+    # power absorption (Sec. 3.5): the same sum of q E v_c dt, added in another order
+    gp, op = sim.power(0), ref.power()
+    for k in ("electrons", "ions"):
+        assert op[k] != 0.0 and abs(gp[k] - op[k]) <= 1e-9 * abs(op[k]), (k, gp[k], op[k])
 
 
 # --------------------------------------------------------------- graph, batch, checkpoint

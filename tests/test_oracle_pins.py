@@ -480,3 +480,34 @@ def test_ifed_normalisation_and_energy():
     en, F = oracle.ifed_normalise(hp, 1.0)
     assert (F * 1.0).sum() == pytest.approx(1.0, rel=1e-12)
     assert dt > 0
+
+
+def test_power_absorption_is_the_work_of_the_field():
+    """Sec. 3.5 power absorption = space-time average of j E.  In a leapfrog
+    step m (v_new - v_old) = q E dt, so q E dt v_c with v_c = (v_old +
+    v_new) / 2 is exactly the change of (m/2) v_x^2: without collisions and
+    absorption, the summed work of the field over the measured steps equals
+    the change of the x kinetic energy, species by species (the ions only on
+    their N_SUB-th steps)."""
+    rng = np.random.default_rng(21)
+    d = wl.reference_discharge(seed=21, capacity=1 << 14)
+    n = 3000
+    e = wl.maxwellian(n, d.gap_m, 2.0 * QE, ME, rng, x=rng.uniform(0.35 * d.gap_m, 0.65 * d.gap_m, n))
+    i = wl.maxwellian(n, d.gap_m, 1.380649e-23 * 350.0, MAR, rng, x=rng.uniform(0.35 * d.gap_m, 0.65 * d.gap_m, n))
+    se, si = wl.constant_cross_sections(1000, wl.CS_DE_EV, (0.0, 0.0, 0.0), (0.0, 0.0))
+    ref = oracle.Sim(d, se, si, wl.CS_DE_EV, e, i)
+    v0 = [ref.particles(sp)[1].copy() for sp in (0, 1)]
+    steps = 2 * d.ion_subcycle
+    ref.step(steps, measure=True)
+    c = ref.counters()
+    assert c["abs_e_pow"] + c["abs_e_gnd"] + c["abs_i_pow"] + c["abs_i_gnd"] == 0
+    v1 = [ref.particles(sp)[1] for sp in (0, 1)]
+    p = ref.power()
+    dt_e = ref.derived()["dt_e"]
+    to_work = d.area_m2 * d.gap_m * p["measured_steps"] * dt_e / d.weight
+    for sp, m, key in ((0, ME, "electrons"), (1, MAR, "ions")):
+        dke = 0.5 * m * (v1[sp] ** 2 - v0[sp] ** 2)
+        work = p[key] * to_work
+        scale = 0.5 * m * float(np.abs(v1[sp] ** 2 - v0[sp] ** 2).sum())
+        assert abs(work - dke.sum()) <= 1e-9 * scale, (key, work, dke.sum())
+        assert abs(work) > 1e-3 * scale  # the field did work

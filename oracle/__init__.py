@@ -108,6 +108,9 @@ def lib():
             L.orc_test_uniform_f32.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
             L.orc_test_uniform_f32.restype = ctypes.c_float
             L.orc_select_process_f32.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_float]
+            L.orc_draw_u24.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int]
+            L.orc_draw_u24.restype = ctypes.c_float
             _lib = L
     return _lib
 
@@ -135,6 +138,11 @@ def u53(a: int, b: int) -> float:
 
 def u24(a: int) -> float:
     return lib().orc_u24(a)
+
+
+def draw_u24(seed: int, slot: int, step: int, species: int, block: int, word: int) -> float:
+    """FP32 per-particle uniform (24 bits) of Philox block `block`, word 0 or 1."""
+    return lib().orc_draw_u24(seed, slot, step, species, block, word)
 
 
 def test_uniform_f32(seed: int, slot: int, step: int, species: int) -> float:

@@ -124,6 +124,15 @@ float orc_test_uniform_f32(uint64_t seed, int64_t slot, int64_t step, int specie
     return orc_u24(w[slot & 3]);
 }
 
+/* FP32 particle mode: 24-bit uniform from word `word` (0: a, 1: c) of the
+ * per-particle block b >= 1, as the FP32 path draws (process, chi), (eta, opal). */
+float orc_draw_u24(uint64_t seed, int64_t slot, int64_t step, int species, int block, int word)
+{
+    uint32_t w[4];
+    philox_words(seed, (uint32_t)slot, step, species, block, w);
+    return orc_u24(word == 0 ? w[0] : w[2]);
+}
+
 /* One per-particle Philox block (b >= 1) for (slot, global step, species). */
 static void draw_block(uint64_t seed, int64_t slot, int64_t step, int species, int block, double u[2])
 {

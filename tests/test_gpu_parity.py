@@ -339,3 +339,42 @@ def test_load_rejects_invalid_particles():
         for c in range(4):  # nothing was copied
             assert np.array_equal(after[c], before[c])
     sim.close()
+
+
+def test_fp32_collision_selection_bit_exact():
+    """FP32 mode, unit level: every electron collides (n sigma v dt > 20, so
+    P_coll rounds to 1.0f) and energies of 30-100 eV keep both inelastic
+    channels open, so the process of slot k is decided only by the 24-bit
+    uniform of its Philox block 1 against the FP32 partition thresholds of
+    Algorithm 6.  Counts per process and the exact set of ionising parents
+    (the products are appended in ascending parent order at the parent's x)
+    must match the oracle's prediction."""
+    d = _quiet(gap_m=0.025, n_grid=101)
+    rng = np.random.default_rng(31)
+    n = 20_000
+    eps = rng.uniform(30.0, 100.0, n) * 1.602176634e-19
+    speed = np.sqrt(2 * eps / 9.1093837015e-31)
+    mu = rng.uniform(-1, 1, n)
+    phi = rng.uniform(0, 2 * np.pi, n)
+    st = np.sqrt(1 - mu * mu)
+    x = rng.uniform(0.3 * d.gap_m, 0.7 * d.gap_m, n)
+    e = wl.Particles(x, speed * mu, speed * st * np.cos(phi), speed * st * np.sin(phi))
+    i = wl.maxwellian(100, d.gap_m, 1.380649e-23 * 350, 6.6335e-26, rng,
+                      x=rng.uniform(0.3 * d.gap_m, 0.7 * d.gap_m, 100))
+    sig = (4e-16, 3e-16, 3e-16)
+    se, si = wl.constant_cross_sections(200_000, DE, sig, (0.0, 0.0))
+    sim = ed.simulation_for([d], ed.FP32, sigma=(se, si), de_ev=DE, particles=[(e, i)])
+    sim.set_graphs(False)
+    sim.step(1)
+    c = sim.counters(0)
+    stot = sum(sig)
+    thr1, thr2 = np.float32(sig[0] / stot), np.float32((sig[0] + sig[1]) / stot)
+    u = np.array([oracle.draw_u24(d.seed, k, 0, 0, 1, 0) for k in range(n)], dtype=np.float32)
+    proc = np.where(u < thr1, 0, np.where(u < thr2, 1, 2))
+    assert c["subthreshold"] == 0 and c["abs_e_pow"] + c["abs_e_gnd"] == 0
+    assert (c["coll_e_ela"], c["coll_e_exc"], c["coll_e_ion"]) == tuple(int((proc == p).sum()) for p in (0, 1, 2))
+    parents = np.flatnonzero(proc == 2)
+    xs = sim.particles(0, ed.ELECTRONS)[0]
+    assert xs.size == n + parents.size and c["created"] == parents.size
+    assert np.array_equal(xs[n:], xs[parents])
+    sim.close()

@@ -28,7 +28,7 @@ MAX_HARM = 4
 N_COUNTERS = 16
 COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela", "coll_e_exc",
                  "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped",
-                 "push_e", "push_i")
+                 "push_e", "push_i", "reflected", "emitted")
 
 
 def build(force: bool = False) -> str:
@@ -52,6 +52,7 @@ class _Params(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("eepf_bins", ctypes.c_int), ("eepf_de_ev", ctypes.c_double),
         ("ifed_bins", ctypes.c_int), ("ifed_de_ev", ctypes.c_double), ("capacity", ctypes.c_int64),
         ("e_exc_ev", ctypes.c_double), ("e_ion_ev", ctypes.c_double),
+        ("see_gamma", ctypes.c_double * 2), ("refl_eta", ctypes.c_double * 2), ("see_te_ev", ctypes.c_double),
     ]
 
 
@@ -228,6 +229,10 @@ def _params(d) -> _Params:
     p.capacity = d.capacity
     p.e_exc_ev = d.e_exc_ev
     p.e_ion_ev = d.e_ion_ev
+    for k in range(2):
+        p.see_gamma[k] = d.see_gamma[k]
+        p.refl_eta[k] = d.refl_eta[k]
+    p.see_te_ev = d.see_te_ev
     return p
 
 

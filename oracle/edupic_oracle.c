@@ -181,6 +181,12 @@ typedef struct {
     int64_t capacity;        /* MAX_N_P analogue, per species */
     double e_exc_ev;         /* lumped excitation threshold */
     double e_ion_ev;         /* ionisation threshold */
+    /* surface processes (Sec. 5): ion-induced secondary electron yield and
+     * elastic electron reflection probability, [0] powered, [1] grounded
+     * electrode; temperature of the emitted electrons (eV) */
+    double see_gamma[2];
+    double refl_eta[2];
+    double see_te_ev;
 } orc_params;
 
 typedef struct {
@@ -216,6 +222,7 @@ typedef struct {
     /* scratch */
     orc_product *prod;
     int64_t prod_cap;
+    orc_product *emit; /* secondary electrons of this step (x, vxe, vye, vze; parent = ion slot) */
     unsigned char *absorbed;
     int error;
 } orc_sim;
@@ -235,7 +242,9 @@ enum {
     ORC_C_CREATED,
     ORC_C_DROPPED,
     ORC_C_PUSH_E,
-    ORC_C_PUSH_I
+    ORC_C_PUSH_I,
+    ORC_C_REFLECTED,
+    ORC_C_EMITTED
 };
 
 /* ------------------------------------------------------------------------ */
@@ -564,6 +573,7 @@ orc_sim *orc_create(const orc_params *p)
     s->ifed_gnd = (int64_t *)calloc((size_t)p->ifed_bins, sizeof(int64_t));
     s->prod_cap = p->capacity;
     s->prod = (orc_product *)calloc((size_t)s->prod_cap, sizeof(orc_product));
+    s->emit = (orc_product *)calloc((size_t)s->prod_cap, sizeof(orc_product));
     s->absorbed = (unsigned char *)calloc((size_t)p->capacity, 1);
     return s;
 }
@@ -593,6 +603,7 @@ void orc_destroy(orc_sim *s)
     free(s->ifed_pow);
     free(s->ifed_gnd);
     free(s->prod);
+    free(s->emit);
     free(s->absorbed);
     free(s);
 }
@@ -751,16 +762,32 @@ static void one_step(orc_sim *s, int measure)
 
     /* (5) absorption at the electrodes (Algorithm 5): x < 0 at the powered
      * electrode, x > L at the grounded one.  Ar+ energies at impact build the
-     * IFEDF (Sec. 3.5). */
+     * IFEDF (Sec. 3.5).  Surface process (Sec. 5): an electron reaching
+     * electrode s is reflected elastically when R01 < eta_s (block 5).
+     * Reading: the reflection mirrors the particle back into the gap (x ->
+     * -x, or 2L - x) and reverses v_x; if the mirror image is still outside
+     * the gap, the electron is absorbed. */
     for (int64_t k = 0; k < E->n; ++k) {
         unsigned char out = 0;
-        if (E->x[k] < 0.0) {
-            s->counters[ORC_C_ABS_E_POW]++;
-            out = 1;
-        }
-        if (E->x[k] > p->gap_m) {
-            s->counters[ORC_C_ABS_E_GND]++;
-            out = 1;
+        const double x = E->x[k];
+        if (x < 0.0 || x > p->gap_m) {
+            const int side = x < 0.0 ? 0 : 1;
+            int reflected = 0;
+            if (p->refl_eta[side] > 0.0) {
+                double u[2];
+                draw_block(p->seed, k, s->step, ORC_SPECIES_E, 5, u);
+                const double xr = side == 0 ? -x : 2.0 * p->gap_m - x;
+                if (u[0] < p->refl_eta[side] && xr >= 0.0 && xr <= p->gap_m) {
+                    E->x[k] = xr;
+                    E->vx[k] = -E->vx[k];
+                    s->counters[ORC_C_REFLECTED]++;
+                    reflected = 1;
+                }
+            }
+            if (!reflected) {
+                s->counters[ORC_C_ABS_E_POW + side]++;
+                out = 1;
+            }
         }
         s->absorbed[k] = out;
     }
@@ -807,10 +834,34 @@ static void one_step(orc_sim *s, int measure)
     }
     compact(E, s->absorbed);
 
+    int64_t nemit = 0;
     if (ion_step) {
         for (int64_t k = 0; k < I->n; ++k) {
             unsigned char out = 0;
             double en = -1.0;
+            /* Surface process (Sec. 5): an ion reaching electrode s emits an
+             * electron when R01 < gamma_s (block 5).  Reading: the electron
+             * starts at the electrode with a half-Maxwellian velocity at
+             * see_te_ev pointing into the gap (blocks 6, 7). */
+            if ((I->x[k] < 0.0 || I->x[k] > p->gap_m) && p->see_gamma[I->x[k] < 0.0 ? 0 : 1] > 0.0) {
+                const int side = I->x[k] < 0.0 ? 0 : 1;
+                double u[2];
+                draw_block(p->seed, k, s->step, ORC_SPECIES_I, 5, u);
+                if (u[0] < p->see_gamma[side]) {
+                    double a[2], b[2], za[2], zb[2];
+                    draw_block(p->seed, k, s->step, ORC_SPECIES_I, 6, a);
+                    draw_block(p->seed, k, s->step, ORC_SPECIES_I, 7, b);
+                    box_muller(a, za);
+                    box_muller(b, zb);
+                    const double sth = sqrt(p->see_te_ev * ORC_EV_TO_J / ORC_E_MASS);
+                    orc_product *em = &s->emit[nemit++];
+                    em->parent = k;
+                    em->x = side == 0 ? 0.0 : p->gap_m;
+                    em->vxe = (side == 0 ? 1.0 : -1.0) * sth * fabs(za[0]);
+                    em->vye = sth * za[1];
+                    em->vze = sth * zb[0];
+                }
+            }
             if (I->x[k] < 0.0 || I->x[k] > p->gap_m) {
                 double v2 = I->vx[k] * I->vx[k] + I->vy[k] * I->vy[k] + I->vz[k] * I->vz[k];
                 en = 0.5 * s->ar_mass * v2 / ORC_EV_TO_J;
@@ -880,6 +931,21 @@ static void one_step(orc_sim *s, int measure)
         I->vz[I->n] = pr->vzi;
         I->n++;
         s->counters[ORC_C_CREATED]++;
+    }
+    /* then the secondary electrons, in ascending order of the emitting ion */
+    for (int64_t j = 0; j < nemit; ++j) {
+        const orc_product *em = &s->emit[j];
+        if (E->n >= p->capacity) {
+            s->counters[ORC_C_DROPPED]++;
+            s->error = 1;
+            continue;
+        }
+        E->x[E->n] = em->x;
+        E->vx[E->n] = em->vxe;
+        E->vy[E->n] = em->vye;
+        E->vz[E->n] = em->vze;
+        E->n++;
+        s->counters[ORC_C_EMITTED]++;
     }
 
     /* grid diagnostics of this step (Sec. 3.6: accumulated after the six steps) */

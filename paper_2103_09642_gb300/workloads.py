@@ -63,6 +63,13 @@ class Discharge:
     capacity: int = 1 << 16              # MAX_N_P analogue, per species
     e_exc_ev: float = 11.5
     e_ion_ev: float = 15.8
+    # surface processes (Sec. 5), (powered, grounded): ion-induced secondary
+    # electron yield gamma, elastic electron reflection probability eta_e;
+    # temperature of the emitted electrons (eV).  Off by default, as in the
+    # paper's code.
+    see_gamma: Tuple[float, float] = (0.0, 0.0)
+    refl_eta: Tuple[float, float] = (0.0, 0.0)
+    see_te_ev: float = 1.0
 
     def replace(self, **kw) -> "Discharge":
         return dataclasses.replace(self, **kw)

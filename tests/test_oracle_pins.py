@@ -511,3 +511,65 @@ def test_power_absorption_is_the_work_of_the_field():
         scale = 0.5 * m * float(np.abs(v1[sp] ** 2 - v0[sp] ** 2).sum())
         assert abs(work - dke.sum()) <= 1e-9 * scale, (key, work, dke.sum())
         assert abs(work) > 1e-3 * scale  # the field did work
+
+
+# ------------------------------------------------------------------ surface processes (Sec. 5)
+def _walls(seed, n, species_mass, speed, rng, d, dt):
+    """n particles within one step of the electrodes, half at each, moving
+    outwards fast enough to cross within dt."""
+    side = rng.integers(0, 2, n)
+    gap = rng.uniform(0.1, 0.9, n) * speed * dt
+    x = np.where(side == 0, gap, d.gap_m - gap)
+    vx = np.where(side == 0, -speed, speed) * rng.uniform(1.0, 1.5, n)
+    vy = rng.normal(0, speed / 3, n)
+    vz = rng.normal(0, speed / 3, n)
+    return wl.Particles(x, vx, vy, vz), side
+
+
+def test_reflection_mirrors_every_electron_when_eta_is_one():
+    d = _quiet(n_grid=101, gap_m=0.02, refl_eta=(1.0, 1.0))
+    rng = np.random.default_rng(41)
+    dt = 1.0 / (d.cycle_freq_hz * d.steps_per_cycle)
+    e, side = _walls(41, 4000, ME, 1e6, rng, d, dt)
+    i = wl.Particles.empty()
+    ref = oracle.Sim(d, *_tables(200_000, wl.CS_DE_EV, sigma_e=(0, 0, 0), sigma_i=(0, 0)), wl.CS_DE_EV, e, i)
+    ref.step(1)
+    c = ref.counters()
+    assert c["reflected"] == e.n and c["abs_e_pow"] + c["abs_e_gnd"] == 0
+    x1, vx1, vy1, vz1 = ref.particles(0)
+    xn = e.x + e.vx * dt  # the push in a zero field
+    mirror = np.where(side == 0, -xn, 2 * d.gap_m - xn)
+    assert np.array_equal(x1, mirror) and np.array_equal(vx1, -e.vx)
+    assert np.array_equal(vy1, e.vy) and np.array_equal(vz1, e.vz)
+
+
+def test_reflection_and_emission_probabilities():
+    d = _quiet(n_grid=101, gap_m=0.02, refl_eta=(0.3, 0.0), see_gamma=(0.25, 0.6), see_te_ev=2.0)
+    rng = np.random.default_rng(42)
+    dt = 1.0 / (d.cycle_freq_hz * d.steps_per_cycle)
+    n = 40_000
+    e, e_side = _walls(42, n, ME, 1e6, rng, d, dt)
+    i, i_side = _walls(43, n, MAR, 3e4, rng, d, d.ion_subcycle * dt)
+    ref = oracle.Sim(d, *_tables(200_000, wl.CS_DE_EV, sigma_e=(0, 0, 0), sigma_i=(0, 0)), wl.CS_DE_EV, e, i)
+    ref.step(1)  # step 0 is an ion step
+    c = ref.counters()
+    n_pow, n_gnd = int((e_side == 0).sum()), int((e_side == 1).sum())
+    # electrons: reflected with probability 0.3 at the powered electrode, never at the grounded one
+    assert c["abs_e_gnd"] == n_gnd
+    assert c["reflected"] + c["abs_e_pow"] == n_pow
+    assert abs(c["reflected"] - 0.3 * n_pow) <= 5 * math.sqrt(0.3 * 0.7 * n_pow)
+    # ions: every one absorbed; each emits an electron with probability gamma of its electrode
+    i_pow, i_gnd = int((i_side == 0).sum()), int((i_side == 1).sum())
+    assert c["abs_i_pow"] == i_pow and c["abs_i_gnd"] == i_gnd
+    expect = 0.25 * i_pow + 0.6 * i_gnd
+    sd = math.sqrt(0.25 * 0.75 * i_pow + 0.6 * 0.4 * i_gnd)
+    assert abs(c["emitted"] - expect) <= 5 * sd
+    # the emitted electrons were appended last, at the electrodes, pointing into the gap
+    x1, vx1, vy1, vz1 = ref.particles(0)
+    k = c["emitted"]
+    xe, vxe = x1[-k:], vx1[-k:]
+    assert np.all((xe == 0.0) | (xe == d.gap_m))
+    assert np.all(vxe[xe == 0.0] > 0) and np.all(vxe[xe == d.gap_m] < 0)
+    # half-Maxwellian at 2 eV: mean kinetic energy 3/2 kT
+    ke = 0.5 * ME * (vxe ** 2 + vy1[-k:] ** 2 + vz1[-k:] ** 2) / QE
+    assert abs(ke.mean() - 3.0) <= 5 * math.sqrt(1.5 * 2.0 ** 2 / k) + 0.02

@@ -76,6 +76,8 @@ extern "C" {
 #define EDUPIC_C_DROPPED 11     /* created pairs dropped at capacity */
 #define EDUPIC_C_PUSH_E 12      /* electron pushes (particle-steps) */
 #define EDUPIC_C_PUSH_I 13      /* ion pushes (particle-steps, ion steps only) */
+#define EDUPIC_C_REFLECTED 14   /* electrons reflected elastically at an electrode (Sec. 5) */
+#define EDUPIC_C_EMITTED 15     /* secondary electrons emitted by ions at an electrode (Sec. 5) */
 
 /* ---------------------------------------------------------------- parameters */
 /* One discharge (Table 1 / Table 2 quantities of the paper).  SI units except
@@ -105,6 +107,22 @@ typedef struct {
     double e_ion_ev;         /* ionisation threshold (15.8 eV for Ar) */
     int32_t cs_entries;      /* capacity of the cross-section tables (CS_RANGES), shared by the object */
     int32_t reserved;
+    /* Surface processes (Sec. 5), index 0 = powered electrode (x = 0), 1 =
+     * grounded (x = L); all zero switches them off (the reference discharge):
+     *  - see_gamma[s]: probability that an Ar+ reaching electrode s emits an
+     *    electron (0..1).  The electron starts at the electrode with a
+     *    half-Maxwellian velocity of temperature see_te_ev pointing into the
+     *    gap, and joins the electrons after the ionisation pairs of the step,
+     *    in ascending order of the emitting ion's slot.
+     *  - refl_eta[s]: probability that an electron reaching electrode s is
+     *    reflected elastically (0..1): mirrored back into the gap (x -> -x,
+     *    or 2L - x) with v_x reversed; absorbed if the mirror image is still
+     *    outside the gap.
+     * Random numbers: electron block 5 (reflection), ion blocks 5 (emission),
+     * 6 and 7 (the emitted velocity). */
+    double see_gamma[2];
+    double refl_eta[2];
+    double see_te_ev;        /* >= 0 */
 } edupic_params;
 
 typedef struct edupic_sim edupic_sim;

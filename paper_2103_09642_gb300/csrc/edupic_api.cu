@@ -77,6 +77,12 @@ Layout layout_of(const edupic_params &p, size_t elem)
     for (int c = 0; c < 3; ++c) L.prod_ve[c] = take((size_t)kEvents * elem);
     for (int c = 0; c < 3; ++c) L.prod_vi[c] = take((size_t)kEvents * elem);
     L.vdrive = take((size_t)p.steps_per_cycle * 8);
+    L.emit = p.see_gamma[0] > 0.0 || p.see_gamma[1] > 0.0;
+    if (L.emit) {
+        L.emit_parent = take((size_t)kEvents * 4);
+        L.emit_x = take((size_t)kEvents * elem);
+        for (int c = 0; c < 3; ++c) L.emit_v[c] = take((size_t)kEvents * elem);
+    }
     L.bytes = o;
     return L;
 }
@@ -109,6 +115,10 @@ int check_params(int nd, const edupic_params *ps, int precision)
             return EDUPIC_EINVAL;
         if (p.cs_entries < 1 || p.cs_entries > EDUPIC_MAX_CS_ENTRIES) return EDUPIC_EINVAL;
         if (!(p.e_exc_ev >= 0) || !(p.e_ion_ev > 0)) return EDUPIC_EINVAL;
+        for (int s = 0; s < 2; ++s)
+            if (!(p.see_gamma[s] >= 0 && p.see_gamma[s] <= 1) || !(p.refl_eta[s] >= 0 && p.refl_eta[s] <= 1))
+                return EDUPIC_EINVAL;
+        if (!(p.see_te_ev >= 0) || !(p.see_te_ev < 1e6)) return EDUPIC_EINVAL;
     }
     return EDUPIC_OK;
 }
@@ -195,6 +205,14 @@ void fill_desc(edupic_sim *S, int d)
     D.ndt_if = (float)(D.n_gas * D.dt_i);
     D.e_idx_ef = (float)(0.5 * kME / kQE / D.cs_de_e);
     D.g_idx_if = (float)(0.5 * mu_arar / kQE / D.cs_de_i);
+    for (int s = 0; s < 2; ++s) {
+        D.refl_eta[s] = p.refl_eta[s];
+        D.see_gamma[s] = p.see_gamma[s];
+        D.refl_etaf[s] = (float)p.refl_eta[s];
+        D.see_gammaf[s] = (float)p.see_gamma[s];
+    }
+    D.see_sth = std::sqrt(p.see_te_ev * kQE / kME);
+    D.see_sthf = (float)D.see_sth;
     D.inv_2dx = 1.0 / (2.0 * D.dx);
     D.edge_c = kQE * D.factor_w * 2.0 / 4294967296.0 * D.dx / (2.0 * kEPS0);
     D.ng = p.n_grid;
@@ -239,6 +257,11 @@ void fill_desc(edupic_sim *S, int d)
     D.ctrl = S->d_ctrl + d;
     D.prod_parent = reinterpret_cast<int *>(b + L.prod_parent);
     D.sort_buf = reinterpret_cast<int *>(b + L.sort_buf);
+    if (L.emit) {
+        D.emit_parent = reinterpret_cast<int *>(b + L.emit_parent);
+        D.emit_x = b + L.emit_x;
+        for (int c = 0; c < 3; ++c) D.emit_v[c] = b + L.emit_v[c];
+    }
     D.prod_x = b + L.prod_x;
     for (int c = 0; c < 3; ++c) {
         D.prod_ve[c] = b + L.prod_ve[c];

@@ -22,6 +22,8 @@ struct Layout {
     size_t x[2], vx[2], vy[2], vz[2];
     size_t q_e, q_i, acc_e, acc_i, n_e, n_i, phi, ef, ef_t, f_cur, fs, sum_qe, sum_qi, sum_f, avg;
     size_t eepf, ifed_pow, ifed_gnd, power, holes[2], prod_parent, sort_buf, prod_x, prod_ve[3], prod_vi[3], vdrive;
+    size_t emit_parent, emit_x, emit_v[3];  // present only when an electrode emits (see_gamma > 0)
+    bool emit;
     size_t bytes;
 };
 

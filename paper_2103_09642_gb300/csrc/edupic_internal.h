@@ -33,6 +33,8 @@ struct Ctrl {
     int holes[2];           // absorbed particles of the current step, per species
     int products;           // ionisations of the current step
     int error;              // kErr* bits
+    int emitted;            // secondary electrons of the current step
+    int pad;
     unsigned long long counters[EDUPIC_N_COUNTERS];
 };
 
@@ -55,12 +57,15 @@ struct DischargeDev {
     double rho_c;       // e FACTOR_W / 2^32
     double harm_freq[EDUPIC_MAX_HARMONICS];
     double harm_volt[EDUPIC_MAX_HARMONICS];
+    double refl_eta[2], see_gamma[2];  // surface processes per electrode (0 = off)
+    double see_sth;                    // thermal speed sqrt(T_see e / m_e) of emitted electrons
     float Lf, inv_dxf, dt_ef, dt_if, factor_ef, factor_if, n_gasf, sig_thf;
     float e_of_v2_ef, e_of_v2_if, e_of_g2_if, mu_ef, e_excf, e_ionf;
     float eepf_lof, eepf_hif, inv_eepf_def, inv_ifed_def, inv_cs_de_ef, inv_cs_de_if;
     float ndt_ef, ndt_if;  // n_gas * dt (electrons, ions)
     float e_idx_ef;        // (m_e / 2e) / DE_CS: table index of v^2
     float g_idx_if;        // (mu / 2e) / DE_CS: table index of g^2
+    float refl_etaf[2], see_gammaf[2], see_sthf;
     double inv_2dx;
     double edge_c;     // e FACTOR_W * 2 / 2^32 * dx / (2 eps0): edge term of E from Q_i - Q_e
     int ng, nt, nsub, n_harm, eepf_bins, ifed_bins, cs_n_e, cs_n_i;
@@ -86,6 +91,8 @@ struct DischargeDev {
     Ctrl *ctrl;
     int *holes[2];
     int *prod_parent;
+    int *emit_parent;          // emitting ion slot of each secondary electron (null without emission)
+    void *emit_x, *emit_v[3];  // secondary electrons of the step (T)
     int *sort_buf;             // kEvents ints: global sort buffer for event lists above kSortShared
     void *prod_x, *prod_ve[3], *prod_vi[3];
     const void *cs_sig[2];     // T[cs_n]

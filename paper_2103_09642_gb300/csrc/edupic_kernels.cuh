@@ -556,14 +556,34 @@ __device__ __forceinline__ void ion_collision(const DischargeDev &D, int slot, c
     atomicAdd(sCnt + EDUPIC_C_COLL_I_ISO + proc, 1u);
 }
 
-// Absorbed particle: record the hole, count it, bin the Ar+ impact energy.
+// Particle that left the gap (Sec. 2.1.5), with the surface processes of
+// Sec. 5.  An electron is first offered elastic reflection (block 5, R01 <
+// eta of the electrode): the mirror image x -> -x (or 2L - x), if inside
+// the gap, is returned and the caller continues with it and v_x reversed.
+// Otherwise the particle is absorbed: its hole is recorded and counted, and
+// for Ar+ the impact energy is binned into the IFED and an electron may be
+// emitted (block 5, R01 < gamma of the electrode; blocks 6, 7: a
+// half-Maxwellian velocity at the emission temperature pointing into the
+// gap).  Emitted electrons start at the electrode, join the next electron
+// densities here and the particle arrays when the step is finalized.
+// Returns the mirror position, or -1 when the particle is absorbed.
 template <typename T, int SP>
-__device__ __noinline__ void absorbed(const DischargeDev *Dp, int slot, T xn, T vx, T vy, T vz, int measure,
-                                      unsigned int *sCnt)
+__device__ __noinline__ T absorbed(const DischargeDev *Dp, const RngKey key, int slot, T xn, T vx, T vy, T vz,
+                                   int measure, unsigned int *sCnt)
 {
     const DischargeDev &D = *Dp;
     const T L = is_f64<T>() ? (T)D.L : (T)D.Lf;
     const int side = xn < (T)0.0 ? 0 : (xn > L ? 1 : -1);
+    if (SP == 0 && side >= 0 && D.refl_eta[side] > 0.0) {
+        T u0, u1;
+        draw<T>(key, (uint32_t)slot, 0, 5, u0, u1);
+        const T eta = is_f64<T>() ? (T)D.refl_eta[side] : (T)D.refl_etaf[side];
+        const T xr = side == 0 ? -xn : (T)2.0 * L - xn;
+        if (u0 < eta && xr >= (T)0.0 && xr <= L) {
+            atomicAdd(sCnt + EDUPIC_C_REFLECTED, 1u);
+            return xr;
+        }
+    }
     if (side < 0)
         atomicOr(&D.ctrl->error, kErrNan);
     else
@@ -589,6 +609,36 @@ __device__ __noinline__ void absorbed(const DischargeDev *Dp, int slot, T xn, T 
         }
         if (ok) atomicAdd((side == 0 ? D.ifed_pow : D.ifed_gnd) + b, 1ull);
     }
+    if (SP == 1 && side >= 0 && D.see_gamma[side] > 0.0) {
+        T u0, u1;
+        draw<T>(key, (uint32_t)slot, 1, 5, u0, u1);
+        const T gam = is_f64<T>() ? (T)D.see_gamma[side] : (T)D.see_gammaf[side];
+        if (u0 < gam) {
+            T a0, a1, b0, b1, za, zb, zc, zd;
+            draw<T>(key, (uint32_t)slot, 1, 6, a0, a1);
+            draw<T>(key, (uint32_t)slot, 1, 7, b0, b1);
+            box_muller(a0, a1, za, zb);
+            box_muller(b0, b1, zc, zd);
+            const T sth = is_f64<T>() ? (T)D.see_sth : (T)D.see_sthf;
+            const T xe = side == 0 ? (T)0.0 : L;
+            const int ei = atomicAdd(&D.ctrl->emitted, 1);
+            if (ei >= kEvents) {
+                atomicOr(&D.ctrl->error, kErrProducts);
+                return (T)-1.0;
+            }
+            D.emit_parent[ei] = slot;
+            reinterpret_cast<T *>(D.emit_x)[ei] = xe;
+            reinterpret_cast<T *>(D.emit_v[0])[ei] = (side == 0 ? sth : -sth) * fabs(za);
+            reinterpret_cast<T *>(D.emit_v[1])[ei] = sth * zb;
+            reinterpret_cast<T *>(D.emit_v[2])[ei] = sth * zc;
+            T d0;
+            const int pp = cell<T>(xe, is_f64<T>() ? (T)D.inv_dx : (T)D.inv_dxf, D.ng, d0);
+            const unsigned long long q2 = split_q2(d0 - (T)pp);
+            atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_e + pp), 4294967296ull - q2);
+            atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_e + pp + 1), q2);
+        }
+    }
+    return (T)-1.0;
 }
 
 // EEPF sample (Sec. 3.5): electrons in the centre 10% of the gap, energy of
@@ -956,8 +1006,12 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             const int slot = base + e;
             if (slot >= n) break;
             if (!in[e]) {
-                absorbed<T, SP>(D, slot, xa[e], vxa[e], vya[e], vza[e], measure, sCnt);
-                continue;
+                const RngKey key{s_lo, s_hi, k0, k1};
+                const T xr = absorbed<T, SP>(D, key, slot, xa[e], vxa[e], vya[e], vza[e], measure, sCnt);
+                if (SP == 1 || xr < (T)0.0) continue;
+                // reflected electron: continues in the gap (v^2 and the table index are unchanged)
+                xa[e] = xr;
+                vxa[e] = -vxa[e];
             }
             const T speed = sqrt(w2[e]);
             T xu;
@@ -1266,6 +1320,52 @@ __device__ void append_products(const DischargeDev &D, int *sA, long long &ne, l
     bar_sync(bar, g);
 }
 
+// Secondary electrons of the step (Sec. 5) appended after the ionisation
+// pairs, in ascending order of the emitting ion's slot (each ion emits at
+// most once per step, so the order is unique).
+template <typename T>
+__device__ void append_emitted(const DischargeDev &D, int *sA, long long &ne, int gtid, int g, int bar)
+{
+    Ctrl *C = D.ctrl;
+    int M = C->emitted;
+    if (M > kEvents) M = kEvents;  // error bit already set by k_push
+    if (M == 0) return;
+    const int *ps = sorted_events(D, D.emit_parent, M, sA, gtid, g, bar);
+    const long long room = D.cap[0] - ne;
+    const long long keep = (long long)M < room ? (long long)M : (room > 0 ? room : 0);
+    T *X0 = reinterpret_cast<T *>(D.x[0]);
+    T *VX0 = reinterpret_cast<T *>(D.vx[0]);
+    T *VY0 = reinterpret_cast<T *>(D.vy[0]);
+    T *VZ0 = reinterpret_cast<T *>(D.vz[0]);
+    for (int i = gtid; i < M; i += g) {
+        const int h = D.emit_parent[i];
+        int lo = 0, hi = M;  // rank of h among the sorted emitters
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (ps[mid] < h)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        if (lo < keep) {
+            const long long se = ne + lo;
+            X0[se] = reinterpret_cast<const T *>(D.emit_x)[i];
+            VX0[se] = reinterpret_cast<const T *>(D.emit_v[0])[i];
+            VY0[se] = reinterpret_cast<const T *>(D.emit_v[1])[i];
+            VZ0[se] = reinterpret_cast<const T *>(D.emit_v[2])[i];
+        }
+    }
+    if (gtid == 0) {
+        C->counters[EDUPIC_C_EMITTED] += (unsigned long long)keep;
+        if (keep < (long long)M) {
+            C->counters[EDUPIC_C_DROPPED] += (unsigned long long)(M - keep);
+            C->error |= kErrCapacity;
+        }
+    }
+    ne += keep;
+    bar_sync(bar, g);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDev *__restrict__ DD, int nd,
                                                                int ion_step, int measure)
@@ -1293,6 +1393,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDe
         long long ne = compact_species<T>(D, 0, sA, sW, gtid, kGroupA, 1);
         long long ni = ion_step ? compact_species<T>(D, 1, sA, sW, gtid, kGroupA, 1) : C->n[1];
         append_products<T>(D, sA, ne, ni, gtid, kGroupA, 1);
+        if (ion_step) append_emitted<T>(D, sA, ne, gtid, kGroupA, 1);
         if (gtid == 0) {
             sN[0] = ne;
             sN[1] = ni;
@@ -1309,6 +1410,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDe
         C->holes[0] = 0;
         C->holes[1] = 0;
         C->products = 0;
+        C->emitted = 0;
         C->step = next;
         if (measure) C->measured += 1;
     }

@@ -25,7 +25,7 @@ N_COUNTERS = 16
 STEP_EVENTS = 65536
 COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela", "coll_e_exc",
                  "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped",
-                 "push_e", "push_i")
+                 "push_e", "push_i", "reflected", "emitted")
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECAPACITY", -4: "ECUDA", -5: "ESTATE", -6: "ENAN",
           -7: "EIO", -8: "ETIMEOUT", -9: "ETOOBIG", -10: "ESTABILITY"}
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
@@ -50,6 +50,7 @@ class Params(ctypes.Structure):
         ("capacity_e", ctypes.c_int64), ("capacity_i", ctypes.c_int64),
         ("e_exc_ev", ctypes.c_double), ("e_ion_ev", ctypes.c_double),
         ("cs_entries", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("see_gamma", ctypes.c_double * 2), ("refl_eta", ctypes.c_double * 2), ("see_te_ev", ctypes.c_double),
     ]
 
 
@@ -68,6 +69,9 @@ def to_params(d: Discharge, cs_entries: int) -> Params:
     p.capacity_e = p.capacity_i = d.capacity
     p.e_exc_ev, p.e_ion_ev = d.e_exc_ev, d.e_ion_ev
     p.cs_entries = cs_entries
+    for k in range(2):
+        p.see_gamma[k], p.refl_eta[k] = d.see_gamma[k], d.refl_eta[k]
+    p.see_te_ev = d.see_te_ev
     return p
 
 

@@ -60,6 +60,17 @@ def test_strerror_and_host_side_checks(lib):
     assert lib.edupic_arena_bytes(1, (ed.Params * 1)(p), ed.FP32, ctypes.byref(out)) == -1
     assert lib.edupic_arena_bytes(0, arr, ed.FP32, ctypes.byref(out)) == -1
     assert lib.edupic_arena_bytes(1, arr, 7, ctypes.byref(out)) == -1
+    # surface process probabilities lie in [0, 1]; emission adds its event lists
+    for kw in ({"see_gamma": (1.5, 0.0)}, {"refl_eta": (0.0, -0.1)}, {"see_te_ev": -1.0},
+               {"refl_eta": (float("nan"), 0.0)}):
+        p = ed.to_params(d.replace(**kw), 1000)
+        assert lib.edupic_arena_bytes(1, (ed.Params * 1)(p), ed.FP32, ctypes.byref(out)) == -1, kw
+    assert lib.edupic_arena_bytes(1, arr, ed.FP64, ctypes.byref(out)) == 0
+    plain = out.value
+    p = ed.to_params(d.replace(refl_eta=(1.0, 1.0)), 1000)
+    assert lib.edupic_arena_bytes(1, (ed.Params * 1)(p), ed.FP64, ctypes.byref(out)) == 0 and out.value == plain
+    p = ed.to_params(d.replace(see_gamma=(0.1, 0.0)), 1000)
+    assert lib.edupic_arena_bytes(1, (ed.Params * 1)(p), ed.FP64, ctypes.byref(out)) == 0 and out.value > plain
 
 
 def test_create_rejects_small_or_misaligned_arena(lib):

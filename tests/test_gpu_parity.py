@@ -185,6 +185,44 @@ def test_steady_shape_fp64_with_ionisation():
         assert op[k] != 0.0 and abs(gp[k] - op[k]) <= 1e-9 * abs(op[k]), (k, gp[k], op[k])
 
 
+def test_surface_processes_fp64_per_step():
+    """Sec. 5 surface processes: ion-induced electron emission and elastic
+    electron reflection, different at the two electrodes, step by step
+    against the oracle (reflected electrons continue in the gap; emitted
+    ones join after the ionisation pairs, by emitting ion)."""
+    d, e, i = wl.reference_steady(seed=5, n=30_000)
+    d = d.replace(harmonics=((13.56e6, 400.0),), see_gamma=(0.4, 0.15), refl_eta=(0.2, 0.6), see_te_ev=2.0)
+    sim, ref = _pair(d, e, i)
+    for _ in range(3):
+        sim.step(40, measure=True)
+        ref.step(40, measure=True)
+        assert sim.counters(0) == ref.counters()
+        _compare_states(sim, ref, d)
+    c = ref.counters()
+    assert c["reflected"] > 0 and c["emitted"] > 0 and c["created"] > 0
+    gd, od = sim.diagnostics(0), ref.diagnostics()
+    for k in ("eepf_counts", "ifed_pow_counts", "ifed_gnd_counts"):
+        assert (gd[k] == od[k]).all(), k
+    assert np.abs(gd["phi"] - od["phi"]).max() <= 1e-12 * np.abs(od["phi"]).max()
+
+
+@pytest.mark.parametrize("precision", [ed.FP64, ed.FP32])
+def test_full_reflection_keeps_every_electron(precision):
+    """eta = 1 at both electrodes: no electron is absorbed unless its mirror
+    image is still outside the gap (a step longer than the gap)."""
+    d, e, i = wl.reference_steady(seed=8, n=20_000)
+    d = d.replace(refl_eta=(1.0, 1.0))
+    sim = ed.simulation_for([d], precision, sigma=(SE, SI), de_ev=DE, particles=[(e, i)])
+    sim.step(200)
+    c = sim.counters(0)
+    assert c["reflected"] > 0 and c["abs_e_pow"] == 0 and c["abs_e_gnd"] == 0
+    assert c["emitted"] == 0
+    xe = sim.particles(0, ed.ELECTRONS)[0]
+    assert xe.size == e.n + c["created"]
+    assert (xe >= 0).all() and (xe <= d.gap_m).all()
+    sim.close()
+
+
 # --------------------------------------------------------------- graph, batch, checkpoint
 def _run(ds, parts, precision, steps, graphs=True, measure=False, grid=0):
     sim = ed.simulation_for(ds, precision, sigma=(SE, SI), de_ev=DE, particles=parts)

@@ -25,10 +25,10 @@ _lock = threading.Lock()
 _lib = None
 
 MAX_HARM = 4
-N_COUNTERS = 16
+N_COUNTERS = 18
 COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela", "coll_e_exc",
                  "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped",
-                 "push_e", "push_i", "reflected", "emitted")
+                 "push_e", "push_i", "reflected", "emitted", "null_tested", "null_over")
 
 
 def build(force: bool = False) -> str:
@@ -53,6 +53,7 @@ class _Params(ctypes.Structure):
         ("ifed_bins", ctypes.c_int), ("ifed_de_ev", ctypes.c_double), ("capacity", ctypes.c_int64),
         ("e_exc_ev", ctypes.c_double), ("e_ion_ev", ctypes.c_double),
         ("see_gamma", ctypes.c_double * 2), ("refl_eta", ctypes.c_double * 2), ("see_te_ev", ctypes.c_double),
+        ("null_collision", ctypes.c_int),
     ]
 
 
@@ -233,6 +234,7 @@ def _params(d) -> _Params:
         p.see_gamma[k] = d.see_gamma[k]
         p.refl_eta[k] = d.refl_eta[k]
     p.see_te_ev = d.see_te_ev
+    p.null_collision = 1 if d.null_collision else 0
     return p
 
 
@@ -328,10 +330,10 @@ class Sim:
         return dict(measured_steps=int(m), electrons=float(out[0]), ions=float(out[1]))
 
     def derived(self) -> dict:
-        out = np.zeros(12)
+        out = np.zeros(16)
         lib().orc_get_derived(self._h, _p(out, ctypes.c_double))
         names = ("dx", "inv_dx", "dt_e", "dt_i", "factor_w", "factor_e", "factor_i", "n_gas", "ar_mass",
-                 "mu_e", "mu_arar", "sigma_th_ar")
+                 "mu_e", "mu_arar", "sigma_th_ar", "nu_star_e", "nu_star_i", "p_star_e", "p_star_i")
         return dict(zip(names, out.tolist()))
 
     # unit collisions with explicit random numbers

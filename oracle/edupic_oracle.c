@@ -187,6 +187,9 @@ typedef struct {
     double see_gamma[2];
     double refl_eta[2];
     double see_te_ev;
+    /* null-collision method (Sec. 2.1.6, Sec. 5) instead of the per-particle
+     * collision probability; 0 = off */
+    int null_collision;
 } orc_params;
 
 typedef struct {
@@ -209,6 +212,8 @@ typedef struct {
     double cs_de[2];
     double *sigma[2];     /* [nproc][n] in m^2 */
     double *sigma_tot[2]; /* n * sigma_tot, [n] in 1/m (Section 3.2) */
+    double nu_star[2];    /* null-collision frequency bound nu* per species (1/s) */
+    double p_star[2];     /* P* = 1 - exp(-nu* dt) */
     orc_species sp[2];
     int64_t step;          /* global step counter s = c * N_T + t */
     int64_t *q_e, *q_i;    /* fixed-point deposition, 2^32 units per particle */
@@ -218,7 +223,7 @@ typedef struct {
     double *sum_ne, *sum_ni, *sum_phi;
     int64_t *eepf, *ifed_pow, *ifed_gnd;
     double work[2]; /* sum over measured pushes of q E_x v_c dt, per unit weight (J), e- and Ar+ */
-    int64_t counters[16];
+    int64_t counters[18];
     /* scratch */
     orc_product *prod;
     int64_t prod_cap;
@@ -244,7 +249,9 @@ enum {
     ORC_C_PUSH_E,
     ORC_C_PUSH_I,
     ORC_C_REFLECTED,
-    ORC_C_EMITTED
+    ORC_C_EMITTED,
+    ORC_C_NULL_TESTED,
+    ORC_C_NULL_OVER
 };
 
 /* ------------------------------------------------------------------------ */
@@ -407,6 +414,29 @@ static void deflect(double gx, double gy, double gz, double g, double cc, double
 }
 
 /* Electron index into a cross-section table (Algorithm 6): nearest bin. */
+/* Null-collision method (Sec. 2.1.6, Sec. 5).  Every particle is offered a
+ * collision with the constant probability P* = 1 - exp(-nu* dt) (its test
+ * uniform, as in the direct method).  Reading: the paper picks N P* particles
+ * at random; a Bernoulli draw per particle is the parallel form of that
+ * choice (the number picked is binomial with mean N P*).  A picked particle
+ * collides for real when R01 < nu / nu* (block 8) and is otherwise a null
+ * collision; nu > nu* (an energy past the table) always collides and is
+ * counted. */
+static int null_real(orc_sim *s, int species, int64_t k, double nu)
+{
+    double u[2];
+    s->counters[ORC_C_NULL_TESTED]++;
+    if (nu > s->nu_star[species]) s->counters[ORC_C_NULL_OVER]++;
+    draw_block(s->p.seed, k, s->step, species, 8, u);
+    return u[0] < nu / s->nu_star[species];
+}
+
+static int null_collides(orc_sim *s, int species, int64_t k, double nu)
+{
+    if (!(test_uniform(s->p.seed, k, s->step, species) < s->p_star[species])) return 0;
+    return null_real(s, species, k, nu);
+}
+
 static int energy_index(double energy, double de, int n)
 {
     double r = energy / de + 0.5;
@@ -628,6 +658,22 @@ int orc_set_cross_sections(orc_sim *s, int species, int n_proc, int n_entries, d
         for (int j = 0; j < n_proc; ++j) t += sigma[(size_t)j * n_entries + k];
         s->sigma_tot[species][k] = t * s->n_gas;
     }
+    /* Null-collision bound (Sec. 2.1.6): nu* = max over the table of
+     * n sigma_tot v.  Energies round to the nearest entry, so entry k serves
+     * energies below (k + 1/2) de, and v is taken there (electrons: lab speed;
+     * ions: relative speed with the reduced mass, as the tables are indexed
+     * by centre-of-mass energy).  Only energies past the table can exceed it. */
+    {
+        const double m = species == 0 ? ORC_E_MASS : s->mu_arar;
+        double best = 0.0;
+        for (int k = 0; k < n_entries; ++k) {
+            const double v = sqrt(2.0 * ((k + 0.5) * de_ev) * ORC_EV_TO_J / m);
+            const double nu = s->sigma_tot[species][k] * v;
+            if (nu > best) best = nu;
+        }
+        s->nu_star[species] = best;
+        s->p_star[species] = 1.0 - exp(-best * (species == 0 ? s->dt_e : s->dt_i));
+    }
     return 0;
 }
 
@@ -802,9 +848,9 @@ static void one_step(orc_sim *s, int measure)
         double energy = 0.5 * ORC_E_MASS * v2 / ORC_EV_TO_J;
         int ei = energy_index(energy, s->cs_de[0], s->cs_n[0]);
         double nu = s->sigma_tot[0][ei] * velocity;
-        double p_coll = 1.0 - exp(-nu * s->dt_e);
-        /* Reading: a collision happens when R01 < P_coll (Algorithm 6) */
-        if (test_uniform(p->seed, k, s->step, ORC_SPECIES_E) < p_coll) {
+        if (p->null_collision ? null_collides(s, 0, k, nu)
+                              : test_uniform(p->seed, k, s->step, ORC_SPECIES_E) < 1.0 - exp(-nu * s->dt_e)) {
+            /* Reading: a collision happens when R01 < P_coll (Algorithm 6) */
             double ua[2], ub[2], vej[3];
             int sub;
             draw_block(p->seed, k, s->step, ORC_SPECIES_E, 1, ua);
@@ -887,6 +933,8 @@ static void one_step(orc_sim *s, int measure)
         /* Ar+ collisions with a thermal partner drawn before P_coll */
         for (int64_t k = 0; k < I->n; ++k) {
             if (s->absorbed[k]) continue;
+            /* null-collision method: only the P* share of the ions draws a partner */
+            if (p->null_collision && !(test_uniform(p->seed, k, s->step, ORC_SPECIES_I) < s->p_star[1])) continue;
             double ua[2], ub[2], za[2], zb[2], uc[2], ud[2];
             draw_block(p->seed, k, s->step, ORC_SPECIES_I, 1, ua);
             draw_block(p->seed, k, s->step, ORC_SPECIES_I, 2, ub);
@@ -899,8 +947,8 @@ static void one_step(orc_sim *s, int measure)
             double energy = 0.5 * s->mu_arar * g_sqr / ORC_EV_TO_J;
             int ei = energy_index(energy, s->cs_de[1], s->cs_n[1]);
             double nu = s->sigma_tot[1][ei] * g;
-            double p_coll = 1.0 - exp(-nu * s->dt_i);
-            if (test_uniform(p->seed, k, s->step, ORC_SPECIES_I) < p_coll) {
+            if (p->null_collision ? null_real(s, 1, k, nu)
+                                  : test_uniform(p->seed, k, s->step, ORC_SPECIES_I) < 1.0 - exp(-nu * s->dt_i)) {
                 draw_block(p->seed, k, s->step, ORC_SPECIES_I, 3, uc);
                 draw_block(p->seed, k, s->step, ORC_SPECIES_I, 4, ud);
                 int proc = orc_collide_ion(s, ei, &I->vx[k], &I->vy[k], &I->vz[k], vx_a, vy_a, vz_a, uc[0], uc[1],
@@ -982,7 +1030,7 @@ void orc_get_fields(const orc_sim *s, double *ne, double *ni, double *phi, doubl
     if (qi) memcpy(qi, s->q_i, sizeof(int64_t) * (size_t)ng);
 }
 
-void orc_get_counters(const orc_sim *s, int64_t out[16]) { memcpy(out, s->counters, sizeof(s->counters)); }
+void orc_get_counters(const orc_sim *s, int64_t out[18]) { memcpy(out, s->counters, sizeof(s->counters)); }
 
 /* Time-averaged diagnostics (Sec. 3.5): densities and potential averaged over
  * the measured steps; EEPF normalised to sum f sqrt(eps) dE = 1 at bin centres;
@@ -1035,8 +1083,12 @@ void orc_ifed_normalise(const int64_t *h, int n, double de, double *energy, doub
 }
 
 /* Derived quantities, for tests. */
-void orc_get_derived(const orc_sim *s, double out[12])
+void orc_get_derived(const orc_sim *s, double out[16])
 {
+    out[12] = s->nu_star[0];
+    out[13] = s->nu_star[1];
+    out[14] = s->p_star[0];
+    out[15] = s->p_star[1];
     out[0] = s->dx;
     out[1] = s->inv_dx;
     out[2] = s->dt_e;

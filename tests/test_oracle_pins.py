@@ -573,3 +573,87 @@ def test_reflection_and_emission_probabilities():
     # half-Maxwellian at 2 eV: mean kinetic energy 3/2 kT
     ke = 0.5 * ME * (vxe ** 2 + vy1[-k:] ** 2 + vz1[-k:] ** 2) / QE
     assert abs(ke.mean() - 3.0) <= 5 * math.sqrt(1.5 * 2.0 ** 2 / k) + 0.02
+
+
+# ------------------------------------------------------------------ null-collision method (Sec. 2.1.6)
+def _mono_electrons(rng, n, eps_ev, lo=0.010, hi=0.015):
+    v = math.sqrt(2 * eps_ev * QE / ME)
+    dirs = rng.normal(size=(3, n))
+    dirs /= np.linalg.norm(dirs, axis=0)
+    return wl.Particles(rng.uniform(lo, hi, n), v * dirs[0], v * dirs[1], v * dirs[2]), v
+
+
+def test_null_collision_bound_closed_form():
+    # constant sigma: nu* = n sigma v at the top of the last table bin
+    nent, de, sig = 1000, 1e-2, 3e-19
+    d = _quiet(null_collision=True)
+    s = oracle.Sim(d, *_tables(nent, de, sigma_e=(sig, 0, 0), sigma_i=(0, sig)), de)
+    dv = s.derived()
+    v_top = math.sqrt(2 * (nent - 0.5) * de * QE / ME)
+    g_top = math.sqrt(2 * (nent - 0.5) * de * QE / (MAR / 2))
+    assert dv["nu_star_e"] == pytest.approx(dv["n_gas"] * sig * v_top, rel=1e-14)
+    assert dv["nu_star_i"] == pytest.approx(dv["n_gas"] * sig * g_top, rel=1e-14)
+    assert dv["p_star_e"] == pytest.approx(-math.expm1(-dv["nu_star_e"] * dv["dt_e"]), rel=1e-12)
+    assert dv["p_star_i"] == pytest.approx(-math.expm1(-dv["nu_star_i"] * dv["dt_i"]), rel=1e-12)
+
+
+def test_null_collision_electron_rates():
+    # mono-energetic electrons, constant sigma, E = 0: a share P* is picked,
+    # and a picked one collides with probability v / v_top (nu / nu*)
+    nent, de, sig, eps = 2000, 1e-2, 2.2e-18, 5.0
+    d = _quiet(gap_m=0.025, n_grid=51, capacity=1 << 17, null_collision=True)
+    se, si = _tables(nent, de, sigma_e=(sig, 0, 0), sigma_i=(0, 0))
+    s = oracle.Sim(d, se, si, de)
+    n, steps = 60_000, 2
+    e, v = _mono_electrons(np.random.default_rng(31), n, eps)
+    s.load(0, e)
+    s.load(1, wl.Particles.empty())
+    s.step(steps)
+    c, dv = s.counters(), s.derived()
+    p_star = dv["p_star_e"]
+    assert 0.05 < p_star < 0.5
+    trials = n * steps
+    assert abs(c["null_tested"] - trials * p_star) <= 5 * math.sqrt(trials * p_star * (1 - p_star))
+    p_real = p_star * v / math.sqrt(2 * (nent - 0.5) * de * QE / ME)
+    assert abs(c["coll_e_ela"] - trials * p_real) <= 5 * math.sqrt(trials * p_real * (1 - p_real))
+    assert c["null_over"] == 0
+    # to first order in nu dt the same rate as the direct test (Algorithm 6)
+    p_direct = -math.expm1(-dv["n_gas"] * sig * v * dv["dt_e"])
+    assert abs(p_real - p_direct) <= 0.5 * p_star * p_direct
+
+
+def test_null_collision_past_the_table_always_collides():
+    # energies beyond the table exceed nu*: every picked electron collides and is counted
+    nent, de, sig = 500, 1e-2, 4e-17
+    d = _quiet(gap_m=0.025, n_grid=51, capacity=1 << 17, null_collision=True)
+    s = oracle.Sim(d, *_tables(nent, de, sigma_e=(sig, 0, 0), sigma_i=(0, 0)), de)
+    e, _ = _mono_electrons(np.random.default_rng(32), 20_000, 40.0)
+    s.load(0, e)
+    s.load(1, wl.Particles.empty())
+    s.step(1)
+    c = s.counters()
+    assert c["null_tested"] > 1000
+    assert c["null_over"] == c["null_tested"] == c["coll_e_ela"]
+
+
+def test_null_collision_ion_rate_thermal_partner():
+    # Ar+ at rest, constant sigma: g is the partner speed, a Maxwell speed of
+    # mean 2 sqrt(2 k T / (pi M)); real collisions P* <g> / g_top
+    nent, de, sig = 1000, 1e-3, 1e-15
+    d = _quiet(gap_m=0.025, n_grid=51, ion_subcycle=1, steps_per_cycle=40, capacity=1 << 18,
+               null_collision=True)
+    s = oracle.Sim(d, *_tables(nent, de, sigma_e=(0, 0, 0), sigma_i=(sig, sig)), de)
+    n = 200_000
+    x = np.random.default_rng(33).uniform(0.01, 0.015, n)
+    s.load(0, wl.Particles.empty())
+    s.load(1, wl.Particles(x, np.zeros(n), np.zeros(n), np.zeros(n)))
+    s.step(1)  # step 0 is an ion step
+    c, dv = s.counters(), s.derived()
+    p_star = dv["p_star_i"]
+    assert abs(c["null_tested"] - n * p_star) <= 5 * math.sqrt(n * p_star * (1 - p_star))
+    g_mean = 2 * math.sqrt(2 * KB * d.gas_temp_k / (math.pi * MAR))
+    p_real = p_star * g_mean / math.sqrt(2 * (nent - 0.5) * de * QE / (MAR / 2))
+    hits = c["coll_i_iso"] + c["coll_i_back"]
+    assert abs(hits - n * p_real) <= 5 * math.sqrt(n * p_real)
+    # backward and isotropic in the ratio of their cross sections (equal here)
+    assert abs(c["coll_i_iso"] - c["coll_i_back"]) <= 5 * math.sqrt(hits)

@@ -14,7 +14,8 @@ of the electron particle kernel against the measured HBM copy bandwidth.
 Beside it, on the same GPU: "plain" (the reference discharge of the paper's
 Table 2 alone, ~4e5 e- + 4e5 Ar+, one RF cycle per bench step),
 "dual_frequency" (1.356 + 27.12 MHz, N_G = 800, ~2e6 per species, one full LF
-cycle) and "served" (a Poisson stream of requests through the continuous-
+cycle), "null_collision_ions" (the batch with the null-collision method for
+Ar+) and "served" (a Poisson stream of requests through the continuous-
 batching server).  With --gpus N under torchrun every rank runs its own batch
 (independent discharges: no collective on the data path).
 
@@ -351,6 +352,34 @@ def leg_dual_frequency(args, peak, peak_kind, flush) -> dict:
             "push_grid": grid, "roofline": roof}
 
 
+def leg_null_collision(args, mix, flush) -> dict:
+    """The 64-discharge batch with the null-collision method (Sec. 2.1.6) for
+    Ar+ + Ar (the thermal partner is drawn for the picked ions only) and the
+    direct test for e- + Ar, the same bench steps as the main line."""
+    from paper_2103_09642_gb300 import edupic as ed
+    from paper_2103_09642_gb300 import workloads as wl
+
+    ds = [m[0].replace(null_collision=2) for m in mix]
+    nd = len(ds)
+    se, si = wl.standin_cross_sections()
+    sim = ed.simulation_for(ds, ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(m[1], m[2]) for m in mix])
+    for _ in range(args.warmup):
+        sim.step(BATCH_STEPS, measure=True)
+    sim.synchronize()
+    tot = lambda key: sum(sim.counters(k)[key] for k in range(nd))
+    c0 = tot("push_e") + tot("push_i")
+    steps = max(3, min(args.steps, 5))
+    ms = _timed(sim.stream, flush, steps, lambda: sim.step(BATCH_STEPS, measure=True))
+    ps = tot("push_e") + tot("push_i") - c0
+    ms_k, launches = sim.profile_steps(BATCH_STEPS, measure=True)
+    sim.close()
+    return {"workload": "the 64-discharge batch, null-collision method for Ar+ (null_collision = 2), direct test "
+                        "for e-", "value": ps / (ms / 1000.0), "unit": UNIT, "steps": steps,
+            "us_per_time_step": 1000.0 * ms / (steps * BATCH_STEPS),
+            "us_per_launch": {k: float(v) / max(int(n), 1) * 1000.0
+                              for k, v, n in zip(("push_e", "push_i", "finalize"), ms_k, launches)}}
+
+
 def leg_served(args) -> dict:
     """A bounded Poisson stream through the request server: 32 requests
     drawn like the 64-discharge batch, 2-10 RF cycles each (the full stream,
@@ -473,6 +502,8 @@ def run_ours(args):
         extra["plain"] = leg_plain(args, peak, peak_kind, flush)
         _log("dual-frequency leg")
         extra["dual_frequency"] = leg_dual_frequency(args, peak, peak_kind, flush)
+        _log("null-collision leg")
+        extra["null_collision_ions"] = leg_null_collision(args, mix, flush)
         _log("served leg")
         extra["served"] = leg_served(args)
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -59,7 +59,7 @@ extern "C" {
 #define EDUPIC_MAX_DISCHARGES 1024 /* discharges per simulation object */
 #define EDUPIC_MAX_CS_ENTRIES 4194304 /* cross-section table length (2^22) */
 #define EDUPIC_STEP_EVENTS 65536   /* absorbed particles (per species) and ionisations per step and discharge */
-#define EDUPIC_N_COUNTERS 16
+#define EDUPIC_N_COUNTERS 18
 
 /* counter indices for edupic_get_counters */
 #define EDUPIC_C_ABS_E_POW 0    /* electrons absorbed at the powered electrode (x < 0) */
@@ -78,6 +78,8 @@ extern "C" {
 #define EDUPIC_C_PUSH_I 13      /* ion pushes (particle-steps, ion steps only) */
 #define EDUPIC_C_REFLECTED 14   /* electrons reflected elastically at an electrode (Sec. 5) */
 #define EDUPIC_C_EMITTED 15     /* secondary electrons emitted by ions at an electrode (Sec. 5) */
+#define EDUPIC_C_NULL_TESTED 16 /* null-collision method: particles picked with probability P* */
+#define EDUPIC_C_NULL_OVER 17   /* null-collision method: picked particles whose nu exceeded nu* */
 
 /* ---------------------------------------------------------------- parameters */
 /* One discharge (Table 1 / Table 2 quantities of the paper).  SI units except
@@ -123,6 +125,18 @@ typedef struct {
     double see_gamma[2];
     double refl_eta[2];
     double see_te_ev;        /* >= 0 */
+    /* Null-collision method (Sec. 2.1.6; proposed in Sec. 5) instead of the
+     * per-particle collision probability, per species: bit 0 (1) electrons,
+     * bit 1 (2) ions, 3 both, 0 off (the paper's code).
+     * nu* = the largest n sigma_tot v of the table, v taken at the top of
+     * each energy bin (e-: lab speed; Ar+: relative speed, reduced mass);
+     * P* = 1 - exp(-nu* dt).  A particle is picked when its collision-test
+     * uniform u is below P*, and then collides when u / P* < nu / nu* (given
+     * the pick, u / P* is uniform on [0, 1)); otherwise the collision is null.
+     * An Ar+ draws its gas partner only when picked.  Energies past the table can exceed nu*; those particles always
+     * collide when picked and are counted (EDUPIC_C_NULL_OVER). */
+    int32_t null_collision;
+    int32_t reserved2;
 } edupic_params;
 
 typedef struct edupic_sim edupic_sim;

@@ -234,7 +234,7 @@ def _params(d) -> _Params:
         p.see_gamma[k] = d.see_gamma[k]
         p.refl_eta[k] = d.refl_eta[k]
     p.see_te_ev = d.see_te_ev
-    p.null_collision = 1 if d.null_collision else 0
+    p.null_collision = int(d.null_collision)
     return p
 
 

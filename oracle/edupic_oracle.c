@@ -188,7 +188,7 @@ typedef struct {
     double refl_eta[2];
     double see_te_ev;
     /* null-collision method (Sec. 2.1.6, Sec. 5) instead of the per-particle
-     * collision probability; 0 = off */
+     * collision probability, per species: bit 0 electrons, bit 1 ions */
     int null_collision;
 } orc_params;
 
@@ -415,26 +415,26 @@ static void deflect(double gx, double gy, double gz, double g, double cc, double
 
 /* Electron index into a cross-section table (Algorithm 6): nearest bin. */
 /* Null-collision method (Sec. 2.1.6, Sec. 5).  Every particle is offered a
- * collision with the constant probability P* = 1 - exp(-nu* dt) (its test
- * uniform, as in the direct method).  Reading: the paper picks N P* particles
- * at random; a Bernoulli draw per particle is the parallel form of that
- * choice (the number picked is binomial with mean N P*).  A picked particle
- * collides for real when R01 < nu / nu* (block 8) and is otherwise a null
- * collision; nu > nu* (an energy past the table) always collides and is
- * counted. */
-static int null_real(orc_sim *s, int species, int64_t k, double nu)
+ * collision with the constant probability P* = 1 - exp(-nu* dt): picked when
+ * its test uniform R < P*.  Reading: the paper picks N P* particles at random;
+ * a Bernoulli draw per particle is the parallel form of that choice (the
+ * number picked is binomial with mean N P*).  A picked particle collides for
+ * real when R' < nu / nu*, otherwise the collision is null.  Reading: R' is
+ * R / P*, which given R < P* is uniform on [0, 1) and independent of the
+ * pick, so no second random number is drawn.  nu > nu* (an energy past the
+ * table) always collides and is counted. */
+static int null_real(orc_sim *s, int species, double u, double nu)
 {
-    double u[2];
     s->counters[ORC_C_NULL_TESTED]++;
     if (nu > s->nu_star[species]) s->counters[ORC_C_NULL_OVER]++;
-    draw_block(s->p.seed, k, s->step, species, 8, u);
-    return u[0] < nu / s->nu_star[species];
+    return u / s->p_star[species] < nu / s->nu_star[species];
 }
 
 static int null_collides(orc_sim *s, int species, int64_t k, double nu)
 {
-    if (!(test_uniform(s->p.seed, k, s->step, species) < s->p_star[species])) return 0;
-    return null_real(s, species, k, nu);
+    const double u = test_uniform(s->p.seed, k, s->step, species);
+    if (!(u < s->p_star[species])) return 0;
+    return null_real(s, species, u, nu);
 }
 
 static int energy_index(double energy, double de, int n)
@@ -848,7 +848,7 @@ static void one_step(orc_sim *s, int measure)
         double energy = 0.5 * ORC_E_MASS * v2 / ORC_EV_TO_J;
         int ei = energy_index(energy, s->cs_de[0], s->cs_n[0]);
         double nu = s->sigma_tot[0][ei] * velocity;
-        if (p->null_collision ? null_collides(s, 0, k, nu)
+        if ((p->null_collision & 1) ? null_collides(s, 0, k, nu)
                               : test_uniform(p->seed, k, s->step, ORC_SPECIES_E) < 1.0 - exp(-nu * s->dt_e)) {
             /* Reading: a collision happens when R01 < P_coll (Algorithm 6) */
             double ua[2], ub[2], vej[3];
@@ -934,7 +934,8 @@ static void one_step(orc_sim *s, int measure)
         for (int64_t k = 0; k < I->n; ++k) {
             if (s->absorbed[k]) continue;
             /* null-collision method: only the P* share of the ions draws a partner */
-            if (p->null_collision && !(test_uniform(p->seed, k, s->step, ORC_SPECIES_I) < s->p_star[1])) continue;
+            const double u_test = test_uniform(p->seed, k, s->step, ORC_SPECIES_I);
+            if ((p->null_collision & 2) && !(u_test < s->p_star[1])) continue;
             double ua[2], ub[2], za[2], zb[2], uc[2], ud[2];
             draw_block(p->seed, k, s->step, ORC_SPECIES_I, 1, ua);
             draw_block(p->seed, k, s->step, ORC_SPECIES_I, 2, ub);
@@ -947,8 +948,7 @@ static void one_step(orc_sim *s, int measure)
             double energy = 0.5 * s->mu_arar * g_sqr / ORC_EV_TO_J;
             int ei = energy_index(energy, s->cs_de[1], s->cs_n[1]);
             double nu = s->sigma_tot[1][ei] * g;
-            if (p->null_collision ? null_real(s, 1, k, nu)
-                                  : test_uniform(p->seed, k, s->step, ORC_SPECIES_I) < 1.0 - exp(-nu * s->dt_i)) {
+            if ((p->null_collision & 2) ? null_real(s, 1, u_test, nu) : u_test < 1.0 - exp(-nu * s->dt_i)) {
                 draw_block(p->seed, k, s->step, ORC_SPECIES_I, 3, uc);
                 draw_block(p->seed, k, s->step, ORC_SPECIES_I, 4, ud);
                 int proc = orc_collide_ion(s, ei, &I->vx[k], &I->vy[k], &I->vz[k], vx_a, vy_a, vz_a, uc[0], uc[1],

@@ -119,6 +119,7 @@ int check_params(int nd, const edupic_params *ps, int precision)
             if (!(p.see_gamma[s] >= 0 && p.see_gamma[s] <= 1) || !(p.refl_eta[s] >= 0 && p.refl_eta[s] <= 1))
                 return EDUPIC_EINVAL;
         if (!(p.see_te_ev >= 0) || !(p.see_te_ev < 1e6)) return EDUPIC_EINVAL;
+        if (p.null_collision < 0 || p.null_collision > 3) return EDUPIC_EINVAL;
     }
     return EDUPIC_OK;
 }
@@ -224,6 +225,7 @@ void fill_desc(edupic_sim *S, int d)
     D.cs_n_e = S->desc.size() > (size_t)d ? S->desc[d].cs_n_e : 1;
     D.cs_n_i = S->desc.size() > (size_t)d ? S->desc[d].cs_n_i : 1;
     D.active = 1;
+    D.null_coll = p.null_collision;
     D.stop_step = LLONG_MAX;
     D.cap[0] = p.capacity_e;
     D.cap[1] = p.capacity_i;
@@ -276,6 +278,34 @@ void fill_desc(edupic_sim *S, int d)
     D.vdrive = reinterpret_cast<const double *>(b + L.vdrive);
     if (S->desc.size() <= (size_t)d) S->desc.resize(d + 1);
     S->desc[d] = D;
+    null_bounds(S, d);
+}
+
+// Null-collision bound of discharge d from the host copy of the tables
+// (Sec. 2.1.6): nu* = max_k (n sigma_tot,k) v_k with v_k the speed at the
+// top of entry k's energy bin (energies round to the nearest entry), and
+// P* = 1 - exp(-nu* dt).  Formed in the same order as the oracle's bound.
+void null_bounds(edupic_sim *S, int d)
+{
+    DischargeDev &D = S->desc[d];
+    if (!D.null_coll) return;
+    for (int sp = 0; sp < 2; ++sp) {
+        const std::vector<double> &st = S->sigsum_host[sp];
+        if (!((D.null_coll >> sp) & 1) || st.empty()) continue;
+        const double m = sp == 0 ? kME : kArMassU * kAMU / 2.0;
+        const double de = S->cs_de_host[sp];
+        double best = 0.0;
+        for (size_t k = 0; k < st.size(); ++k) {
+            const double v = std::sqrt(2.0 * ((k + 0.5) * de) * kQE / m);
+            const double nu = st[k] * D.n_gas * v;
+            if (nu > best) best = nu;
+        }
+        const double dt = sp == 0 ? D.dt_e : D.dt_i;
+        D.nu_star[sp] = best;
+        D.p_star[sp] = 1.0 - std::exp(-best * dt);
+        D.p_starf[sp] = (float)D.p_star[sp];
+        D.null_ratf[sp] = best > 0.0 ? (float)(D.n_gas / best) : 0.0f;
+    }
 }
 
 int upload_desc(edupic_sim *S)
@@ -679,6 +709,15 @@ int edupic_set_cross_sections(edupic_sim *S, int species, int n_proc, int n_entr
         }
         S->sigv_max[species] = best;
     }
+    S->sigsum_host[species].resize((size_t)n_entries);
+    for (int k = 0; k < n_entries; ++k) {
+        // processes summed in order from zero, as the collision test's table
+        double st = 0.0;
+        for (int q = 0; q < n_proc; ++q) st += sigma_m2[(size_t)q * n_entries + k];
+        S->sigsum_host[species][(size_t)k] = st;
+    }
+    S->cs_de_host[species] = de_ev;
+    for (int d = 0; d < S->nd; ++d) null_bounds(S, d);
     S->cs_set[species] = true;
     return upload_desc(S);
 }

@@ -60,6 +60,8 @@ struct edupic_sim {
     bool graphs = true;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     double sigv_max[2] = {0.0, 0.0};  // largest sigma_tot * v of each species' table
+    std::vector<double> sigsum_host[2];  // sum of the process cross sections per table entry (m^2)
+    double cs_de_host[2] = {0.0, 0.0};
     void *pinned = nullptr;  // page-locked staging buffer for particle uploads
     size_t pinned_bytes = 0;
 
@@ -91,6 +93,7 @@ void carve_shared(edupic_sim *S, int cs_entries);
 int setup_grid(edupic_sim *S);
 // fill the host copy of discharge d's descriptor from its params, layout and base
 void fill_desc(edupic_sim *S, int d);
+void null_bounds(edupic_sim *S, int d);
 int upload_desc(edupic_sim *S);
 int upload_desc_one(edupic_sim *S, int d);
 int upload_drive(edupic_sim *S, int d);

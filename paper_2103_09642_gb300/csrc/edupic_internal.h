@@ -59,6 +59,7 @@ struct DischargeDev {
     double harm_volt[EDUPIC_MAX_HARMONICS];
     double refl_eta[2], see_gamma[2];  // surface processes per electrode (0 = off)
     double see_sth;                    // thermal speed sqrt(T_see e / m_e) of emitted electrons
+    double nu_star[2], p_star[2];      // null-collision bound nu* and P* = 1 - exp(-nu* dt), per species
     float Lf, inv_dxf, dt_ef, dt_if, factor_ef, factor_if, n_gasf, sig_thf;
     float e_of_v2_ef, e_of_v2_if, e_of_g2_if, mu_ef, e_excf, e_ionf;
     float eepf_lof, eepf_hif, inv_eepf_def, inv_ifed_def, inv_cs_de_ef, inv_cs_de_if;
@@ -66,11 +67,13 @@ struct DischargeDev {
     float e_idx_ef;        // (m_e / 2e) / DE_CS: table index of v^2
     float g_idx_if;        // (mu / 2e) / DE_CS: table index of g^2
     float refl_etaf[2], see_gammaf[2], see_sthf;
+    float p_starf[2];   // P* in FP32
+    float null_ratf[2]; // n_gas / nu*: nu / nu* = sigsum v null_ratf
     double inv_2dx;
     double edge_c;     // e FACTOR_W * 2 / 2^32 * dx / (2 eps0): edge term of E from Q_i - Q_e
     int ng, nt, nsub, n_harm, eepf_bins, ifed_bins, cs_n_e, cs_n_i;
     int active;
-    int pad0;
+    int null_coll;  // null-collision method: bit 0 electrons, bit 1 ions
     long long stop_step;       // the discharge is frozen (skipped) once its step count reaches this
     long long cap[2];
     unsigned long long seed;

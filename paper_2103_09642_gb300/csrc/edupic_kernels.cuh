@@ -447,6 +447,29 @@ __device__ __forceinline__ __int128 group_sum128(__int128 v, __int128 *s_w, int 
 // is the same as executing the collision in place.
 constexpr int kWarpQueue = 512;  // queued colliders per warp before the warp drains them
 
+// Null-collision method (Sec. 2.1.6): a particle picked by its test uniform
+// u < P* collides for real when u / P* < nu / nu* (given the pick, u / P* is
+// uniform on [0, 1)), nu = n sigma_tot(k) q with q the speed (e-) or
+// relative speed (Ar+) whose square is q2.  Counts nu > nu* (an energy past
+// the table).
+template <typename T, int SP>
+__device__ __forceinline__ bool null_real(const DischargeDev &D, int k, T q2, T u, unsigned int *sCnt)
+{
+    const T sg = reinterpret_cast<const T *>(D.cs_sig[SP])[k];
+    bool over, real;
+    if constexpr (is_f64<T>()) {
+        const double nu = sg * D.n_gas * sqrt(q2);
+        over = nu > D.nu_star[SP];
+        real = u / D.p_star[SP] < nu / D.nu_star[SP];
+    } else {
+        const float r = sg * sqrtf(q2) * D.null_ratf[SP];
+        over = r > 1.0f;
+        real = u < r * D.p_starf[SP];
+    }
+    if (over) atomicAdd(sCnt + EDUPIC_C_NULL_OVER, 1u);
+    return real;
+}
+
 // e- + Ar collision of the particle in `slot` (post-push state in memory),
 // including the append record and the deposition of an ionisation pair.
 template <typename T>
@@ -529,6 +552,33 @@ __device__ __forceinline__ int ion_index(const DischargeDev &D, T g_sqr, T idx_s
         return cs_index(D.half_mu_arar * g_sqr / EDUPIC_QE, idx_scale, cs_n);
     else
         return cs_index_f(g_sqr * idx_scale + 0.5f, cs_n);
+}
+
+// Null-collision test of a particle picked by its test uniform u < P*
+// (post-push velocity): the table index of its energy (e-) or of its relative
+// energy with a thermal partner drawn now (Ar+, the same draws the collider
+// makes), then u / P* < nu / nu*.  Called for the picked particles only.
+template <typename T, int SP>
+__device__ __noinline__ bool null_pick(const DischargeDev *Dp, const RngKey key, int slot, T vx, T vy, T vz, T u,
+                                       T idx_scale, int cs_n, unsigned int *sCnt)
+{
+    const DischargeDev &D = *Dp;
+    T q2;
+    int k;
+    if constexpr (SP == 0) {
+        q2 = vx * vx + vy * vy + vz * vz;
+        if constexpr (is_f64<T>())
+            k = cs_index(D.half_me * q2 / EDUPIC_QE, idx_scale, cs_n);
+        else
+            k = cs_index_f(q2 * idx_scale + 0.5f, cs_n);
+    } else {
+        T vax, vay, vaz;
+        ion_partner<T>(D, key, (uint32_t)slot, vax, vay, vaz);
+        const T gx = vx - vax, gy = vy - vay, gz = vz - vaz;
+        q2 = gx * gx + gy * gy + gz * gz;
+        k = ion_index<T>(D, q2, idx_scale, cs_n);
+    }
+    return null_real<T, SP>(D, k, q2, u, sCnt);
 }
 
 // Ar+ + Ar collision of the ion in `slot` with its thermal partner.
@@ -769,6 +819,8 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     const T *sig = nullptr;
     T *X = nullptr, *VX = nullptr, *VY = nullptr, *VZ = nullptr;
     bool eepf_on = false;
+    bool nullc = false;  // null-collision method for the current discharge
+    T pstar = 0;         // its P*
 
     // execute the collisions queued by this warp (the 32 lanes of the warp;
     // the particles were stored by lanes of the same warp, ordered by the
@@ -805,6 +857,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     };
 
     double pw_acc = 0.0;  // E_x (v_old + v_new) of this thread's measured pushes (current discharge)
+    int picks = 0;        // null-collision picks of this thread (current discharge)
 
     auto flush = [&](bool last) {
         drain();
@@ -816,6 +869,14 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
             if (lane == 0 && v != 0.0) atomicAdd(D->power + SP, v);
             pw_acc = 0.0;
+        }
+        {
+            // null-collision picks: warp sums, one add per warp
+            int pk = picks;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pk += __shfl_down_sync(0xffffffffu, pk, o);
+            if (lane == 0 && pk) atomicAdd(D->ctrl->counters + EDUPIC_C_NULL_TESTED, (unsigned long long)pk);
+            picks = 0;
         }
         if (tid < EDUPIC_N_COUNTERS) {
             const unsigned int c = sCnt[tid];
@@ -893,6 +954,8 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             VZ = reinterpret_cast<T *>(D->vz[SP]);
             cs_n = SP == 0 ? D->cs_n_e : D->cs_n_i;
             eepf_on = SP == 0 && measure;
+            nullc = ((D->null_coll >> SP) & 1) != 0;
+            pstar = is_f64<T>() ? (T)D->p_star[SP] : (T)D->p_starf[SP];
             const T *ef = reinterpret_cast<const T *>(D->ef_t);
             for (int p = tid; p < ng; p += blockDim.x) {
                 sE2[p] = T2{ef[p], p + 1 < ng ? ef[p + 1] : (T)0};
@@ -962,6 +1025,9 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             xa[e] = live ? xn : x;
             vxa[e] = live ? vxn : vx;
             in[e] = live && (xn >= (T)0.0) && (xn <= L);
+            w2[e] = (T)0;
+            kk[e] = 0;
+            if (nullc) continue;  // the null-collision test needs neither
             T q2;
             if (SP == 0) {
                 q2 = vxn * vxn + vya[e] * vya[e] + vza[e] * vza[e];
@@ -1013,20 +1079,44 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
                 xa[e] = xr;
                 vxa[e] = -vxa[e];
             }
-            const T speed = sqrt(w2[e]);
-            T xu;
-            if constexpr (is_f64<T>())
-                xu = sC[kk[e] >> cs_shift] * ndt * speed * dt * 1.000001 + 1e-15;
-            else
-                xu = sC[kk[e] >> cs_shift] * ndt * speed * 1.00001f + 1e-6f;
-            if (ut[e] < xu) {
-                const T sg = __ldg(sig + kk[e]);
-                T pc;
+            if (nullc) {
+                // null-collision method: picked with P*, tested in place; only
+                // real collisions are queued
+                if (ut[e] < pstar) {
+                    ++picks;
+                    bool real;
+                    if constexpr (SP == 0) {
+                        // e-: the energy's table entry, in line
+                        const T q2 = vxa[e] * vxa[e] + vya[e] * vya[e] + vza[e] * vza[e];
+                        int k;
+                        if constexpr (is_f64<T>())
+                            k = cs_index(D->half_me * q2 / EDUPIC_QE, idx_scale, cs_n);
+                        else
+                            k = cs_index_f(q2 * idx_scale + 0.5f, cs_n);
+                        real = null_real<T, 0>(*D, k, q2, ut[e], sCnt);
+                    } else {
+                        // Ar+: the thermal partner is drawn out of line
+                        const RngKey key{s_lo, s_hi, k0, k1};
+                        real = null_pick<T, SP>(D, key, slot, vxa[e], vya[e], vza[e], ut[e], idx_scale, cs_n, sCnt);
+                    }
+                    if (real) sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;
+                }
+            } else {
+                const T speed = sqrt(w2[e]);
+                T xu;
                 if constexpr (is_f64<T>())
-                    pc = p_coll(sg * ndt * speed * dt);
+                    xu = sC[kk[e] >> cs_shift] * ndt * speed * dt * 1.000001 + 1e-15;
                 else
-                    pc = p_coll(sg * ndt * speed);
-                if (ut[e] < pc) sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;  // executed after the stores below
+                    xu = sC[kk[e] >> cs_shift] * ndt * speed * 1.00001f + 1e-6f;
+                if (ut[e] < xu) {
+                    const T sg = __ldg(sig + kk[e]);
+                    T pc;
+                    if constexpr (is_f64<T>())
+                        pc = p_coll(sg * ndt * speed * dt);
+                    else
+                        pc = p_coll(sg * ndt * speed);
+                    if (ut[e] < pc) sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;  // executed after the stores below
+                }
             }
             // deposition of the new position for the next step (Sec. 2.1.1)
             T d0;

@@ -21,11 +21,11 @@ LIB_PATH = os.path.join(HERE, "_build", "libedupic_gb300.so")
 FP64, FP32 = 0, 1
 ELECTRONS, IONS = 0, 1
 MAX_HARMONICS = 4
-N_COUNTERS = 16
+N_COUNTERS = 18
 STEP_EVENTS = 65536
 COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela", "coll_e_exc",
                  "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped",
-                 "push_e", "push_i", "reflected", "emitted")
+                 "push_e", "push_i", "reflected", "emitted", "null_tested", "null_over")
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECAPACITY", -4: "ECUDA", -5: "ESTATE", -6: "ENAN",
           -7: "EIO", -8: "ETIMEOUT", -9: "ETOOBIG", -10: "ESTABILITY"}
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
@@ -51,6 +51,7 @@ class Params(ctypes.Structure):
         ("e_exc_ev", ctypes.c_double), ("e_ion_ev", ctypes.c_double),
         ("cs_entries", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("see_gamma", ctypes.c_double * 2), ("refl_eta", ctypes.c_double * 2), ("see_te_ev", ctypes.c_double),
+        ("null_collision", ctypes.c_int32), ("reserved2", ctypes.c_int32),
     ]
 
 
@@ -72,6 +73,7 @@ def to_params(d: Discharge, cs_entries: int) -> Params:
     for k in range(2):
         p.see_gamma[k], p.refl_eta[k] = d.see_gamma[k], d.refl_eta[k]
     p.see_te_ev = d.see_te_ev
+    p.null_collision = int(d.null_collision)
     return p
 
 

@@ -70,7 +70,9 @@ class Discharge:
     see_gamma: Tuple[float, float] = (0.0, 0.0)
     refl_eta: Tuple[float, float] = (0.0, 0.0)
     see_te_ev: float = 1.0
-    null_collision: bool = False  # null-collision method (Sec. 2.1.6) instead of the direct test
+    # null-collision method (Sec. 2.1.6) instead of the direct test, per
+    # species: 1 electrons, 2 ions, 3 both, 0 off
+    null_collision: int = 0
 
     def replace(self, **kw) -> "Discharge":
         return dataclasses.replace(self, **kw)

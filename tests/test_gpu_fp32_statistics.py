@@ -57,10 +57,10 @@ def _stats(diag, cnt0, cnt1, d):
     }
 
 
-def _gpu_runs():
+def _gpu_runs(null_collision=0):
     se, si = wl.standin_cross_sections()
     runs = [wl.reference_steady(seed=s, n=N) for s in SEEDS]
-    ds = [r[0] for r in runs]
+    ds = [r[0].replace(null_collision=null_collision) for r in runs]
     sim = ed.simulation_for(ds, ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(r[1], r[2]) for r in runs])
     sim.step(WARM * ds[0].steps_per_cycle, measure=False)
     c0 = [sim.counters(k) for k in range(len(ds))]
@@ -95,3 +95,22 @@ def test_fp32_matches_fp64_oracle_statistically():
     for k in o:
         rel = np.abs(np.asarray(g[k]) - np.asarray(o[k])) / np.abs(np.asarray(o[k]))
         assert np.all(rel <= TOL), f"{k}: GPU FP32 {g[k]} vs oracle {o[k]} (relative {rel})"
+
+
+def test_null_collision_matches_direct_statistically():
+    """The null-collision method (both species) against the direct test, both
+    on the GPU in FP32, over the same 5 seeds and figures.  Besides the Monte
+    Carlo noise (<= 1% per figure, as above), the method has a bias: with
+    a = nu dt, a* = nu* dt, its collision probability (1 - e^-a*) a / a* is
+    below 1 - e^-a by at most (a* - a) / 2 < P* / 2 relative."""
+    import oracle
+
+    null, d = _gpu_runs(null_collision=3)
+    direct, _ = _gpu_runs(null_collision=0)
+    se, si = wl.standin_cross_sections()
+    dv = oracle.Sim(d.replace(null_collision=3), se, si, wl.CS_DE_EV).derived()
+    tol = TOL + max(dv["p_star_e"], dv["p_star_i"]) / 2
+    g, o = _summary(null, d), _summary(direct, d)
+    for k in o:
+        rel = np.abs(np.asarray(g[k]) - np.asarray(o[k])) / np.abs(np.asarray(o[k]))
+        assert np.all(rel <= tol), f"{k}: null {g[k]} vs direct {o[k]} (relative {rel}, tolerance {tol})"

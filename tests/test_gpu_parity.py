@@ -10,6 +10,8 @@ Tolerances (derived in the design notes):
   (the field difference above plus last-bit differences of libm functions
   in colliding particles).
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -221,6 +223,42 @@ def test_full_reflection_keeps_every_electron(precision):
     assert xe.size == e.n + c["created"]
     assert (xe >= 0).all() and (xe <= d.gap_m).all()
     sim.close()
+
+
+@pytest.mark.parametrize("mask", [1, 2, 3])
+def test_null_collision_fp64_per_step(mask):
+    """Null-collision method (Sec. 2.1.6) for electrons (1), ions (2) or both
+    (3): picks by P*, real collisions by nu/nu*, step by step against the
+    oracle's null-collision mode (the same counters, including the picks)."""
+    d, e, i = wl.reference_steady(seed=9, n=30_000)
+    d = d.replace(harmonics=((13.56e6, 400.0),), null_collision=mask)
+    sim, ref = _pair(d, e, i)
+    for _ in range(3):
+        sim.step(40, measure=True)
+        ref.step(40, measure=True)
+        assert sim.counters(0) == ref.counters()
+        _compare_states(sim, ref, d)
+    c = ref.counters()
+    assert c["null_tested"] > 0
+    assert c["coll_e_ela"] > 0 and (mask == 1 or c["coll_i_back"] > 0)
+    gd, od = sim.diagnostics(0), ref.diagnostics()
+    for k in ("eepf_counts", "ifed_pow_counts", "ifed_gnd_counts"):
+        assert (gd[k] == od[k]).all(), k
+
+
+def test_null_collision_fp32_pick_rate():
+    """FP32: the share of in-gap electrons picked per step is P* (binomial)."""
+    d, e, i = wl.reference_steady(seed=10, n=40_000)
+    d = d.replace(null_collision=1)
+    sim = ed.simulation_for([d], ed.FP32, sigma=(SE, SI), de_ev=DE, particles=[(e, i)])
+    sim.step(100)
+    c = sim.counters(0)
+    sim.close()
+    p_star = oracle.Sim(d, SE, SI, DE, e, i).derived()["p_star_e"]
+    trials = c["push_e"] - c["abs_e_pow"] - c["abs_e_gnd"]
+    mean, sd = trials * p_star, math.sqrt(trials * p_star * (1 - p_star))
+    assert abs(c["null_tested"] - mean) <= 5 * sd, (c["null_tested"], mean, sd)
+    assert c["coll_e_ela"] < c["null_tested"]
 
 
 # --------------------------------------------------------------- graph, batch, checkpoint

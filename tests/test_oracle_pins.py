@@ -586,7 +586,7 @@ def _mono_electrons(rng, n, eps_ev, lo=0.010, hi=0.015):
 def test_null_collision_bound_closed_form():
     # constant sigma: nu* = n sigma v at the top of the last table bin
     nent, de, sig = 1000, 1e-2, 3e-19
-    d = _quiet(null_collision=True)
+    d = _quiet(null_collision=3)
     s = oracle.Sim(d, *_tables(nent, de, sigma_e=(sig, 0, 0), sigma_i=(0, sig)), de)
     dv = s.derived()
     v_top = math.sqrt(2 * (nent - 0.5) * de * QE / ME)
@@ -601,7 +601,7 @@ def test_null_collision_electron_rates():
     # mono-energetic electrons, constant sigma, E = 0: a share P* is picked,
     # and a picked one collides with probability v / v_top (nu / nu*)
     nent, de, sig, eps = 2000, 1e-2, 2.2e-18, 5.0
-    d = _quiet(gap_m=0.025, n_grid=51, capacity=1 << 17, null_collision=True)
+    d = _quiet(gap_m=0.025, n_grid=51, capacity=1 << 17, null_collision=1)
     se, si = _tables(nent, de, sigma_e=(sig, 0, 0), sigma_i=(0, 0))
     s = oracle.Sim(d, se, si, de)
     n, steps = 60_000, 2
@@ -625,7 +625,7 @@ def test_null_collision_electron_rates():
 def test_null_collision_past_the_table_always_collides():
     # energies beyond the table exceed nu*: every picked electron collides and is counted
     nent, de, sig = 500, 1e-2, 4e-17
-    d = _quiet(gap_m=0.025, n_grid=51, capacity=1 << 17, null_collision=True)
+    d = _quiet(gap_m=0.025, n_grid=51, capacity=1 << 17, null_collision=1)
     s = oracle.Sim(d, *_tables(nent, de, sigma_e=(sig, 0, 0), sigma_i=(0, 0)), de)
     e, _ = _mono_electrons(np.random.default_rng(32), 20_000, 40.0)
     s.load(0, e)
@@ -641,7 +641,7 @@ def test_null_collision_ion_rate_thermal_partner():
     # mean 2 sqrt(2 k T / (pi M)); real collisions P* <g> / g_top
     nent, de, sig = 1000, 1e-3, 1e-15
     d = _quiet(gap_m=0.025, n_grid=51, ion_subcycle=1, steps_per_cycle=40, capacity=1 << 18,
-               null_collision=True)
+               null_collision=2)
     s = oracle.Sim(d, *_tables(nent, de, sigma_e=(0, 0, 0), sigma_i=(sig, sig)), de)
     n = 200_000
     x = np.random.default_rng(33).uniform(0.01, 0.015, n)

@@ -281,6 +281,20 @@ void fill_desc(edupic_sim *S, int d)
     null_bounds(S, d);
 }
 
+// Which push-kernel variant the species need: the null-collision one when
+// an active discharge asks for the method.  Captured graphs carry the
+// variant, so they are dropped when it changes.
+void update_null_any(edupic_sim *S)
+{
+    int any[2] = {0, 0};
+    for (int d = 0; d < S->nd && d < (int)S->desc.size(); ++d)
+        if (S->desc[d].active)
+            for (int sp = 0; sp < 2; ++sp) any[sp] |= (S->desc[d].null_coll >> sp) & 1;
+    if (any[0] != S->null_any[0] || any[1] != S->null_any[1]) S->drop_graphs();
+    S->null_any[0] = any[0];
+    S->null_any[1] = any[1];
+}
+
 // Null-collision bound of discharge d from the host copy of the tables
 // (Sec. 2.1.6): nu* = max_k (n sigma_tot,k) v_k with v_k the speed at the
 // top of entry k's energy bin (energies round to the nearest entry), and
@@ -367,9 +381,11 @@ int setup_grid(edupic_sim *S)
 template <typename T>
 int launch_step(edupic_sim *S, bool ion, int measure)
 {
-    cudaError_t e = Launch<T>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max, S->stream);
+    cudaError_t e = Launch<T>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max, S->null_any[0],
+                                    S->stream);
     if (e == cudaSuccess && ion)
-        e = Launch<T>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max, S->stream);
+        e = Launch<T>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max, S->null_any[1],
+                            S->stream);
     if (e == cudaSuccess) e = Launch<T>::finalize(S->d_desc, S->nd, ion ? 1 : 0, measure, S->stream);
     return cuda_status(e);
 }
@@ -632,6 +648,7 @@ int edupic_create(int nd, const edupic_params *params, int precision, void *devi
         o += S->layouts.back().bytes;
     }
     for (int d = 0; d < nd; ++d) fill_desc(S, d);
+    update_null_any(S);
     cudaError_t e = cudaMemsetAsync(S->arena, 0, need, S->stream);
     if (e != cudaSuccess) {
         delete S;
@@ -811,18 +828,22 @@ int edupic_profile_steps(edupic_sim *S, int64_t n_steps, int measure, double out
             e = cudaEventRecord(E[0], S->stream);
             if (S->precision == EDUPIC_FP32) {
                 if (e == cudaSuccess)
-                    e = Launch<float>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max, S->stream);
+                    e = Launch<float>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max,
+                                            S->null_any[0], S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[1], S->stream);
                 if (e == cudaSuccess && ion[i])
-                    e = Launch<float>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max, S->stream);
+                    e = Launch<float>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max,
+                                            S->null_any[1], S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[2], S->stream);
                 if (e == cudaSuccess) e = Launch<float>::finalize(S->d_desc, S->nd, ion[i], measure, S->stream);
             } else {
                 if (e == cudaSuccess)
-                    e = Launch<double>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max, S->stream);
+                    e = Launch<double>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max,
+                                            S->null_any[0], S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[1], S->stream);
                 if (e == cudaSuccess && ion[i])
-                    e = Launch<double>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max, S->stream);
+                    e = Launch<double>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max,
+                                            S->null_any[1], S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[2], S->stream);
                 if (e == cudaSuccess) e = Launch<double>::finalize(S->d_desc, S->nd, ion[i], measure, S->stream);
             }

@@ -62,6 +62,7 @@ struct edupic_sim {
     double sigv_max[2] = {0.0, 0.0};  // largest sigma_tot * v of each species' table
     std::vector<double> sigsum_host[2];  // sum of the process cross sections per table entry (m^2)
     double cs_de_host[2] = {0.0, 0.0};
+    int null_any[2] = {0, 0};  // some active discharge uses the null-collision method, per species
     void *pinned = nullptr;  // page-locked staging buffer for particle uploads
     size_t pinned_bytes = 0;
 
@@ -94,6 +95,7 @@ int setup_grid(edupic_sim *S);
 // fill the host copy of discharge d's descriptor from its params, layout and base
 void fill_desc(edupic_sim *S, int d);
 void null_bounds(edupic_sim *S, int d);
+void update_null_any(edupic_sim *S);
 int upload_desc(edupic_sim *S);
 int upload_desc_one(edupic_sim *S, int d);
 int upload_drive(edupic_sim *S, int d);

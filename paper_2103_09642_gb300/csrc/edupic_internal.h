@@ -112,7 +112,7 @@ struct Launch {
     static cudaError_t fields(const DischargeDev *dd, int nd, int d, cudaStream_t st);
     static cudaError_t averages(const DischargeDev *dd, int nd, int d, cudaStream_t st);
     static cudaError_t push(const DischargeDev *dd, int nd, int species, int measure, int grid, int ng_max,
-                            int eepf_max, cudaStream_t st);
+                            int eepf_max, int null_any, cudaStream_t st);
     static cudaError_t finalize(const DischargeDev *dd, int nd, int ion_step, int measure, cudaStream_t st);
     static size_t push_smem(int nd, int ng_max, int eepf_max);
     static int push_blocks_per_sm(int species, size_t smem);

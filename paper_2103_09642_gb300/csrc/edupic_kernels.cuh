@@ -733,7 +733,10 @@ __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eep
            (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 12 + (size_t)(nd + 1) * 4 + 0 * (size_t)eepf_max;
 }
 
-template <typename T, int SP>
+// NC: the variant that also runs the null-collision method for the
+// discharges that ask for it (launched only when one does; the direct-test
+// variant carries none of its code).
+template <typename T, int SP, bool NC>
 __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BLOCKS)
     k_push(const DischargeDev *__restrict__ DD, int nd, int ng_max, int eepf_max, int measure)
 {
@@ -870,7 +873,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             if (lane == 0 && v != 0.0) atomicAdd(D->power + SP, v);
             pw_acc = 0.0;
         }
-        {
+        if constexpr (NC) {
             // null-collision picks: warp sums, one add per warp
             int pk = picks;
 #pragma unroll
@@ -954,8 +957,10 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             VZ = reinterpret_cast<T *>(D->vz[SP]);
             cs_n = SP == 0 ? D->cs_n_e : D->cs_n_i;
             eepf_on = SP == 0 && measure;
-            nullc = ((D->null_coll >> SP) & 1) != 0;
-            pstar = is_f64<T>() ? (T)D->p_star[SP] : (T)D->p_starf[SP];
+            if constexpr (NC) {
+                nullc = ((D->null_coll >> SP) & 1) != 0;
+                pstar = is_f64<T>() ? (T)D->p_star[SP] : (T)D->p_starf[SP];
+            }
             const T *ef = reinterpret_cast<const T *>(D->ef_t);
             for (int p = tid; p < ng; p += blockDim.x) {
                 sE2[p] = T2{ef[p], p + 1 < ng ? ef[p + 1] : (T)0};
@@ -1025,9 +1030,11 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             xa[e] = live ? xn : x;
             vxa[e] = live ? vxn : vx;
             in[e] = live && (xn >= (T)0.0) && (xn <= L);
-            w2[e] = (T)0;
-            kk[e] = 0;
-            if (nullc) continue;  // the null-collision test needs neither
+            if constexpr (NC) {
+                w2[e] = (T)0;
+                kk[e] = 0;
+                if (nullc) continue;  // the null-collision test needs neither
+            }
             T q2;
             if (SP == 0) {
                 q2 = vxn * vxn + vya[e] * vya[e] + vza[e] * vza[e];
@@ -1079,7 +1086,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
                 xa[e] = xr;
                 vxa[e] = -vxa[e];
             }
-            if (nullc) {
+            if (NC && nullc) {
                 // null-collision method: picked with P*, tested in place; only
                 // real collisions are queued
                 if (ut[e] < pstar) {

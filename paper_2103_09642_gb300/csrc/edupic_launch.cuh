@@ -16,14 +16,22 @@ int Launch<T>::push_blocks_per_sm(int species, size_t smem)
 {
     int nb = 0;
     cudaError_t e;
+    int nb_nc = 0;
     if (species == 0) {
-        cudaFuncSetAttribute(k_push<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<T, 0>, kThreads, smem);
+        cudaFuncSetAttribute(k_push<T, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaFuncSetAttribute(k_push<T, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<T, 0, false>, kThreads, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_nc, k_push<T, 0, true>, kThreads, smem);
     } else {
-        cudaFuncSetAttribute(k_push<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<T, 1>, kThreads, smem);
+        cudaFuncSetAttribute(k_push<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaFuncSetAttribute(k_push<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<T, 1, false>, kThreads, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_nc, k_push<T, 1, true>, kThreads, smem);
     }
-    return e == cudaSuccess ? nb : -1;
+    // one grid serves both variants: the smaller resident limit
+    return e == cudaSuccess ? (nb < nb_nc ? nb : nb_nc) : -1;
 }
 
 template <typename T>
@@ -71,13 +79,17 @@ static cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cuda
 
 template <typename T>
 cudaError_t Launch<T>::push(const DischargeDev *dd, int nd, int species, int measure, int grid, int ng_max,
-                            int eepf_max, cudaStream_t st)
+                            int eepf_max, int null_any, cudaStream_t st)
 {
     const int eb = species == 0 && measure ? eepf_max : 0;
     const size_t smem = push_smem(nd, ng_max, eb);
     if (species == 0)
-        return launch_pdl(k_push<T, 0>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, eb, measure);
-    return launch_pdl(k_push<T, 1>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, 0, measure);
+        return null_any ? launch_pdl(k_push<T, 0, true>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, eb,
+                                     measure)
+                        : launch_pdl(k_push<T, 0, false>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, eb,
+                                     measure);
+    return null_any ? launch_pdl(k_push<T, 1, true>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, 0, measure)
+                    : launch_pdl(k_push<T, 1, false>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, 0, measure);
 }
 
 template <typename T>

@@ -207,6 +207,7 @@ int open_slot(edupic_server *V, uint64_t ticket, int d)
     if (rc == EDUPIC_OK) {
         fill_desc(S, d);
         S->desc[d].stop_step = r.target;
+        update_null_any(S);
         rc = upload_desc_one(S, d);
     }
     if (rc == EDUPIC_OK) rc = upload_drive(S, d);
@@ -263,6 +264,7 @@ void close_slot(edupic_server *V, int d, int status)
     r.state = rc == EDUPIC_OK ? EDUPIC_REQ_DONE : EDUPIC_REQ_FAILED;
     r.t_done = V->now();
     S->desc[d] = idle_desc(S, d);
+    update_null_any(S);
     upload_desc_one(S, d);
     V->heap.release(r.off, r.bytes);
     V->slot_ticket[d] = 0;

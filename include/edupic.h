@@ -59,7 +59,7 @@ extern "C" {
 #define EDUPIC_MAX_DISCHARGES 1024 /* discharges per simulation object */
 #define EDUPIC_MAX_CS_ENTRIES 4194304 /* cross-section table length (2^22) */
 #define EDUPIC_STEP_EVENTS 65536   /* absorbed particles (per species) and ionisations per step and discharge */
-#define EDUPIC_N_COUNTERS 18
+#define EDUPIC_N_COUNTERS 19
 
 /* counter indices for edupic_get_counters */
 #define EDUPIC_C_ABS_E_POW 0    /* electrons absorbed at the powered electrode (x < 0) */
@@ -77,9 +77,10 @@ extern "C" {
 #define EDUPIC_C_PUSH_E 12      /* electron pushes (particle-steps) */
 #define EDUPIC_C_PUSH_I 13      /* ion pushes (particle-steps, ion steps only) */
 #define EDUPIC_C_REFLECTED 14   /* electrons reflected elastically at an electrode (Sec. 5) */
-#define EDUPIC_C_EMITTED 15     /* secondary electrons emitted by ions at an electrode (Sec. 5) */
-#define EDUPIC_C_NULL_TESTED 16 /* null-collision method: particles picked with probability P* */
-#define EDUPIC_C_NULL_OVER 17   /* null-collision method: picked particles whose nu exceeded nu* */
+#define EDUPIC_C_EMITTED_POW 15 /* secondary electrons emitted by ions at the powered electrode (Sec. 5) */
+#define EDUPIC_C_EMITTED_GND 16 /* ... at the grounded electrode */
+#define EDUPIC_C_NULL_TESTED 17 /* null-collision method: particles picked with probability P* */
+#define EDUPIC_C_NULL_OVER 18   /* null-collision method: picked particles whose nu exceeded nu* */
 
 /* ---------------------------------------------------------------- parameters */
 /* One discharge (Table 1 / Table 2 quantities of the paper).  SI units except
@@ -269,6 +270,30 @@ int edupic_reset_diagnostics(edupic_sim *sim, int d);
  * order that depends on the launch, so results agree to rounding, not bit
  * for bit, between runs. */
 int edupic_get_power(edupic_sim *sim, int d, double out[2]);
+
+/* DC self-bias (Sec. 5: the bias is adjusted in an iteration until the
+ * currents of the oppositely charged particles reaching an electrode
+ * compensate on time average).  The bias is a constant voltage added to the
+ * drive at the powered electrode: phi_0 = V(t) + v_bias.
+ *
+ * edupic_set_bias sets it for discharge d (finite volts; 0 at creation) and
+ * forms the field of the coming step again with it.  edupic_get_bias reads it.
+ *
+ * edupic_self_bias_step is one iteration for every discharge: it runs n_steps
+ * time steps (edupic_step, measuring if `measure`), counts over them the ions
+ * N_i and electrons N_e absorbed at the powered electrode and the secondary
+ * electrons N_s it emitted, and for each discharge d with gain_v[d] != 0 sets
+ *     v_bias += gain_v[d] * (N_i - N_e + N_s) / (N_i + N_e + N_s)
+ * (the normalised net positive charge the electrode received; unchanged when
+ * nothing arrived).  gain_v: host, nd values (volts; 0 = leave d alone).
+ * v_bias: host, nd values written with the new biases, or NULL.  Take n_steps
+ * a multiple of the RF cycles so that the window is a time average; the
+ * iteration converges for gains small against the bias scale (a few volts
+ * for the discharges here).  Synchronises the stream; device errors are
+ * returned. */
+int edupic_set_bias(edupic_sim *sim, int d, double v_bias);
+int edupic_get_bias(edupic_sim *sim, int d, double *v_bias);
+int edupic_self_bias_step(edupic_sim *sim, int64_t n_steps, int measure, const double *gain_v, double *v_bias);
 
 /* Accuracy and stability conditions of Sec. 2.2 (the checks the paper's
  * code writes to info.txt, Sec. 3.5), evaluated for discharge d from its

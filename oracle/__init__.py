@@ -25,10 +25,11 @@ _lock = threading.Lock()
 _lib = None
 
 MAX_HARM = 4
-N_COUNTERS = 18
+N_COUNTERS = 19
 COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela", "coll_e_exc",
                  "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped",
-                 "push_e", "push_i", "reflected", "emitted", "null_tested", "null_over")
+                 "push_e", "push_i", "reflected", "emitted_pow", "emitted_gnd",
+                 "null_tested", "null_over")
 
 
 def build(force: bool = False) -> str:
@@ -102,6 +103,8 @@ def lib():
             L.orc_eepf_normalise.argtypes = [_Q, ctypes.c_int, ctypes.c_double, _D, _D]
             L.orc_ifed_normalise.argtypes = [_Q, ctypes.c_int, ctypes.c_double, _D, _D]
             L.orc_get_derived.argtypes = [ctypes.c_void_p, _D]
+            L.orc_set_bias.argtypes = [ctypes.c_void_p, ctypes.c_double]
+            L.orc_set_bias.restype = None
             L.orc_unit_collide_electron.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_double,
                                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, _D]
             L.orc_unit_collide_ion.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, _D, ctypes.c_double,
@@ -328,6 +331,9 @@ class Sim:
         out = np.zeros(2)
         m = lib().orc_get_power(self._h, _p(out, ctypes.c_double))
         return dict(measured_steps=int(m), electrons=float(out[0]), ions=float(out[1]))
+
+    def set_bias(self, v_bias: float) -> None:
+        lib().orc_set_bias(self._h, ctypes.c_double(v_bias))
 
     def derived(self) -> dict:
         out = np.zeros(16)

@@ -223,7 +223,8 @@ typedef struct {
     double *sum_ne, *sum_ni, *sum_phi;
     int64_t *eepf, *ifed_pow, *ifed_gnd;
     double work[2]; /* sum over measured pushes of q E_x v_c dt, per unit weight (J), e- and Ar+ */
-    int64_t counters[18];
+    double v_bias;  /* DC voltage added at the powered electrode (Sec. 5 self-bias) */
+    int64_t counters[19];
     /* scratch */
     orc_product *prod;
     int64_t prod_cap;
@@ -249,7 +250,8 @@ enum {
     ORC_C_PUSH_E,
     ORC_C_PUSH_I,
     ORC_C_REFLECTED,
-    ORC_C_EMITTED,
+    ORC_C_EMITTED_POW,
+    ORC_C_EMITTED_GND,
     ORC_C_NULL_TESTED,
     ORC_C_NULL_OVER
 };
@@ -381,8 +383,12 @@ static double drive_voltage(const orc_sim *s, int64_t t_in_cycle)
     double t = (double)t_in_cycle * s->dt_e;
     double v = 0.0;
     for (int h = 0; h < s->p.n_harm; ++h) v += s->p.harm_volt_v[h] * cos(2.0 * ORC_PI * s->p.harm_freq_hz[h] * t);
-    return v;
+    return v + s->v_bias;
 }
+
+/* DC self-bias (Sec. 5): a constant voltage added to the powered electrode's
+ * potential, from the next field solve on. */
+void orc_set_bias(orc_sim *s, double v_bias) { s->v_bias = v_bias; }
 
 /* ------------------------------------------------------------------------ */
 /* Step 6 -- collisions (Sec. 2.1.6; Algorithm 6).                            */
@@ -900,6 +906,7 @@ static void one_step(orc_sim *s, int measure)
                     box_muller(a, za);
                     box_muller(b, zb);
                     const double sth = sqrt(p->see_te_ev * ORC_EV_TO_J / ORC_E_MASS);
+                    s->counters[ORC_C_EMITTED_POW + side]++;
                     orc_product *em = &s->emit[nemit++];
                     em->parent = k;
                     em->x = side == 0 ? 0.0 : p->gap_m;
@@ -993,7 +1000,6 @@ static void one_step(orc_sim *s, int measure)
         E->vy[E->n] = em->vye;
         E->vz[E->n] = em->vze;
         E->n++;
-        s->counters[ORC_C_EMITTED]++;
     }
 
     /* grid diagnostics of this step (Sec. 3.6: accumulated after the six steps) */
@@ -1030,7 +1036,7 @@ void orc_get_fields(const orc_sim *s, double *ne, double *ni, double *phi, doubl
     if (qi) memcpy(qi, s->q_i, sizeof(int64_t) * (size_t)ng);
 }
 
-void orc_get_counters(const orc_sim *s, int64_t out[18]) { memcpy(out, s->counters, sizeof(s->counters)); }
+void orc_get_counters(const orc_sim *s, int64_t out[19]) { memcpy(out, s->counters, sizeof(s->counters)); }
 
 /* Time-averaged diagnostics (Sec. 3.5): densities and potential averaged over
  * the measured steps; EEPF normalised to sum f sqrt(eps) dE = 1 at bin centres;

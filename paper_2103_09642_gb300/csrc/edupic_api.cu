@@ -473,12 +473,13 @@ int upload_drive(edupic_sim *S, int d)
 {
     const edupic_params &p = S->params[d];
     const double dt_e = S->desc[d].dt_e, pi = 3.14159265358979323846;
+    const double bias = (size_t)d < S->v_bias.size() ? S->v_bias[(size_t)d] : 0.0;
     std::vector<double> v((size_t)p.steps_per_cycle);
     for (int tc = 0; tc < p.steps_per_cycle; ++tc) {
         const double t = (double)tc * dt_e;
         double a = 0.0;
         for (int h = 0; h < p.n_harmonics; ++h) a += p.harm_volt_v[h] * std::cos(2.0 * pi * p.harm_freq_hz[h] * t);
-        v[tc] = a;
+        v[tc] = a + bias;
     }
     cudaError_t e = cudaMemcpyAsync(const_cast<double *>(S->desc[d].vdrive), v.data(), sizeof(double) * v.size(),
                                     cudaMemcpyHostToDevice, S->stream);
@@ -629,6 +630,7 @@ int edupic_create(int nd, const edupic_params *params, int precision, void *devi
     S->precision = precision;
     S->elem = precision == EDUPIC_FP32 ? 4 : 8;
     S->params.assign(params, params + nd);
+    S->v_bias.assign((size_t)nd, 0.0);
     S->arena = static_cast<unsigned char *>(device_arena);
     S->arena_bytes = arena_bytes;
     S->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -1196,6 +1198,58 @@ int edupic_get_power(edupic_sim *S, int d, double out[2])
     const double t = (double)c.measured * D.dt_e;
     for (int k = 0; k < 2; ++k) out[k] = t > 0.0 ? work[k] * p.weight / (p.area_m2 * p.gap_m * t) : 0.0;
     return error_of(c);
+}
+
+int edupic_set_bias(edupic_sim *S, int d, double v_bias)
+{
+    if (!valid_d(S, d) || !std::isfinite(v_bias)) return EDUPIC_EINVAL;
+    S->v_bias[(size_t)d] = v_bias;
+    int rc = upload_drive(S, d);
+    if (rc) return rc;
+    // the field of the coming step was formed with the old drive: form it again
+    cudaError_t e = S->precision == EDUPIC_FP32 ? Launch<float>::fields(S->d_desc, S->nd, d, S->stream)
+                                                : Launch<double>::fields(S->d_desc, S->nd, d, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    return cuda_status(e);
+}
+
+int edupic_get_bias(edupic_sim *S, int d, double *v_bias)
+{
+    if (!valid_d(S, d) || !v_bias) return EDUPIC_EINVAL;
+    *v_bias = S->v_bias[(size_t)d];
+    return EDUPIC_OK;
+}
+
+int edupic_self_bias_step(edupic_sim *S, int64_t n_steps, int measure, const double *gain_v, double *v_bias)
+{
+    if (!S || n_steps < 1 || !gain_v) return EDUPIC_EINVAL;
+    for (int d = 0; d < S->nd; ++d)
+        if (!std::isfinite(gain_v[d])) return EDUPIC_EINVAL;
+    std::vector<Ctrl> c0((size_t)S->nd), c1((size_t)S->nd);
+    for (int d = 0; d < S->nd; ++d) {
+        int rc = read_ctrl(S, d, &c0[(size_t)d]);
+        if (rc) return rc;
+    }
+    int rc = edupic_step(S, n_steps, measure);
+    if (rc == EDUPIC_OK) rc = edupic_synchronize(S);
+    if (rc) return rc;
+    for (int d = 0; d < S->nd; ++d) {
+        rc = read_ctrl(S, d, &c1[(size_t)d]);
+        if (rc) return rc;
+        if (gain_v[d] != 0.0) {
+            // charges reaching the powered electrode over the window: ions
+            // (+), electrons (-), and the secondary electrons it emitted (+)
+            const auto delta = [&](int k) { return (double)(c1[(size_t)d].counters[k] - c0[(size_t)d].counters[k]); };
+            const double ni = delta(EDUPIC_C_ABS_I_POW), ne = delta(EDUPIC_C_ABS_E_POW), ns = delta(EDUPIC_C_EMITTED_POW);
+            const double tot = ni + ne + ns;
+            if (tot > 0.0) {
+                rc = edupic_set_bias(S, d, S->v_bias[(size_t)d] + gain_v[d] * (ni - ne + ns) / tot);
+                if (rc) return rc;
+            }
+        }
+        if (v_bias) v_bias[d] = S->v_bias[(size_t)d];
+    }
+    return EDUPIC_OK;
 }
 
 int edupic_check_accuracy(edupic_sim *S, int d, edupic_accuracy *out)

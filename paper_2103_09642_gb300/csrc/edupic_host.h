@@ -63,6 +63,7 @@ struct edupic_sim {
     std::vector<double> sigsum_host[2];  // sum of the process cross sections per table entry (m^2)
     double cs_de_host[2] = {0.0, 0.0};
     int null_any[2] = {0, 0};  // some active discharge uses the null-collision method, per species
+    std::vector<double> v_bias;  // DC voltage added at the powered electrode, per discharge (Sec. 5 self-bias)
     void *pinned = nullptr;  // page-locked staging buffer for particle uploads
     size_t pinned_bytes = 0;
 

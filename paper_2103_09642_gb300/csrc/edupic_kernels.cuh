@@ -671,6 +671,7 @@ __device__ __noinline__ T absorbed(const DischargeDev *Dp, const RngKey key, int
             box_muller(b0, b1, zc, zd);
             const T sth = is_f64<T>() ? (T)D.see_sth : (T)D.see_sthf;
             const T xe = side == 0 ? (T)0.0 : L;
+            atomicAdd(sCnt + EDUPIC_C_EMITTED_POW + side, 1u);
             const int ei = atomicAdd(&D.ctrl->emitted, 1);
             if (ei >= kEvents) {
                 atomicOr(&D.ctrl->error, kErrProducts);
@@ -1453,7 +1454,6 @@ __device__ void append_emitted(const DischargeDev &D, int *sA, long long &ne, in
         }
     }
     if (gtid == 0) {
-        C->counters[EDUPIC_C_EMITTED] += (unsigned long long)keep;
         if (keep < (long long)M) {
             C->counters[EDUPIC_C_DROPPED] += (unsigned long long)(M - keep);
             C->error |= kErrCapacity;

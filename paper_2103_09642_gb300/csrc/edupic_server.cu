@@ -210,6 +210,7 @@ int open_slot(edupic_server *V, uint64_t ticket, int d)
         update_null_any(S);
         rc = upload_desc_one(S, d);
     }
+    S->v_bias[(size_t)d] = 0.0;
     if (rc == EDUPIC_OK) rc = upload_drive(S, d);
     for (int sp = 0; sp < 2 && rc == EDUPIC_OK; ++sp) {
         const double *src[4] = {r.part[sp][0].data(), r.part[sp][1].data(), r.part[sp][2].data(),
@@ -317,6 +318,7 @@ int edupic_server_create(const edupic_server_config *cfg, int precision, void *d
     S->eepf_max = cfg->max_eepf_bins;
     carve_shared(S, cfg->cs_entries);
     S->params.assign(nd, idle_params(*cfg));
+    S->v_bias.assign((size_t)nd, 0.0);
     S->layouts.assign(nd, Layout{});
     S->base.assign(nd, 0);
     S->desc.clear();

@@ -21,11 +21,12 @@ LIB_PATH = os.path.join(HERE, "_build", "libedupic_gb300.so")
 FP64, FP32 = 0, 1
 ELECTRONS, IONS = 0, 1
 MAX_HARMONICS = 4
-N_COUNTERS = 18
+N_COUNTERS = 19
 STEP_EVENTS = 65536
 COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela", "coll_e_exc",
                  "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped",
-                 "push_e", "push_i", "reflected", "emitted", "null_tested", "null_over")
+                 "push_e", "push_i", "reflected", "emitted_pow", "emitted_gnd",
+                 "null_tested", "null_over")
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECAPACITY", -4: "ECUDA", -5: "ESTATE", -6: "ENAN",
           -7: "EIO", -8: "ETIMEOUT", -9: "ETOOBIG", -10: "ESTABILITY"}
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
@@ -132,6 +133,9 @@ def load_library(path: str = LIB_PATH):
         "edupic_autotune": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]),
         "edupic_check_accuracy": ([_VP, ctypes.c_int, ctypes.POINTER(Accuracy)]),
         "edupic_get_power": ([_VP, ctypes.c_int, _D]),
+        "edupic_set_bias": ([_VP, ctypes.c_int, ctypes.c_double]),
+        "edupic_get_bias": ([_VP, ctypes.c_int, _D]),
+        "edupic_self_bias_step": ([_VP, ctypes.c_int64, ctypes.c_int, _D, _D]),
         "edupic_get_counts": ([_VP, ctypes.c_int, _Q, _Q, _Q]),
         "edupic_get_particles": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _D, _D, _D, _D, _Q]),
         "edupic_get_fields": ([_VP, ctypes.c_int, _D, _D, _D, _D, _Q, _Q]),
@@ -337,6 +341,24 @@ class Simulation:
         out = np.zeros(2)
         _ck(self.L.edupic_get_power(self._h, d, _ptr(out)), "get_power")
         return {"electrons": float(out[0]), "ions": float(out[1])}
+
+    def set_bias(self, d: int, v_bias: float) -> None:
+        """DC self-bias voltage added at the powered electrode (Sec. 5)."""
+        _ck(self.L.edupic_set_bias(self._h, d, float(v_bias)), "set_bias")
+
+    def bias(self, d: int = 0) -> float:
+        out = np.zeros(1)
+        _ck(self.L.edupic_get_bias(self._h, d, _ptr(out)), "get_bias")
+        return float(out[0])
+
+    def self_bias_step(self, n_steps: int, gain_v, measure: bool = False) -> np.ndarray:
+        """One self-bias iteration (Sec. 5) over n_steps time steps; gain_v
+        (volts) per discharge or one value for all.  Returns the biases."""
+        g = np.ascontiguousarray(np.broadcast_to(np.asarray(gain_v, dtype=np.float64), (len(self.discharges),)))
+        out = np.zeros(len(self.discharges))
+        _ck(self.L.edupic_self_bias_step(self._h, int(n_steps), 1 if measure else 0, _ptr(g), _ptr(out)),
+            "self_bias_step")
+        return out
 
     def check_accuracy(self, d: int = 0) -> dict:
         """Accuracy and stability conditions of Sec. 2.2 from the measured

@@ -275,3 +275,40 @@ def batch_mix(n_discharges: int = 64, seed0: int = 1000, n_min: float = 1e4, n_m
     """Independent discharges drawn by draw_discharge with seeds seed0 + k."""
     return [draw_discharge(np.random.default_rng(seed0 + k), seed0 + k, n_min, n_max, scale)
             for k in range(n_discharges)]
+
+
+# The dual-frequency parameter sets of Table 3: L = 25 mm, T_g = 350 K,
+# f_LF = 2 MHz, V_LF = 0..400 V; per (pressure, f_HF / V_HF) row the weight W,
+# N_G and N_T (time steps per LF cycle) of each V_LF column.
+DF_SWEEP_VLF = (0.0, 100.0, 200.0, 300.0, 400.0)
+DF_SWEEP_ROWS = (
+    # (case, p [Pa], f_HF [Hz], V_HF [V], W per V_LF, N_G per V_LF, N_T per V_LF)
+    (1, 20.0, 10e6, 500.0, (1.1e5, 1.0e5, 8.2e4, 6.1e4, 4.2e4), (600, 600, 600, 600, 600),
+     (31100, 31200, 31400, 31700, 33200)),
+    (1, 20.0, 20e6, 250.0, (1.7e5, 1.2e5, 9.2e4, 7.8e4, 6.8e4), (600, 500, 500, 500, 500),
+     (30700, 25800, 26100, 26200, 26400)),
+    (2, 3.0, 30e6, 250.0, (1.6e5, 1.5e5, 1.5e5, 5.5e4, 1.9e4), (500, 500, 500, 500, 400),
+     (30800, 30900, 31300, 31900, 27200)),
+    (2, 3.0, 40e6, 150.0, (1.5e5, 1.3e5, 1.1e5, 8.8e4, 2.8e4), (500, 500, 500, 500, 400),
+     (30700, 30900, 31100, 31300, 26300)),
+)
+
+
+def df_sweep(n: int = 100_000, seed0: int = 3000) -> List[Tuple[Discharge, Particles, Particles]]:
+    """The 20 dual-frequency discharges of Table 3 (CASE 1: 20 Pa with 10 MHz /
+    500 V or 20 MHz / 250 V; CASE 2: 3 Pa with 30 MHz / 250 V or 40 MHz /
+    150 V; each with a 2 MHz component of 0-400 V), with the table's W, N_G
+    and N_T, each in a steady-shape state of `n` particles per species
+    (density n W / (A L)).  Seeds seed0 + k in table order."""
+    out = []
+    k = 0
+    for _, p, f_hf, v_hf, ws, ngs, nts in DF_SWEEP_ROWS:
+        for j, v_lf in enumerate(DF_SWEEP_VLF):
+            d = Discharge(gap_m=0.025, pressure_pa=p, gas_temp_k=350.0, weight=ws[j], n_grid=ngs[j],
+                          steps_per_cycle=nts[j], ion_subcycle=20, cycle_freq_hz=2e6,
+                          harmonics=((f_hf, v_hf), (2e6, v_lf)), seed=seed0 + k, capacity=2 * n + 4096)
+            rng = np.random.default_rng(seed0 + k)
+            e, i = steady_shape(matched_electrons(n, sheath_fraction(d, n)), n, d, rng)
+            out.append((d, e, i))
+            k += 1
+    return out

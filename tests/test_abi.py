@@ -82,3 +82,20 @@ def test_create_rejects_small_or_misaligned_arena(lib):
     # never dereferenced: both are rejected before any device call
     assert lib.edupic_create(1, arr, ed.FP32, ctypes.c_void_p(256), out.value - 1, None, ctypes.byref(h)) == -2
     assert lib.edupic_create(1, arr, ed.FP32, ctypes.c_void_p(257), out.value, None, ctypes.byref(h)) == -1
+
+
+def test_df_sweep_workload_is_valid(lib):
+    """The 20 dual-frequency discharges of Table 3 pass the host checks: N_T a
+    multiple of N_SUB, every drive frequency a multiple of the 2 MHz cycle."""
+    mix = wl.df_sweep(n=500)
+    assert len(mix) == 20
+    ds = [m[0] for m in mix]
+    assert {(d.pressure_pa, d.harmonics[0]) for d in ds} == {
+        (20.0, (10e6, 500.0)), (20.0, (20e6, 250.0)), (3.0, (30e6, 250.0)), (3.0, (40e6, 150.0))}
+    assert sorted({d.harmonics[1][1] for d in ds}) == [0.0, 100.0, 200.0, 300.0, 400.0]
+    out = ctypes.c_size_t(0)
+    arr = (ed.Params * 20)(*[ed.to_params(d, 1000) for d in ds])
+    assert lib.edupic_arena_bytes(20, arr, ed.FP32, ctypes.byref(out)) == 0 and out.value > 0
+    for d, e, i in mix:
+        assert d.steps_per_cycle % d.ion_subcycle == 0
+        assert e.n > 0 and i.n == 500 and (e.x > 0).all() and (e.x < d.gap_m).all()

@@ -561,12 +561,11 @@ def test_reflection_and_emission_probabilities():
     # ions: every one absorbed; each emits an electron with probability gamma of its electrode
     i_pow, i_gnd = int((i_side == 0).sum()), int((i_side == 1).sum())
     assert c["abs_i_pow"] == i_pow and c["abs_i_gnd"] == i_gnd
-    expect = 0.25 * i_pow + 0.6 * i_gnd
-    sd = math.sqrt(0.25 * 0.75 * i_pow + 0.6 * 0.4 * i_gnd)
-    assert abs(c["emitted"] - expect) <= 5 * sd
+    for key, g, n_side in (("emitted_pow", 0.25, i_pow), ("emitted_gnd", 0.6, i_gnd)):
+        assert abs(c[key] - g * n_side) <= 5 * math.sqrt(g * (1 - g) * n_side), key
     # the emitted electrons were appended last, at the electrodes, pointing into the gap
     x1, vx1, vy1, vz1 = ref.particles(0)
-    k = c["emitted"]
+    k = c["emitted_pow"] + c["emitted_gnd"]
     xe, vxe = x1[-k:], vx1[-k:]
     assert np.all((xe == 0.0) | (xe == d.gap_m))
     assert np.all(vxe[xe == 0.0] > 0) and np.all(vxe[xe == d.gap_m] < 0)
@@ -657,3 +656,22 @@ def test_null_collision_ion_rate_thermal_partner():
     assert abs(hits - n * p_real) <= 5 * math.sqrt(n * p_real)
     # backward and isotropic in the ratio of their cross sections (equal here)
     assert abs(c["coll_i_iso"] - c["coll_i_back"]) <= 5 * math.sqrt(hits)
+
+
+# ------------------------------------------------------------------ DC self-bias (Sec. 5)
+def test_self_bias_adds_to_the_powered_electrode():
+    # no space charge (W = 0): phi = (V + V_bias)(1 - x/L) and E = (V + V_bias)/L
+    V, vb = 0.02, -0.35
+    d = _quiet(harmonics=((0.0, V),), gap_m=0.025, n_grid=101)
+    se, si = _tables(1000, sigma_e=(0, 0, 0), sigma_i=(0, 0))
+    rng = np.random.default_rng(9)
+    e = wl.Particles(rng.uniform(0.01, 0.015, 8), np.zeros(8), np.zeros(8), np.zeros(8))
+    s = oracle.Sim(d, se, si, 1e-3, e, wl.Particles.empty())
+    s.set_bias(vb)
+    s.step(1)
+    f = s.fields()
+    x = np.arange(d.n_grid) * d.gap_m / (d.n_grid - 1)
+    assert np.abs(f["phi"] - (V + vb) * (1 - x / d.gap_m)).max() <= 1e-12 * abs(V + vb)
+    assert np.abs(f["efield"] - (V + vb) / d.gap_m).max() <= 1e-12
+    # the electrons accelerate towards the more positive electrode (x = L here)
+    assert (s.particles(0)[1] > 0).all()

@@ -14,7 +14,8 @@ of the electron particle kernel against the measured HBM copy bandwidth.
 Beside it, on the same GPU: "plain" (the reference discharge of the paper's
 Table 2 alone, ~4e5 e- + 4e5 Ar+, one RF cycle per bench step),
 "dual_frequency" (1.356 + 27.12 MHz, N_G = 800, ~2e6 per species, one full LF
-cycle), "null_collision_ions" (the batch with the null-collision method for
+cycle), "df_sweep_table3" (the 20 dual-frequency discharges of Table 3 as one
+batch), "null_collision_ions" (the batch with the null-collision method for
 Ar+) and "served" (a Poisson stream of requests through the continuous-
 batching server).  With --gpus N under torchrun every rank runs its own batch
 (independent discharges: no collective on the data path).
@@ -52,6 +53,7 @@ BATCH_DISCHARGES = 64
 BATCH_STEPS = 400             # time steps per bench step (20 ion subcycles)
 N_STEADY = 500_000            # plain leg: particles per species of the steady-shape state
 DF_N = 2_000_000              # dual-frequency particles per species
+DF_SWEEP_N = 100_000  # particles per species in each Table 3 discharge
 SERVED_REQUESTS = 32
 SERVED_CYCLES = (2, 10)
 # 0.8 x (batched capacity ~1e11 particle-steps/s) / mean request work
@@ -380,6 +382,37 @@ def leg_null_collision(args, mix, flush) -> dict:
                               for k, v, n in zip(("push_e", "push_i", "finalize"), ms_k, launches)}}
 
 
+def leg_df_sweep(args, peak, peak_kind, flush) -> dict:
+    """The 20 dual-frequency discharges of Table 3 (2 MHz + 10/20 MHz at 20 Pa,
+    2 MHz + 30/40 MHz at 3 Pa, V_LF 0-400 V; the table's W, N_G and N_T),
+    1e5 particles per species each, stepped as one batch."""
+    from paper_2103_09642_gb300 import edupic as ed
+    from paper_2103_09642_gb300 import workloads as wl
+
+    mix = wl.df_sweep(n=DF_SWEEP_N)
+    ds = [m[0] for m in mix]
+    nd = len(ds)
+    se, si = wl.standin_cross_sections()
+    sim = ed.simulation_for(ds, ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(m[1], m[2]) for m in mix])
+    del mix
+    for _ in range(args.warmup):
+        sim.step(BATCH_STEPS, measure=True)
+    sim.synchronize()
+    tot = lambda: sum(sim.counters(k)["push_e"] + sim.counters(k)["push_i"] for k in range(nd))
+    c0 = tot()
+    steps = max(3, min(args.steps, 5))
+    ms = _timed(sim.stream, flush, steps, lambda: sim.step(BATCH_STEPS, measure=True))
+    ps = tot() - c0
+    n_e = sum(sim.counts(k)[0] for k in range(nd))
+    roof = _roofline(sim, nd, peak, peak_kind, steps=BATCH_STEPS)
+    sim.close()
+    return {"workload": "Table 3 dual-frequency sweep: 20 discharges (CASE 1 20 Pa, CASE 2 3 Pa; f_LF 2 MHz, "
+                        "V_LF 0-400 V), 1e5 particles per species each, one batch",
+            "discharges": nd, "particles_e": int(n_e), "value": ps / (ms / 1000.0), "unit": UNIT, "steps": steps,
+            "time_steps_per_step": BATCH_STEPS, "us_per_time_step": 1000.0 * ms / (steps * BATCH_STEPS),
+            "roofline": roof}
+
+
 def leg_served(args) -> dict:
     """A bounded Poisson stream through the request server: 32 requests
     drawn like the 64-discharge batch, 2-10 RF cycles each (the full stream,
@@ -502,6 +535,8 @@ def run_ours(args):
         extra["plain"] = leg_plain(args, peak, peak_kind, flush)
         _log("dual-frequency leg")
         extra["dual_frequency"] = leg_dual_frequency(args, peak, peak_kind, flush)
+        _log("Table 3 sweep leg")
+        extra["df_sweep_table3"] = leg_df_sweep(args, peak, peak_kind, flush)
         _log("null-collision leg")
         extra["null_collision_ions"] = leg_null_collision(args, mix, flush)
         _log("served leg")

@@ -26,6 +26,7 @@ _lib = None
 
 MAX_HARM = 4
 N_COUNTERS = 19
+XT_NAMES = ("pot", "efield", "ne", "ni", "je", "ji", "powere", "poweri", "meanee", "meanei", "ioniz")
 COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela", "coll_e_exc",
                  "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped",
                  "push_e", "push_i", "reflected", "emitted_pow", "emitted_gnd",
@@ -54,7 +55,7 @@ class _Params(ctypes.Structure):
         ("ifed_bins", ctypes.c_int), ("ifed_de_ev", ctypes.c_double), ("capacity", ctypes.c_int64),
         ("e_exc_ev", ctypes.c_double), ("e_ion_ev", ctypes.c_double),
         ("see_gamma", ctypes.c_double * 2), ("refl_eta", ctypes.c_double * 2), ("see_te_ev", ctypes.c_double),
-        ("null_collision", ctypes.c_int),
+        ("null_collision", ctypes.c_int), ("xt_bins", ctypes.c_int),
     ]
 
 
@@ -104,6 +105,8 @@ def lib():
             L.orc_ifed_normalise.argtypes = [_Q, ctypes.c_int, ctypes.c_double, _D, _D]
             L.orc_get_derived.argtypes = [ctypes.c_void_p, _D]
             L.orc_set_bias.argtypes = [ctypes.c_void_p, ctypes.c_double]
+            L.orc_get_xt.argtypes = [ctypes.c_void_p, ctypes.c_int, _D]
+            L.orc_get_xt.restype = ctypes.c_int
             L.orc_set_bias.restype = None
             L.orc_unit_collide_electron.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_double,
                                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, _D]
@@ -238,6 +241,7 @@ def _params(d) -> _Params:
         p.refl_eta[k] = d.refl_eta[k]
     p.see_te_ev = d.see_te_ev
     p.null_collision = int(d.null_collision)
+    p.xt_bins = int(d.xt_bins)
     return p
 
 
@@ -331,6 +335,13 @@ class Sim:
         out = np.zeros(2)
         m = lib().orc_get_power(self._h, _p(out, ctypes.c_double))
         return dict(measured_steps=int(m), electrons=float(out[0]), ions=float(out[1]))
+
+    def xt(self, quantity: int) -> np.ndarray:
+        """xt map [n_grid, xt_bins] of quantity (XT_NAMES order)."""
+        out = np.zeros((self.d.n_grid, self.d.xt_bins))
+        if lib().orc_get_xt(self._h, int(quantity), _p(out, ctypes.c_double)) != 0:
+            raise ValueError("no xt diagnostics")
+        return out
 
     def set_bias(self, v_bias: float) -> None:
         lib().orc_set_bias(self._h, ctypes.c_double(v_bias))

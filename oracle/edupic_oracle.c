@@ -190,6 +190,8 @@ typedef struct {
     /* null-collision method (Sec. 2.1.6, Sec. 5) instead of the per-particle
      * collision probability, per species: bit 0 electrons, bit 1 ions */
     int null_collision;
+    /* spatio-temporal diagnostics (Sec. 3.5): time bins per RF cycle, 0 = off */
+    int xt_bins;
 } orc_params;
 
 typedef struct {
@@ -224,6 +226,14 @@ typedef struct {
     int64_t *eepf, *ifed_pow, *ifed_gnd;
     double work[2]; /* sum over measured pushes of q E_x v_c dt, per unit weight (J), e- and Ar+ */
     double v_bias;  /* DC voltage added at the powered electrode (Sec. 5 self-bias) */
+    /* xt diagnostics (Sec. 3.5), [n_grid][xt_bins] sums over the measured steps
+     * of each time bin: phi, E, n_e, n_i; per species the weighted sums of
+     * v_c,x, of the energy (1/2) m |v_c|^2 in eV and of the weights; the
+     * weighted ionisation events; and the number of measured steps per bin
+     * (electrons and grid every step, ions on ion steps) */
+    int nxt, nbin;
+    double *xt_phi, *xt_ef, *xt_ne, *xt_ni, *xt_wv[2], *xt_we[2], *xt_w[2], *xt_ion;
+    int64_t *xt_steps[2];
     int64_t counters[19];
     /* scratch */
     orc_product *prod;
@@ -570,7 +580,8 @@ int orc_collide_ion(const orc_sim *s, int k, double *vx, double *vy, double *vz,
 orc_sim *orc_create(const orc_params *p)
 {
     if (p->n_grid < 3 || p->steps_per_cycle < 1 || p->ion_subcycle < 1 || p->n_harm < 0 || p->n_harm > ORC_MAX_HARM ||
-        p->capacity < 1 || p->eepf_bins < 1 || p->ifed_bins < 1)
+        p->capacity < 1 || p->eepf_bins < 1 || p->ifed_bins < 1 || p->xt_bins < 0 ||
+        (p->xt_bins > 0 && p->steps_per_cycle % p->xt_bins != 0))
         return NULL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     s->p = *p;
@@ -611,6 +622,22 @@ orc_sim *orc_create(const orc_params *p)
     s->prod = (orc_product *)calloc((size_t)s->prod_cap, sizeof(orc_product));
     s->emit = (orc_product *)calloc((size_t)s->prod_cap, sizeof(orc_product));
     s->absorbed = (unsigned char *)calloc((size_t)p->capacity, 1);
+    if (p->xt_bins > 0) {
+        const size_t m = (size_t)ng * (size_t)p->xt_bins;
+        s->nxt = p->xt_bins;
+        s->nbin = p->steps_per_cycle / p->xt_bins;
+        s->xt_phi = (double *)calloc(m, sizeof(double));
+        s->xt_ef = (double *)calloc(m, sizeof(double));
+        s->xt_ne = (double *)calloc(m, sizeof(double));
+        s->xt_ni = (double *)calloc(m, sizeof(double));
+        s->xt_ion = (double *)calloc(m, sizeof(double));
+        for (int sp = 0; sp < 2; ++sp) {
+            s->xt_wv[sp] = (double *)calloc(m, sizeof(double));
+            s->xt_we[sp] = (double *)calloc(m, sizeof(double));
+            s->xt_w[sp] = (double *)calloc(m, sizeof(double));
+            s->xt_steps[sp] = (int64_t *)calloc((size_t)p->xt_bins, sizeof(int64_t));
+        }
+    }
     return s;
 }
 
@@ -635,6 +662,17 @@ void orc_destroy(orc_sim *s)
     free(s->sum_ne);
     free(s->sum_ni);
     free(s->sum_phi);
+    free(s->xt_phi);
+    free(s->xt_ef);
+    free(s->xt_ne);
+    free(s->xt_ni);
+    free(s->xt_ion);
+    for (int sp = 0; sp < 2; ++sp) {
+        free(s->xt_wv[sp]);
+        free(s->xt_we[sp]);
+        free(s->xt_w[sp]);
+        free(s->xt_steps[sp]);
+    }
     free(s->eepf);
     free(s->ifed_pow);
     free(s->ifed_gnd);
@@ -749,6 +787,28 @@ static void compact(orc_species *sp, const unsigned char *absorbed)
     sp->n = nn;
 }
 
+/* Adds (c1 a, c2 a) to grid points (c, c+1) of time bin b of an xt array
+ * (the weights of the density assignment, Sec. 2.1.1). */
+static void xt_add(const orc_sim *s, double *xt, double x, int b, double a)
+{
+    int c;
+    double c0;
+    cell_of(x, s->inv_dx, s->p.n_grid, &c, &c0);
+    xt[(size_t)c * s->nxt + b] += (c + 1 - c0) * a;
+    xt[(size_t)(c + 1) * s->nxt + b] += (c0 - c) * a;
+}
+
+/* One particle's contribution to the xt sums of its species: at x(t), with
+ * the time-centred velocity v_c (Sec. 3.5). */
+static void xt_particle(const orc_sim *s, int species, double x, double vcx, double vy, double vz, int b)
+{
+    const double m = species == ORC_SPECIES_E ? ORC_E_MASS : s->ar_mass;
+    const double en = 0.5 * m * (vcx * vcx + vy * vy + vz * vz) / ORC_EV_TO_J;
+    xt_add(s, s->xt_wv[species], x, b, vcx);
+    xt_add(s, s->xt_we[species], x, b, en);
+    xt_add(s, s->xt_w[species], x, b, 1.0);
+}
+
 /* One PIC/MCC time step (Sec. 2.1, Fig. 2; Algorithms 2-6). */
 static void one_step(orc_sim *s, int measure)
 {
@@ -757,6 +817,8 @@ static void one_step(orc_sim *s, int measure)
     const int64_t t = s->step % p->steps_per_cycle; /* within-cycle step */
     const int ion_step = (t % p->ion_subcycle) == 0;
     orc_species *E = &s->sp[ORC_SPECIES_E], *I = &s->sp[ORC_SPECIES_I];
+    const int xt_on = measure && s->nxt > 0;
+    const int xb = s->nxt > 0 ? (int)(t / s->nbin) : 0; /* time bin of this step */
 
     /* (1) densities (Algorithm 2), every step for e-, every N_SUB-th for Ar+.
      * Reading: the densities are reset before every deposition. */
@@ -795,6 +857,7 @@ static void one_step(orc_sim *s, int measure)
                 double r = en / p->eepf_de_ev;
                 if (r < (double)p->eepf_bins) s->eepf[(int)r] += 1;
             }
+            if (xt_on) xt_particle(s, ORC_SPECIES_E, xo, 0.5 * (vx_old + E->vx[k]), E->vy[k], E->vz[k], xb);
         }
         E->x[k] += E->vx[k] * s->dt_e;
     }
@@ -808,6 +871,7 @@ static void one_step(orc_sim *s, int measure)
             double vx_old = I->vx[k];
             I->vx[k] += e_x * s->factor_i;
             if (measure) s->work[ORC_SPECIES_I] += ORC_E_CHARGE * e_x * (0.5 * (vx_old + I->vx[k])) * s->dt_i;
+            if (xt_on) xt_particle(s, ORC_SPECIES_I, I->x[k], 0.5 * (vx_old + I->vx[k]), I->vy[k], I->vz[k], xb);
             I->x[k] += I->vx[k] * s->dt_i;
         }
     }
@@ -866,6 +930,8 @@ static void one_step(orc_sim *s, int measure)
             s->counters[ORC_C_COLL_E_ELA + proc]++;
             s->counters[ORC_C_SUBTHRESHOLD] += sub;
             if (proc == 2) {
+                /* ionisation rate map: the event at the collision position */
+                if (xt_on) xt_add(s, s->xt_ion, E->x[k], xb, 1.0);
                 /* Reading: the new Ar+ is drawn from the gas Maxwellian */
                 double n1[2], n2[2], z1[2], z2[2];
                 draw_block(p->seed, k, s->step, ORC_SPECIES_E, 3, n1);
@@ -1011,6 +1077,17 @@ static void one_step(orc_sim *s, int measure)
         }
         s->measured_steps++;
     }
+    if (xt_on) {
+        for (int k = 0; k < ng; ++k) {
+            const size_t j = (size_t)k * s->nxt + xb;
+            s->xt_phi[j] += s->phi[k];
+            s->xt_ef[j] += s->efield[k];
+            s->xt_ne[j] += s->n_e[k];
+            s->xt_ni[j] += s->n_i[k];
+        }
+        s->xt_steps[0][xb]++;
+        if (ion_step) s->xt_steps[1][xb]++;
+    }
     s->step++;
 }
 
@@ -1089,6 +1166,47 @@ void orc_ifed_normalise(const int64_t *h, int n, double de, double *energy, doub
 }
 
 /* Derived quantities, for tests. */
+/* The xt map of quantity q (0 phi, 1 E, 2 n_e, 3 n_i, 4 j_e, 5 j_i, 6 power
+ * e-, 7 power Ar+, 8 mean e- energy, 9 mean Ar+ energy, 10 ionisation rate),
+ * [n_grid][xt_bins], averaged over the measured steps of each bin (ions: the
+ * ion steps).  Readings: j = q FACTOR_W sum(w v_c,x) per step, with the
+ * density's doubling at the two half-volume edge points; the power map is the
+ * product j E of the current and field maps (Sec. 3.5 describes the power as
+ * the average of j E and its xt file as that product); the mean energies are
+ * in eV; the ionisation rate is FACTOR_W sum(w) per step (doubled at the
+ * edges) over dt_e.  Returns -1 without xt diagnostics. */
+int orc_get_xt(const orc_sim *s, int q, double *out)
+{
+    if (s->nxt < 1 || q < 0 || q > 10) return -1;
+    const int ng = s->p.n_grid, nxt = s->nxt;
+    for (int k = 0; k < ng; ++k) {
+        const double edge = (k == 0 || k == ng - 1) ? 2.0 : 1.0;
+        for (int b = 0; b < nxt; ++b) {
+            const size_t j = (size_t)k * nxt + b;
+            const double n0 = (double)s->xt_steps[0][b], n1 = (double)s->xt_steps[1][b];
+            const double je = n0 > 0 ? -ORC_E_CHARGE * s->factor_w * edge * s->xt_wv[0][j] / n0 : 0.0;
+            const double ji = n1 > 0 ? ORC_E_CHARGE * s->factor_w * edge * s->xt_wv[1][j] / n1 : 0.0;
+            const double ef = n0 > 0 ? s->xt_ef[j] / n0 : 0.0;
+            double v = 0.0;
+            switch (q) {
+                case 0: v = n0 > 0 ? s->xt_phi[j] / n0 : 0.0; break;
+                case 1: v = ef; break;
+                case 2: v = n0 > 0 ? s->xt_ne[j] / n0 : 0.0; break;
+                case 3: v = n0 > 0 ? s->xt_ni[j] / n0 : 0.0; break;
+                case 4: v = je; break;
+                case 5: v = ji; break;
+                case 6: v = je * ef; break;
+                case 7: v = ji * ef; break;
+                case 8: v = s->xt_w[0][j] > 0 ? s->xt_we[0][j] / s->xt_w[0][j] : 0.0; break;
+                case 9: v = s->xt_w[1][j] > 0 ? s->xt_we[1][j] / s->xt_w[1][j] : 0.0; break;
+                default: v = n0 > 0 ? s->factor_w * edge * s->xt_ion[j] / (n0 * s->dt_e) : 0.0; break;
+            }
+            out[j] = v;
+        }
+    }
+    return 0;
+}
+
 void orc_get_derived(const orc_sim *s, double out[16])
 {
     out[12] = s->nu_star[0];

@@ -73,6 +73,8 @@ class Discharge:
     # null-collision method (Sec. 2.1.6) instead of the direct test, per
     # species: 1 electrons, 2 ions, 3 both, 0 off
     null_collision: int = 0
+    # spatio-temporal diagnostics (Sec. 3.5): time bins per RF cycle, 0 = off
+    xt_bins: int = 0
 
     def replace(self, **kw) -> "Discharge":
         return dataclasses.replace(self, **kw)

@@ -675,3 +675,61 @@ def test_self_bias_adds_to_the_powered_electrode():
     assert np.abs(f["efield"] - (V + vb) / d.gap_m).max() <= 1e-12
     # the electrons accelerate towards the more positive electrode (x = L here)
     assert (s.particles(0)[1] > 0).all()
+
+
+# ------------------------------------------------------------------ xt diagnostics (Sec. 3.5)
+XT = {name: k for k, name in enumerate(oracle.XT_NAMES)}
+
+
+def test_xt_uniform_drift_closed_form():
+    # e- all moving with v0 along x, a weight so small that the field is ~0:
+    # j_e = -e v0 n_e and the mean energy (1/2) m v0^2 at every point and bin
+    v0, n = 1.0e5, 4000
+    d = _quiet(weight=1e-9, n_grid=51, steps_per_cycle=400, ion_subcycle=20, xt_bins=20)
+    se, si = _tables(1000, sigma_e=(0, 0, 0), sigma_i=(0, 0))
+    rng = np.random.default_rng(21)
+    e = wl.Particles(rng.uniform(0.005, 0.02, n), np.full(n, v0), np.zeros(n), np.zeros(n))
+    s = oracle.Sim(d, se, si, 1e-3, e, wl.Particles.empty())
+    s.step(60, measure=True)  # bins 0, 1, 2 of 20 steps
+    ne, je, mee = s.xt(XT["ne"]), s.xt(XT["je"]), s.xt(XT["meanee"])
+    assert (ne[:, 3:] == 0).all() and (ne[:, :3] > 0).any()
+    assert np.abs(je + QE * v0 * ne).max() <= 1e-9 * QE * v0 * ne.max()
+    hit = s.xt(XT["ne"]) > 0
+    assert np.abs(mee[hit] - 0.5 * ME * v0 ** 2 / QE).max() <= 1e-9 * 0.5 * ME * v0 ** 2 / QE
+    assert (mee[~hit] == 0).all() and (s.xt(XT["ji"]) == 0).all()
+    # the field map is the drive's (none) plus the tiny space charge
+    assert np.abs(s.xt(XT["efield"])).max() < 1e-3
+    assert np.array_equal(s.xt(XT["powere"]), je * s.xt(XT["efield"]))
+
+
+def test_xt_bins_average_to_the_time_averages():
+    # over whole bins, the step-weighted mean of the n_e, n_i, phi maps is the
+    # time average of the measured steps
+    d, e, i = wl.reference_steady(seed=3, n=3000)
+    d = d.replace(xt_bins=400)  # 10 steps per bin
+    se, si = wl.standin_cross_sections(20_000)
+    s = oracle.Sim(d, se, si, wl.CS_DE_EV, e, i)
+    s.step(50, measure=True)
+    diag = s.diagnostics()
+    for key, name in (("n_e", "ne"), ("n_i", "ni"), ("phi", "pot")):
+        m = s.xt(XT[name])[:, :5].mean(axis=1)  # 5 full bins of 10 steps
+        assert np.abs(m - diag[key]).max() <= 1e-12 * np.abs(diag[key]).max(), key
+
+
+def test_xt_ionisation_rate_integrates_to_the_events():
+    # sum over space and time of the rate map: W x (ionisations of the measured steps)
+    d, e, i = wl.reference_steady(seed=4, n=8000)
+    d = d.replace(xt_bins=200, harmonics=((13.56e6, 400.0),))  # N_BIN = 20
+    se, si = wl.standin_cross_sections(300_000)
+    s = oracle.Sim(d, se, si, wl.CS_DE_EV, e, i)
+    s.step(200, measure=True)
+    events = s.counters()["coll_e_ion"]
+    assert events > 10
+    dv = s.derived()
+    rate = s.xt(XT["ioniz"])
+    vol = np.full(d.n_grid, d.area_m2 * dv["dx"])
+    vol[[0, -1]] *= 0.5
+    steps = np.zeros(d.xt_bins)
+    steps[:10] = 20
+    total = (rate * vol[:, None] * steps[None, :] * dv["dt_e"]).sum()
+    assert total == pytest.approx(d.weight * events, rel=1e-12)

@@ -137,7 +137,10 @@ typedef struct {
      * An Ar+ draws its gas partner only when picked.  Energies past the table can exceed nu*; those particles always
      * collide when picked and are counted (EDUPIC_C_NULL_OVER). */
     int32_t null_collision;
-    int32_t reserved2;
+    /* Spatio-temporal ("xt") diagnostics (Sec. 3.5): N_XT time bins per RF
+     * cycle (N_T a multiple of it, N_BIN = N_T / N_XT steps per bin), 0 = off.
+     * Read with edupic_get_xt. */
+    int32_t xt_bins;
 } edupic_params;
 
 typedef struct edupic_sim edupic_sim;
@@ -294,6 +297,41 @@ int edupic_get_power(edupic_sim *sim, int d, double out[2]);
 int edupic_set_bias(edupic_sim *sim, int d, double v_bias);
 int edupic_get_bias(edupic_sim *sim, int d, double *v_bias);
 int edupic_self_bias_step(edupic_sim *sim, int64_t n_steps, int measure, const double *gain_v, double *v_bias);
+
+/* Spatio-temporal ("xt") diagnostics of Sec. 3.5, for a discharge created
+ * with xt_bins = N_XT > 0.  Every measured step adds to time bin
+ * b = (t mod N_T) / N_BIN: the grid quantities after the field solve, and in
+ * the particle push the particle quantities at the position x(t) with the
+ * time-centred velocity v_c = (v(t-1/2) + v(t+1/2)) / 2, weighted to the two
+ * grid points like the density deposition (Sec. 2.1.1); ionisations add at
+ * the collision position.  Maps are averages over the measured steps of each
+ * bin (ions: over the ion steps).  quantity:
+ *   EDUPIC_XT_POT, EDUPIC_XT_EFIELD  potential (V), electric field (V/m)
+ *   EDUPIC_XT_NE, EDUPIC_XT_NI       densities (m^-3)
+ *   EDUPIC_XT_JE, EDUPIC_XT_JI       current densities q n <v_c,x> (A/m^2)
+ *   EDUPIC_XT_POWERE, _POWERI        power absorption j E (W/m^3), the product
+ *                                    of the current and field maps
+ *   EDUPIC_XT_MEANEE, _MEANEI        mean energies (1/2) m <|v_c|^2> (eV; 0
+ *                                    where no particle was counted)
+ *   EDUPIC_XT_IONIZ                  ionisation rate (m^-3 s^-1)
+ * out: host, n_grid x xt_bins doubles, row-major (row = grid point, column =
+ * time bin).  Bins that no measured step reached are 0.  EDUPIC_ESTATE if
+ * the discharge has no xt diagnostics.  Synchronises the stream.
+ * (The request server does not keep xt maps: requests with xt_bins > 0 are
+ * refused there.) */
+#define EDUPIC_XT_POT 0
+#define EDUPIC_XT_EFIELD 1
+#define EDUPIC_XT_NE 2
+#define EDUPIC_XT_NI 3
+#define EDUPIC_XT_JE 4
+#define EDUPIC_XT_JI 5
+#define EDUPIC_XT_POWERE 6
+#define EDUPIC_XT_POWERI 7
+#define EDUPIC_XT_MEANEE 8
+#define EDUPIC_XT_MEANEI 9
+#define EDUPIC_XT_IONIZ 10
+#define EDUPIC_XT_QUANTITIES 11
+int edupic_get_xt(edupic_sim *sim, int d, int quantity, double *out);
 
 /* Accuracy and stability conditions of Sec. 2.2 (the checks the paper's
  * code writes to info.txt, Sec. 3.5), evaluated for discharge d from its

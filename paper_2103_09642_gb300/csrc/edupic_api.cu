@@ -77,6 +77,11 @@ Layout layout_of(const edupic_params &p, size_t elem)
     for (int c = 0; c < 3; ++c) L.prod_ve[c] = take((size_t)kEvents * elem);
     for (int c = 0; c < 3; ++c) L.prod_vi[c] = take((size_t)kEvents * elem);
     L.vdrive = take((size_t)p.steps_per_cycle * 8);
+    if (p.xt_bins > 0) {
+        const size_t m = ng * (size_t)p.xt_bins;
+        L.xt_bytes = 9 * m * 8 + 4 * (size_t)p.xt_bins * 8;
+        L.xt = take(L.xt_bytes);
+    }
     L.emit = p.see_gamma[0] > 0.0 || p.see_gamma[1] > 0.0;
     if (L.emit) {
         L.emit_parent = take((size_t)kEvents * 4);
@@ -120,6 +125,9 @@ int check_params(int nd, const edupic_params *ps, int precision)
                 return EDUPIC_EINVAL;
         if (!(p.see_te_ev >= 0) || !(p.see_te_ev < 1e6)) return EDUPIC_EINVAL;
         if (p.null_collision < 0 || p.null_collision > 3) return EDUPIC_EINVAL;
+        if (p.xt_bins < 0 || (p.xt_bins > 0 && p.steps_per_cycle % p.xt_bins != 0) ||
+            (int64_t)p.xt_bins * p.n_grid > (1 << 24))
+            return EDUPIC_EINVAL;
     }
     return EDUPIC_OK;
 }
@@ -226,6 +234,8 @@ void fill_desc(edupic_sim *S, int d)
     D.cs_n_i = S->desc.size() > (size_t)d ? S->desc[d].cs_n_i : 1;
     D.active = 1;
     D.null_coll = p.null_collision;
+    D.nxt = p.xt_bins;
+    D.nbin = p.xt_bins > 0 ? p.steps_per_cycle / p.xt_bins : 0;
     D.stop_step = LLONG_MAX;
     D.cap[0] = p.capacity_e;
     D.cap[1] = p.capacity_i;
@@ -259,6 +269,22 @@ void fill_desc(edupic_sim *S, int d)
     D.ctrl = S->d_ctrl + d;
     D.prod_parent = reinterpret_cast<int *>(b + L.prod_parent);
     D.sort_buf = reinterpret_cast<int *>(b + L.sort_buf);
+    if (p.xt_bins > 0) {
+        const size_t m = (size_t)p.n_grid * (size_t)p.xt_bins;
+        double *x = reinterpret_cast<double *>(b + L.xt);
+        D.xt_f = x;
+        D.xt_qe = x + m;
+        D.xt_qi = x + 2 * m;
+        D.xt_cnti = x + 3 * m;
+        D.xt_v[0] = x + 4 * m;
+        D.xt_v[1] = x + 5 * m;
+        D.xt_en[0] = x + 6 * m;
+        D.xt_en[1] = x + 7 * m;
+        D.xt_ion = x + 8 * m;
+        D.xt_V = x + 9 * m;
+        D.xt_d0 = D.xt_V + p.xt_bins;
+        D.xt_steps = reinterpret_cast<long long *>(D.xt_d0 + p.xt_bins);
+    }
     if (L.emit) {
         D.emit_parent = reinterpret_cast<int *>(b + L.emit_parent);
         D.emit_x = b + L.emit_x;
@@ -366,26 +392,33 @@ int setup_grid(edupic_sim *S)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (int sp = 0; sp < 2; ++sp) {
         const int eb = sp == 0 ? S->eepf_max : 0;
-        const size_t smem = S->precision == EDUPIC_FP32 ? Launch<float>::push_smem(S->nd, S->ng_max, eb)
-                                                        : Launch<double>::push_smem(S->nd, S->ng_max, eb);
-        const int nb = S->precision == EDUPIC_FP32 ? Launch<float>::push_blocks_per_sm(sp, smem)
-                                                   : Launch<double>::push_blocks_per_sm(sp, smem);
-        if (nb < 1) return EDUPIC_ECUDA;
-        S->grid[sp] = nb * std::max(sms, 1);
+        for (int xt = 0; xt < 2; ++xt) {
+            const size_t smem = S->precision == EDUPIC_FP32 ? Launch<float>::push_smem(S->nd, S->ng_max, eb, xt)
+                                                            : Launch<double>::push_smem(S->nd, S->ng_max, eb, xt);
+            const int nb = S->precision == EDUPIC_FP32 ? Launch<float>::push_blocks_per_sm(sp, smem, xt)
+                                                       : Launch<double>::push_blocks_per_sm(sp, smem, xt);
+            if (nb < 1 && (!xt || S->xt_any)) return EDUPIC_ECUDA;
+            (xt ? S->grid_xt[sp] : S->grid[sp]) = std::max(nb, 0) * std::max(sms, 1);
+        }
         S->grid_max[sp] = S->grid[sp];
     }
     S->sms = std::max(sms, 1);
     return EDUPIC_OK;
 }
 
+// The xt-accumulating kernel runs on the measured steps of a simulation that
+// keeps xt diagnostics, on its own resident grid.
+int xt_on(const edupic_sim *S, int measure) { return measure && S->xt_any ? 1 : 0; }
+int push_grid(const edupic_sim *S, int sp, int measure) { return xt_on(S, measure) ? S->grid_xt[sp] : S->grid[sp]; }
+
 template <typename T>
 int launch_step(edupic_sim *S, bool ion, int measure)
 {
-    cudaError_t e = Launch<T>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max, S->null_any[0],
-                                    S->stream);
+    cudaError_t e = Launch<T>::push(S->d_desc, S->nd, 0, measure, push_grid(S, 0, measure), S->ng_max,
+                                    S->eepf_max, S->null_any[0], xt_on(S, measure), S->stream);
     if (e == cudaSuccess && ion)
-        e = Launch<T>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max, S->null_any[1],
-                            S->stream);
+        e = Launch<T>::push(S->d_desc, S->nd, 1, measure, push_grid(S, 1, measure), S->ng_max,
+                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->stream);
     if (e == cudaSuccess) e = Launch<T>::finalize(S->d_desc, S->nd, ion ? 1 : 0, measure, S->stream);
     return cuda_status(e);
 }
@@ -651,6 +684,7 @@ int edupic_create(int nd, const edupic_params *params, int precision, void *devi
     }
     for (int d = 0; d < nd; ++d) fill_desc(S, d);
     update_null_any(S);
+    for (int d = 0; d < nd; ++d) S->xt_any |= params[d].xt_bins > 0 ? 1 : 0;
     cudaError_t e = cudaMemsetAsync(S->arena, 0, need, S->stream);
     if (e != cudaSuccess) {
         delete S;
@@ -830,22 +864,22 @@ int edupic_profile_steps(edupic_sim *S, int64_t n_steps, int measure, double out
             e = cudaEventRecord(E[0], S->stream);
             if (S->precision == EDUPIC_FP32) {
                 if (e == cudaSuccess)
-                    e = Launch<float>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max,
-                                            S->null_any[0], S->stream);
+                    e = Launch<float>::push(S->d_desc, S->nd, 0, measure, push_grid(S, 0, measure), S->ng_max,
+                                            S->eepf_max, S->null_any[0], xt_on(S, measure), S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[1], S->stream);
                 if (e == cudaSuccess && ion[i])
-                    e = Launch<float>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max,
-                                            S->null_any[1], S->stream);
+                    e = Launch<float>::push(S->d_desc, S->nd, 1, measure, push_grid(S, 1, measure), S->ng_max,
+                                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[2], S->stream);
                 if (e == cudaSuccess) e = Launch<float>::finalize(S->d_desc, S->nd, ion[i], measure, S->stream);
             } else {
                 if (e == cudaSuccess)
-                    e = Launch<double>::push(S->d_desc, S->nd, 0, measure, S->grid[0], S->ng_max, S->eepf_max,
-                                            S->null_any[0], S->stream);
+                    e = Launch<double>::push(S->d_desc, S->nd, 0, measure, push_grid(S, 0, measure), S->ng_max,
+                                            S->eepf_max, S->null_any[0], xt_on(S, measure), S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[1], S->stream);
                 if (e == cudaSuccess && ion[i])
-                    e = Launch<double>::push(S->d_desc, S->nd, 1, measure, S->grid[1], S->ng_max, S->eepf_max,
-                                            S->null_any[1], S->stream);
+                    e = Launch<double>::push(S->d_desc, S->nd, 1, measure, push_grid(S, 1, measure), S->ng_max,
+                                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[2], S->stream);
                 if (e == cudaSuccess) e = Launch<double>::finalize(S->d_desc, S->nd, ion[i], measure, S->stream);
             }
@@ -1097,8 +1131,80 @@ int edupic_reset_diagnostics(edupic_sim *S, int d)
     if (e == cudaSuccess) e = cudaMemsetAsync(D.ifed_gnd, 0, (size_t)p.ifed_bins * 8, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.power, 0, 2 * sizeof(double), S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&D.ctrl->measured, 0, sizeof(long long), S->stream);
+    if (e == cudaSuccess && D.nxt > 0)
+        e = cudaMemsetAsync(S->arena + S->base[d] + S->layouts[d].xt, 0, S->layouts[d].xt_bytes, S->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
     return cuda_status(e);
+}
+
+// xt maps (Sec. 3.5) from the binned sums: the grid quantities through the
+// same prefix-sum form as the time averages (per bin: sum phi_p = S_V + p S_d0
+// - c sum_{j<p} S_F,j; E from the mean phi and the mean charge density at the
+// edges), the particle quantities normalised per step of the bin.
+int edupic_get_xt(edupic_sim *S, int d, int quantity, double *out)
+{
+    if (!valid_d(S, d) || !out || quantity < 0 || quantity >= EDUPIC_XT_QUANTITIES) return EDUPIC_EINVAL;
+    const DischargeDev &D = S->desc[d];
+    if (D.nxt < 1) return EDUPIC_ESTATE;
+    Ctrl c;
+    int rc = read_ctrl(S, d, &c);
+    if (rc) return rc;
+    const int ng = D.ng, nxt = D.nxt, M = ng - 1;
+    const size_t m = (size_t)ng * nxt;
+    std::vector<double> raw(9 * m + 2 * (size_t)nxt);
+    std::vector<long long> steps(2 * (size_t)nxt);
+    cudaError_t e = cudaMemcpy(raw.data(), D.xt_f, raw.size() * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(steps.data(), D.xt_steps, steps.size() * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return EDUPIC_ECUDA;
+    const double *F = raw.data(), *Qe = F + m, *Qi = F + 2 * m, *Ci = F + 3 * m, *Ve = F + 4 * m, *Vi = F + 5 * m;
+    const double *Ee = F + 6 * m, *Ei = F + 7 * m, *Io = F + 8 * m, *SV = F + 9 * m, *Sd0 = SV + nxt;
+    const double q2 = 1.0 / 4294967296.0;
+    std::vector<double> phi((size_t)ng), ne((size_t)ng), ni((size_t)ng);
+    for (int b = 0; b < nxt; ++b) {
+        const double n0 = (double)steps[(size_t)b], n1 = (double)steps[(size_t)nxt + b];
+        if (n0 <= 0.0) {
+            for (int p = 0; p < ng; ++p) out[(size_t)p * nxt + b] = 0.0;
+            continue;
+        }
+        double g = 0.0;
+        for (int p = 0; p < ng; ++p) {
+            const size_t j = (size_t)p * nxt + b;
+            const double edge = (p == 0 || p == M) ? 2.0 : 1.0;
+            phi[(size_t)p] = p == M ? 0.0 : (SV[b] + (double)p * Sd0[b] - D.poisson_c * g) / n0;
+            if (p <= M - 1) g += F[j];
+            ne[(size_t)p] = edge * D.factor_w * (Qe[j] * q2) / n0;
+            ni[(size_t)p] = edge * D.factor_w * (Qi[j] * q2) / n0;
+        }
+        for (int p = 0; p < ng; ++p) {
+            const size_t j = (size_t)p * nxt + b;
+            const double edge = (p == 0 || p == M) ? 2.0 : 1.0;
+            double ef;
+            if (p == 0)
+                ef = (phi[0] - phi[1]) / D.dx - kQE * (ni[0] - ne[0]) * D.dx / (2.0 * kEPS0);
+            else if (p == M)
+                ef = (phi[(size_t)M - 1] - phi[(size_t)M]) / D.dx + kQE * (ni[(size_t)M] - ne[(size_t)M]) * D.dx / (2.0 * kEPS0);
+            else
+                ef = (phi[(size_t)p - 1] - phi[(size_t)p + 1]) / (2.0 * D.dx);
+            const double je = -kQE * D.factor_w * edge * Ve[j] / n0;
+            const double ji = n1 > 0.0 ? kQE * D.factor_w * edge * Vi[j] / n1 : 0.0;
+            double v = 0.0;
+            switch (quantity) {
+                case EDUPIC_XT_POT: v = phi[(size_t)p]; break;
+                case EDUPIC_XT_EFIELD: v = ef; break;
+                case EDUPIC_XT_NE: v = ne[(size_t)p]; break;
+                case EDUPIC_XT_NI: v = ni[(size_t)p]; break;
+                case EDUPIC_XT_JE: v = je; break;
+                case EDUPIC_XT_JI: v = ji; break;
+                case EDUPIC_XT_POWERE: v = je * ef; break;
+                case EDUPIC_XT_POWERI: v = ji * ef; break;
+                case EDUPIC_XT_MEANEE: v = Qe[j] > 0.0 ? Ee[j] / (Qe[j] * q2) : 0.0; break;
+                case EDUPIC_XT_MEANEI: v = Ci[j] > 0.0 ? Ei[j] / (Ci[j] * q2) : 0.0; break;
+                default: v = D.factor_w * edge * Io[j] / (n0 * D.dt_e); break;
+            }
+            out[j] = v;
+        }
+    }
+    return error_of(c);
 }
 
 // Checkpoint file: magic, version, step, counts, then x, vx, vy, vz of the

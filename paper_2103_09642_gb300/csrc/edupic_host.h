@@ -24,6 +24,7 @@ struct Layout {
     size_t eepf, ifed_pow, ifed_gnd, power, holes[2], prod_parent, sort_buf, prod_x, prod_ve[3], prod_vi[3], vdrive;
     size_t emit_parent, emit_x, emit_v[3];  // present only when an electrode emits (see_gamma > 0)
     bool emit;
+    size_t xt, xt_bytes;  // xt diagnostics block (xt_bins > 0), zeroed as one
     size_t bytes;
 };
 
@@ -63,6 +64,8 @@ struct edupic_sim {
     std::vector<double> sigsum_host[2];  // sum of the process cross sections per table entry (m^2)
     double cs_de_host[2] = {0.0, 0.0};
     int null_any[2] = {0, 0};  // some active discharge uses the null-collision method, per species
+    int xt_any = 0;            // some discharge keeps xt diagnostics (the accumulating kernel variant)
+    int grid_xt[2] = {0, 0};   // resident limit of the accumulating particle kernel
     std::vector<double> v_bias;  // DC voltage added at the powered electrode, per discharge (Sec. 5 self-bias)
     void *pinned = nullptr;  // page-locked staging buffer for particle uploads
     size_t pinned_bytes = 0;

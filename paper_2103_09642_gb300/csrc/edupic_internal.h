@@ -74,6 +74,7 @@ struct DischargeDev {
     int ng, nt, nsub, n_harm, eepf_bins, ifed_bins, cs_n_e, cs_n_i;
     int active;
     int null_coll;  // null-collision method: bit 0 electrons, bit 1 ions
+    int nxt, nbin;  // xt diagnostics: time bins per cycle and steps per bin (nxt = 0: off)
     long long stop_step;       // the discharge is frozen (skipped) once its step count reaches this
     long long cap[2];
     unsigned long long seed;
@@ -91,6 +92,12 @@ struct DischargeDev {
     unsigned long long *eepf;  // [kEepfStripes][eepf_bins], summed on read
     unsigned long long *ifed_pow, *ifed_gnd;
     double *power;             // [2] e-, Ar+: sum over measured pushes of E_x (v_old + v_new)
+    // xt diagnostics, [ng][nxt] sums over the measured steps of each time bin:
+    // F, Q_e, Q_i (all steps), Q_i of the ion steps, sum w v_c,x and sum w
+    // eps_c (eV) per species, ionisation weights; [nxt] sums of V and d_0;
+    // [2][nxt] measured steps (all, ion steps).  Null when off.
+    double *xt_f, *xt_qe, *xt_qi, *xt_cnti, *xt_v[2], *xt_en[2], *xt_ion, *xt_V, *xt_d0;
+    long long *xt_steps;
     Ctrl *ctrl;
     int *holes[2];
     int *prod_parent;
@@ -111,11 +118,12 @@ struct Launch {
     static cudaError_t deposit(const DischargeDev *dd, int nd, int d, int species, int also_acc, cudaStream_t st);
     static cudaError_t fields(const DischargeDev *dd, int nd, int d, cudaStream_t st);
     static cudaError_t averages(const DischargeDev *dd, int nd, int d, cudaStream_t st);
+    // xt: the instantiation that accumulates the xt diagnostics (measured steps)
     static cudaError_t push(const DischargeDev *dd, int nd, int species, int measure, int grid, int ng_max,
-                            int eepf_max, int null_any, cudaStream_t st);
+                            int eepf_max, int null_any, int xt, cudaStream_t st);
     static cudaError_t finalize(const DischargeDev *dd, int nd, int ion_step, int measure, cudaStream_t st);
-    static size_t push_smem(int nd, int ng_max, int eepf_max);
-    static int push_blocks_per_sm(int species, size_t smem);
+    static size_t push_smem(int nd, int ng_max, int eepf_max, int xt);
+    static int push_blocks_per_sm(int species, size_t smem, int xt);
 };
 
 }  // namespace edupic

@@ -474,7 +474,8 @@ __device__ __forceinline__ bool null_real(const DischargeDev &D, int k, T q2, T 
 // including the append record and the deposition of an ionisation pair.
 template <typename T>
 __device__ __forceinline__ void electron_collision(const DischargeDev &D, int slot, const RngKey &key, T idx_scale,
-                                                   int cs_n, T inv_dx, const DepAcc &acc, unsigned int *sCnt)
+                                                   int cs_n, T inv_dx, const DepAcc &acc, int xcol,
+                                                   unsigned int *sCnt)
 {
     using T2 = typename VecOf<T>::pair;
     T *X = reinterpret_cast<T *>(D.x[0]);
@@ -527,6 +528,11 @@ __device__ __forceinline__ void electron_collision(const DischargeDev &D, int sl
     dep_add(acc, pp, q2);
     atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp), 4294967296ull - q2);
     atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp + 1), q2);
+    if (xcol >= 0) {
+        // ionisation rate map: the event at the collision position
+        atomicAdd(D.xt_ion + (size_t)pp * D.nxt + xcol, (double)((T)(pp + 1) - d0));
+        atomicAdd(D.xt_ion + (size_t)(pp + 1) * D.nxt + xcol, (double)(d0 - (T)pp));
+    }
 }
 
 // Thermal Ar partner of an ion (drawn before the collision probability).
@@ -718,26 +724,30 @@ __device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy,
 // ---------------------------------------------------------------- particle kernel
 // Tiles in the shared-memory ring: 4 in FP32 (16 KB each), 3 in FP64 (also
 // 16 KB each), so that two blocks fit an SM in both modes.
-template <typename T>
+template <typename T, bool XT>
 __host__ __device__ constexpr int ring_stages()
 {
-    return is_f64<T>() ? 3 : 4;
+    return (is_f64<T>() || XT) ? 3 : 4;  // the xt accumulators take the fourth FP32 stage's room
 }
 
 // Dynamic shared memory: [tile ring: stages x 4 arrays x TILE T][coarse
 // sigma_max: kCoarse T][E pairs: ng_max T2][deposition: 3 x ng_max u32]
-// [tile prefix: nd+1 int].
-template <typename T>
+// [tile prefix: nd+1 int][xt variant, from the next 16-byte boundary: sum
+// w v_c,x and sum w eps_c, ng_max T each].
+template <typename T, bool XT>
 __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eepf_max)
 {
-    return (size_t)ring_stages<T>() * 4 * kThreads * VecOf<T>::n * sizeof(T) + (size_t)kCoarse * sizeof(T) +
-           (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 12 + (size_t)(nd + 1) * 4 + 0 * (size_t)eepf_max;
+    return (size_t)ring_stages<T, XT>() * 4 * kThreads * VecOf<T>::n * sizeof(T) + (size_t)kCoarse * sizeof(T) +
+           (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 12 + (size_t)(nd + 1) * 4 +
+           (XT ? 16 + (size_t)ng_max * 2 * sizeof(T) : 0) + 0 * (size_t)eepf_max;
 }
 
 // NC: the variant that also runs the null-collision method for the
 // discharges that ask for it (launched only when one does; the direct-test
 // variant carries none of its code).
-template <typename T, int SP, bool NC>
+// XT: the variant that also accumulates the xt diagnostics of the measured
+// steps (launched only for measured steps of a simulation that keeps them).
+template <typename T, int SP, bool NC, bool XT>
 __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BLOCKS)
     k_push(const DischargeDev *__restrict__ DD, int nd, int ng_max, int eepf_max, int measure)
 {
@@ -745,7 +755,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     using T2 = typename VecOf<T>::pair;
     constexpr int VEC = VecOf<T>::n;  // slots per thread: one Philox test block
     constexpr int TILE = kThreads * VEC;
-    constexpr int S = ring_stages<T>();
+    constexpr int S = ring_stages<T, XT>();
     constexpr int kWarps = kThreads / 32;
     static_assert(kWarpQueue >= 2 * 32 * VEC, "a warp queue takes at least two tiles of colliders");
     extern __shared__ __align__(128) unsigned char smem[];
@@ -757,6 +767,10 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     acc.lo = acc.cnt + ng_max;
     acc.hi = acc.lo + ng_max;
     int *sPre = reinterpret_cast<int *>(acc.hi + ng_max);
+    // xt variant: sum w v_c,x and sum w eps_c of the block, per grid point, on a
+    // 16-byte boundary after the prefix (whose end is 4-byte aligned only)
+    T *sXv = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(sPre + nd + 1) + 15) & ~(uintptr_t)15);
+    T *sXe = sXv + ng_max;
     (void)eepf_max;
     __shared__ unsigned int sCnt[EDUPIC_N_COUNTERS];
     __shared__ int sW[33];
@@ -825,6 +839,8 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     bool eepf_on = false;
     bool nullc = false;  // null-collision method for the current discharge
     T pstar = 0;         // its P*
+    int xcol = -1;       // xt time bin of this step for the current discharge (-1: none)
+    T e_of_v2 = 0;       // energy in eV of v^2 (xt variant)
 
     // execute the collisions queued by this warp (the 32 lanes of the warp;
     // the particles were stored by lanes of the same warp, ordered by the
@@ -836,7 +852,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         const RngKey key{s_lo, s_hi, k0, k1};
         for (int i = lane; i < qn; i += 32) {
             if (SP == 0)
-                electron_collision<T>(*D, sQueue[warp][i], key, idx_scale, cs_n, inv_dx, acc, sCnt);
+                electron_collision<T>(*D, sQueue[warp][i], key, idx_scale, cs_n, inv_dx, acc, XT ? xcol : -1, sCnt);
             else
                 ion_collision<T>(*D, sQueue[warp][i], key, idx_scale, cs_n, sCnt);
         }
@@ -853,10 +869,20 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             const unsigned long long q = ((unsigned long long)acc.cnt[p] << 32) - dep_sum(acc, p) +
                                          (p > 0 ? dep_sum(acc, p - 1) : 0ull);
             if (q) atomicAdd(reinterpret_cast<unsigned long long *>(accq + p), q);
+            if constexpr (XT) {
+                if (xcol >= 0) {
+                    const size_t j = (size_t)p * D->nxt + xcol;
+                    if (sXv[p] != (T)0) atomicAdd(D->xt_v[SP] + j, (double)sXv[p]);
+                    if (sXe[p] != (T)0) atomicAdd(D->xt_en[SP] + j, (double)sXe[p]);
+                }
+            }
         }
         if (!clear) return;
         __syncthreads();
-        for (int p = tid; p < ng; p += blockDim.x) acc.cnt[p] = acc.lo[p] = acc.hi[p] = 0u;
+        for (int p = tid; p < ng; p += blockDim.x) {
+            acc.cnt[p] = acc.lo[p] = acc.hi[p] = 0u;
+            if constexpr (XT) sXv[p] = sXe[p] = (T)0;
+        }
         __syncthreads();
     };
 
@@ -962,10 +988,18 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
                 nullc = ((D->null_coll >> SP) & 1) != 0;
                 pstar = is_f64<T>() ? (T)D->p_star[SP] : (T)D->p_starf[SP];
             }
+            if constexpr (XT) {
+                xcol = (measure && D->nxt > 0) ? (int)((long long)(s % (unsigned long long)D->nt) / D->nbin) : -1;
+                if constexpr (is_f64<T>())
+                    e_of_v2 = (SP == 0 ? D->half_me : D->half_mar) / EDUPIC_QE;
+                else
+                    e_of_v2 = SP == 0 ? D->e_of_v2_ef : D->e_of_v2_if;
+            }
             const T *ef = reinterpret_cast<const T *>(D->ef_t);
             for (int p = tid; p < ng; p += blockDim.x) {
                 sE2[p] = T2{ef[p], p + 1 < ng ? ef[p + 1] : (T)0};
                 acc.cnt[p] = acc.lo[p] = acc.hi[p] = 0u;
+                if constexpr (XT) sXv[p] = sXe[p] = (T)0;
             }
             since_flush = 0;
             __syncthreads();
@@ -1027,6 +1061,18 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             if (measure && live) pw += e_x * (vx + vxn);
             if (SP == 0 && eepf_on && live && x >= lo && x <= hi)
                 eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e]);
+            if constexpr (XT) {
+                // xt sums at x(t) with the time-centred velocity, weighted like the deposition
+                if (xcol >= 0 && live) {
+                    const T vc = (T)0.5 * (vx + vxn);
+                    const T en = e_of_v2 * (vc * vc + vya[e] * vya[e] + vza[e] * vza[e]);
+                    const T w1 = (T)(p + 1) - c0, w2 = c0 - (T)p;
+                    atomicAdd(sXv + p, w1 * vc);
+                    atomicAdd(sXv + p + 1, w2 * vc);
+                    atomicAdd(sXe + p, w1 * en);
+                    atomicAdd(sXe + p + 1, w2 * en);
+                }
+            }
             const T xn = x + vxn * dt;
             xa[e] = live ? xn : x;
             vxa[e] = live ? vxn : vx;
@@ -1497,8 +1543,27 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDe
         }
     } else {
         // (B) density swap, diagnostics, field of the next step
+        const int gb = threadIdx.x - kGroupA;
+        if (measure && D.nxt > 0) {
+            // xt sums of the grid quantities of this step, before the swap
+            const int b = (int)((C->step % D.nt) / D.nbin);
+            for (int p = gb; p < D.ng; p += kGroupB) {
+                const size_t j = (size_t)p * D.nxt + b;
+                D.xt_f[j] += (double)D.f_cur[p];
+                D.xt_qe[j] += (double)D.q_e[p];
+                D.xt_qi[j] += (double)D.q_i[p];
+                if (ion_step) D.xt_cnti[j] += (double)D.q_i[p];
+            }
+            if (gb == 0) {
+                D.xt_V[b] += D.fs->V;
+                D.xt_d0[b] += D.fs->d0;
+                D.xt_steps[b] += 1;
+                if (ion_step) D.xt_steps[D.nxt + b] += 1;
+            }
+            bar_sync(2, kGroupB);
+        }
         const long long tc = next % D.nt;
-        solve_field<T, kGroupB>(D, tc, true, (tc % D.nsub) == 0, measure != 0, false, threadIdx.x - kGroupA, 2, sF);
+        solve_field<T, kGroupB>(D, tc, true, (tc % D.nsub) == 0, measure != 0, false, gb, 2, sF);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -6,32 +6,30 @@
 namespace edupic {
 
 template <typename T>
-size_t Launch<T>::push_smem(int nd, int ng_max, int eepf_max)
+size_t Launch<T>::push_smem(int nd, int ng_max, int eepf_max, int xt)
 {
-    return push_smem_bytes<T>(nd, ng_max, eepf_max);
+    return xt ? push_smem_bytes<T, true>(nd, ng_max, eepf_max) : push_smem_bytes<T, false>(nd, ng_max, eepf_max);
+}
+
+// Resident blocks per SM of the particle kernel of one species: the smaller of
+// its direct-test and null-collision instantiations (one grid serves both),
+// for the plain (xt = 0) or the xt-accumulating pair.
+template <typename T, int SP, bool XT>
+int blocks_per_sm(size_t smem)
+{
+    int a = 0, b = 0;
+    cudaFuncSetAttribute(k_push<T, SP, false, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(k_push<T, SP, true, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_push<T, SP, false, XT>, kThreads, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_push<T, SP, true, XT>, kThreads, smem);
+    return e == cudaSuccess ? (a < b ? a : b) : -1;
 }
 
 template <typename T>
-int Launch<T>::push_blocks_per_sm(int species, size_t smem)
+int Launch<T>::push_blocks_per_sm(int species, size_t smem, int xt)
 {
-    int nb = 0;
-    cudaError_t e;
-    int nb_nc = 0;
-    if (species == 0) {
-        cudaFuncSetAttribute(k_push<T, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        cudaFuncSetAttribute(k_push<T, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<T, 0, false>, kThreads, smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_nc, k_push<T, 0, true>, kThreads, smem);
-    } else {
-        cudaFuncSetAttribute(k_push<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        cudaFuncSetAttribute(k_push<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<T, 1, false>, kThreads, smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_nc, k_push<T, 1, true>, kThreads, smem);
-    }
-    // one grid serves both variants: the smaller resident limit
-    return e == cudaSuccess ? (nb < nb_nc ? nb : nb_nc) : -1;
+    if (species == 0) return xt ? blocks_per_sm<T, 0, true>(smem) : blocks_per_sm<T, 0, false>(smem);
+    return xt ? blocks_per_sm<T, 1, true>(smem) : blocks_per_sm<T, 1, false>(smem);
 }
 
 template <typename T>
@@ -77,19 +75,27 @@ static cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cuda
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+template <typename T, int SP, bool XT>
+cudaError_t push_variant(const DischargeDev *dd, int nd, int measure, int grid, int ng_max, int eb, int null_any,
+                         size_t smem, cudaStream_t st)
+{
+    return null_any ? launch_pdl(k_push<T, SP, true, XT>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, eb,
+                                 measure)
+                    : launch_pdl(k_push<T, SP, false, XT>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, eb,
+                                 measure);
+}
+
 template <typename T>
 cudaError_t Launch<T>::push(const DischargeDev *dd, int nd, int species, int measure, int grid, int ng_max,
-                            int eepf_max, int null_any, cudaStream_t st)
+                            int eepf_max, int null_any, int xt, cudaStream_t st)
 {
     const int eb = species == 0 && measure ? eepf_max : 0;
-    const size_t smem = push_smem(nd, ng_max, eb);
+    const size_t smem = push_smem(nd, ng_max, eb, xt);
     if (species == 0)
-        return null_any ? launch_pdl(k_push<T, 0, true>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, eb,
-                                     measure)
-                        : launch_pdl(k_push<T, 0, false>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, eb,
-                                     measure);
-    return null_any ? launch_pdl(k_push<T, 1, true>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, 0, measure)
-                    : launch_pdl(k_push<T, 1, false>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, 0, measure);
+        return xt ? push_variant<T, 0, true>(dd, nd, measure, grid, ng_max, eb, null_any, smem, st)
+                  : push_variant<T, 0, false>(dd, nd, measure, grid, ng_max, eb, null_any, smem, st);
+    return xt ? push_variant<T, 1, true>(dd, nd, measure, grid, ng_max, 0, null_any, smem, st)
+              : push_variant<T, 1, false>(dd, nd, measure, grid, ng_max, 0, null_any, smem, st);
 }
 
 template <typename T>

@@ -186,6 +186,7 @@ int check_request(const edupic_server *V, const edupic_params *p, int n_cycles)
     if (rc) return rc;
     if (p->n_grid > V->cfg.max_grid || p->eepf_bins > V->cfg.max_eepf_bins) return EDUPIC_EINVAL;
     if (p->ion_subcycle != V->cfg.ion_subcycle || p->cs_entries != V->cfg.cs_entries) return EDUPIC_EINVAL;
+    if (p->xt_bins != 0) return EDUPIC_EINVAL;  // xt maps are read from simulation objects only
     return EDUPIC_OK;
 }
 

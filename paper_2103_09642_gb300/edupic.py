@@ -22,6 +22,7 @@ FP64, FP32 = 0, 1
 ELECTRONS, IONS = 0, 1
 MAX_HARMONICS = 4
 N_COUNTERS = 19
+XT_NAMES = ("pot", "efield", "ne", "ni", "je", "ji", "powere", "poweri", "meanee", "meanei", "ioniz")
 STEP_EVENTS = 65536
 COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela", "coll_e_exc",
                  "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped",
@@ -52,7 +53,7 @@ class Params(ctypes.Structure):
         ("e_exc_ev", ctypes.c_double), ("e_ion_ev", ctypes.c_double),
         ("cs_entries", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("see_gamma", ctypes.c_double * 2), ("refl_eta", ctypes.c_double * 2), ("see_te_ev", ctypes.c_double),
-        ("null_collision", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+        ("null_collision", ctypes.c_int32), ("xt_bins", ctypes.c_int32),
     ]
 
 
@@ -75,6 +76,7 @@ def to_params(d: Discharge, cs_entries: int) -> Params:
         p.see_gamma[k], p.refl_eta[k] = d.see_gamma[k], d.refl_eta[k]
     p.see_te_ev = d.see_te_ev
     p.null_collision = int(d.null_collision)
+    p.xt_bins = int(d.xt_bins)
     return p
 
 
@@ -134,6 +136,7 @@ def load_library(path: str = LIB_PATH):
         "edupic_check_accuracy": ([_VP, ctypes.c_int, ctypes.POINTER(Accuracy)]),
         "edupic_get_power": ([_VP, ctypes.c_int, _D]),
         "edupic_set_bias": ([_VP, ctypes.c_int, ctypes.c_double]),
+        "edupic_get_xt": ([_VP, ctypes.c_int, ctypes.c_int, _D]),
         "edupic_get_bias": ([_VP, ctypes.c_int, _D]),
         "edupic_self_bias_step": ([_VP, ctypes.c_int64, ctypes.c_int, _D, _D]),
         "edupic_get_counts": ([_VP, ctypes.c_int, _Q, _Q, _Q]),
@@ -341,6 +344,15 @@ class Simulation:
         out = np.zeros(2)
         _ck(self.L.edupic_get_power(self._h, d, _ptr(out)), "get_power")
         return {"electrons": float(out[0]), "ions": float(out[1])}
+
+    def xt(self, d: int, quantity) -> np.ndarray:
+        """Spatio-temporal map [n_grid, xt_bins] (Sec. 3.5) of a quantity
+        named in XT_NAMES (or its index)."""
+        q = XT_NAMES.index(quantity) if isinstance(quantity, str) else int(quantity)
+        dd = self.discharges[d]
+        out = np.zeros((dd.n_grid, dd.xt_bins))
+        _ck(self.L.edupic_get_xt(self._h, d, q, _ptr(out)), "get_xt")
+        return out
 
     def set_bias(self, d: int, v_bias: float) -> None:
         """DC self-bias voltage added at the powered electrode (Sec. 5)."""

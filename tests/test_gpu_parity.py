@@ -352,6 +352,62 @@ def test_self_bias_electrical_asymmetry_sign():
     assert abs(v_sym) < 0.5 * abs(v_eae), (v_sym, v_eae)
 
 
+# --------------------------------------------------------------- xt diagnostics (Sec. 3.5)
+def test_xt_maps_fp64_against_the_oracle():
+    """All eleven xt maps after 160 measured steps (bins of 20 steps; a bin
+    boundary inside the run and an ion step in every bin), against the
+    oracle's maps from the plain per-particle sums."""
+    d, e, i = wl.reference_steady(seed=15, n=30_000)
+    d = d.replace(harmonics=((13.56e6, 400.0),), xt_bins=200)
+    sim, ref = _pair(d, e, i)
+    sim.step(30)
+    ref.step(30)
+    sim.step(160, measure=True)
+    ref.step(160, measure=True)
+    assert sim.counters(0) == ref.counters()
+    for k, name in enumerate(ed.XT_NAMES):
+        g, o = sim.xt(0, name), ref.xt(k)
+        scale = np.abs(o).max()
+        assert scale > 0 or name == "ioniz", name
+        # sums of the same terms in another order (FP64), fixed-point counts
+        # against FP64 weights for the mean energies
+        assert np.abs(g - o).max() <= 1e-9 * max(scale, 1e-300), (name, np.abs(g - o).max(), scale)
+    assert (sim.xt(0, "ne")[:, 11:] == 0).all()  # bins after the run
+
+
+@pytest.mark.parametrize("precision", [ed.FP64, ed.FP32])
+def test_xt_diagnostics_leave_the_run_unchanged(precision):
+    """The accumulating kernel instantiation changes no particle, counter or
+    time-averaged diagnostic."""
+    d, e, i = wl.reference_steady(seed=16, n=20_000)
+    a = _run([d], [(e, i)], precision, 60, measure=True)
+    b = _run([d.replace(xt_bins=400)], [(e, i)], precision, 60, measure=True)
+    assert a[2] == b[2]
+    for sp in (0, 1):
+        for c in range(4):
+            assert np.array_equal(a[0][0][sp][c], b[0][0][sp][c])
+    for k in ("n_e", "n_i", "phi", "eepf_counts", "ifed_pow_counts", "ifed_gnd_counts"):
+        assert np.array_equal(a[1][0][k], b[1][0][k]), k
+
+
+def test_xt_fp32_consistency():
+    """FP32 particles: the bins average to the time averages, the power map
+    is j E, and the maps have the discharge's signs."""
+    d, e, i = wl.reference_steady(seed=17, n=40_000)
+    d = d.replace(xt_bins=100)  # 40 steps per bin
+    sim = ed.simulation_for([d], ed.FP32, sigma=(SE, SI), de_ev=DE, particles=[(e, i)])
+    sim.run_cycles(1, measure=True)
+    diag = sim.diagnostics(0)
+    for key, name in (("n_e", "ne"), ("n_i", "ni"), ("phi", "pot")):
+        m = sim.xt(0, name).mean(axis=1)
+        assert np.abs(m - diag[key]).max() <= 1e-9 * np.abs(diag[key]).max(), key
+    je, ef = sim.xt(0, "je"), sim.xt(0, "efield")
+    assert np.array_equal(sim.xt(0, "powere"), je * ef)
+    assert (sim.xt(0, "meanee") >= 0).all() and sim.xt(0, "meanee").max() > 1.0
+    assert (sim.xt(0, "ioniz") >= 0).all()
+    sim.close()
+
+
 # --------------------------------------------------------------- graph, batch, checkpoint
 def _run(ds, parts, precision, steps, graphs=True, measure=False, grid=0):
     sim = ed.simulation_for(ds, precision, sigma=(SE, SI), de_ev=DE, particles=parts)

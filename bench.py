@@ -315,8 +315,20 @@ def leg_plain(args, peak, peak_kind, flush) -> dict:
             tot_t += time.perf_counter() - t0
             tot_ps += (cb["push_e"] - ca["push_e"]) + (cb["push_i"] - ca["push_i"])
     sim2.close()
+    # the same cycle with the xt diagnostics (N_XT = 200) accumulated
+    simx = ed.simulation_for([d.replace(xt_bins=200)], ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV,
+                             particles=[(e, i)])
+    simx.run_cycles(1, measure=True)
+    simx.synchronize()
+    cx0 = simx.counters(0)
+    msx = _timed(simx.stream, flush, steps, lambda: simx.run_cycles(1, measure=True))
+    cx1 = simx.counters(0)
+    psx = (cx1["push_e"] - cx0["push_e"]) + (cx1["push_i"] - cx0["push_i"])
+    simx.close()
     return {"workload": "reference argon discharge (Table 2 settings, N_G=400, N_T=4000, N_SUB=20) in a "
                         "steady-shape state, weight 1.4e4, one RF cycle per bench step",
+            "with_xt_diagnostics": {"value": psx / (msx / 1000.0), "unit": UNIT, "xt_bins": 200,
+                                    "ms_per_rf_cycle": msx / steps},
             "particles_e": int(n_e), "particles_i": int(n_i), "value": ps / (ms / 1000.0), "unit": UNIT,
             "ms_per_rf_cycle": ms / steps, "us_per_time_step": 1000.0 * ms / (steps * d.steps_per_cycle),
             "steps": steps, "push_grid": grid, "roofline": roof,

@@ -7,8 +7,11 @@
 #include <atomic>
 #include <climits>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
@@ -520,22 +523,94 @@ int upload_drive(edupic_sim *S, int d)
     return cuda_status(e);
 }
 
-// Run f(lo, hi) over [0, n) on up to 16 host threads (ranges of at least
-// 256 Ki elements; small n runs on the calling thread).
+// A fixed team of host threads for the particle conversions, created on first
+// use (up to 16 with the calling thread) and kept for the process.  One run
+// at a time; run(nt, f) calls f(t) for t = 0..nt-1, t = 0 on the caller.
+class HostTeam {
+public:
+    static HostTeam &get()
+    {
+        static HostTeam team;
+        return team;
+    }
+    int size() const { return (int)workers_.size() + 1; }
+    void run(int nt, const std::function<void(int)> &f)
+    {
+        std::lock_guard<std::mutex> serial(run_mutex_);
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            job_ = &f;
+            n_ = nt;
+            left_ = nt - 1;
+            ++gen_;
+        }
+        cv_.notify_all();
+        f(0);
+        std::unique_lock<std::mutex> lk(m_);
+        done_.wait(lk, [&] { return left_ == 0; });
+        job_ = nullptr;
+    }
+    ~HostTeam()
+    {
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            stop_ = true;
+            ++gen_;
+        }
+        cv_.notify_all();
+        for (auto &w : workers_) w.join();
+    }
+
+private:
+    HostTeam()
+    {
+        const int hw = std::max(1, (int)std::thread::hardware_concurrency());
+        for (int i = 1; i < std::min(hw, 16); ++i) workers_.emplace_back([this, i] { loop(i); });
+    }
+    void loop(int id)
+    {
+        unsigned long long seen = 0;
+        for (;;) {
+            const std::function<void(int)> *f;
+            int n;
+            {
+                std::unique_lock<std::mutex> lk(m_);
+                cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+                if (stop_) return;
+                seen = gen_;
+                f = job_;
+                n = n_;
+            }
+            if (id < n) {  // a run does not end before its workers report, so none is missed
+                (*f)(id);
+                std::lock_guard<std::mutex> lk(m_);
+                if (--left_ == 0) done_.notify_one();
+            }
+        }
+    }
+    std::vector<std::thread> workers_;
+    std::mutex run_mutex_, m_;
+    std::condition_variable cv_, done_;
+    const std::function<void(int)> *job_ = nullptr;
+    int n_ = 0, left_ = 0;
+    unsigned long long gen_ = 0;
+    bool stop_ = false;
+};
+
+// Run f(lo, hi) over [0, n) on the host team (ranges of at least 64 Ki
+// elements; small n runs on the calling thread).
 template <typename F>
 void parallel_ranges(int64_t n, F f)
 {
-    constexpr int64_t kGrain = 1 << 18;
-    const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
-    const int64_t nt = std::min<int64_t>({hw, 16, (n + kGrain - 1) / kGrain});
-    if (nt <= 1) {
+    constexpr int64_t kGrain = 1 << 16;
+    const int64_t chunks = (n + kGrain - 1) / kGrain;
+    if (chunks <= 1) {
         f((int64_t)0, n);
         return;
     }
-    std::vector<std::thread> ts;
-    ts.reserve((size_t)nt);
-    for (int64_t t = 0; t < nt; ++t) ts.emplace_back(f, n * t / nt, n * (t + 1) / nt);
-    for (auto &t : ts) t.join();
+    HostTeam &team = HostTeam::get();
+    const int nt = (int)std::min<int64_t>(team.size(), chunks);
+    team.run(nt, [&](int t) { f(n * t / nt, n * (t + 1) / nt); });
 }
 
 // Page-locked host staging buffer of the object (grown on demand, freed with it).
@@ -552,39 +627,38 @@ void *pinned_reserve(edupic_sim *S, size_t bytes)
     return p;
 }
 
-// x, vx, vy, vz checked (0 <= x <= L, finite velocities) and converted to
-// T in one parallel pass into the pinned buffer, then copied to the device
-// as four DMA transfers and one synchronisation.  EDUPIC_EINVAL (nothing
-// copied) if a particle fails the check.
+// x, vx, vy, vz checked (0 <= x <= L, finite velocities; a value v is finite
+// when v - v == 0) and converted to T in one parallel pass into the pinned
+// stage, arrays one after another.  Loops without branches, so that they
+// vectorise.
 template <typename T>
-int upload_particles(edupic_sim *S, int d, int sp, int64_t n, const double *const src[4])
+int convert_stage(edupic_sim *S, int d, int64_t n, const double *const src[4], T *stage)
 {
-    void *dst[4] = {S->desc[d].x[sp], S->desc[d].vx[sp], S->desc[d].vy[sp], S->desc[d].vz[sp]};
-    T *stage = static_cast<T *>(pinned_reserve(S, 4 * sizeof(T) * (size_t)n));
-    if (!stage) return EDUPIC_ENOMEM;
     const double L = S->params[d].gap_m;
-    std::atomic<bool> bad{false};
+    std::atomic<int> bad{0};
     parallel_ranges(n, [&](int64_t lo, int64_t hi) {
-        T *o0 = stage, *o1 = stage + (size_t)n, *o2 = stage + 2 * (size_t)n, *o3 = stage + 3 * (size_t)n;
-        const double *x = src[0], *vx = src[1], *vy = src[2], *vz = src[3];
-        bool ok = true;
-        for (int64_t j = lo; j < hi; ++j) {
-            ok = ok && (x[j] >= 0.0 && x[j] <= L) && std::isfinite(vx[j]) && std::isfinite(vy[j]) &&
-                 std::isfinite(vz[j]);
-            o0[j] = (T)x[j];
-            o1[j] = (T)vx[j];
-            o2[j] = (T)vy[j];
-            o3[j] = (T)vz[j];
+        int b = 0;
+        {
+            const double *x = src[0];
+            T *o = stage;
+            for (int64_t j = lo; j < hi; ++j) {
+                const double v = x[j];
+                o[j] = (T)v;
+                b |= (int)!(v >= 0.0) | (int)!(v <= L);
+            }
         }
-        if (!ok) bad.store(true, std::memory_order_relaxed);
+        for (int c = 1; c < 4; ++c) {
+            const double *v = src[c];
+            T *o = stage + (size_t)c * (size_t)n;
+            for (int64_t j = lo; j < hi; ++j) {
+                const double a = v[j];
+                o[j] = (T)a;
+                b |= (int)!(a - a == 0.0);
+            }
+        }
+        if (b) bad.store(1, std::memory_order_relaxed);
     });
-    if (bad.load()) return EDUPIC_EINVAL;
-    cudaError_t e = cudaSuccess;
-    for (int c = 0; c < 4 && e == cudaSuccess; ++c)
-        e = cudaMemcpyAsync(dst[c], stage + (size_t)c * (size_t)n, sizeof(T) * (size_t)n, cudaMemcpyHostToDevice,
-                            S->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);  // the stage is reused by the next upload
-    return cuda_status(e);
+    return bad.load() ? EDUPIC_EINVAL : EDUPIC_OK;
 }
 
 template <typename T>
@@ -601,31 +675,44 @@ int download_particles(edupic_sim *S, int d, int sp, int64_t n, double *const ds
     return EDUPIC_OK;
 }
 
-// Recompute the densities of one species and the field of the current step.
-int refresh_species(edupic_sim *S, int d, int sp)
+// Replace the particles of species sp of discharge d (Algorithm 1's
+// initialisation, or a reload): check and convert the host arrays into the
+// pinned stage, copy them and the count, and form the densities and the field
+// of the current step again.  One synchronisation, as the stage is reused by
+// the next load.
+int load_species(edupic_sim *S, int d, int sp, int64_t n, const double *const src[4])
 {
+    const size_t body = align_up(4 * S->elem * (size_t)n, 16);
+    unsigned char *stage = static_cast<unsigned char *>(pinned_reserve(S, body + 16));
+    if (!stage) return EDUPIC_ENOMEM;
     const DischargeDev &D = S->desc[d];
-    const size_t ng = (size_t)S->params[d].n_grid;
-    cudaError_t e = cudaMemsetAsync(sp == 0 ? D.q_e : D.q_i, 0, ng * 8, S->stream);
-    if (e == cudaSuccess && sp == 1) e = cudaMemsetAsync(D.acc_i, 0, ng * 8, S->stream);
-    if (e != cudaSuccess) return EDUPIC_ECUDA;
-    const int also_acc = (sp == 1 && S->phase != 0) ? 1 : 0;
-    if (S->precision == EDUPIC_FP32) {
-        e = Launch<float>::deposit(S->d_desc, S->nd, d, sp, also_acc, S->stream);
-        if (e == cudaSuccess) e = Launch<float>::fields(S->d_desc, S->nd, d, S->stream);
-    } else {
-        e = Launch<double>::deposit(S->d_desc, S->nd, d, sp, also_acc, S->stream);
-        if (e == cudaSuccess) e = Launch<double>::fields(S->d_desc, S->nd, d, S->stream);
+    void *dst[4] = {D.x[sp], D.vx[sp], D.vy[sp], D.vz[sp]};
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        const int rc = S->precision == EDUPIC_FP32
+                           ? convert_stage<float>(S, d, n, src, reinterpret_cast<float *>(stage))
+                           : convert_stage<double>(S, d, n, src, reinterpret_cast<double *>(stage));
+        if (rc) return rc;
+        for (int c = 0; c < 4 && e == cudaSuccess; ++c)
+            e = cudaMemcpyAsync(dst[c], stage + (size_t)c * S->elem * (size_t)n, S->elem * (size_t)n,
+                                cudaMemcpyHostToDevice, S->stream);
     }
+    long long *count = reinterpret_cast<long long *>(stage + body);
+    *count = n;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&S->ctrl(d)->n[sp], count, sizeof(long long), cudaMemcpyHostToDevice, S->stream);
+    const size_t ng = (size_t)S->params[d].n_grid;
+    if (e == cudaSuccess) e = cudaMemsetAsync(sp == 0 ? D.q_e : D.q_i, 0, ng * 8, S->stream);
+    if (e == cudaSuccess && sp == 1) e = cudaMemsetAsync(D.acc_i, 0, ng * 8, S->stream);
+    const int also_acc = (sp == 1 && S->phase != 0) ? 1 : 0;
+    if (e == cudaSuccess)
+        e = S->precision == EDUPIC_FP32 ? Launch<float>::deposit(S->d_desc, S->nd, d, sp, also_acc, S->stream)
+                                        : Launch<double>::deposit(S->d_desc, S->nd, d, sp, also_acc, S->stream);
+    if (e == cudaSuccess)
+        e = S->precision == EDUPIC_FP32 ? Launch<float>::fields(S->d_desc, S->nd, d, S->stream)
+                                        : Launch<double>::fields(S->d_desc, S->nd, d, S->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
     return cuda_status(e);
-}
-
-int upload_species(edupic_sim *S, int d, int sp, int64_t n, const double *const src[4])
-{
-    if (n == 0) return EDUPIC_OK;
-    return S->precision == EDUPIC_FP32 ? upload_particles<float>(S, d, sp, n, src)
-                                       : upload_particles<double>(S, d, sp, n, src);
 }
 
 bool valid_d(const edupic_sim *S, int d) { return S && d >= 0 && d < S->nd; }
@@ -782,13 +869,7 @@ int edupic_load_particles(edupic_sim *S, int d, int species, int64_t n, const do
     if (n > (species == 0 ? S->params[d].capacity_e : S->params[d].capacity_i)) return EDUPIC_ECAPACITY;
     if (n > 0 && (!x || !vx || !vy || !vz)) return EDUPIC_EINVAL;
     const double *src[4] = {x, vx, vy, vz};  // checked while they are converted
-    int rc = upload_species(S, d, species, n, src);
-    if (rc) return rc;
-    long long nn = n;
-    cudaError_t e = cudaMemcpyAsync(&S->ctrl(d)->n[species], &nn, sizeof(nn), cudaMemcpyHostToDevice, S->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-    if (e != cudaSuccess) return EDUPIC_ECUDA;
-    return refresh_species(S, d, species);
+    return load_species(S, d, species, n, src);
 }
 
 int edupic_step(edupic_sim *S, int64_t n_steps, int measure)

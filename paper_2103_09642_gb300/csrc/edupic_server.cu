@@ -216,13 +216,7 @@ int open_slot(edupic_server *V, uint64_t ticket, int d)
     for (int sp = 0; sp < 2 && rc == EDUPIC_OK; ++sp) {
         const double *src[4] = {r.part[sp][0].data(), r.part[sp][1].data(), r.part[sp][2].data(),
                                 r.part[sp][3].data()};
-        rc = upload_species(S, d, sp, r.n0[sp], src);
-        if (rc == EDUPIC_OK) {
-            const long long nn = r.n0[sp];
-            rc = cuda_status(cudaMemcpyAsync(&S->ctrl(d)->n[sp], &nn, sizeof(nn), cudaMemcpyHostToDevice, S->stream));
-            if (rc == EDUPIC_OK) rc = cuda_status(cudaStreamSynchronize(S->stream));
-        }
-        if (rc == EDUPIC_OK) rc = refresh_species(S, d, sp);
+        rc = load_species(S, d, sp, r.n0[sp], src);
     }
     if (rc) {
         S->desc[d] = idle_desc(S, d);

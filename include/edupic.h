@@ -208,6 +208,8 @@ int edupic_profile_steps(edupic_sim *sim, int64_t n_steps, int measure, double o
 /* Use (1, default) or bypass (0) the CUDA graph that replays one ion
  * subcycle of kernel launches.  Results are identical either way. */
 int edupic_set_graphs(edupic_sim *sim, int enable);
+/* Writes 1 if graph replay is in use (as set, or as edupic_autotune chose). */
+int edupic_get_graphs(edupic_sim *sim, int *enabled);
 
 /* Launch shape of the particle kernels (no counterpart in the paper, whose
  * particle loops are serial).  The particle kernel runs a persistent grid

@@ -1064,6 +1064,13 @@ int edupic_set_graphs(edupic_sim *S, int enable)
     return EDUPIC_OK;
 }
 
+int edupic_get_graphs(edupic_sim *S, int *enabled)
+{
+    if (!S || !enabled) return EDUPIC_EINVAL;
+    *enabled = S->graphs ? 1 : 0;
+    return EDUPIC_OK;
+}
+
 int edupic_get_counts(edupic_sim *S, int d, int64_t *n_e, int64_t *n_i, int64_t *step)
 {
     if (!valid_d(S, d)) return EDUPIC_EINVAL;

@@ -136,6 +136,7 @@ def load_library(path: str = LIB_PATH):
         "edupic_check_accuracy": ([_VP, ctypes.c_int, ctypes.POINTER(Accuracy)]),
         "edupic_get_power": ([_VP, ctypes.c_int, _D]),
         "edupic_set_bias": ([_VP, ctypes.c_int, ctypes.c_double]),
+        "edupic_get_graphs": ([_VP, ctypes.POINTER(ctypes.c_int)]),
         "edupic_get_xt": ([_VP, ctypes.c_int, ctypes.c_int, _D]),
         "edupic_get_bias": ([_VP, ctypes.c_int, _D]),
         "edupic_self_bias_step": ([_VP, ctypes.c_int64, ctypes.c_int, _D, _D]),
@@ -268,6 +269,11 @@ class Simulation:
 
     def set_graphs(self, enable: bool):
         _ck(self.L.edupic_set_graphs(self._h, 1 if enable else 0), "set_graphs")
+
+    def graphs(self) -> bool:
+        v = ctypes.c_int(0)
+        _ck(self.L.edupic_get_graphs(self._h, ctypes.byref(v)), "get_graphs")
+        return bool(v.value)
 
     def set_push_grid(self, species: int, blocks: int):
         _ck(self.L.edupic_set_push_grid(self._h, species, int(blocks)), "set_push_grid")

@@ -491,8 +491,10 @@ def run_ours(args):
     for _ in range(args.warmup):
         sim.step(BATCH_STEPS, measure=True)
     sim.synchronize()
-    tot = lambda: sum(sim.counters(k)["push_e"] + sim.counters(k)["push_i"] for k in range(nd))
-    c0 = tot()
+    split = lambda: [sum(sim.counters(k)[key] for k in range(nd)) for key in ("push_e", "push_i")]
+    tot = lambda: sum(split())
+    s0 = split()
+    c0 = sum(s0)
     _log("timed steps")
     clocks = Clocks(local)
     barrier()
@@ -500,9 +502,13 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     sim.synchronize()
-    ps = tot() - c0
+    s1 = split()
+    ps = sum(s1) - c0
     ms_max, ps_all = reduce_over_ranks(ms_total, ps, ws, "cuda")
     value = ps_all / (ms_max / 1000.0)
+    # electron pushes (every step) and ion pushes (ion steps), this rank, per second of its device time
+    pushes = {"electrons": (s1[0] - s0[0]) / (ms_total / 1000.0), "ions": (s1[1] - s0[1]) / (ms_total / 1000.0),
+              "unit": "particle-steps/s", "scope": "rank 0" if ws > 1 else "all"}
     n_e = sum(sim.counts(k)[0] for k in range(nd))
     n_i = sum(sim.counts(k)[1] for k in range(nd))
     _log("roofline")
@@ -574,6 +580,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}", "cross_sections": "stand-in set",
                        "push_grid": grid},
             "roofline": roof,
+            "pushes": pushes,
             "gpu_launches": int(args.steps * (2 * BATCH_STEPS + BATCH_STEPS // ds[0].ion_subcycle)),
             "clocks": clk,
         }

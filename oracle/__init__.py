@@ -105,6 +105,8 @@ def lib():
             L.orc_ifed_normalise.argtypes = [_Q, ctypes.c_int, ctypes.c_double, _D, _D]
             L.orc_get_derived.argtypes = [ctypes.c_void_p, _D]
             L.orc_set_bias.argtypes = [ctypes.c_void_p, ctypes.c_double]
+            L.orc_seed.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+            L.orc_seed.restype = ctypes.c_int
             L.orc_get_xt.argtypes = [ctypes.c_void_p, ctypes.c_int, _D]
             L.orc_get_xt.restype = ctypes.c_int
             L.orc_set_bias.restype = None
@@ -276,6 +278,11 @@ class Sim:
         a = [_f64(getattr(parts, k)) for k in ("x", "vx", "vy", "vz")]
         if lib().orc_load_particles(self._h, species, a[0].size, *[_p(v, ctypes.c_double) for v in a]):
             raise ValueError("oracle: bad particle load")
+
+    def seed(self, n: int) -> None:
+        """init(N_INIT) of Algorithm 1: n e- and n Ar+ at rest, uniform in the gap."""
+        if lib().orc_seed(self._h, ctypes.c_int64(int(n))):
+            raise ValueError("oracle: bad seed count")
 
     def step(self, n: int, measure: bool = False):
         rc = lib().orc_step(self._h, n, 1 if measure else 0)

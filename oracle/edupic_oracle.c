@@ -737,6 +737,27 @@ int orc_load_particles(orc_sim *s, int species, int64_t n, const double *x, cons
     return 0;
 }
 
+/* Initialisation of Algorithm 1, init(N_INIT): n electrons and n Ar+ at
+ * random positions in the gap with zero velocities.  Reading: particle k of
+ * species s sits at x = L R01 with R01 from block 9 of its counter (slot k,
+ * the current step), so that the seeding is reproducible in any order. */
+int orc_seed(orc_sim *s, int64_t n)
+{
+    if (n < 0 || n > s->p.capacity) return -1;
+    for (int species = 0; species < 2; ++species) {
+        orc_species *sp = &s->sp[species];
+        for (int64_t k = 0; k < n; ++k) {
+            double u[2];
+            draw_block(s->p.seed, k, s->step, species, 9, u);
+            sp->x[k] = s->p.gap_m * u[0];
+            sp->vx[k] = sp->vy[k] = sp->vz[k] = 0.0;
+        }
+        sp->n = n;
+        orc_deposit_fixed(sp->x, n, s->p.n_grid, s->inv_dx, species == 0 ? s->q_e : s->q_i);
+    }
+    return 0;
+}
+
 /* Steps (1)-(2) of the current step without advancing it: the densities and
  * the field that the next call of one_step() will use. */
 void orc_prepare_fields(orc_sim *s)

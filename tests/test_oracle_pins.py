@@ -733,3 +733,24 @@ def test_xt_ionisation_rate_integrates_to_the_events():
     steps[:10] = 20
     total = (rate * vol[:, None] * steps[None, :] * dv["dt_e"]).sum()
     assert total == pytest.approx(d.weight * events, rel=1e-12)
+
+
+# ------------------------------------------------------------------ init(N_INIT) of Algorithm 1
+def test_seed_uniform_at_rest():
+    # n electrons and n ions, uniform on (0, L) (KS test) and at rest; the
+    # deposited charge is n 2^32 per species; the two species are independent
+    from scipy import stats
+
+    d = wl.reference_discharge(capacity=50_000)
+    se, si = _tables(1000)
+    s = oracle.Sim(d, se, si, 1e-3)
+    s.seed(20_000)
+    assert s.count(0) == s.count(1) == 20_000
+    for sp in (0, 1):
+        x, vx, vy, vz = s.particles(sp)
+        assert (x >= 0).all() and (x < d.gap_m).all()
+        assert stats.kstest(x / d.gap_m, "uniform").pvalue > 1e-3
+        assert not vx.any() and not vy.any() and not vz.any()
+    f = s.fields()
+    assert int(f["q_e"].sum()) == int(f["q_i"].sum()) == 20_000 * 2 ** 32
+    assert not np.array_equal(s.particles(0)[0], s.particles(1)[0])

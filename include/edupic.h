@@ -180,6 +180,15 @@ int edupic_set_cross_sections(edupic_sim *sim, int species, int n_proc, int n_en
 int edupic_load_particles(edupic_sim *sim, int d, int species, int64_t n, const double *x, const double *vx,
                           const double *vy, const double *vz);
 
+/* init(N_INIT) of Algorithm 1: replace both species of discharge d by n_init
+ * electrons and n_init Ar+ ions at random positions in the gap with zero
+ * velocities, and form the densities and the field of the current step.
+ * Positions: x = L R01, R01 from block 9 of each particle's counter-based
+ * random numbers (slot, current step, species), so the state depends only on
+ * the seed and the step.  EDUPIC_ECAPACITY beyond either capacity.
+ * Synchronises the stream. */
+int edupic_seed(edupic_sim *sim, int d, int64_t n_init);
+
 /* ---------------------------------------------------------------- stepping */
 
 /* Enqueue n_steps PIC/MCC time steps (Sec. 2.1, Fig. 2) of every discharge.

@@ -701,6 +701,17 @@ int load_species(edupic_sim *S, int d, int sp, int64_t n, const double *const sr
     *count = n;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&S->ctrl(d)->n[sp], count, sizeof(long long), cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = enqueue_refresh(S, d, sp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    return cuda_status(e);
+}
+
+// Densities of species sp of discharge d from its particles, and the field
+// of the current step, queued on the stream.
+cudaError_t enqueue_refresh(edupic_sim *S, int d, int sp)
+{
+    const DischargeDev &D = S->desc[d];
+    cudaError_t e = cudaSuccess;
     const size_t ng = (size_t)S->params[d].n_grid;
     if (e == cudaSuccess) e = cudaMemsetAsync(sp == 0 ? D.q_e : D.q_i, 0, ng * 8, S->stream);
     if (e == cudaSuccess && sp == 1) e = cudaMemsetAsync(D.acc_i, 0, ng * 8, S->stream);
@@ -711,8 +722,7 @@ int load_species(edupic_sim *S, int d, int sp, int64_t n, const double *const sr
     if (e == cudaSuccess)
         e = S->precision == EDUPIC_FP32 ? Launch<float>::fields(S->d_desc, S->nd, d, S->stream)
                                         : Launch<double>::fields(S->d_desc, S->nd, d, S->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-    return cuda_status(e);
+    return e;
 }
 
 bool valid_d(const edupic_sim *S, int d) { return S && d >= 0 && d < S->nd; }
@@ -870,6 +880,20 @@ int edupic_load_particles(edupic_sim *S, int d, int species, int64_t n, const do
     if (n > 0 && (!x || !vx || !vy || !vz)) return EDUPIC_EINVAL;
     const double *src[4] = {x, vx, vy, vz};  // checked while they are converted
     return load_species(S, d, species, n, src);
+}
+
+int edupic_seed(edupic_sim *S, int d, int64_t n_init)
+{
+    if (!valid_d(S, d) || n_init < 0) return EDUPIC_EINVAL;
+    if (n_init > S->params[d].capacity_e || n_init > S->params[d].capacity_i) return EDUPIC_ECAPACITY;
+    cudaError_t e = cudaSuccess;
+    for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
+        e = S->precision == EDUPIC_FP32 ? Launch<float>::seed(S->d_desc, d, sp, n_init, S->stream)
+                                        : Launch<double>::seed(S->d_desc, d, sp, n_init, S->stream);
+        if (e == cudaSuccess) e = enqueue_refresh(S, d, sp);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    return cuda_status(e);
 }
 
 int edupic_step(edupic_sim *S, int64_t n_steps, int measure)

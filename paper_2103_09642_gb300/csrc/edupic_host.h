@@ -104,6 +104,7 @@ int upload_desc(edupic_sim *S);
 int upload_desc_one(edupic_sim *S, int d);
 int upload_drive(edupic_sim *S, int d);
 int load_species(edupic_sim *S, int d, int sp, int64_t n, const double *const src[4]);
+cudaError_t enqueue_refresh(edupic_sim *S, int d, int sp);
 int build_graph(edupic_sim *S, int measure);
 int read_ctrl(edupic_sim *S, int d, Ctrl *c);
 int error_of(const Ctrl &c);

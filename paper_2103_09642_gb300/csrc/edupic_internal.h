@@ -116,6 +116,7 @@ struct DischargeDev {
 template <typename T>
 struct Launch {
     static cudaError_t deposit(const DischargeDev *dd, int nd, int d, int species, int also_acc, cudaStream_t st);
+    static cudaError_t seed(const DischargeDev *dd, int d, int species, long long n, cudaStream_t st);
     static cudaError_t fields(const DischargeDev *dd, int nd, int d, cudaStream_t st);
     static cudaError_t averages(const DischargeDev *dd, int nd, int d, cudaStream_t st);
     // xt: the instantiation that accumulates the xt diagnostics (measured steps)

@@ -1578,6 +1578,30 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDe
     }
 }
 
+// init(N_INIT) of Algorithm 1: n particles of species sp of discharge d at
+// rest at x = L R01, R01 from block 9 of each slot's counter (current step);
+// sets the count.
+template <typename T>
+__global__ void k_seed(const DischargeDev *__restrict__ DD, int d, int sp, long long n)
+{
+    const DischargeDev &D = DD[d];
+    const unsigned long long s = (unsigned long long)D.ctrl->step;
+    const RngKey key{(uint32_t)s, (uint32_t)(s >> 32), (uint32_t)D.seed, (uint32_t)(D.seed >> 32)};
+    T *X = reinterpret_cast<T *>(D.x[sp]);
+    T *VX = reinterpret_cast<T *>(D.vx[sp]);
+    T *VY = reinterpret_cast<T *>(D.vy[sp]);
+    T *VZ = reinterpret_cast<T *>(D.vz[sp]);
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        double u, u_unused;
+        draw<double>(key, (uint32_t)j, sp, 9, u, u_unused);
+        X[j] = (T)(D.L * u);
+        VX[j] = (T)0;
+        VY[j] = (T)0;
+        VZ[j] = (T)0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) D.ctrl->n[sp] = n;
+}
+
 // Densities of one species from its particles (after a load), into q and,
 // for ions between ion steps, also into the pending accumulator.
 template <typename T>

@@ -33,6 +33,13 @@ int Launch<T>::push_blocks_per_sm(int species, size_t smem, int xt)
 }
 
 template <typename T>
+cudaError_t Launch<T>::seed(const DischargeDev *dd, int d, int species, long long n, cudaStream_t st)
+{
+    k_seed<T><<<1024, 256, 0, st>>>(dd, d, species, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Launch<T>::deposit(const DischargeDev *dd, int nd, int d, int species, int also_acc, cudaStream_t st)
 {
     (void)nd;

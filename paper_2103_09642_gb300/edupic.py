@@ -136,6 +136,7 @@ def load_library(path: str = LIB_PATH):
         "edupic_check_accuracy": ([_VP, ctypes.c_int, ctypes.POINTER(Accuracy)]),
         "edupic_get_power": ([_VP, ctypes.c_int, _D]),
         "edupic_set_bias": ([_VP, ctypes.c_int, ctypes.c_double]),
+        "edupic_seed": ([_VP, ctypes.c_int, ctypes.c_int64]),
         "edupic_get_graphs": ([_VP, ctypes.POINTER(ctypes.c_int)]),
         "edupic_get_xt": ([_VP, ctypes.c_int, ctypes.c_int, _D]),
         "edupic_get_bias": ([_VP, ctypes.c_int, _D]),
@@ -359,6 +360,11 @@ class Simulation:
         out = np.zeros((dd.n_grid, dd.xt_bins))
         _ck(self.L.edupic_get_xt(self._h, d, q, _ptr(out)), "get_xt")
         return out
+
+    def seed(self, d: int, n_init: int) -> None:
+        """init(N_INIT) of Algorithm 1: n_init e- and n_init Ar+ at rest,
+        uniform in the gap (replaces discharge d's particles)."""
+        _ck(self.L.edupic_seed(self._h, d, int(n_init)), "seed")
 
     def set_bias(self, d: int, v_bias: float) -> None:
         """DC self-bias voltage added at the powered electrode (Sec. 5)."""

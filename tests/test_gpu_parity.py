@@ -143,6 +143,32 @@ def test_absorption_compaction_order():
     assert c["abs_e_pow"] > 100 and c["abs_e_gnd"] > 100 and c["abs_i_pow"] > 10
 
 
+# --------------------------------------------------------------- init(N_INIT) of Algorithm 1
+@pytest.mark.parametrize("precision", [ed.FP64, ed.FP32])
+def test_seed_matches_the_oracle(precision):
+    """edupic_seed places the same particles as the oracle's init (x = L R01
+    from block 9 of each slot's counter, at rest); FP64 then steps along."""
+    d = wl.reference_discharge(seed=21, capacity=1 << 16)
+    sim = ed.simulation_for([d], precision, sigma=(SE, SI), de_ev=DE)
+    ref = oracle.Sim(d, SE, SI, DE)
+    sim.seed(0, 1000)
+    ref.seed(1000)
+    dtype = np.float64 if precision == ed.FP64 else np.float32
+    for sp in (0, 1):
+        g, o = sim.particles(0, sp), ref.particles(sp)
+        assert np.array_equal(g[0], o[0].astype(dtype).astype(np.float64))
+        assert not any(g[c].any() for c in (1, 2, 3))
+    f = sim.fields(0)
+    assert int(f["q_e"].sum()) == int(f["q_i"].sum()) == 1000 * 2 ** 32
+    if precision == ed.FP64:
+        for chunk in (1, 39, 160):
+            sim.step(chunk)
+            ref.step(chunk)
+            assert sim.counters(0) == ref.counters()
+            _compare_states(sim, ref, d)
+    sim.close()
+
+
 # --------------------------------------------------------------- multi-step FP64 parity
 @pytest.mark.parametrize("seed", [1, 2])
 def test_reference_start_fp64_per_step(seed):

@@ -48,7 +48,7 @@ BYTES_PER_PUSH_FP32 = 24     # read x, vx, vy, vz (16 B) + write x, vx (8 B)
 # particle kernel on the 64-discharge batch, from one ncu capture
 # (profiles/k_push_electron_batch64.md), valid for the kernel source whose
 # hash is given; null otherwise.
-TRAFFIC = {"sha": "d11c91e81e524dd4", "bytes_per_launch": 462379776}
+TRAFFIC = {"sha": "b46620b2895f7547", "bytes_per_launch": 462356224}
 BATCH_DISCHARGES = 64
 BATCH_STEPS = 400             # time steps per bench step (20 ion subcycles)
 N_STEADY = 500_000            # plain leg: particles per species of the steady-shape state

@@ -1148,35 +1148,45 @@ int edupic_get_diagnostics(edupic_sim *S, int d, double *ne_avg, double *ni_avg,
                            int64_t *measured_steps)
 {
     if (!valid_d(S, d)) return EDUPIC_EINVAL;
-    Ctrl c;
-    int rc = read_ctrl(S, d, &c);
-    if (rc) return rc;
     const DischargeDev &D = S->desc[d];
     const edupic_params &p = S->params[d];
-    const size_t ng = (size_t)p.n_grid;
+    const size_t ng = (size_t)p.n_grid, ne = (size_t)kEepfStripes * p.eepf_bins, ni = (size_t)p.ifed_bins;
+    // everything is queued into the page-locked stage behind the averages kernel; one synchronisation
+    const size_t o_avg = align_up(sizeof(Ctrl), 16), o_eepf = o_avg + 3 * ng * 8, o_ifed = o_eepf + ne * 8;
+    unsigned char *st = static_cast<unsigned char *>(pinned_reserve(S, o_ifed + 2 * ni * 8));
+    if (!st) return EDUPIC_ENOMEM;
     double *outs[3] = {ne_avg, ni_avg, phi_avg};
-    if (ne_avg || ni_avg || phi_avg) {
-        cudaError_t e = S->precision == EDUPIC_FP32 ? Launch<float>::averages(S->d_desc, S->nd, d, S->stream)
-                                                    : Launch<double>::averages(S->d_desc, S->nd, d, S->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-        if (e != cudaSuccess) return EDUPIC_ECUDA;
+    const bool avg = ne_avg || ni_avg || phi_avg;
+    cudaError_t e = cudaMemcpyAsync(st, S->ctrl(d), sizeof(Ctrl), cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess && avg) {
+        e = S->precision == EDUPIC_FP32 ? Launch<float>::averages(S->d_desc, S->nd, d, S->stream)
+                                        : Launch<double>::averages(S->d_desc, S->nd, d, S->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(st + o_avg, D.avg, 3 * ng * 8, cudaMemcpyDeviceToHost, S->stream);
     }
+    if (e == cudaSuccess && eepf_counts)
+        e = cudaMemcpyAsync(st + o_eepf, D.eepf, ne * 8, cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess && ifed_pow_counts)
+        e = cudaMemcpyAsync(st + o_ifed, D.ifed_pow, ni * 8, cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess && ifed_gnd_counts)
+        e = cudaMemcpyAsync(st + o_ifed + ni * 8, D.ifed_gnd, ni * 8, cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    if (e != cudaSuccess) return EDUPIC_ECUDA;
+    Ctrl c;
+    std::memcpy(&c, st, sizeof(Ctrl));
+    const double *av = reinterpret_cast<const double *>(st + o_avg);
     for (int k = 0; k < 3; ++k)
-        if (outs[k] && cudaMemcpy(outs[k], D.avg + k * ng, ng * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
-            return EDUPIC_ECUDA;
+        if (outs[k]) std::memcpy(outs[k], av + k * ng, ng * 8);
     if (eepf_counts) {
-        std::vector<int64_t> st((size_t)kEepfStripes * p.eepf_bins);
-        if (cudaMemcpy(st.data(), D.eepf, st.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return EDUPIC_ECUDA;
+        const int64_t *h = reinterpret_cast<const int64_t *>(st + o_eepf);
         for (int b = 0; b < p.eepf_bins; ++b) {
             int64_t t = 0;
-            for (int k = 0; k < kEepfStripes; ++k) t += st[(size_t)k * p.eepf_bins + b];
+            for (int k = 0; k < kEepfStripes; ++k) t += h[(size_t)k * p.eepf_bins + b];
             eepf_counts[b] = t;
         }
     }
-    if (ifed_pow_counts && cudaMemcpy(ifed_pow_counts, D.ifed_pow, (size_t)p.ifed_bins * 8, cudaMemcpyDeviceToHost))
-        return EDUPIC_ECUDA;
-    if (ifed_gnd_counts && cudaMemcpy(ifed_gnd_counts, D.ifed_gnd, (size_t)p.ifed_bins * 8, cudaMemcpyDeviceToHost))
-        return EDUPIC_ECUDA;
+    if (ifed_pow_counts) std::memcpy(ifed_pow_counts, st + o_ifed, ni * 8);
+    if (ifed_gnd_counts) std::memcpy(ifed_gnd_counts, st + o_ifed + ni * 8, ni * 8);
     if (measured_steps) *measured_steps = c.measured;
     return error_of(c);
 }

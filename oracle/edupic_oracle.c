@@ -5,9 +5,15 @@
  * arXiv 2103.09642).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product library may link, load or
- * call this file; only the tests, the package's smoke check and the CPU
- * baseline leg of bench.py use it.  It shares no code, header, table or
- * constant generator with the CUDA path.
+ * call this file; only the tests, the package's smoke check and bench.py's
+ * CPU baseline leg and reference arm use it.  It shares no code, header,
+ * table or constant generator with the CUDA path.
+ *
+ * Besides the particle loop of Sec. 2.1 it covers: init(N_INIT) of
+ * Algorithm 1, the diagnostics of Sec. 3.5 (time averages, EEPF, IFED, power
+ * absorption, the spatio-temporal "xt" maps), the null-collision method of
+ * Sec. 2.1.6, and the extensions Sec. 5 proposes (ion-induced secondary
+ * electrons, elastic electron reflection, a DC self-bias).
  *
  * Each function follows the paper's equations and algorithms in the paper's
  * order, one particle at a time, with no blocking, fusion or reordering beyond

@@ -754,3 +754,23 @@ def test_seed_uniform_at_rest():
     f = s.fields()
     assert int(f["q_e"].sum()) == int(f["q_i"].sum()) == 20_000 * 2 ** 32
     assert not np.array_equal(s.particles(0)[0], s.particles(1)[0])
+
+
+def test_xt_ion_drift_closed_form():
+    # Ar+ all moving with v0 along x, bins of N_SUB steps (one ion step each):
+    # j_i = e v0 n_i and the mean ion energy (1/2) M v0^2, normalised per ion
+    # step (a division by all steps of the bin would be N_SUB times smaller)
+    v0, n = 1.0e3, 4000
+    d = _quiet(weight=1e-9, n_grid=51, steps_per_cycle=400, ion_subcycle=20, xt_bins=20)
+    se, si = _tables(1000, sigma_e=(0, 0, 0), sigma_i=(0, 0))
+    rng = np.random.default_rng(22)
+    i = wl.Particles(rng.uniform(0.005, 0.02, n), np.full(n, v0), np.zeros(n), np.zeros(n))
+    s = oracle.Sim(d, se, si, 1e-3, wl.Particles.empty(), i)
+    s.step(60, measure=True)  # bins 0, 1, 2, one ion step each
+    ni, ji, mei = s.xt(XT["ni"]), s.xt(XT["ji"]), s.xt(XT["meanei"])
+    assert (ni[:, :3] > 0).any() and (ni[:, 3:] == 0).all()
+    assert np.abs(ji - QE * v0 * ni).max() <= 1e-9 * QE * v0 * ni.max()
+    hit = ni > 0
+    e_ion = 0.5 * MAR * v0 ** 2 / QE
+    assert np.abs(mei[hit] - e_ion).max() <= 1e-9 * e_ion
+    assert (s.xt(XT["je"]) == 0).all() and (s.xt(XT["ne"]) == 0).all()

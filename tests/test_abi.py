@@ -71,6 +71,16 @@ def test_strerror_and_host_side_checks(lib):
     assert lib.edupic_arena_bytes(1, (ed.Params * 1)(p), ed.FP64, ctypes.byref(out)) == 0 and out.value == plain
     p = ed.to_params(d.replace(see_gamma=(0.1, 0.0)), 1000)
     assert lib.edupic_arena_bytes(1, (ed.Params * 1)(p), ed.FP64, ctypes.byref(out)) == 0 and out.value > plain
+    # null-collision mask 0..3; xt bins dividing N_T; the xt block only when asked for
+    for kw in ({"null_collision": 4}, {"null_collision": -1}, {"xt_bins": 3}, {"xt_bins": -1},
+               {"xt_bins": 8200, "n_grid": 2048, "steps_per_cycle": 16400}):  # N_G N_XT > 2^24
+        p = ed.to_params(d.replace(**kw), 1000)
+        assert lib.edupic_arena_bytes(1, (ed.Params * 1)(p), ed.FP32, ctypes.byref(out)) == -1, kw
+    p = ed.to_params(d.replace(null_collision=3), 1000)
+    assert lib.edupic_arena_bytes(1, (ed.Params * 1)(p), ed.FP64, ctypes.byref(out)) == 0 and out.value == plain
+    p = ed.to_params(d.replace(xt_bins=200), 1000)
+    assert lib.edupic_arena_bytes(1, (ed.Params * 1)(p), ed.FP64, ctypes.byref(out)) == 0
+    assert out.value - plain >= (9 * d.n_grid * 200 + 4 * 200) * 8
 
 
 def test_create_rejects_small_or_misaligned_arena(lib):

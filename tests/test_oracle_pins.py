@@ -774,3 +774,165 @@ def test_xt_ion_drift_closed_form():
     e_ion = 0.5 * MAR * v0 ** 2 / QE
     assert np.abs(mei[hit] - e_ion).max() <= 1e-9 * e_ion
     assert (s.xt(XT["je"]) == 0).all() and (s.xt(XT["ne"]) == 0).all()
+
+
+# ------------------------------------------------------------------ drive V(t) (Sec. 2, Sec. 4.2)
+def _phi0_and_field(d, steps):
+    """Boundary potential phi_0 and field of the solve made at each global
+    step, with no space charge (W = 0): phi_0 = V(t) and E = V(t) / L."""
+    se, si = _tables(1000, sigma_e=(0, 0, 0), sigma_i=(0, 0))
+    s = oracle.Sim(d, se, si, 1e-3, wl.Particles.empty(), wl.Particles.empty())
+    out = []
+    for st in steps:
+        s.step_index = st
+        f = s.prepare_fields()
+        out.append((f["phi"][0], f["efield"].copy()))
+    return out
+
+
+def _check_drive(d, expected, v_scale):
+    got = _phi0_and_field(d, list(expected))
+    for (st, v), (phi0, ef) in zip(expected.items(), got):
+        assert abs(phi0 - v) <= 1e-10 * v_scale, (st, phi0, v)
+        assert np.abs(ef - v / d.gap_m).max() <= 1e-10 * v_scale / d.gap_m, st
+
+
+def test_drive_single_frequency_special_phases():
+    # V(t) = V0 cos(2 pi f t) at the cycle's quarter points, an eighth, and
+    # after cycle wraps (the phase is that of the step inside the cycle)
+    V0, nt = 250.0, 4000
+    d = _quiet(harmonics=((13.56e6, V0),), cycle_freq_hz=13.56e6, steps_per_cycle=nt)
+    r = 1.0 / math.sqrt(2.0)
+    _check_drive(d, {0: V0, nt // 8: V0 * r, nt // 4: 0.0, nt // 2: -V0, 3 * nt // 4: 0.0,
+                     nt + nt // 8: V0 * r, 3 * nt + nt // 2: -V0, 7 * nt: V0}, V0)
+    # the step itself solves with the same boundary value (one step after a wrap)
+    se, si = _tables(1000, sigma_e=(0, 0, 0), sigma_i=(0, 0))
+    s = oracle.Sim(d, se, si, 1e-3, wl.Particles.empty(), wl.Particles.empty())
+    s.step_index = 2 * nt + nt // 2
+    s.step(1)
+    assert abs(s.fields()["phi"][0] + V0) <= 1e-10 * V0
+
+
+def test_drive_two_harmonics_special_phases():
+    # V(t) = V1 cos(2 pi f t) + V2 cos(4 pi f t), cycle = the lower frequency:
+    # t = 0 -> V1 + V2, T/8 -> V1/sqrt2, T/4 -> -V2, T/2 -> V2 - V1
+    f, V1, V2, nt = 13.56e6, 120.0, 80.0, 4000
+    d = _quiet(harmonics=((f, V1), (2 * f, V2)), cycle_freq_hz=f, steps_per_cycle=nt)
+    _check_drive(d, {0: V1 + V2, nt // 8: V1 / math.sqrt(2.0), nt // 4: -V2, nt // 2: V2 - V1,
+                     5 * nt + nt // 4: -V2}, V1 + V2)
+
+
+def test_drive_dual_frequency_lf_cycle():
+    # the dual-frequency drive of Sec. 4.2 (1.356 MHz + 27.12 MHz, the cycle is
+    # the low-frequency period, 20 HF periods): T/4 -> V_HF, T/8 -> V_LF/sqrt2 - V_HF
+    V_lf, V_hf, nt = 300.0, 100.0, 320_000
+    d = _quiet(harmonics=((1.356e6, V_lf), (27.12e6, V_hf)), cycle_freq_hz=1.356e6, steps_per_cycle=nt)
+    _check_drive(d, {0: V_lf + V_hf, nt // 4: V_hf, nt // 8: V_lf / math.sqrt(2.0) - V_hf,
+                     nt // 2: V_hf - V_lf, nt + nt // 40: -V_hf + V_lf * math.cos(math.pi / 20)}, V_lf + V_hf)
+
+
+# ------------------------------------------------------------------ Ar+ direct collision test (Sec. 2.1.6, Alg. 6)
+def test_ion_collision_rate_direct_thermal_partner():
+    # Ar+ at rest in a field-free gap, constant sigma, direct test on an ion
+    # step (dt_i = N_SUB dt_e): the relative speed is the partner's Maxwell
+    # speed, so the collision probability is the Maxwell average of
+    # 1 - exp(-n sigma g dt_i), evaluated here by quadrature
+    from scipy import integrate
+    sig = 2.0e-15
+    d = _quiet(gap_m=0.025, n_grid=51, ion_subcycle=20, steps_per_cycle=4000, capacity=1 << 18)
+    se, si = _tables(1000, 1e-3, sigma_e=(0, 0, 0), sigma_i=(0.6 * sig, 0.4 * sig))
+    s = oracle.Sim(d, se, si, 1e-3)
+    n = 200_000
+    x = np.random.default_rng(41).uniform(0.01, 0.015, n)
+    s.load(0, wl.Particles.empty())
+    s.load(1, wl.Particles(x, np.zeros(n), np.zeros(n), np.zeros(n)))
+    s.step(1)  # step 0 is an ion step
+    c, dv = s.counters(), s.derived()
+    assert dv["dt_i"] == pytest.approx(20 * dv["dt_e"], rel=1e-15)
+    a = MAR / (2 * KB * d.gas_temp_k)
+    lam = dv["n_gas"] * sig * dv["dt_i"]
+
+    def maxwell(g):
+        return 4 * math.pi * (a / math.pi) ** 1.5 * g * g * math.exp(-a * g * g)
+
+    gmax = 12 / math.sqrt(a)
+    norm = integrate.quad(maxwell, 0, gmax, epsabs=0, epsrel=1e-12)[0]
+    p = integrate.quad(lambda g: maxwell(g) * -math.expm1(-lam * g), 0, gmax, epsabs=0, epsrel=1e-12)[0]
+    assert norm == pytest.approx(1.0, rel=1e-10)
+    assert 0.3 < p < 0.6  # far from the linear regime: 1 - exp matters
+    hits = c["coll_i_iso"] + c["coll_i_back"]
+    assert abs(hits - n * p) <= 4.5 * math.sqrt(n * p * (1 - p))
+    # isotropic against backward in the ratio of their cross sections
+    assert abs(c["coll_i_iso"] - 0.6 * hits) <= 4.5 * math.sqrt(hits * 0.24)
+    # the ions still sit where they were (E = 0) and no electron is involved
+    assert s.count(1) == n and c["coll_e_ela"] + c["coll_e_exc"] + c["coll_e_ion"] == 0
+
+
+# ------------------------------------------------------------------ ionisation products (Sec. 2.1.6, reading 17)
+def test_ionisation_ions_come_from_the_gas_maxwellian():
+    # every electron ionises (ionisation only, P_coll = 1): the new Ar+ sits at
+    # its parent's position with a velocity of the gas Maxwellian at T_g,
+    # so <M v^2 / 2> = 3/2 k T_g and each component has variance k T_g / M
+    d = _quiet(gap_m=0.025, n_grid=51, capacity=1 << 17)
+    se, si = _tables(200_000, 1e-3, sigma_e=(0, 0, 1e-16), sigma_i=(0, 0))
+    s = oracle.Sim(d, se, si, 1e-3)
+    n = 40_000
+    e, _ = _mono_electrons(np.random.default_rng(42), n, 100.0)
+    s.load(0, e)
+    s.load(1, wl.Particles.empty())
+    s.step(1)
+    c = s.counters()
+    assert c["coll_e_ion"] == n and c["created"] == n
+    assert s.count(0) == 2 * n and s.count(1) == n
+    xe = s.particles(0)[0]
+    xi, vx, vy, vz = s.particles(1)
+    assert np.array_equal(xi, xe[:n])  # parents keep their slots; products follow in parent order
+    kt_m = KB * d.gas_temp_k / MAR
+    mean_e = 0.5 * MAR * np.mean(vx ** 2 + vy ** 2 + vz ** 2)
+    assert abs(mean_e / (1.5 * KB * d.gas_temp_k) - 1) <= 4.5 * math.sqrt(2.0 / 3.0 / n)
+    for comp in (vx, vy, vz):
+        assert abs(np.mean(comp)) <= 4.5 * math.sqrt(kt_m / n)
+        assert abs(np.mean(comp ** 2) / kt_m - 1) <= 4.5 * math.sqrt(2.0 / n)
+
+
+# ------------------------------------------------------------------ table index (Algorithm 6)
+def test_table_index_is_the_nearest_entry_electrons():
+    # sigma non-zero only in entry k + 1: energies (k + 0.7) de round to it and
+    # always collide, energies (k + 0.3) de round to entry k and never do;
+    # flooring the index would swap the two outcomes
+    k, de, nent = 5000, 1e-3, 20_000
+    sig = np.zeros(nent)
+    sig[k + 1] = 1e-15
+    se = np.stack([sig, np.zeros(nent), np.zeros(nent)])
+    si = np.zeros((2, nent))
+    d = _quiet(gap_m=0.025, n_grid=51, capacity=1 << 15)
+    for frac, expect_all in ((0.7, True), (0.3, False)):
+        s = oracle.Sim(d, se, si, de)
+        e, _ = _mono_electrons(np.random.default_rng(43), 5000, (k + frac) * de)
+        s.load(0, e)
+        s.load(1, wl.Particles.empty())
+        s.step(1)
+        assert s.counters()["coll_e_ela"] == (5000 if expect_all else 0), frac
+
+
+def test_table_index_is_the_nearest_entry_ions_by_com_energy():
+    # the ion table is indexed by the centre-of-mass energy mu g^2 / 2 (mu =
+    # M / 2); a near-zero gas temperature makes g the ion's own speed
+    k, de, nent = 5, 1e-3, 200
+    sig = np.zeros(nent)
+    sig[k + 1] = 1e-14
+    se = np.zeros((3, nent))
+    si = np.stack([sig, np.zeros(nent)])
+    d = _quiet(gap_m=0.025, n_grid=51, capacity=1 << 15, gas_temp_k=1e-5, pressure_pa=1e-5)
+    n = 5000
+    rng = np.random.default_rng(44)
+    for frac, expect_all in ((0.7, True), (0.3, False)):
+        s = oracle.Sim(d, se, si, de)
+        g = math.sqrt(2 * (k + frac) * de * QE / (MAR / 2))
+        dirs = rng.normal(size=(3, n))
+        dirs /= np.linalg.norm(dirs, axis=0)
+        s.load(0, wl.Particles.empty())
+        s.load(1, wl.Particles(rng.uniform(0.01, 0.015, n), g * dirs[0], g * dirs[1], g * dirs[2]))
+        s.step(1)
+        c = s.counters()
+        assert c["coll_i_iso"] == (n if expect_all else 0), frac

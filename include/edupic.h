@@ -495,9 +495,10 @@ int edupic_server_stats(edupic_server *srv, edupic_server_stats_t *out);
 /* Densities, potential and field of given particle positions, computed
  * without allocating any device memory.  (The paper has no counterpart: it
  * is an interface for callers that cannot call cudaMalloc mid-run, e.g.
- * code whose device memory is pre-budgeted by another framework's pool, code
- * inside a plugin or a real-time loop, or code issuing work while a stream is
- * being captured.)
+ * code whose device memory is pre-budgeted by another framework's pool,
+ * where an allocation would fail or break the budget, or code inside a
+ * plugin or a real-time loop that must not touch the allocator, which can
+ * block on the device.)
  *
  * Computes what edupic_load_particles followed by edupic_get_fields gives in
  * EDUPIC_FP64 mode: fixed-point deposition of x_e and x_i (Algorithm 2) and
@@ -506,10 +507,12 @@ int edupic_server_stats(edupic_server *srv, edupic_server_stats_t *out);
  * cycle_freq_hz and the harmonics.
  *
  * x_e, x_i: device FP64 positions in [0, L] (n_e, n_i entries, may be NULL
- * when the count is 0).  n_e_out, n_i_out (m^-3), phi_out (V), efield_out
- * (V/m): device FP64 arrays of n_grid entries, written by the call.
+ * when the count is 0).  A position outside [0, L], or not a number, is
+ * reported as EDUPIC_EINVAL; the outputs are then unspecified.
+ * n_e_out, n_i_out (m^-3), phi_out (V), efield_out (V/m): device FP64 arrays
+ * of n_grid entries, written by the call.
  * cuda_stream: cudaStream_t (NULL = legacy default stream); the call
- * synchronises it before returning.
+ * synchronises it before returning (it reads the position check back).
  *
  * Working memory is one fixed array of 49,408 bytes in the library's device
  * image, held by every GPU that loads the library until the process exits;

@@ -2,9 +2,10 @@
 // allocation (edupic_fields_noalloc in include/edupic.h).
 //
 // Some callers cannot allocate device memory in the middle of a run: code
-// whose device memory is owned and pre-budgeted by another framework's pool,
-// code running inside a plugin or a real-time loop that must not touch the
-// allocator, or code issuing work while a stream is being captured.  This
+// whose device memory is owned and pre-budgeted by another framework's pool
+// (an allocation there would fail or break the budget), or code running
+// inside a plugin or a real-time loop that must not touch the allocator (an
+// allocation can block on the device or grow the process's footprint).  This
 // entry point serves them: the caller passes the particle positions and the
 // output arrays, and the only working memory is a fixed array in the
 // library's own device image (g_scratch below), which every GPU that loads
@@ -24,13 +25,14 @@ using namespace edupic;
 namespace {
 
 // Scratch layout: fixed-point densities Q_e, Q_i and the prefix sums F (each
-// EDUPIC_MAX_GRID int64), then the field scalars and the drive voltage.
+// EDUPIC_MAX_GRID int64), then the field scalars, the drive voltage and the
+// flag of positions outside [0, L].
 constexpr size_t kGridBytes = (size_t)EDUPIC_MAX_GRID * sizeof(long long);
 constexpr size_t kScratchBytes = 3 * kGridBytes + 256;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-static_assert(sizeof(FieldState) + sizeof(double) <= 256, "field scalars must fit the scratch tail");
+static_assert(sizeof(FieldState) + sizeof(double) + sizeof(int) <= 256, "field scalars must fit the scratch tail");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_lock;
@@ -53,17 +55,28 @@ int scratch_address(void **out)
     return EDUPIC_OK;
 }
 
-__global__ void k_na_clear(long long *q, int n, double *vdrive, double v)
+__global__ void k_na_clear(long long *q, int n, double *vdrive, double v, int *bad)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) q[i] = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) vdrive[0] = v;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        vdrive[0] = v;
+        *bad = 0;
+    }
 }
 
-__global__ void k_na_deposit(const double *__restrict__ x, long long n, double inv_dx, int ng, long long *q)
+// A position outside [0, L] (or not a number) is not deposited: it sets the
+// flag, and the call reports EDUPIC_EINVAL.
+__global__ void k_na_deposit(const double *__restrict__ x, long long n, double L, double inv_dx, int ng, long long *q,
+                             int *bad)
 {
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        const double xj = x[j];
+        if (!(xj >= 0.0 && xj <= L)) {
+            *bad = 1;
+            continue;
+        }
         double c0;
-        const int p = cell<double>(x[j], inv_dx, ng, c0);
+        const int p = cell<double>(xj, inv_dx, ng, c0);
         const unsigned long long q2 = split_q2(c0 - (double)p);
         atomicAdd(reinterpret_cast<unsigned long long *>(q + p), 4294967296ull - q2);
         atomicAdd(reinterpret_cast<unsigned long long *>(q + p + 1), q2);
@@ -98,6 +111,7 @@ extern "C" int edupic_fields_noalloc(const edupic_params *p, int64_t step, const
     long long *f = reinterpret_cast<long long *>(b + 2 * kGridBytes);
     FieldState *fs = reinterpret_cast<FieldState *>(b + 3 * kGridBytes);
     double *vdrive = reinterpret_cast<double *>(b + 3 * kGridBytes + sizeof(FieldState));
+    int *bad = reinterpret_cast<int *>(b + 3 * kGridBytes + sizeof(FieldState) + sizeof(double));
 
     // the same derived quantities and drive voltage as the simulation object
     const double kQE = 1.602176634e-19, kEPS0 = 8.8541878128e-12, pi = 3.14159265358979323846;
@@ -126,12 +140,16 @@ extern "C" int edupic_fields_noalloc(const edupic_params *p, int64_t step, const
     D.ef_t = efield_out;  // FP64: the particle-precision copy is the field itself
 
     // every call starts from zeroed densities (the array keeps the last call's contents)
-    k_na_clear<<<8, 256, 0, st>>>(q_e, 2 * EDUPIC_MAX_GRID, vdrive, v);
+    k_na_clear<<<8, 256, 0, st>>>(q_e, 2 * EDUPIC_MAX_GRID, vdrive, v, bad);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && n_e > 0) k_na_deposit<<<256, 256, 0, st>>>(x_e, n_e, D.inv_dx, D.ng, q_e);
-    if (e == cudaSuccess && n_i > 0) k_na_deposit<<<256, 256, 0, st>>>(x_i, n_i, D.inv_dx, D.ng, q_i);
+    if (e == cudaSuccess && n_e > 0) k_na_deposit<<<256, 256, 0, st>>>(x_e, n_e, p->gap_m, D.inv_dx, D.ng, q_e, bad);
+    if (e == cudaSuccess && n_i > 0) k_na_deposit<<<256, 256, 0, st>>>(x_i, n_i, p->gap_m, D.inv_dx, D.ng, q_i, bad);
     if (e == cudaSuccess) k_na_solve<<<1, kGroupB, 0, st>>>(D);
     if (e == cudaSuccess) e = cudaGetLastError();
+    // the flag is read into a stack variable (a pageable copy, no allocation)
+    int bad_h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    return e == cudaSuccess ? EDUPIC_OK : EDUPIC_ECUDA;
+    if (e != cudaSuccess) return EDUPIC_ECUDA;
+    return bad_h ? EDUPIC_EINVAL : EDUPIC_OK;
 }

@@ -206,6 +206,15 @@ int edupic_run_cycles(edupic_sim *sim, int n_cycles, int measure);
 /* Wait for the stream and return the first device-side error (or OK). */
 int edupic_synchronize(edupic_sim *sim);
 
+/* Self-test of the bounded waits (no counterpart in the paper: every wait of
+ * the particle kernel on its asynchronous copies gives up after a limit and
+ * records an error instead of waiting forever).  One block waits, with the
+ * same bounded wait, limit_ns nanoseconds (1e3..1e9) on a barrier that
+ * nothing ever arrives on, records the expiry in discharge d's error bits
+ * and returns.  Returns EDUPIC_ETIMEOUT (as edupic_synchronize will from then
+ * on: the error bits are sticky).  The GPU context stays usable. */
+int edupic_selftest_wait_expiry(edupic_sim *sim, int d, int64_t limit_ns);
+
 /* Run n_steps exactly as edupic_step does, but launch by launch (no graph)
  * with a CUDA event pair on the object's stream around every kernel, and
  * synchronise after each step.  out_ms[0..2] receive the summed device time
@@ -377,7 +386,13 @@ int edupic_check_accuracy(edupic_sim *sim, int d, edupic_accuracy *out);
 
 /* Save / restore the state of discharge d (counts, step index, particle
  * coordinates), the analogue of picdata.bin (Algorithm 1).  The file has a
- * versioned header; a restore recomputes the densities and field. */
+ * versioned header; a restore recomputes the densities and field.
+ * edupic_load_state reads and checks the whole file before it changes
+ * anything: EDUPIC_EIO for a file that is missing, short, longer than its
+ * counts, of another version or another N_G; EDUPIC_ECAPACITY for counts
+ * above the capacity; EDUPIC_ESTATE for a step of another ion-subcycle
+ * phase than the object's; EDUPIC_EINVAL for a position outside [0, L] or a
+ * non-finite velocity.  On any error the simulation is unchanged. */
 int edupic_save_state(edupic_sim *sim, int d, const char *path);
 int edupic_load_state(edupic_sim *sim, int d, const char *path);
 
@@ -484,7 +499,12 @@ int edupic_server_result(edupic_server *srv, uint64_t ticket, double *ne_avg, do
                          int64_t *eepf_counts, int64_t *ifed_pow_counts, int64_t *ifed_gnd_counts,
                          int64_t counters[EDUPIC_N_COUNTERS], int64_t *measured_steps);
 
-/* Forget a finished or failed request (its host-side results). */
+/* Forget a request.  A queued request leaves the queue.  A running request
+ * is cancelled: the call waits for the steps already enqueued on the
+ * server's stream, then returns the request's slot and heap memory; the
+ * other running requests are not affected (their results stay the same).  A
+ * finished or failed request loses its host-side results.  EDUPIC_EINVAL for
+ * an unknown ticket. */
 int edupic_server_release(edupic_server *srv, uint64_t ticket);
 
 /* Clock, step count, heap use and slot occupancy. */

@@ -661,6 +661,27 @@ int convert_stage(edupic_sim *S, int d, int64_t n, const double *const src[4], T
     return bad.load() ? EDUPIC_EINVAL : EDUPIC_OK;
 }
 
+// The same checks without conversion: true when every value is acceptable.
+bool particles_valid(edupic_sim *S, int d, int64_t n, const double *const src[4])
+{
+    const double L = S->params[d].gap_m;
+    std::atomic<int> bad{0};
+    parallel_ranges(n, [&](int64_t lo, int64_t hi) {
+        int b = 0;
+        for (int64_t j = lo; j < hi; ++j) {
+            const double v = src[0][j];
+            b |= (int)!(v >= 0.0) | (int)!(v <= L);
+        }
+        for (int c = 1; c < 4; ++c)
+            for (int64_t j = lo; j < hi; ++j) {
+                const double a = src[c][j];
+                b |= (int)!(a - a == 0.0);
+            }
+        if (b) bad.store(1, std::memory_order_relaxed);
+    });
+    return bad.load() == 0;
+}
+
 template <typename T>
 int download_particles(edupic_sim *S, int d, int sp, int64_t n, double *const dst[4])
 {
@@ -941,6 +962,19 @@ int edupic_synchronize(edupic_sim *S)
         if (rc) return rc;
     }
     return EDUPIC_OK;
+}
+
+int edupic_selftest_wait_expiry(edupic_sim *S, int d, int64_t limit_ns)
+{
+    if (!valid_d(S, d) || limit_ns < 1000 || limit_ns > (int64_t)kWaitLimitNs) return EDUPIC_EINVAL;
+    int *err = &S->ctrl(d)->error;
+    cudaError_t e = S->precision == EDUPIC_FP32 ? Launch<float>::wait_expiry((unsigned long long)limit_ns, err, S->stream)
+                                                : Launch<double>::wait_expiry((unsigned long long)limit_ns, err, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    if (e != cudaSuccess) return EDUPIC_ECUDA;
+    Ctrl c;
+    int rc = read_ctrl(S, d, &c);
+    return rc ? rc : error_of(c);
 }
 
 int edupic_profile_steps(edupic_sim *S, int64_t n_steps, int measure, double out_ms[3], int64_t launches[3])
@@ -1398,8 +1432,14 @@ int edupic_load_state(edupic_sim *S, int d, const char *path)
             a[sp][k].resize((size_t)vals[1 + sp]);
             ok = std::fread(a[sp][k].data(), 8, a[sp][k].size(), f) == a[sp][k].size();
         }
+    ok = ok && std::fgetc(f) == EOF;  // a longer file is not a checkpoint of these counts
     std::fclose(f);
     if (!ok) return EDUPIC_EIO;
+    // every value is checked before anything of the simulation changes
+    for (int sp = 0; sp < 2; ++sp) {
+        const double *src[4] = {a[sp][0].data(), a[sp][1].data(), a[sp][2].data(), a[sp][3].data()};
+        if (!particles_valid(S, d, vals[1 + sp], src)) return EDUPIC_EINVAL;
+    }
     long long step = vals[0];
     if (cudaMemcpy(&S->ctrl(d)->step, &step, sizeof(step), cudaMemcpyHostToDevice) != cudaSuccess)
         return EDUPIC_ECUDA;

@@ -15,6 +15,7 @@ constexpr int kEvents = EDUPIC_STEP_EVENTS;
 constexpr int kSortShared = 8192;      // event lists up to this size are sorted in shared memory
 constexpr int kCoarse = 2048;          // entries of the coarse sigma_max tables (shared memory)
 constexpr int kEepfStripes = 16;       // copies of the EEPF histogram the particle kernel spreads its atomics over
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // limit of every bounded device wait (1 s)
 
 // Device error bits (ctrl->error).
 enum : int {
@@ -123,6 +124,8 @@ struct Launch {
     static cudaError_t push(const DischargeDev *dd, int nd, int species, int measure, int grid, int ng_max,
                             int eepf_max, int null_any, int xt, cudaStream_t st);
     static cudaError_t finalize(const DischargeDev *dd, int nd, int ion_step, int measure, cudaStream_t st);
+    // one block waiting on a barrier that is never armed, for limit_ns (sets kErrTimeout in *err)
+    static cudaError_t wait_expiry(unsigned long long limit_ns, int *err, cudaStream_t st);
     static size_t push_smem(int nd, int ng_max, int eepf_max, int xt);
     static int push_blocks_per_sm(int species, size_t smem, int xt);
 };

@@ -368,15 +368,30 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Wait for phase `parity` of the barrier for at most about one second; false
-// if the wait expired.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Wait for phase `parity` of the barrier for at most limit_ns (one second by
+// default); false if the wait expired.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitLimitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > 1000000000ull) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
+}
+
+// Test of the bounded wait: one block waits on a barrier that nothing ever
+// arrives on, so every wait expires after limit_ns; the block records the
+// expiry in *err (kErrTimeout) and returns.
+static __global__ void k_wait_expiry(unsigned long long limit_ns, int *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0, limit_ns)) atomicOr(err, kErrTimeout);
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -779,6 +794,10 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     __shared__ DischargeDev sD;  // descriptor of the discharge being processed
     __shared__ __align__(8) uint64_t sFull[S];   // stage holds its tile (bulk-copy transactions)
     __shared__ __align__(8) uint64_t sEmpty[S];  // every warp has read the stage
+    // set when a bounded wait expired: no further copies are issued and the
+    // remaining tiles are skipped (the error bit is set), so the block still
+    // reaches all its barriers and ends
+    __shared__ volatile int sAbort;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -795,6 +814,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     }
     if (tid < kWarps) sQn[tid] = 0;
     if (tid == 0) {
+        sAbort = 0;
         for (int k = 0; k < S; ++k) {
             mbar_init(sFull + k, 1);
             mbar_init(sEmpty + k, kWarps);
@@ -922,6 +942,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
     // Producer (thread 0): bulk-copy tile `pt` (x, vx, vy, vz; a whole TILE,
     // inside the padded capacity) into ring stage `st`.
     int pt = t0, pcur = 0;
+    int seen0 = 0;  // tiles whose arrival thread 0 has observed (its own waits)
     auto issue = [&](int st) {
         while (pt >= sPre[pcur + 1]) ++pcur;
         const DischargeDev *Dq = DD + pcur;
@@ -1008,7 +1029,15 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         if (tid == 0) atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_PUSH_E : EDUPIC_C_PUSH_I), (unsigned)min(TILE, n - tbase));
         const int base = tbase + tid * VEC;
         // this tile's particles from the ring; each warp then marks the stage read
-        if (!mbar_wait_bounded(sFull + st, (uint32_t)((it / S) & 1))) atomicOr(&D->ctrl->error, kErrTimeout);
+        const bool aborted = sAbort != 0;
+        if (!aborted) {
+            if (mbar_wait_bounded(sFull + st, (uint32_t)((it / S) & 1))) {
+                if (tid == 0) seen0 = it + 1;
+            } else {
+                atomicOr(&D->ctrl->error, kErrTimeout);
+                sAbort = 1;
+            }
+        }
         {
             const T *rs = sRing + (size_t)st * 4 * TILE + tid * VEC;
             unpack(*reinterpret_cast<const V *>(rs), xa);
@@ -1021,12 +1050,15 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         // the producer refills the stage read in the previous iteration (every
         // warp marked it then, so this wait rarely blocks) with the tile S - 1
         // ahead
-        if (tid == 0 && it > 0 && pt < t1) {
+        if (tid == 0 && it > 0 && pt < t1 && !sAbort) {
             const int ps = (it - 1) % S;
-            if (!mbar_wait_bounded(sEmpty + ps, (uint32_t)(((it - 1) / S) & 1)))
+            if (mbar_wait_bounded(sEmpty + ps, (uint32_t)(((it - 1) / S) & 1))) {
+                fence_proxy_async();
+                issue(ps);
+            } else {
                 atomicOr(&D->ctrl->error, kErrTimeout);
-            fence_proxy_async();
-            issue(ps);
+                sAbort = 1;
+            }
         }
         if (since_flush >= kDepFlush) {
             flush_dep(true);
@@ -1035,7 +1067,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         since_flush += TILE;
         // a tile adds at most 32 * VEC colliders to this warp's queue
         if (sQn[warp] > kWarpQueue - 32 * VEC) drain();
-        if (base >= n) continue;
+        if (base >= n || sAbort) continue;  // after an expired wait the stage contents are not used
 
         // phase 1: gather (Sec. 2.1.3), leapfrog push (Sec. 2.1.4), absorption
         // test (Sec. 2.1.5), energy and table index
@@ -1181,6 +1213,10 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         *reinterpret_cast<V *>(VX + base) = pack(vxa, V{});
     }
     if (cur >= 0) flush(true);
+    // after an expired wait: wait (bounded) for the copies issued but never
+    // observed, so that none is still writing shared memory when the block ends
+    if (tid == 0 && sAbort)
+        for (int j = seen0; j < pt - t0; ++j) (void)mbar_wait_bounded(sFull + j % S, (uint32_t)((j / S) & 1));
 }
 
 // ---------------------------------------------------------------- field solve

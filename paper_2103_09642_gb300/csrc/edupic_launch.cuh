@@ -111,4 +111,11 @@ cudaError_t Launch<T>::finalize(const DischargeDev *dd, int nd, int ion_step, in
     return launch_pdl(k_finalize<T>, dim3(nd), dim3(kFinalizeThreads), 0, st, dd, nd, ion_step, measure);
 }
 
+template <typename T>
+cudaError_t Launch<T>::wait_expiry(unsigned long long limit_ns, int *err, cudaStream_t st)
+{
+    k_wait_expiry<<<1, 32, 0, st>>>(limit_ns, err);
+    return cudaGetLastError();
+}
+
 }  // namespace edupic

@@ -233,6 +233,18 @@ int open_slot(edupic_server *V, uint64_t ticket, int d)
     return EDUPIC_OK;
 }
 
+// Return slot d and its heap memory (the slot's steps must have completed).
+void free_slot(edupic_server *V, int d)
+{
+    edupic_sim *S = V->S;
+    Request &r = V->reqs[V->slot_ticket[d]];
+    S->desc[d] = idle_desc(S, d);
+    update_null_any(S);
+    upload_desc_one(S, d);
+    V->heap.release(r.off, r.bytes);
+    V->slot_ticket[d] = 0;
+}
+
 // Read the results of the request in slot d and free the slot.
 void close_slot(edupic_server *V, int d, int status)
 {
@@ -259,11 +271,7 @@ void close_slot(edupic_server *V, int d, int status)
     r.status = rc;
     r.state = rc == EDUPIC_OK ? EDUPIC_REQ_DONE : EDUPIC_REQ_FAILED;
     r.t_done = V->now();
-    S->desc[d] = idle_desc(S, d);
-    update_null_any(S);
-    upload_desc_one(S, d);
-    V->heap.release(r.off, r.bytes);
-    V->slot_ticket[d] = 0;
+    free_slot(V, d);
 }
 
 }  // namespace
@@ -489,7 +497,15 @@ int edupic_server_release(edupic_server *V, uint64_t ticket)
     if (!V) return EDUPIC_EINVAL;
     auto it = V->reqs.find(ticket);
     if (it == V->reqs.end()) return EDUPIC_EINVAL;
-    if (it->second.state != EDUPIC_REQ_DONE && it->second.state != EDUPIC_REQ_FAILED) return EDUPIC_ESTATE;
+    Request &r = it->second;
+    if (r.state == EDUPIC_REQ_QUEUED) {
+        V->queue.erase(std::find(V->queue.begin(), V->queue.end(), ticket));
+    } else if (r.state == EDUPIC_REQ_RUNNING) {
+        // cancelled mid-run: the steps already enqueued complete first, then
+        // the slot and its memory are returned; other slots are not touched
+        if (cudaStreamSynchronize(V->S->stream) != cudaSuccess) return EDUPIC_ECUDA;
+        free_slot(V, r.slot);
+    }
     V->reqs.erase(it);
     return EDUPIC_OK;
 }

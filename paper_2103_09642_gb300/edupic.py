@@ -128,6 +128,7 @@ def load_library(path: str = LIB_PATH):
         "edupic_step": ([_VP, ctypes.c_int64, ctypes.c_int]),
         "edupic_run_cycles": ([_VP, ctypes.c_int, ctypes.c_int]),
         "edupic_synchronize": ([_VP]),
+        "edupic_selftest_wait_expiry": ([_VP, ctypes.c_int, ctypes.c_int64]),
         "edupic_set_graphs": ([_VP, ctypes.c_int]),
         "edupic_profile_steps": ([_VP, ctypes.c_int64, ctypes.c_int, _D, _Q]),
         "edupic_set_push_grid": ([_VP, ctypes.c_int, ctypes.c_int]),
@@ -258,6 +259,10 @@ class Simulation:
 
     def synchronize(self):
         _ck(self.L.edupic_synchronize(self._h), "synchronize")
+
+    def selftest_wait_expiry(self, d: int, limit_ns: int) -> int:
+        """Status of a bounded wait on a barrier nothing arms (EDUPIC_ETIMEOUT)."""
+        return int(self.L.edupic_selftest_wait_expiry(self._h, d, int(limit_ns)))
 
     def profile_steps(self, n: int, measure: bool = False):
         """Per-kernel device time (ms) and launch counts over n steps:

@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s and % HBM roofline; batched/served vs plain at ≤2% profile error"
 UNIT = "particle-steps/s"
-HBM_PEAK_FALLBACK = 6754.5   # GB/s, STREAM-style copy measured on this machine's GB300
+HBM_PEAK_FALLBACK = 6800.0   # GB/s: the profiling recipe's fallback, used only without MEASURED_PEAKS.json
 BYTES_PER_PUSH_FP32 = 24     # read x, vx, vy, vz (16 B) + write x, vx (8 B)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the electron
 # particle kernel on the 64-discharge batch, from one ncu capture
@@ -95,7 +95,7 @@ def _peak_hbm():
     try:
         return float(json.load(open(p))["hbm_gbs"]), "measured"
     except Exception:
-        return HBM_PEAK_FALLBACK, "measured (earlier copy of the same pool figure)"
+        return HBM_PEAK_FALLBACK, "fallback"
 
 
 def _kernel_sha():
@@ -163,6 +163,14 @@ def reduce_over_ranks(ms_total: float, work: float, ws: int, device: str):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(w, op=dist.ReduceOp.SUM)
     return float(t.item()), float(w.item())
+
+
+def _shapes_desc(shapes) -> dict:
+    """The particle kernel's launch shapes the autotuner chose, per species."""
+    from paper_2103_09642_gb300 import edupic as ed
+
+    return {name: dict(index=int(sh), **ed.describe_push_shape(ed.FP32, int(sh)))
+            for name, sh in zip(("electrons", "ions"), shapes)}
 
 
 def _batch(rank: int):
@@ -287,6 +295,7 @@ def leg_plain(args, peak, peak_kind, flush) -> dict:
     sim = ed.simulation_for([d], ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV, particles=[(e, i)])
     grid, _ = sim.autotune(subcycles=10, measure=True)
     graphs = sim.graphs()
+    shapes = sim.push_shape()
     for _ in range(args.warmup):
         sim.run_cycles(1, measure=True)
     sim.synchronize()
@@ -300,8 +309,8 @@ def leg_plain(args, peak, peak_kind, flush) -> dict:
     sim.close()
     # end to end through the public API: particles from host arrays, one cycle, diagnostics back
     sim2 = ed.simulation_for([d], ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV)
-    sim2.set_push_grid(0, grid)
-    sim2.set_push_grid(1, grid)
+    for sp in (0, 1):
+        sim2.set_push_shape(sp, shapes[sp])  # the launch the autotuner chose
     sim2.set_graphs(graphs)
     tot_ps, tot_t = 0, 0.0
     for r in range(3):
@@ -333,7 +342,7 @@ def leg_plain(args, peak, peak_kind, flush) -> dict:
                                     "ms_per_rf_cycle": msx / steps},
             "particles_e": int(n_e), "particles_i": int(n_i), "value": ps / (ms / 1000.0), "unit": UNIT,
             "ms_per_rf_cycle": ms / steps, "us_per_time_step": 1000.0 * ms / (steps * d.steps_per_cycle),
-            "steps": steps, "push_grid": grid, "roofline": roof,
+            "steps": steps, "push_grid": grid, "push_shape": _shapes_desc(shapes), "roofline": roof,
             "e2e": {"value": tot_ps / tot_t, "unit": UNIT, "h2d_bytes_per_step": 16 * (e.n + i.n),
                     "d2h_bytes_per_step": 8 * (3 * d.n_grid + d.eepf_bins + 2 * d.ifed_bins)}}
 
@@ -478,8 +487,10 @@ def run_ours(args):
     stream = sim.stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     _log("batch created; autotuning the stepping mode")
-    grid, _ = sim.autotune(subcycles=5, measure=True)  # graph replay or not, by timing (warm-up steps)
+    grid, _ = sim.autotune(subcycles=5, measure=True)  # launch shapes and graph replay, by timing (warm-up steps)
     graphs = sim.graphs()
+    shapes = sim.push_shape()
+    grids = sim.push_grid()
     _log("warm-up")
 
     def barrier():
@@ -524,8 +535,8 @@ def run_ours(args):
     if not args.no_e2e:
         _log("end to end")
         sim2 = ed.simulation_for(ds, ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV)
-        sim2.set_push_grid(0, grid)
-        sim2.set_push_grid(1, grid)
+        for sp in (0, 1):
+            sim2.set_push_shape(sp, shapes[sp])  # the launch shapes and
         sim2.set_graphs(graphs)  # the stepping mode the autotuner chose
         h2d = 16 * sum(m[1].n + m[2].n for m in mix)
         d2h = sum(8 * (3 * d.n_grid + d.eepf_bins + 2 * d.ifed_bins) for d in ds)
@@ -578,7 +589,7 @@ def run_ours(args):
                        "l2": "256 MB buffer written between timed steps (outside the timed events); "
                              "particle state 0.7 GB > L2",
                        "parallelism": f"replicas x{ws}", "cross_sections": "stand-in set",
-                       "push_grid": grid},
+                       "push_grid": list(grids), "push_shape": _shapes_desc(shapes), "graph_replay": graphs},
             "roofline": roof,
             "pushes": pushes,
             "gpu_launches": int(args.steps * (2 * BATCH_STEPS + BATCH_STEPS // ds[0].ion_subcycle)),

@@ -229,25 +229,45 @@ int edupic_set_graphs(edupic_sim *sim, int enable);
 /* Writes 1 if graph replay is in use (as set, or as edupic_autotune chose). */
 int edupic_get_graphs(edupic_sim *sim, int *enabled);
 
-/* Launch shape of the particle kernels (no counterpart in the paper, whose
+/* Launch of the particle kernels (no counterpart in the paper, whose
  * particle loops are serial).  The particle kernel runs a persistent grid
  * of thread blocks that share the particle tiles of all discharges: the
  * resident limit (blocks per SM that fit the registers and shared memory,
- * times the SM count).  edupic_set_push_grid accepts blocks = 0 or that
- * limit (anything else is EDUPIC_EINVAL: smaller persistent grids stalled on
- * large batches and are not offered).  edupic_get_push_grid writes the
- * grids of the electron and ion kernels to out[0..1] (host memory). */
+ * times the SM count) of its launch shape.  edupic_set_push_grid accepts
+ * blocks = 0 or that limit (anything else is EDUPIC_EINVAL: smaller
+ * persistent grids stalled on large batches and are not offered).
+ * edupic_get_push_grid writes the grids of the electron and ion kernels to
+ * out[0..1] (host memory). */
 int edupic_set_push_grid(edupic_sim *sim, int species, int blocks);
 int edupic_get_push_grid(edupic_sim *sim, int out[2]);
 
-/* Autotuner of the stepping mode: times `subcycles` ion subcycles replayed
- * through one CUDA graph per ion subcycle and the same launched kernel by
- * kernel, and keeps the faster (results are identical either way).  The
- * trial steps are real simulation steps (the simulation advances by
- * 2 x (subcycles + 1) ion subcycles, measured if `measure`); call it at the
- * start of a run, at ion phase 0 (else EDUPIC_ESTATE).  out_blocks[0..1]
- * and out_ms_per_step (host, may be NULL) receive the grids in use and the
- * trial time per step of the faster mode. */
+/* Launch shapes of the particle kernel: EDUPIC_PUSH_SHAPES compiled
+ * variants that differ in threads per block, tile-ring stages and the
+ * blocks per SM their register budget targets; every shape gives the same
+ * particles, densities, counters and histograms.  edupic_set_push_shape
+ * selects shape 0..EDUPIC_PUSH_SHAPES-1 for one species (EDUPIC_EINVAL if
+ * out of range or if it does not fit the object's grid size and tables);
+ * edupic_get_push_shape writes the shapes in use (out[0..1], host memory);
+ * edupic_describe_push_shape writes a shape's threads per block, ring
+ * stages and targeted blocks per SM (pointers may be NULL). */
+#define EDUPIC_PUSH_SHAPES 4
+int edupic_set_push_shape(edupic_sim *sim, int species, int shape);
+int edupic_get_push_shape(edupic_sim *sim, int out[2]);
+int edupic_describe_push_shape(int precision, int shape, int *threads, int *stages, int *min_blocks);
+
+/* Autotuner of the launch (block and tile sizes picked by timing).  First,
+ * every launch shape that fits is run for `subcycles` ion subcycles launch
+ * by launch with an event pair around each particle-kernel launch, and each
+ * species keeps the shape of its fastest mean launch.  Then it times
+ * `subcycles` ion subcycles replayed through one CUDA graph per ion
+ * subcycle against the same launched kernel by kernel, and keeps the faster
+ * stepping mode.  Results are identical for every choice.  The trial steps
+ * are real simulation steps (the simulation advances by
+ * (fitting shapes + 2) x (subcycles + 1) ion subcycles, measured if
+ * `measure`); call it at the start of a run, at ion phase 0 (else
+ * EDUPIC_ESTATE).  out_blocks[0..1] and out_ms_per_step (host, may be NULL)
+ * receive the grids in use and the trial time per step of the faster
+ * mode. */
 int edupic_autotune(edupic_sim *sim, int subcycles, int measure, int out_blocks[2], double *out_ms_per_step);
 
 /* ---------------------------------------------------------------- read-back (synchronising) */

@@ -393,19 +393,28 @@ int setup_grid(edupic_sim *S)
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return EDUPIC_ECUDA;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    sms = std::max(sms, 1);
+    const bool f32 = S->precision == EDUPIC_FP32;
     for (int sp = 0; sp < 2; ++sp) {
         const int eb = sp == 0 ? S->eepf_max : 0;
-        for (int xt = 0; xt < 2; ++xt) {
-            const size_t smem = S->precision == EDUPIC_FP32 ? Launch<float>::push_smem(S->nd, S->ng_max, eb, xt)
-                                                            : Launch<double>::push_smem(S->nd, S->ng_max, eb, xt);
-            const int nb = S->precision == EDUPIC_FP32 ? Launch<float>::push_blocks_per_sm(sp, smem, xt)
-                                                       : Launch<double>::push_blocks_per_sm(sp, smem, xt);
-            if (nb < 1 && (!xt || S->xt_any)) return EDUPIC_ECUDA;
-            (xt ? S->grid_xt[sp] : S->grid[sp]) = std::max(nb, 0) * std::max(sms, 1);
+        for (int sh = 0; sh < kPushShapeCount; ++sh) {
+            const size_t smem = f32 ? Launch<float>::push_smem(S->nd, S->ng_max, eb, 0, sh)
+                                    : Launch<double>::push_smem(S->nd, S->ng_max, eb, 0, sh);
+            const int nb = f32 ? Launch<float>::push_blocks_per_sm(sp, smem, 0, sh)
+                               : Launch<double>::push_blocks_per_sm(sp, smem, 0, sh);
+            S->grid_shape[sp][sh] = std::max(nb, 0) * sms;
         }
-        S->grid_max[sp] = S->grid[sp];
+        if (S->grid_shape[sp][0] < 1) return EDUPIC_ECUDA;  // the default shape must fit
+        if (S->grid_shape[sp][S->shape[sp]] < 1) S->shape[sp] = 0;
+        const size_t smem_xt = f32 ? Launch<float>::push_smem(S->nd, S->ng_max, eb, 1, 0)
+                                   : Launch<double>::push_smem(S->nd, S->ng_max, eb, 1, 0);
+        const int nb_xt = f32 ? Launch<float>::push_blocks_per_sm(sp, smem_xt, 1, 0)
+                              : Launch<double>::push_blocks_per_sm(sp, smem_xt, 1, 0);
+        if (nb_xt < 1 && S->xt_any) return EDUPIC_ECUDA;
+        S->grid_xt[sp] = std::max(nb_xt, 0) * sms;
+        S->grid[sp] = S->grid_max[sp] = S->grid_shape[sp][S->shape[sp]];
     }
-    S->sms = std::max(sms, 1);
+    S->sms = sms;
     return EDUPIC_OK;
 }
 
@@ -418,10 +427,10 @@ template <typename T>
 int launch_step(edupic_sim *S, bool ion, int measure)
 {
     cudaError_t e = Launch<T>::push(S->d_desc, S->nd, 0, measure, push_grid(S, 0, measure), S->ng_max,
-                                    S->eepf_max, S->null_any[0], xt_on(S, measure), S->stream);
+                                    S->eepf_max, S->null_any[0], xt_on(S, measure), S->shape[0], S->stream);
     if (e == cudaSuccess && ion)
         e = Launch<T>::push(S->d_desc, S->nd, 1, measure, push_grid(S, 1, measure), S->ng_max,
-                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->stream);
+                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->shape[1], S->stream);
     if (e == cudaSuccess) e = Launch<T>::finalize(S->d_desc, S->nd, ion ? 1 : 0, measure, S->stream);
     return cuda_status(e);
 }
@@ -1004,21 +1013,21 @@ int edupic_profile_steps(edupic_sim *S, int64_t n_steps, int measure, double out
             if (S->precision == EDUPIC_FP32) {
                 if (e == cudaSuccess)
                     e = Launch<float>::push(S->d_desc, S->nd, 0, measure, push_grid(S, 0, measure), S->ng_max,
-                                            S->eepf_max, S->null_any[0], xt_on(S, measure), S->stream);
+                                            S->eepf_max, S->null_any[0], xt_on(S, measure), S->shape[0], S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[1], S->stream);
                 if (e == cudaSuccess && ion[i])
                     e = Launch<float>::push(S->d_desc, S->nd, 1, measure, push_grid(S, 1, measure), S->ng_max,
-                                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->stream);
+                                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->shape[1], S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[2], S->stream);
                 if (e == cudaSuccess) e = Launch<float>::finalize(S->d_desc, S->nd, ion[i], measure, S->stream);
             } else {
                 if (e == cudaSuccess)
                     e = Launch<double>::push(S->d_desc, S->nd, 0, measure, push_grid(S, 0, measure), S->ng_max,
-                                            S->eepf_max, S->null_any[0], xt_on(S, measure), S->stream);
+                                            S->eepf_max, S->null_any[0], xt_on(S, measure), S->shape[0], S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[1], S->stream);
                 if (e == cudaSuccess && ion[i])
                     e = Launch<double>::push(S->d_desc, S->nd, 1, measure, push_grid(S, 1, measure), S->ng_max,
-                                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->stream);
+                                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->shape[1], S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[2], S->stream);
                 if (e == cudaSuccess) e = Launch<double>::finalize(S->d_desc, S->nd, ion[i], measure, S->stream);
             }
@@ -1068,20 +1077,85 @@ int edupic_get_push_grid(edupic_sim *S, int out[2])
     return EDUPIC_OK;
 }
 
+// Make shape sh the particle kernel's launch shape for species sp.
+static void select_shape(edupic_sim *S, int sp, int sh)
+{
+    if (S->shape[sp] == sh && S->grid[sp] == S->grid_shape[sp][sh]) return;
+    S->shape[sp] = sh;
+    S->grid[sp] = S->grid_max[sp] = S->grid_shape[sp][sh];
+    S->drop_graphs();  // captured launches carry the shape and grid
+}
+
+int edupic_set_push_shape(edupic_sim *S, int species, int shape)
+{
+    if (!S || (species != 0 && species != 1) || shape < 0 || shape >= kPushShapeCount) return EDUPIC_EINVAL;
+    if (S->grid_shape[species][shape] < 1) return EDUPIC_EINVAL;  // does not fit this object's limits
+    select_shape(S, species, shape);
+    return EDUPIC_OK;
+}
+
+int edupic_get_push_shape(edupic_sim *S, int out[2])
+{
+    if (!S || !out) return EDUPIC_EINVAL;
+    out[0] = S->shape[0];
+    out[1] = S->shape[1];
+    return EDUPIC_OK;
+}
+
+int edupic_describe_push_shape(int precision, int shape, int *threads, int *stages, int *min_blocks)
+{
+    if ((precision != EDUPIC_FP64 && precision != EDUPIC_FP32) || shape < 0 || shape >= kPushShapeCount)
+        return EDUPIC_EINVAL;
+    const PushShape p = push_shape_of(precision == EDUPIC_FP64, shape);
+    if (threads) *threads = p.threads;
+    if (stages) *stages = p.stages;
+    if (min_blocks) *min_blocks = p.min_blocks;
+    return EDUPIC_OK;
+}
+
 int edupic_autotune(edupic_sim *S, int subcycles, int measure, int out_blocks[2], double *out_ms_per_step)
 {
     if (!S || subcycles < 1) return EDUPIC_EINVAL;
     if (!S->cs_set[0] || !S->cs_set[1]) return EDUPIC_ESTATE;
     if (S->phase != 0) return EDUPIC_ESTATE;  // trials are whole ion subcycles
-    // candidates: step replay through one CUDA graph per ion subcycle, or
-    // launch by launch (both at the resident grid); results are identical
+    const int64_t steps = (int64_t)subcycles * S->nsub;
+    int rc = EDUPIC_OK;
+    // 1. launch shape of each species' particle kernel: every shape that fits
+    // is timed on the live workload with an event pair around each launch
+    // (both species in the same trial, each kernel on its own events); the
+    // fastest mean launch per species is kept
+    const int keep_shape[2] = {S->shape[0], S->shape[1]};
+    int best_sh[2] = {keep_shape[0], keep_shape[1]};
+    double best_t[2] = {-1.0, -1.0};
+    for (int sh = 0; sh < kPushShapeCount && rc == EDUPIC_OK; ++sh) {
+        bool fits[2];
+        for (int sp = 0; sp < 2; ++sp) {
+            fits[sp] = S->grid_shape[sp][sh] > 0;
+            if (fits[sp]) select_shape(S, sp, sh);
+        }
+        if (!fits[0] && !fits[1]) continue;
+        double ms[3];
+        int64_t cnt[3];
+        rc = edupic_profile_steps(S, S->nsub, measure, ms, cnt);  // warm
+        if (rc == EDUPIC_OK) rc = edupic_profile_steps(S, steps, measure, ms, cnt);
+        for (int sp = 0; sp < 2 && rc == EDUPIC_OK; ++sp) {
+            if (!fits[sp] || cnt[sp] < 1) continue;
+            const double t = ms[sp] / (double)cnt[sp];
+            if (best_t[sp] < 0.0 || t < best_t[sp]) {
+                best_t[sp] = t;
+                best_sh[sp] = sh;
+            }
+        }
+    }
+    for (int sp = 0; sp < 2; ++sp) select_shape(S, sp, rc ? keep_shape[sp] : best_sh[sp]);
+    if (rc) return rc;
+    // 2. stepping mode: replay through one CUDA graph per ion subcycle, or
+    // launch by launch (results are identical)
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return EDUPIC_ECUDA;
-    const int64_t steps = (int64_t)subcycles * S->nsub;
     const bool keep = S->graphs;
     bool best = keep;
     double best_ms = -1.0;
-    int rc = EDUPIC_OK;
     for (int c = 0; c < 2 && rc == EDUPIC_OK; ++c) {
         const bool graphs = c == 0;
         S->graphs = graphs;

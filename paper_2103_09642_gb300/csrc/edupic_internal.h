@@ -7,15 +7,34 @@
 
 namespace edupic {
 
-constexpr int kThreads = 256;          // particle-kernel block size
 constexpr int kFinalizeThreads = 512;  // one CTA per discharge for compaction + field solve
 constexpr int kGroupA = 128;           // finalize threads doing compaction and append
 constexpr int kGroupB = kFinalizeThreads - kGroupA;  // finalize threads doing the field solve
 constexpr int kEvents = EDUPIC_STEP_EVENTS;
+constexpr int kPushShapeCount = EDUPIC_PUSH_SHAPES;  // launch shapes of the particle kernel the autotuner chooses among
 constexpr int kSortShared = 8192;      // event lists up to this size are sorted in shared memory
 constexpr int kCoarse = 2048;          // entries of the coarse sigma_max tables (shared memory)
 constexpr int kEepfStripes = 16;       // copies of the EEPF histogram the particle kernel spreads its atomics over
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // limit of every bounded device wait (1 s)
+
+// Launch shapes of the particle kernel: threads per block, tiles in the
+// shared-memory ring, and the blocks per SM the register budget is set for
+// (__launch_bounds__).  The autotuner times the shapes on the live workload;
+// every shape gives the same results (the arithmetic of a slot does not
+// depend on which block or warp takes it, and deposition is exact).  A tile
+// is threads x VEC particles (VEC = one Philox block's test uniforms per
+// thread: 4 in FP32, 2 in FP64); tiles stay within the 1024-particle
+// padding of the particle arrays.
+struct PushShape {
+    int threads, stages, min_blocks;
+};
+__host__ __device__ constexpr PushShape push_shape_of(bool f64, int s)
+{
+    return f64 ? (s == 0 ? PushShape{256, 3, 2} : s == 1 ? PushShape{256, 2, 2}
+                  : s == 2 ? PushShape{128, 3, 3} : PushShape{128, 2, 4})
+               : (s == 0 ? PushShape{256, 4, 2} : s == 1 ? PushShape{256, 3, 2}
+                  : s == 2 ? PushShape{128, 3, 4} : PushShape{256, 2, 3});
+}
 
 // Device error bits (ctrl->error).
 enum : int {
@@ -120,14 +139,16 @@ struct Launch {
     static cudaError_t seed(const DischargeDev *dd, int d, int species, long long n, cudaStream_t st);
     static cudaError_t fields(const DischargeDev *dd, int nd, int d, cudaStream_t st);
     static cudaError_t averages(const DischargeDev *dd, int nd, int d, cudaStream_t st);
-    // xt: the instantiation that accumulates the xt diagnostics (measured steps)
+    // xt: the instantiation that accumulates the xt diagnostics (measured steps);
+    // shape: launch shape of the others (0..kPushShapes-1, see push_shape)
     static cudaError_t push(const DischargeDev *dd, int nd, int species, int measure, int grid, int ng_max,
-                            int eepf_max, int null_any, int xt, cudaStream_t st);
+                            int eepf_max, int null_any, int xt, int shape, cudaStream_t st);
     static cudaError_t finalize(const DischargeDev *dd, int nd, int ion_step, int measure, cudaStream_t st);
     // one block waiting on a barrier that is never armed, for limit_ns (sets kErrTimeout in *err)
     static cudaError_t wait_expiry(unsigned long long limit_ns, int *err, cudaStream_t st);
-    static size_t push_smem(int nd, int ng_max, int eepf_max, int xt);
-    static int push_blocks_per_sm(int species, size_t smem, int xt);
+    static size_t push_smem(int nd, int ng_max, int eepf_max, int xt, int shape);
+    static int push_blocks_per_sm(int species, size_t smem, int xt, int shape);
+    static int push_threads(int xt, int shape);
 };
 
 }  // namespace edupic

@@ -151,25 +151,29 @@ __device__ __forceinline__ unsigned long long split_q2(float c2)
 
 // Per-block deposition accumulator in shared memory.  A particle in cell p
 // adds q1 = 2^32 - q2 to point p and q2 to point p+1; the block keeps, per
-// cell, the count and the sum of q2 in two 16-bit halves (32-bit shared
-// atomics), and forms Q_p = 2^32 cnt_p - S_p + S_{p-1} when it flushes.  The
-// halves cannot overflow while a cell holds fewer than 65536 particles of
-// one flush (the kernel flushes every kDepFlush particles).
+// cell, one 64-bit word with the deposit count in bits 48-63 and the sum S_p
+// of q2 in bits 0-47 (one 64-bit shared atomic per deposit), and forms
+// Q_p = 2^32 cnt_p - S_p + S_{p-1} when it flushes.  Neither field can
+// overflow while a cell takes fewer than 2^16 deposits between flushes: the
+// kernel flushes every kDepFlush particles, and a flush interval holds at
+// most kDepFlush + one tile particles plus one ionisation product each and
+// the products of the colliders still queued (< 2^16 deposits, so
+// S_p < 2^16 * 2^32 = 2^48).
 struct DepAcc {
-    unsigned int *cnt, *lo, *hi;
+    unsigned long long *w;
 };
-constexpr int kDepFlush = 30000;
+constexpr int kDepFlush = 28000;
+constexpr unsigned long long kDepCount = 1ull << 48;
 
 __device__ __forceinline__ void dep_add(const DepAcc &a, int p, unsigned long long q2)
 {
-    atomicAdd(a.cnt + p, 1u);
-    atomicAdd(a.lo + p, (unsigned int)(q2 & 0xFFFFull));
-    atomicAdd(a.hi + p, (unsigned int)(q2 >> 16));
+    atomicAdd(a.w + p, kDepCount + q2);
 }
 
+__device__ __forceinline__ unsigned long long dep_cnt(const DepAcc &a, int p) { return a.w[p] >> 48; }
 __device__ __forceinline__ unsigned long long dep_sum(const DepAcc &a, int p)  // S_p
 {
-    return (unsigned long long)a.lo[p] + ((unsigned long long)a.hi[p] << 16);
+    return a.w[p] & (kDepCount - 1);
 }
 
 // Nearest cross-section bin (Algorithm 6).
@@ -737,23 +741,33 @@ __device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy,
 }
 
 // ---------------------------------------------------------------- particle kernel
-// Tiles in the shared-memory ring: 4 in FP32 (16 KB each), 3 in FP64 (also
-// 16 KB each), so that two blocks fit an SM in both modes.
-template <typename T, bool XT>
-__host__ __device__ constexpr int ring_stages()
+// Launch shapes (push_shape_of): the xt-accumulating variant has a shape of
+// its own, whose fourth FP32 stage's room holds the xt sums.
+template <typename T>
+__host__ __device__ constexpr PushShape push_shape(int s)
 {
-    return (is_f64<T>() || XT) ? 3 : 4;  // the xt accumulators take the fourth FP32 stage's room
+    return push_shape_of(is_f64<T>(), s);
+}
+template <typename T>
+__host__ __device__ constexpr PushShape push_shape_xt()
+{
+    return PushShape{256, 3, 2};
+}
+template <typename T, bool XT, int SH>
+__host__ __device__ constexpr PushShape shape_of()
+{
+    return XT ? push_shape_xt<T>() : push_shape<T>(SH);
 }
 
 // Dynamic shared memory: [tile ring: stages x 4 arrays x TILE T][coarse
-// sigma_max: kCoarse T][E pairs: ng_max T2][deposition: 3 x ng_max u32]
+// sigma_max: kCoarse T][E pairs: ng_max T2][deposition: ng_max u64]
 // [tile prefix: nd+1 int][xt variant, from the next 16-byte boundary: sum
 // w v_c,x and sum w eps_c, ng_max T each].
-template <typename T, bool XT>
+template <typename T, bool XT, int SH>
 __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eepf_max)
 {
-    return (size_t)ring_stages<T, XT>() * 4 * kThreads * VecOf<T>::n * sizeof(T) + (size_t)kCoarse * sizeof(T) +
-           (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 12 + (size_t)(nd + 1) * 4 +
+    return (size_t)shape_of<T, XT, SH>().stages * 4 * shape_of<T, XT, SH>().threads * VecOf<T>::n * sizeof(T) +
+           (size_t)kCoarse * sizeof(T) + (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 8 + (size_t)(nd + 1) * 4 +
            (XT ? 16 + (size_t)ng_max * 2 * sizeof(T) : 0) + 0 * (size_t)eepf_max;
 }
 
@@ -762,26 +776,26 @@ __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eep
 // variant carries none of its code).
 // XT: the variant that also accumulates the xt diagnostics of the measured
 // steps (launched only for measured steps of a simulation that keeps them).
-template <typename T, int SP, bool NC, bool XT>
-__global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BLOCKS)
+template <typename T, int SP, bool NC, bool XT, int SH>
+__global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT, SH>().min_blocks)
     k_push(const DischargeDev *__restrict__ DD, int nd, int ng_max, int eepf_max, int measure)
 {
     using V = typename VecOf<T>::type;
     using T2 = typename VecOf<T>::pair;
     constexpr int VEC = VecOf<T>::n;  // slots per thread: one Philox test block
-    constexpr int TILE = kThreads * VEC;
-    constexpr int S = ring_stages<T, XT>();
-    constexpr int kWarps = kThreads / 32;
+    constexpr int NTHR = shape_of<T, XT, SH>().threads;
+    constexpr int TILE = NTHR * VEC;
+    constexpr int S = shape_of<T, XT, SH>().stages;
+    constexpr int kWarps = NTHR / 32;
+    static_assert(TILE <= 1024 && 1024 % TILE == 0, "tiles stay inside the particle arrays' padding");
     static_assert(kWarpQueue >= 2 * 32 * VEC, "a warp queue takes at least two tiles of colliders");
     extern __shared__ __align__(128) unsigned char smem[];
     T *sRing = reinterpret_cast<T *>(smem);  // [stage][array x, vx, vy, vz][TILE]
     T *sC = sRing + S * 4 * TILE;
     T2 *sE2 = reinterpret_cast<T2 *>(sC + kCoarse);
     DepAcc acc;
-    acc.cnt = reinterpret_cast<unsigned int *>(sE2 + ng_max);
-    acc.lo = acc.cnt + ng_max;
-    acc.hi = acc.lo + ng_max;
-    int *sPre = reinterpret_cast<int *>(acc.hi + ng_max);
+    acc.w = reinterpret_cast<unsigned long long *>(sE2 + ng_max);
+    int *sPre = reinterpret_cast<int *>(acc.w + ng_max);
     // xt variant: sum w v_c,x and sum w eps_c of the block, per grid point, on a
     // 16-byte boundary after the prefix (whose end is 4-byte aligned only)
     T *sXv = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(sPre + nd + 1) + 15) & ~(uintptr_t)15);
@@ -886,7 +900,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         __syncthreads();
         long long *accq = SP == 0 ? D->acc_e : D->acc_i;
         for (int p = tid; p < ng; p += blockDim.x) {
-            const unsigned long long q = ((unsigned long long)acc.cnt[p] << 32) - dep_sum(acc, p) +
+            const unsigned long long q = (dep_cnt(acc, p) << 32) - dep_sum(acc, p) +
                                          (p > 0 ? dep_sum(acc, p - 1) : 0ull);
             if (q) atomicAdd(reinterpret_cast<unsigned long long *>(accq + p), q);
             if constexpr (XT) {
@@ -900,7 +914,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
         if (!clear) return;
         __syncthreads();
         for (int p = tid; p < ng; p += blockDim.x) {
-            acc.cnt[p] = acc.lo[p] = acc.hi[p] = 0u;
+            acc.w[p] = 0ull;
             if constexpr (XT) sXv[p] = sXe[p] = (T)0;
         }
         __syncthreads();
@@ -1019,7 +1033,7 @@ __global__ void __launch_bounds__(kThreads, is_f64<T>() ? 2 : EDUPIC_PUSH_MIN_BL
             const T *ef = reinterpret_cast<const T *>(D->ef_t);
             for (int p = tid; p < ng; p += blockDim.x) {
                 sE2[p] = T2{ef[p], p + 1 < ng ? ef[p + 1] : (T)0};
-                acc.cnt[p] = acc.lo[p] = acc.hi[p] = 0u;
+                acc.w[p] = 0ull;
                 if constexpr (XT) sXv[p] = sXe[p] = (T)0;
             }
             since_flush = 0;

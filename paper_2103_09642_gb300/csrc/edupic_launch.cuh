@@ -1,35 +1,63 @@
 // Launchers for one particle precision; included by kernels_f32.cu and
 // kernels_f64.cu, which differ only in T and in their compile flags.
 #pragma once
+#include <type_traits>
+
 #include "edupic_kernels.cuh"
 
 namespace edupic {
 
-template <typename T>
-size_t Launch<T>::push_smem(int nd, int ng_max, int eepf_max, int xt)
+// Calls f(std::integral_constant<int, SH>{}) for the run-time shape index sh.
+template <typename F>
+static auto with_shape(int sh, F f)
 {
-    return xt ? push_smem_bytes<T, true>(nd, ng_max, eepf_max) : push_smem_bytes<T, false>(nd, ng_max, eepf_max);
+    switch (sh) {
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 3: return f(std::integral_constant<int, 3>{});
+    default: return f(std::integral_constant<int, 0>{});
+    }
+}
+static_assert(kPushShapeCount == 4, "with_shape covers every shape");
+
+template <typename T>
+size_t Launch<T>::push_smem(int nd, int ng_max, int eepf_max, int xt, int shape)
+{
+    if (xt) return push_smem_bytes<T, true, 0>(nd, ng_max, eepf_max);
+    return with_shape(shape, [&](auto sh) { return push_smem_bytes<T, false, decltype(sh)::value>(nd, ng_max, eepf_max); });
 }
 
-// Resident blocks per SM of the particle kernel of one species: the smaller of
-// its direct-test and null-collision instantiations (one grid serves both),
-// for the plain (xt = 0) or the xt-accumulating pair.
-template <typename T, int SP, bool XT>
+// Resident blocks per SM of the particle kernel of one species and shape:
+// the smaller of its direct-test and null-collision instantiations (one
+// grid serves both), for the plain (xt = 0) or the xt-accumulating pair.
+template <typename T, int SP, bool XT, int SH>
 int blocks_per_sm(size_t smem)
 {
+    constexpr int nthr = shape_of<T, XT, SH>().threads;
     int a = 0, b = 0;
-    cudaFuncSetAttribute(k_push<T, SP, false, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    cudaFuncSetAttribute(k_push<T, SP, true, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_push<T, SP, false, XT>, kThreads, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_push<T, SP, true, XT>, kThreads, smem);
+    cudaFuncSetAttribute(k_push<T, SP, false, XT, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_push<T, SP, true, XT, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_push<T, SP, false, XT, SH>, nthr, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_push<T, SP, true, XT, SH>, nthr, smem);
     return e == cudaSuccess ? (a < b ? a : b) : -1;
 }
 
 template <typename T>
-int Launch<T>::push_blocks_per_sm(int species, size_t smem, int xt)
+int Launch<T>::push_blocks_per_sm(int species, size_t smem, int xt, int shape)
 {
-    if (species == 0) return xt ? blocks_per_sm<T, 0, true>(smem) : blocks_per_sm<T, 0, false>(smem);
-    return xt ? blocks_per_sm<T, 1, true>(smem) : blocks_per_sm<T, 1, false>(smem);
+    if (xt) return species == 0 ? blocks_per_sm<T, 0, true, 0>(smem) : blocks_per_sm<T, 1, true, 0>(smem);
+    return with_shape(shape, [&](auto sh) {
+        constexpr int SH = decltype(sh)::value;
+        return species == 0 ? blocks_per_sm<T, 0, false, SH>(smem) : blocks_per_sm<T, 1, false, SH>(smem);
+    });
+}
+
+template <typename T>
+int Launch<T>::push_threads(int xt, int shape)
+{
+    if (xt) return push_shape_xt<T>().threads;
+    return push_shape<T>(shape).threads;
 }
 
 template <typename T>
@@ -82,27 +110,31 @@ static cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cuda
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <typename T, int SP, bool XT>
+template <typename T, int SP, bool XT, int SH>
 cudaError_t push_variant(const DischargeDev *dd, int nd, int measure, int grid, int ng_max, int eb, int null_any,
                          size_t smem, cudaStream_t st)
 {
-    return null_any ? launch_pdl(k_push<T, SP, true, XT>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, eb,
+    constexpr int nthr = shape_of<T, XT, SH>().threads;
+    return null_any ? launch_pdl(k_push<T, SP, true, XT, SH>, dim3(grid), dim3(nthr), smem, st, dd, nd, ng_max, eb,
                                  measure)
-                    : launch_pdl(k_push<T, SP, false, XT>, dim3(grid), dim3(kThreads), smem, st, dd, nd, ng_max, eb,
+                    : launch_pdl(k_push<T, SP, false, XT, SH>, dim3(grid), dim3(nthr), smem, st, dd, nd, ng_max, eb,
                                  measure);
 }
 
 template <typename T>
 cudaError_t Launch<T>::push(const DischargeDev *dd, int nd, int species, int measure, int grid, int ng_max,
-                            int eepf_max, int null_any, int xt, cudaStream_t st)
+                            int eepf_max, int null_any, int xt, int shape, cudaStream_t st)
 {
     const int eb = species == 0 && measure ? eepf_max : 0;
-    const size_t smem = push_smem(nd, ng_max, eb, xt);
-    if (species == 0)
-        return xt ? push_variant<T, 0, true>(dd, nd, measure, grid, ng_max, eb, null_any, smem, st)
-                  : push_variant<T, 0, false>(dd, nd, measure, grid, ng_max, eb, null_any, smem, st);
-    return xt ? push_variant<T, 1, true>(dd, nd, measure, grid, ng_max, 0, null_any, smem, st)
-              : push_variant<T, 1, false>(dd, nd, measure, grid, ng_max, 0, null_any, smem, st);
+    const size_t smem = push_smem(nd, ng_max, eb, xt, shape);
+    if (xt)
+        return species == 0 ? push_variant<T, 0, true, 0>(dd, nd, measure, grid, ng_max, eb, null_any, smem, st)
+                            : push_variant<T, 1, true, 0>(dd, nd, measure, grid, ng_max, 0, null_any, smem, st);
+    return with_shape(shape, [&](auto sh) {
+        constexpr int SH = decltype(sh)::value;
+        return species == 0 ? push_variant<T, 0, false, SH>(dd, nd, measure, grid, ng_max, eb, null_any, smem, st)
+                            : push_variant<T, 1, false, SH>(dd, nd, measure, grid, ng_max, 0, null_any, smem, st);
+    });
 }
 
 template <typename T>

@@ -53,6 +53,7 @@ class Heap {
     }
     void release(size_t off, size_t n)
     {
+        used_ -= std::min(used_, n);  // the block's own size, before it merges with free neighbours
         auto next = free_.lower_bound(off);
         if (next != free_.begin()) {
             auto prev = std::prev(next);
@@ -67,7 +68,6 @@ class Heap {
             free_.erase(next);
         }
         free_[off] = n;
-        used_ -= std::min(used_, n);
     }
     size_t size() const { return size_; }
     size_t used() const { return used_; }

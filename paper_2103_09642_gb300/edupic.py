@@ -133,6 +133,10 @@ def load_library(path: str = LIB_PATH):
         "edupic_profile_steps": ([_VP, ctypes.c_int64, ctypes.c_int, _D, _Q]),
         "edupic_set_push_grid": ([_VP, ctypes.c_int, ctypes.c_int]),
         "edupic_get_push_grid": ([_VP, ctypes.POINTER(ctypes.c_int)]),
+        "edupic_set_push_shape": ([_VP, ctypes.c_int, ctypes.c_int]),
+        "edupic_get_push_shape": ([_VP, ctypes.POINTER(ctypes.c_int)]),
+        "edupic_describe_push_shape": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "edupic_autotune": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]),
         "edupic_check_accuracy": ([_VP, ctypes.c_int, ctypes.POINTER(Accuracy)]),
         "edupic_get_power": ([_VP, ctypes.c_int, _D]),
@@ -289,6 +293,17 @@ class Simulation:
         _ck(self.L.edupic_get_push_grid(self._h, g), "get_push_grid")
         return g[0], g[1]
 
+    def set_push_shape(self, species: int, shape: int):
+        _ck(self.L.edupic_set_push_shape(self._h, species, int(shape)), "set_push_shape")
+
+    def push_shape(self):
+        g = (ctypes.c_int * 2)()
+        _ck(self.L.edupic_get_push_shape(self._h, g), "get_push_shape")
+        return g[0], g[1]
+
+    def describe_push_shape(self, shape: int) -> dict:
+        return describe_push_shape(self.precision, shape)
+
     def autotune(self, subcycles: int = 5, measure: bool = False):
         """Pick graph replay or kernel-by-kernel stepping by timing (advances
         the simulation); returns (grid in use, trial ms per step)."""
@@ -408,6 +423,18 @@ class Simulation:
 
     def load_state(self, d: int, path: str):
         _ck(self.L.edupic_load_state(self._h, d, path.encode()), "load_state")
+
+
+PUSH_SHAPES = 4
+
+
+def describe_push_shape(precision: int, shape: int) -> dict:
+    """Threads per block, ring stages and targeted blocks per SM of a launch shape."""
+    L = load_library()
+    t, s, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _ck(L.edupic_describe_push_shape(precision, shape, ctypes.byref(t), ctypes.byref(s), ctypes.byref(m)),
+        "describe_push_shape")
+    return dict(threads=t.value, stages=s.value, min_blocks=m.value)
 
 
 def simulation_for(discharges: Iterable, precision: int = FP64, sigma=None, de_ev: float = 1e-3,

@@ -497,10 +497,10 @@ def test_autotune_keeps_results():
     parts = [(m[1], m[2]) for m in mix]
     ref = ed.simulation_for(ds, ed.FP32, sigma=(SE, SI), de_ev=DE, particles=parts)
     sim = ed.simulation_for(ds, ed.FP32, sigma=(SE, SI), de_ev=DE, particles=parts)
-    limit = sim.push_grid()
     grid, ms = sim.autotune(subcycles=2)
-    assert grid == limit[0] and ms > 0
-    n = 2 * (2 + 1) * ds[0].ion_subcycle  # the trial steps
+    assert grid == sim.push_grid()[0] and ms > 0
+    n = sim.counts(0)[2]  # the trial steps: every fitting shape, then the two stepping modes
+    assert n % ds[0].ion_subcycle == 0 and n >= 2 * (2 + 1) * ds[0].ion_subcycle
     ref.step(n + 40)
     sim.step(40)
     for k in range(len(ds)):
@@ -511,6 +511,42 @@ def test_autotune_keeps_results():
                 assert np.array_equal(a[c], b[c])
     sim.close()
     ref.close()
+
+
+@pytest.mark.parametrize("precision", [ed.FP32, ed.FP64])
+def test_every_launch_shape_gives_the_same_results(precision):
+    # the autotuner's candidates: particles, counters, densities and
+    # histograms bit for bit, power absorption to the rounding of its sums
+    mix = wl.batch_mix(n_discharges=5, seed0=330, scale=0.06)
+    ds = [m[0] for m in mix]
+    parts = [(m[1], m[2]) for m in mix]
+    runs = []
+    for shape in range(ed.PUSH_SHAPES):
+        sim = ed.simulation_for(ds, precision, sigma=(SE, SI), de_ev=DE, particles=parts)
+        try:
+            sim.set_push_shape(0, shape)
+            sim.set_push_shape(1, shape)
+        except ed.EdupicError:
+            sim.close()
+            continue
+        assert sim.push_shape() == (shape, shape)
+        sim.step(60)
+        sim.step(100, measure=True)
+        runs.append((shape, [(sim.counters(k), [sim.particles(k, sp) for sp in (0, 1)], sim.diagnostics(k),
+                              sim.power(k)) for k in range(len(ds))]))
+        sim.close()
+    assert len(runs) >= 3 and runs[0][0] == 0
+    base = runs[0][1]
+    for shape, res in runs[1:]:
+        for k in range(len(ds)):
+            assert res[k][0] == base[k][0], (shape, k)
+            for sp in (0, 1):
+                for c in range(4):
+                    assert np.array_equal(res[k][1][sp][c], base[k][1][sp][c]), (shape, k, sp, c)
+            for key in ("n_e", "n_i", "phi", "eepf_counts", "ifed_pow_counts", "ifed_gnd_counts"):
+                assert np.array_equal(res[k][2][key], base[k][2][key]), (shape, k, key)
+            for key in ("electrons", "ions"):
+                assert res[k][3][key] == pytest.approx(base[k][3][key], rel=1e-12, abs=1e-300), (shape, k, key)
 
 
 def test_checkpoint_resume_is_exact(tmp_path):

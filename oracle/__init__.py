@@ -55,7 +55,7 @@ class _Params(ctypes.Structure):
         ("ifed_bins", ctypes.c_int), ("ifed_de_ev", ctypes.c_double), ("capacity", ctypes.c_int64),
         ("e_exc_ev", ctypes.c_double), ("e_ion_ev", ctypes.c_double),
         ("see_gamma", ctypes.c_double * 2), ("refl_eta", ctypes.c_double * 2), ("see_te_ev", ctypes.c_double),
-        ("null_collision", ctypes.c_int), ("xt_bins", ctypes.c_int),
+        ("null_collision", ctypes.c_int), ("xt_bins", ctypes.c_int), ("sort_every", ctypes.c_int),
     ]
 
 
@@ -244,6 +244,7 @@ def _params(d) -> _Params:
     p.see_te_ev = d.see_te_ev
     p.null_collision = int(d.null_collision)
     p.xt_bins = int(d.xt_bins)
+    p.sort_every = int(d.sort_every)
     return p
 
 

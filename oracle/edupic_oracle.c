@@ -198,6 +198,9 @@ typedef struct {
     int null_collision;
     /* spatio-temporal diagnostics (Sec. 3.5): time bins per RF cycle, 0 = off */
     int xt_bins;
+    /* periodic cell sort of the particle arrays (not in the paper): every
+     * sort_every ion subcycles, 0 = off */
+    int sort_every;
 } orc_params;
 
 typedef struct {
@@ -587,7 +590,7 @@ orc_sim *orc_create(const orc_params *p)
 {
     if (p->n_grid < 3 || p->steps_per_cycle < 1 || p->ion_subcycle < 1 || p->n_harm < 0 || p->n_harm > ORC_MAX_HARM ||
         p->capacity < 1 || p->eepf_bins < 1 || p->ifed_bins < 1 || p->xt_bins < 0 ||
-        (p->xt_bins > 0 && p->steps_per_cycle % p->xt_bins != 0))
+        (p->xt_bins > 0 && p->steps_per_cycle % p->xt_bins != 0) || p->sort_every < 0)
         return NULL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     s->p = *p;
@@ -812,6 +815,49 @@ static void compact(orc_species *sp, const unsigned char *absorbed)
         ++src;
     }
     sp->n = nn;
+}
+
+/* Periodic cell sort (not part of the paper's method; the GPU build keeps
+ * particles of a cell together so that its block-local deposition and field
+ * gathers touch few cells).  Reading: after a step whose new index s is a
+ * multiple of sort_every * N_SUB, the particles of each species are put in
+ * ascending order of their cell p (the cell of the deposition, Algorithm 2),
+ * keeping the order of the slots within a cell (a stable sort).  The slot of
+ * a particle, and with it the counter of its random numbers, follows the new
+ * order.  A counting sort: the cell histogram, its exclusive prefix sum as
+ * the first slot of each cell, then one pass in slot order. */
+static void sort_species(orc_sim *s, orc_species *sp)
+{
+    const int ng = s->p.n_grid;
+    const int64_t n = sp->n;
+    if (n < 2) return;
+    int64_t *first = (int64_t *)calloc((size_t)ng, sizeof(int64_t));
+    int *cellv = (int *)malloc(sizeof(int) * (size_t)n);
+    for (int64_t j = 0; j < n; ++j) {
+        int c;
+        double c0;
+        cell_of(sp->x[j], s->inv_dx, ng, &c, &c0);
+        cellv[j] = c;
+        first[c] += 1;
+    }
+    int64_t run = 0;
+    for (int c = 0; c < ng; ++c) {
+        const int64_t h = first[c];
+        first[c] = run;
+        run += h;
+    }
+    double *a[4] = {sp->x, sp->vx, sp->vy, sp->vz};
+    for (int k = 0; k < 4; ++k) {
+        double *out = (double *)malloc(sizeof(double) * (size_t)n);
+        int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (size_t)ng);
+        memcpy(next, first, sizeof(int64_t) * (size_t)ng);
+        for (int64_t j = 0; j < n; ++j) out[next[cellv[j]]++] = a[k][j];
+        memcpy(a[k], out, sizeof(double) * (size_t)n);
+        free(out);
+        free(next);
+    }
+    free(first);
+    free(cellv);
 }
 
 /* Adds (c1 a, c2 a) to grid points (c, c+1) of time bin b of an xt array
@@ -1116,6 +1162,10 @@ static void one_step(orc_sim *s, int measure)
         if (ion_step) s->xt_steps[1][xb]++;
     }
     s->step++;
+    if (p->sort_every > 0 && s->step % ((int64_t)p->sort_every * p->ion_subcycle) == 0) {
+        sort_species(s, E);
+        sort_species(s, I);
+    }
 }
 
 int orc_step(orc_sim *s, int64_t n_steps, int measure)

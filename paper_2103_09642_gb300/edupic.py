@@ -51,7 +51,7 @@ class Params(ctypes.Structure):
         ("eepf_de_ev", ctypes.c_double), ("ifed_de_ev", ctypes.c_double),
         ("capacity_e", ctypes.c_int64), ("capacity_i", ctypes.c_int64),
         ("e_exc_ev", ctypes.c_double), ("e_ion_ev", ctypes.c_double),
-        ("cs_entries", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("cs_entries", ctypes.c_int32), ("sort_every", ctypes.c_int32),
         ("see_gamma", ctypes.c_double * 2), ("refl_eta", ctypes.c_double * 2), ("see_te_ev", ctypes.c_double),
         ("null_collision", ctypes.c_int32), ("xt_bins", ctypes.c_int32),
     ]
@@ -77,6 +77,7 @@ def to_params(d: Discharge, cs_entries: int) -> Params:
     p.see_te_ev = d.see_te_ev
     p.null_collision = int(d.null_collision)
     p.xt_bins = int(d.xt_bins)
+    p.sort_every = int(d.sort_every)
     return p
 
 

@@ -75,6 +75,9 @@ class Discharge:
     null_collision: int = 0
     # spatio-temporal diagnostics (Sec. 3.5): time bins per RF cycle, 0 = off
     xt_bins: int = 0
+    # periodic cell sort of the particle arrays (GPU locality, not in the
+    # paper): every sort_every ion subcycles, 0 = off
+    sort_every: int = 0
 
     def replace(self, **kw) -> "Discharge":
         return dataclasses.replace(self, **kw)

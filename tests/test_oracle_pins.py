@@ -936,3 +936,52 @@ def test_table_index_is_the_nearest_entry_ions_by_com_energy():
         s.step(1)
         c = s.counters()
         assert c["coll_i_iso"] == (n if expect_all else 0), frac
+
+
+# ------------------------------------------------------------------ periodic cell sort (slot order)
+def _cells(x, d):
+    # the cell of the deposition (Algorithm 2): floor(x / dx), the last cell taking x = L
+    dx = d.gap_m / (d.n_grid - 1)
+    return np.minimum(np.floor(x / dx).astype(np.int64), d.n_grid - 2)
+
+
+def _sort_pair(sort_every, steps):
+    d, e, i = wl.reference_start(seed=31, n0=3000)
+    se, si = wl.standin_cross_sections(300_000)
+    a = oracle.Sim(d.replace(sort_every=sort_every), se, si, wl.CS_DE_EV, e, i)
+    b = oracle.Sim(d, se, si, wl.CS_DE_EV, e, i)
+    a.step(steps)
+    b.step(steps)
+    return d, a, b
+
+
+def test_cell_sort_is_a_stable_counting_sort_by_cell():
+    # after the 20th step (one ion subcycle) the arrays are the unsorted run's
+    # arrays in numpy's stable order of their deposition cells
+    d, a, b = _sort_pair(1, 20)
+    for sp in (0, 1):
+        pa, pb = a.particles(sp), b.particles(sp)
+        order = np.argsort(_cells(pb[0], d), kind="stable")
+        for k in range(4):
+            assert np.array_equal(pa[k], pb[k][order]), (sp, k)
+        assert (np.diff(_cells(pa[0], d)) >= 0).all()
+    # the densities do not depend on the order
+    assert np.array_equal(a.prepare_fields()["q_e"], b.prepare_fields()["q_e"])
+    assert np.array_equal(a.prepare_fields()["q_i"], b.prepare_fields()["q_i"])
+
+
+def test_cell_sort_happens_only_every_sort_every_subcycles():
+    # sort_every = 2: nothing before step 40, sorted right after it
+    d, a, b = _sort_pair(2, 39)
+    for sp in (0, 1):
+        assert all(np.array_equal(u, v) for u, v in zip(a.particles(sp), b.particles(sp)))
+    a.step(1)
+    b.step(1)
+    pa, pb = a.particles(0), b.particles(0)
+    order = np.argsort(_cells(pb[0], d), kind="stable")
+    assert np.array_equal(pa[0], pb[0][order]) and not np.array_equal(pa[0], pb[0])
+    # after that, the sorted run draws other random numbers per particle
+    # (slots moved) but keeps the same particle count bookkeeping
+    a.step(20)
+    c = a.counters()
+    assert a.count(0) == 3000 - c["abs_e_pow"] - c["abs_e_gnd"] + c["created"]

@@ -109,7 +109,15 @@ typedef struct {
     double e_exc_ev;         /* lumped excitation threshold (11.5 eV for Ar) */
     double e_ion_ev;         /* ionisation threshold (15.8 eV for Ar) */
     int32_t cs_entries;      /* capacity of the cross-section tables (CS_RANGES), shared by the object */
-    int32_t reserved;
+    /* Periodic cell sort (no counterpart in the paper; the particle loop's
+     * memory locality): every sort_every ion subcycles (>= 0, 0 = off), after
+     * the step whose index s becomes a multiple of sort_every * N_SUB, each
+     * species is put in ascending order of its deposition cell floor(x/dx)
+     * (Algorithm 2), keeping the slot order within a cell.  Slots, and with
+     * them the random-number counters, follow the new order (the oracle
+     * applies the same permutation).  Needs a scratch copy of the larger
+     * species and one int per (2048-particle chunk, cell) in the arena. */
+    int32_t sort_every;
     /* Surface processes (Sec. 5), index 0 = powered electrode (x = 0), 1 =
      * grounded (x = L); all zero switches them off (the reference discharge):
      *  - see_gamma[s]: probability that an Ar+ reaching electrode s emits an

@@ -4,7 +4,8 @@ Five translation units are compiled in parallel and linked into
 ``paper_2103_09642_gb300/_build/libedupic_gb300.so``:
 
 * ``kernels_f64.cu``  FP64 particle mode, ``-fmad=false`` (no FMA contraction)
-* ``kernels_f32.cu``  FP32 particle mode, FMA and fast division allowed
+* ``kernels_f32.cu``  FP32 particle mode, fast division and square root; fused
+  multiply-adds only where the source writes them (every launch shape rounds alike)
 * ``edupic_api.cu``   host orchestration of the C ABI (``include/edupic.h``)
 * ``edupic_noalloc.cu``  the entry point that works in a fixed static scratch
 * ``edupic_server.cu``  the request server (continuous batching)
@@ -26,7 +27,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
           "-Xcompiler", "-fno-fast-math", "-Xcompiler", "-pthread"]
 UNITS = {
     "kernels_f64.cu": ["-fmad=false"],
-    "kernels_f32.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+    "kernels_f32.cu": ["-fmad=false", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "edupic_api.cu": ["-fmad=false"],
     "edupic_noalloc.cu": ["-fmad=false"],
     "edupic_server.cu": ["-fmad=false"],

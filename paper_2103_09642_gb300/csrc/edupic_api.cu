@@ -85,6 +85,11 @@ Layout layout_of(const edupic_params &p, size_t elem)
         L.xt_bytes = 9 * m * 8 + 4 * (size_t)p.xt_bins * 8;
         L.xt = take(L.xt_bytes);
     }
+    if (p.sort_every > 0) {
+        const long long cmax = std::max(cap[0], cap[1]);
+        L.sort_cnt = take((size_t)((cmax + kSortChunk - 1) / kSortChunk) * ng * 4);
+        for (int c = 0; c < 4; ++c) L.sort_tmp[c] = take((size_t)cmax * elem);
+    }
     L.emit = p.see_gamma[0] > 0.0 || p.see_gamma[1] > 0.0;
     if (L.emit) {
         L.emit_parent = take((size_t)kEvents * 4);
@@ -128,6 +133,7 @@ int check_params(int nd, const edupic_params *ps, int precision)
                 return EDUPIC_EINVAL;
         if (!(p.see_te_ev >= 0) || !(p.see_te_ev < 1e6)) return EDUPIC_EINVAL;
         if (p.null_collision < 0 || p.null_collision > 3) return EDUPIC_EINVAL;
+        if (p.sort_every < 0) return EDUPIC_EINVAL;
         if (p.xt_bins < 0 || (p.xt_bins > 0 && p.steps_per_cycle % p.xt_bins != 0) ||
             (int64_t)p.xt_bins * p.n_grid > (1 << 24))
             return EDUPIC_EINVAL;
@@ -305,6 +311,11 @@ void fill_desc(edupic_sim *S, int d)
         D.cs_shift[sp] = S->desc.size() > (size_t)d ? S->desc[d].cs_shift[sp] : 0;
     }
     D.vdrive = reinterpret_cast<const double *>(b + L.vdrive);
+    D.sort_every = p.sort_every;
+    if (p.sort_every > 0) {
+        D.sort_cnt = reinterpret_cast<unsigned int *>(b + L.sort_cnt);
+        for (int c = 0; c < 4; ++c) D.sort_tmp[c] = b + L.sort_tmp[c];
+    }
     if (S->desc.size() <= (size_t)d) S->desc.resize(d + 1);
     S->desc[d] = D;
     null_bounds(S, d);
@@ -331,6 +342,27 @@ void update_null_any(edupic_sim *S)
 void null_bounds(edupic_sim *S, int d)
 {
     DischargeDev &D = S->desc[d];
+    // Short cut of the direct test (Algorithm 6).  An energy rounds to the
+    // nearest entry k, so it lies below (k + 1/2) DE and its speed below v_k
+    // at that energy: n sigma_tot,k v <= n max_k(sigma_tot,k v_k) = nu_b, and
+    // P_coll <= 1 - exp(-nu_b dt), for every speed up to that of the last
+    // entry.  The bound is widened far beyond the rounding of either
+    // precision's test.  An Ar+ collides at its relative speed to a partner
+    // drawn by Box-Muller, whose speed is at most about 12.1 sigma_th (the
+    // largest normal the uniforms can give), so the ion's own speed must stay
+    // below the last entry's by 12.2 sigma_th.
+    for (int sp = 0; sp < 2; ++sp) {
+        const double m = sp == 0 ? kME : kArMassU * kAMU / 2.0;
+        const int n = S->sigsum_host[sp].empty() ? 0 : (int)S->sigsum_host[sp].size();
+        const double dt = sp == 0 ? D.dt_e : D.dt_i;
+        const double pb = 1.0 - std::exp(-D.n_gas * S->sigv_top[sp] * (1.0 + 1e-9) * dt);
+        double vtop = n ? std::sqrt(2.0 * ((n - 0.5) * S->cs_de_host[sp]) * kQE / m) : 0.0;
+        if (sp == 1) vtop -= 12.2 * D.sig_th;
+        D.tbound[sp] = n ? pb * (1.0 + 1e-9) + 1e-300 : 0.0;
+        D.tboundf[sp] = n ? (float)(pb * (1.0 + 2e-5) + 1e-6) : 0.0f;
+        D.v2lim[sp] = vtop > 0.0 ? vtop * vtop * (1.0 - 1e-9) : -1.0;
+        D.v2limf[sp] = vtop > 0.0 ? (float)(vtop * vtop * (1.0 - 1e-5)) : -1.0f;
+    }
     if (!D.null_coll) return;
     for (int sp = 0; sp < 2; ++sp) {
         const std::vector<double> &st = S->sigsum_host[sp];
@@ -435,9 +467,21 @@ int launch_step(edupic_sim *S, bool ion, int measure)
     return cuda_status(e);
 }
 
-int launch_one(edupic_sim *S, bool ion, int measure)
+cudaError_t launch_sort(edupic_sim *S);
+
+// One time step; `last` (the final step of an ion subcycle) adds the periodic
+// cell sort, which every discharge decides on from its own step count.
+int launch_one(edupic_sim *S, bool ion, int measure, bool last)
 {
-    return S->precision == EDUPIC_FP32 ? launch_step<float>(S, ion, measure) : launch_step<double>(S, ion, measure);
+    int rc = S->precision == EDUPIC_FP32 ? launch_step<float>(S, ion, measure) : launch_step<double>(S, ion, measure);
+    if (rc == EDUPIC_OK && last && S->sort_any) rc = cuda_status(launch_sort(S));
+    return rc;
+}
+
+cudaError_t launch_sort(edupic_sim *S)
+{
+    return S->precision == EDUPIC_FP32 ? Launch<float>::sort(S->d_desc, S->nd, S->ng_max, S->sms, S->stream)
+                                       : Launch<double>::sort(S->d_desc, S->nd, S->ng_max, S->sms, S->stream);
 }
 
 // One ion subcycle (N_SUB steps starting at phase 0) as a CUDA graph.
@@ -447,7 +491,7 @@ int build_graph(edupic_sim *S, int measure)
     cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return EDUPIC_ECUDA;
     int rc = EDUPIC_OK;
-    for (int k = 0; k < S->nsub && rc == EDUPIC_OK; ++k) rc = launch_one(S, k == 0, measure);
+    for (int k = 0; k < S->nsub && rc == EDUPIC_OK; ++k) rc = launch_one(S, k == 0, measure, k == S->nsub - 1);
     e = cudaStreamEndCapture(S->stream, &g);
     if (rc != EDUPIC_OK || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -812,6 +856,7 @@ int edupic_create(int nd, const edupic_params *params, int precision, void *devi
     for (int d = 0; d < nd; ++d) fill_desc(S, d);
     update_null_any(S);
     for (int d = 0; d < nd; ++d) S->xt_any |= params[d].xt_bins > 0 ? 1 : 0;
+    for (int d = 0; d < nd; ++d) S->sort_any |= params[d].sort_every > 0 ? 1 : 0;
     cudaError_t e = cudaMemsetAsync(S->arena, 0, need, S->stream);
     if (e != cudaSuccess) {
         delete S;
@@ -890,12 +935,16 @@ int edupic_set_cross_sections(edupic_sim *S, int species, int n_proc, int n_entr
         S->sigv_max[species] = best;
     }
     S->sigsum_host[species].resize((size_t)n_entries);
+    double top = 0.0;
     for (int k = 0; k < n_entries; ++k) {
         // processes summed in order from zero, as the collision test's table
         double st = 0.0;
         for (int q = 0; q < n_proc; ++q) st += sigma_m2[(size_t)q * n_entries + k];
         S->sigsum_host[species][(size_t)k] = st;
+        const double m = species == 0 ? kME : 0.5 * kArMassU * kAMU;
+        top = std::max(top, st * std::sqrt(2.0 * ((k + 0.5) * de_ev) * kQE / m));
     }
+    S->sigv_top[species] = top;
     S->cs_de_host[species] = de_ev;
     for (int d = 0; d < S->nd; ++d) null_bounds(S, d);
     S->cs_set[species] = true;
@@ -944,7 +993,7 @@ int edupic_step(edupic_sim *S, int64_t n_steps, int measure)
             i += S->nsub;
             continue;
         }
-        int rc = launch_one(S, S->phase == 0, measure);
+        int rc = launch_one(S, S->phase == 0, measure, S->phase == S->nsub - 1);
         if (rc) return rc;
         S->phase = (S->phase + 1) % S->nsub;
         ++i;
@@ -1031,6 +1080,7 @@ int edupic_profile_steps(edupic_sim *S, int64_t n_steps, int measure, double out
                 if (e == cudaSuccess) e = cudaEventRecord(E[2], S->stream);
                 if (e == cudaSuccess) e = Launch<double>::finalize(S->d_desc, S->nd, ion[i], measure, S->stream);
             }
+            if (e == cudaSuccess && S->sort_any && S->phase == S->nsub - 1) e = launch_sort(S);
             if (e == cudaSuccess) e = cudaEventRecord(E[3], S->stream);
             S->phase = (S->phase + 1) % S->nsub;
         }

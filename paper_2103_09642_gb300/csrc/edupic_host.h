@@ -25,6 +25,7 @@ struct Layout {
     size_t emit_parent, emit_x, emit_v[3];  // present only when an electrode emits (see_gamma > 0)
     bool emit;
     size_t xt, xt_bytes;  // xt diagnostics block (xt_bins > 0), zeroed as one
+    size_t sort_cnt, sort_tmp[4];  // periodic cell sort (sort_every > 0): chunk counts, scratch copy
     size_t bytes;
 };
 
@@ -63,10 +64,12 @@ struct edupic_sim {
     bool graphs = true;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     double sigv_max[2] = {0.0, 0.0};  // largest sigma_tot * v of each species' table
+    double sigv_top[2] = {0.0, 0.0};  // largest sigma_tot * v at the top of each entry's energy bin
     std::vector<double> sigsum_host[2];  // sum of the process cross sections per table entry (m^2)
     double cs_de_host[2] = {0.0, 0.0};
     int null_any[2] = {0, 0};  // some active discharge uses the null-collision method, per species
     int xt_any = 0;            // some discharge keeps xt diagnostics (the accumulating kernel variant)
+    int sort_any = 0;          // some discharge sorts its particles by cell (sort_every > 0)
     int grid_xt[2] = {0, 0};   // resident limit of the accumulating particle kernel
     std::vector<double> v_bias;  // DC voltage added at the powered electrode, per discharge (Sec. 5 self-bias)
     void *pinned = nullptr;  // page-locked staging buffer for particle uploads

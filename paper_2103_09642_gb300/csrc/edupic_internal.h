@@ -14,6 +14,7 @@ constexpr int kEvents = EDUPIC_STEP_EVENTS;
 constexpr int kPushShapeCount = EDUPIC_PUSH_SHAPES;  // launch shapes of the particle kernel the autotuner chooses among
 constexpr int kSortShared = 8192;      // event lists up to this size are sorted in shared memory
 constexpr int kCoarse = 2048;          // entries of the coarse sigma_max tables (shared memory)
+constexpr int kSortChunk = 2048;       // particles per chunk (one warp) of the periodic cell sort
 constexpr int kEepfStripes = 16;       // copies of the EEPF histogram the particle kernel spreads its atomics over
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // limit of every bounded device wait (1 s)
 
@@ -89,12 +90,20 @@ struct DischargeDev {
     float refl_etaf[2], see_gammaf[2], see_sthf;
     float p_starf[2];   // P* in FP32
     float null_ratf[2]; // n_gas / nu*: nu / nu* = sigsum v null_ratf
+    // exact short cut of the direct collision test, per species: with R the
+    // test uniform and v2 the particle's own squared speed, R >= tbound and
+    // v2 <= v2lim imply P_coll < R for every table entry and (Ar+) every
+    // partner the generator can draw, so the particle does not collide
+    double tbound[2], v2lim[2];
+    float tboundf[2], v2limf[2];
     double inv_2dx;
     double edge_c;     // e FACTOR_W * 2 / 2^32 * dx / (2 eps0): edge term of E from Q_i - Q_e
     int ng, nt, nsub, n_harm, eepf_bins, ifed_bins, cs_n_e, cs_n_i;
     int active;
     int null_coll;  // null-collision method: bit 0 electrons, bit 1 ions
     int nxt, nbin;  // xt diagnostics: time bins per cycle and steps per bin (nxt = 0: off)
+    int sort_every;  // periodic cell sort: every sort_every ion subcycles (0: off)
+    int pad_sort;
     long long stop_step;       // the discharge is frozen (skipped) once its step count reaches this
     long long cap[2];
     unsigned long long seed;
@@ -130,6 +139,10 @@ struct DischargeDev {
     const void *cs_max[2];     // T[kCoarse]: max of cs_sig over 2^cs_shift consecutive entries, rounded up
     int cs_shift[2];
     const double *vdrive;      // V(t) at the N_T steps of one cycle
+    // periodic cell sort (sort_every > 0): [chunk][ng] counts, then first
+    // slots, of kSortChunk-particle chunks; scratch copy of one species (T)
+    unsigned int *sort_cnt;
+    void *sort_tmp[4];
 };
 
 // Launchers implemented per precision (kernels_f32.cu / kernels_f64.cu).
@@ -146,6 +159,8 @@ struct Launch {
     static cudaError_t finalize(const DischargeDev *dd, int nd, int ion_step, int measure, cudaStream_t st);
     // one block waiting on a barrier that is never armed, for limit_ns (sets kErrTimeout in *err)
     static cudaError_t wait_expiry(unsigned long long limit_ns, int *err, cudaStream_t st);
+    // periodic cell sort of both species of every discharge due at its current step
+    static cudaError_t sort(const DischargeDev *dd, int nd, int ng_max, int sms, cudaStream_t st);
     static size_t push_smem(int nd, int ng_max, int eepf_max, int xt, int shape);
     static int push_blocks_per_sm(int species, size_t smem, int xt, int shape);
     static int push_threads(int xt, int shape);

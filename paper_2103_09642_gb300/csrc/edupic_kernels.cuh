@@ -58,6 +58,21 @@ __device__ __forceinline__ double2 pack(const double *a, double2) { return make_
 template <typename T>
 __host__ __device__ constexpr bool is_f64() { return std::is_same<T, double>::value; }
 
+// a * b + c.  FP32: one fused rounding (fmaf).  FP64: two roundings, the
+// plain CPU evaluation of the same expression (the FP64 kernels match the
+// oracle).  Both units are compiled without automatic contraction, so every
+// fused operation is one of these, and each launch shape of a kernel rounds
+// exactly as the others do.
+__device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double madd(double a, double b, double c) { return a * b + c; }
+
+// v_x^2 + v_y^2 + v_z^2, summed left to right
+template <typename T>
+__device__ __forceinline__ T sq3(T x, T y, T z)
+{
+    return madd(z, z, madd(y, y, x * x));
+}
+
 // ---------------------------------------------------------------- RNG
 // Philox-4x32-10 (Salmon et al., SC'11).  Counter (c0, step lo, step hi,
 // species << 8 | block), key = seed.  Block 0 holds collision-test uniforms:
@@ -196,7 +211,8 @@ __device__ __forceinline__ int cs_index_f(float r, int n)  // r = energy / de + 
 __device__ __forceinline__ double p_coll(double x) { return 1.0 - exp(-x); }
 __device__ __forceinline__ float p_coll(float x)
 {
-    const float series = x * (1.0f - x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f)))));
+    const float series =
+        x * madd(-x, madd(-x, madd(-x, madd(-x, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f), 0.5f), 1.0f);
     const float direct = 1.0f - __expf(-x);
     return x < 0.125f ? series : direct;
 }
@@ -503,12 +519,12 @@ __device__ __forceinline__ void electron_collision(const DischargeDev &D, int sl
     T *VZ = reinterpret_cast<T *>(D.vz[0]);
     const T xn = X[slot];
     T vx = VX[slot], vy = VY[slot], vz = VZ[slot];
-    const T v2 = vx * vx + vy * vy + vz * vz;
+    const T v2 = sq3(vx, vy, vz);
     int k;
     if constexpr (is_f64<T>())
         k = cs_index(D.half_me * v2 / EDUPIC_QE, idx_scale, cs_n);
     else
-        k = cs_index_f(v2 * idx_scale + 0.5f, cs_n);
+        k = cs_index_f(madd(v2, idx_scale, 0.5f), cs_n);
     const T2 thr = reinterpret_cast<const T2 *>(D.cs_thr[0])[k];
     T u_proc, u_chi, u_eta, u_opal, vej[3];
     draw<T>(key, (uint32_t)slot, 0, 1, u_proc, u_chi);
@@ -576,7 +592,7 @@ __device__ __forceinline__ int ion_index(const DischargeDev &D, T g_sqr, T idx_s
     if constexpr (is_f64<T>())
         return cs_index(D.half_mu_arar * g_sqr / EDUPIC_QE, idx_scale, cs_n);
     else
-        return cs_index_f(g_sqr * idx_scale + 0.5f, cs_n);
+        return cs_index_f(madd(g_sqr, idx_scale, 0.5f), cs_n);
 }
 
 // Null-collision test of a particle picked by its test uniform u < P*
@@ -591,16 +607,16 @@ __device__ __noinline__ bool null_pick(const DischargeDev *Dp, const RngKey key,
     T q2;
     int k;
     if constexpr (SP == 0) {
-        q2 = vx * vx + vy * vy + vz * vz;
+        q2 = sq3(vx, vy, vz);
         if constexpr (is_f64<T>())
             k = cs_index(D.half_me * q2 / EDUPIC_QE, idx_scale, cs_n);
         else
-            k = cs_index_f(q2 * idx_scale + 0.5f, cs_n);
+            k = cs_index_f(madd(q2, idx_scale, 0.5f), cs_n);
     } else {
         T vax, vay, vaz;
         ion_partner<T>(D, key, (uint32_t)slot, vax, vay, vaz);
         const T gx = vx - vax, gy = vy - vay, gz = vz - vaz;
-        q2 = gx * gx + gy * gy + gz * gz;
+        q2 = sq3(gx, gy, gz);
         k = ion_index<T>(D, q2, idx_scale, cs_n);
     }
     return null_real<T, SP>(D, k, q2, u, sCnt);
@@ -619,7 +635,7 @@ __device__ __forceinline__ void ion_collision(const DischargeDev &D, int slot, c
     T vax, vay, vaz;
     ion_partner<T>(D, key, (uint32_t)slot, vax, vay, vaz);
     const T gx = vx - vax, gy = vy - vay, gz = vz - vaz;
-    const int k = ion_index<T>(D, gx * gx + gy * gy + gz * gz, idx_scale, cs_n);
+    const int k = ion_index<T>(D, sq3(gx, gy, gz), idx_scale, cs_n);
     const T thr1 = reinterpret_cast<const T2 *>(D.cs_thr[1])[k].x;
     T u_proc, u_chi, u_eta, u_dummy;
     draw<T>(key, (uint32_t)slot, 1, 3, u_proc, u_chi);
@@ -723,7 +739,7 @@ template <typename T>
 __device__ __forceinline__ void eepf_sample(const DischargeDev *Dp, T vxc, T vy, T vz)
 {
     const DischargeDev &D = *Dp;
-    const T v2c = vxc * vxc + vy * vy + vz * vz;
+    const T v2c = sq3(vxc, vy, vz);
     int b;
     bool ok;
     if constexpr (is_f64<T>()) {
@@ -873,6 +889,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
     bool eepf_on = false;
     bool nullc = false;  // null-collision method for the current discharge
     T pstar = 0;         // its P*
+    T tbound = 0, v2lim = 0;  // short cut of the direct collision test
     int xcol = -1;       // xt time bin of this step for the current discharge (-1: none)
     T e_of_v2 = 0;       // energy in eV of v^2 (xt variant)
 
@@ -1023,6 +1040,13 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 nullc = ((D->null_coll >> SP) & 1) != 0;
                 pstar = is_f64<T>() ? (T)D->p_star[SP] : (T)D->p_starf[SP];
             }
+            if constexpr (is_f64<T>()) {
+                tbound = D->tbound[SP];
+                v2lim = D->v2lim[SP];
+            } else {
+                tbound = D->tboundf[SP];
+                v2lim = D->v2limf[SP];
+            }
             if constexpr (XT) {
                 xcol = (measure && D->nxt > 0) ? (int)((long long)(s % (unsigned long long)D->nt) / D->nbin) : -1;
                 if constexpr (is_f64<T>())
@@ -1085,9 +1109,8 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
 
         // phase 1: gather (Sec. 2.1.3), leapfrog push (Sec. 2.1.4), absorption
         // test (Sec. 2.1.5), energy and table index
-        int kk[VEC];
         bool in[VEC];
-        T w2[VEC];  // v^2 (e-) or g^2 (Ar+)
+        T w2[VEC];  // v^2 after the push
         T pw = (T)0;  // E_x (v_old + v_new) of the measured pushes of this tile
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
@@ -1101,10 +1124,10 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 const T c1 = (T)(p + 1) - c0, c2 = c0 - (T)p;
                 e_x = c1 * ep.x + c2 * ep.y;
             } else {
-                e_x = ep.x + (c0 - (T)p) * (ep.y - ep.x);  // same linear weights
+                e_x = madd(c0 - (T)p, ep.y - ep.x, ep.x);  // same linear weights
             }
-            const T vxn = SP == 0 ? vx - e_x * factor : vx + e_x * factor;
-            if (measure && live) pw += e_x * (vx + vxn);
+            const T vxn = SP == 0 ? madd(-e_x, factor, vx) : madd(e_x, factor, vx);
+            if (measure && live) pw = madd(e_x, vx + vxn, pw);
             if (SP == 0 && eepf_on && live && x >= lo && x <= hi)
                 eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e]);
             if constexpr (XT) {
@@ -1119,33 +1142,12 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                     atomicAdd(sXe + p + 1, w2 * en);
                 }
             }
-            const T xn = x + vxn * dt;
+            const T xn = madd(vxn, dt, x);
             xa[e] = live ? xn : x;
             vxa[e] = live ? vxn : vx;
             in[e] = live && (xn >= (T)0.0) && (xn <= L);
-            if constexpr (NC) {
-                w2[e] = (T)0;
-                kk[e] = 0;
-                if (nullc) continue;  // the null-collision test needs neither
-            }
-            T q2;
-            if (SP == 0) {
-                q2 = vxn * vxn + vya[e] * vya[e] + vza[e] * vza[e];
-            } else {
-                // thermal partner drawn before the collision probability
-                T vax = 0, vay = 0, vaz = 0;
-                if (in[e]) {
-                    const RngKey key{s_lo, s_hi, k0, k1};
-                    ion_partner<T>(*D, key, (uint32_t)(base + e), vax, vay, vaz);
-                }
-                const T gx = vxn - vax, gy = vya[e] - vay, gz = vza[e] - vaz;
-                q2 = gx * gx + gy * gy + gz * gz;
-            }
-            w2[e] = q2;
-            if constexpr (is_f64<T>())
-                kk[e] = cs_index((SP == 0 ? D->half_me : D->half_mu_arar) * q2 / EDUPIC_QE, idx_scale, cs_n);
-            else
-                kk[e] = cs_index_f(q2 * idx_scale + 0.5f, cs_n);
+            // own squared speed after the push (the direct test's short cut)
+            w2[e] = sq3(vxn, vya[e], vza[e]);
         }
         if (measure) pw_acc += (double)pw;
         // phase 2: collision-test uniforms (one Philox block per thread)
@@ -1187,12 +1189,12 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                     bool real;
                     if constexpr (SP == 0) {
                         // e-: the energy's table entry, in line
-                        const T q2 = vxa[e] * vxa[e] + vya[e] * vya[e] + vza[e] * vza[e];
+                        const T q2 = sq3(vxa[e], vya[e], vza[e]);
                         int k;
                         if constexpr (is_f64<T>())
                             k = cs_index(D->half_me * q2 / EDUPIC_QE, idx_scale, cs_n);
                         else
-                            k = cs_index_f(q2 * idx_scale + 0.5f, cs_n);
+                            k = cs_index_f(madd(q2, idx_scale, 0.5f), cs_n);
                         real = null_real<T, 0>(*D, k, q2, ut[e], sCnt);
                     } else {
                         // Ar+: the thermal partner is drawn out of line
@@ -1201,15 +1203,31 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                     }
                     if (real) sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;
                 }
-            } else {
-                const T speed = sqrt(w2[e]);
+            } else if (ut[e] < tbound || w2[e] > v2lim) {
+                // R >= tbound with v^2 <= v2lim: P_coll < R for every table
+                // entry (and partner), so only the other particles are tested
+                T q2 = w2[e];
+                if constexpr (SP == 1) {
+                    // thermal partner drawn before the collision probability
+                    T vax, vay, vaz;
+                    const RngKey key{s_lo, s_hi, k0, k1};
+                    ion_partner<T>(*D, key, (uint32_t)slot, vax, vay, vaz);
+                    const T gx = vxa[e] - vax, gy = vya[e] - vay, gz = vza[e] - vaz;
+                    q2 = sq3(gx, gy, gz);
+                }
+                int k;
+                if constexpr (is_f64<T>())
+                    k = cs_index((SP == 0 ? D->half_me : D->half_mu_arar) * q2 / EDUPIC_QE, idx_scale, cs_n);
+                else
+                    k = cs_index_f(madd(q2, idx_scale, 0.5f), cs_n);
+                const T speed = sqrt(q2);
                 T xu;
                 if constexpr (is_f64<T>())
-                    xu = sC[kk[e] >> cs_shift] * ndt * speed * dt * 1.000001 + 1e-15;
+                    xu = sC[k >> cs_shift] * ndt * speed * dt * 1.000001 + 1e-15;
                 else
-                    xu = sC[kk[e] >> cs_shift] * ndt * speed * 1.00001f + 1e-6f;
+                    xu = madd(sC[k >> cs_shift] * ndt * speed, 1.00001f, 1e-6f);
                 if (ut[e] < xu) {
-                    const T sg = __ldg(sig + kk[e]);
+                    const T sg = __ldg(sig + k);
                     T pc;
                     if constexpr (is_f64<T>())
                         pc = p_coll(sg * ndt * speed * dt);
@@ -1625,6 +1643,213 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const DischargeDe
         C->emitted = 0;
         C->step = next;
         if (measure) C->measured += 1;
+    }
+}
+
+// ---------------------------------------------------------------- periodic cell sort
+// Every sort_every ion subcycles, after the step that reaches a multiple of
+// sort_every * N_SUB, each species is put in ascending order of its
+// deposition cell, keeping the slot order within a cell (a stable counting
+// sort), so that the particles a warp reads next share few cells.  The slot,
+// and with it the random-number counter, follows the new order.  Four
+// launches per species, each over the chunks of kSortChunk particles of
+// every discharge that is due: chunk histograms, their scan into the first
+// slot of every (cell, chunk), the stable scatter into a scratch copy, and
+// the copy back.  Idempotent: a discharge that stays at a due step (a
+// finished request) is sorted again without change.
+__device__ __forceinline__ bool sort_due(const DischargeDev &D, int sp)
+{
+    if (!D.active || D.sort_every <= 0) return false;
+    const long long s = D.ctrl->step;
+    return s > 0 && s % ((long long)D.sort_every * D.nsub) == 0 && D.ctrl->n[sp] > 1;
+}
+
+// Chunks of the due discharges -> exclusive prefix sPre[0..nd] in shared memory.
+__device__ __forceinline__ void sort_chunk_prefix(const DischargeDev *DD, int nd, int sp, int *sPre, int *sW)
+{
+    int running = 0;
+    for (int base = 0; base < nd; base += blockDim.x) {
+        const int d = base + threadIdx.x;
+        int cnt = 0;
+        if (d < nd && sort_due(DD[d], sp)) cnt = (int)((DD[d].ctrl->n[sp] + kSortChunk - 1) / kSortChunk);
+        int tot;
+        const int ex = group_excl_scan(cnt, sW, tot, threadIdx.x, blockDim.x, 1);
+        if (d < nd) sPre[d] = running + ex;
+        running += tot;
+    }
+    if (threadIdx.x == 0) sPre[nd] = running;
+    __syncthreads();
+}
+
+__device__ __forceinline__ int sort_owner(const int *sPre, int nd, int chunk)  // discharge of a global chunk
+{
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sPre[mid] <= chunk)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Pass 1: per chunk, the count of particles in each cell ([chunk][ng]).
+template <typename T>
+__global__ void __launch_bounds__(256) k_sort_count(const DischargeDev *__restrict__ DD, int nd, int sp, int ng_max)
+{
+    extern __shared__ __align__(16) unsigned int sHist[];  // [warps][ng_max], then the chunk prefix
+    int *sPre = reinterpret_cast<int *>(sHist + (blockDim.x / 32) * ng_max);
+    __shared__ int sW[33];
+    sort_chunk_prefix(DD, nd, sp, sPre, sW);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned int *h = sHist + warp * ng_max;
+    const int total = sPre[nd];
+    for (int chunk = blockIdx.x * (blockDim.x / 32) + warp; chunk < total; chunk += gridDim.x * (blockDim.x / 32)) {
+        const int d = sort_owner(sPre, nd, chunk);
+        const DischargeDev &D = DD[d];
+        const int ng = D.ng;
+        const long long n = D.ctrl->n[sp];
+        const long long base = (long long)(chunk - sPre[d]) * kSortChunk;
+        const T *X = reinterpret_cast<const T *>(D.x[sp]);
+        const T inv_dx = is_f64<T>() ? (T)D.inv_dx : (T)D.inv_dxf;
+        for (int p = lane; p < ng; p += 32) h[p] = 0u;
+        __syncwarp();
+        for (int k = lane; k < kSortChunk; k += 32) {
+            const long long j = base + k;
+            if (j >= n) break;
+            T c0;
+            atomicAdd(h + cell<T>(X[j], inv_dx, ng, c0), 1u);
+        }
+        __syncwarp();
+        unsigned int *out = D.sort_cnt + (size_t)(chunk - sPre[d]) * ng;
+        for (int p = lane; p < ng; p += 32) out[p] = h[p];
+        __syncwarp();
+    }
+}
+
+// Pass 2 (one block per discharge): counts -> first slot of every (cell,
+// chunk): cells in ascending order, chunks (slot order) within a cell.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sort_scan(const DischargeDev *__restrict__ DD, int sp)
+{
+    extern __shared__ __align__(16) unsigned int sTot[];  // [ng_max]
+    __shared__ unsigned int sW[33];
+    const DischargeDev &D = DD[blockIdx.x];
+    if (!sort_due(D, sp)) return;
+    const int ng = D.ng;
+    const int nch = (int)((D.ctrl->n[sp] + kSortChunk - 1) / kSortChunk);
+    unsigned int *cnt = D.sort_cnt;
+    for (int p = threadIdx.x; p < ng; p += blockDim.x) {
+        unsigned int t = 0;
+        for (int c = 0; c < nch; ++c) t += cnt[(size_t)c * ng + p];
+        sTot[p] = t;
+    }
+    __syncthreads();
+    // exclusive prefix over the cells (each thread a run of consecutive cells)
+    const int per = (ng + blockDim.x - 1) / blockDim.x;
+    const int first = threadIdx.x * per, last = min(first + per, ng);
+    unsigned int run = 0;
+    for (int p = first; p < last; ++p) run += sTot[p];
+    unsigned int tot;
+    unsigned int off = group_excl_scan(run, sW, tot, threadIdx.x, blockDim.x, 1);
+    for (int p = first; p < last; ++p) {
+        const unsigned int v = sTot[p];
+        sTot[p] = off;
+        off += v;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < ng; p += blockDim.x) {
+        unsigned int r = sTot[p];
+        for (int c = 0; c < nch; ++c) {
+            const unsigned int v = cnt[(size_t)c * ng + p];
+            cnt[(size_t)c * ng + p] = r;
+            r += v;
+        }
+    }
+}
+
+// Pass 3: every chunk's particles, in slot order, to the next free slot of
+// their cell in the scratch copy (a warp takes 32 slots at a time; lanes in
+// the same cell are ranked by lane).
+template <typename T>
+__global__ void __launch_bounds__(256) k_sort_scatter(const DischargeDev *__restrict__ DD, int nd, int sp, int ng_max)
+{
+    extern __shared__ __align__(16) unsigned int sRun[];  // [warps][ng_max], then the chunk prefix
+    int *sPre = reinterpret_cast<int *>(sRun + (blockDim.x / 32) * ng_max);
+    __shared__ int sW[33];
+    sort_chunk_prefix(DD, nd, sp, sPre, sW);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned int *run = sRun + warp * ng_max;
+    const int total = sPre[nd];
+    for (int chunk = blockIdx.x * (blockDim.x / 32) + warp; chunk < total; chunk += gridDim.x * (blockDim.x / 32)) {
+        const int d = sort_owner(sPre, nd, chunk);
+        const DischargeDev &D = DD[d];
+        const int ng = D.ng;
+        const long long n = D.ctrl->n[sp];
+        const long long base = (long long)(chunk - sPre[d]) * kSortChunk;
+        const T *src[4] = {reinterpret_cast<const T *>(D.x[sp]), reinterpret_cast<const T *>(D.vx[sp]),
+                           reinterpret_cast<const T *>(D.vy[sp]), reinterpret_cast<const T *>(D.vz[sp])};
+        T *dst[4] = {reinterpret_cast<T *>(D.sort_tmp[0]), reinterpret_cast<T *>(D.sort_tmp[1]),
+                     reinterpret_cast<T *>(D.sort_tmp[2]), reinterpret_cast<T *>(D.sort_tmp[3])};
+        const T inv_dx = is_f64<T>() ? (T)D.inv_dx : (T)D.inv_dxf;
+        const unsigned int *first = D.sort_cnt + (size_t)(chunk - sPre[d]) * ng;
+        for (int p = lane; p < ng; p += 32) run[p] = first[p];
+        __syncwarp();
+        for (int k = 0; k < kSortChunk; k += 32) {
+            const long long j = base + k + lane;
+            const bool act = j < n;
+            const unsigned int mask = __ballot_sync(0xffffffffu, act);
+            if (mask == 0u) break;
+            int p = 0;
+            unsigned int peers = 0u, rank = 0u;
+            if (act) {
+                T c0;
+                const T x = src[0][j];
+                p = cell<T>(x, inv_dx, ng, c0);
+                peers = __match_any_sync(mask, p);
+                rank = (unsigned int)__popc(peers & ((1u << lane) - 1u));
+                const unsigned int o = run[p] + rank;
+                if (o < (unsigned long long)n) {
+                    dst[0][o] = x;
+                    dst[1][o] = src[1][j];
+                    dst[2][o] = src[2][j];
+                    dst[3][o] = src[3][j];
+                } else {
+                    atomicOr(&D.ctrl->error, kErrHoles);  // inconsistent counts (never expected)
+                }
+            }
+            __syncwarp();
+            if (act && rank == 0u) run[p] += (unsigned int)__popc(peers);
+            __syncwarp();
+        }
+    }
+}
+
+// Pass 4: the sorted scratch copy back into the particle arrays.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sort_copy(const DischargeDev *__restrict__ DD, int nd, int sp)
+{
+    extern __shared__ __align__(16) int sPreC[];  // chunk prefix
+    __shared__ int sW[33];
+    sort_chunk_prefix(DD, nd, sp, sPreC, sW);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int total = sPreC[nd];
+    for (int chunk = blockIdx.x * (blockDim.x / 32) + warp; chunk < total; chunk += gridDim.x * (blockDim.x / 32)) {
+        const int d = sort_owner(sPreC, nd, chunk);
+        const DischargeDev &D = DD[d];
+        const long long n = D.ctrl->n[sp];
+        const long long base = (long long)(chunk - sPreC[d]) * kSortChunk;
+        void *arr[4] = {D.x[sp], D.vx[sp], D.vy[sp], D.vz[sp]};
+        for (int a = 0; a < 4; ++a) {
+            const T *s = reinterpret_cast<const T *>(D.sort_tmp[a]);
+            T *o = reinterpret_cast<T *>(arr[a]);
+            for (int k = lane; k < kSortChunk; k += 32) {
+                const long long j = base + k;
+                if (j >= n) break;
+                o[j] = s[j];
+            }
+        }
     }
 }
 

@@ -144,6 +144,33 @@ cudaError_t Launch<T>::finalize(const DischargeDev *dd, int nd, int ion_step, in
 }
 
 template <typename T>
+cudaError_t Launch<T>::sort(const DischargeDev *dd, int nd, int ng_max, int sms, cudaStream_t st)
+{
+    constexpr int threads = 256, warps = threads / 32;
+    const size_t smem = (size_t)warps * ng_max * 4 + (size_t)(nd + 1) * 4;
+    cudaFuncSetAttribute(k_sort_count<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_sort_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaSuccess;
+    for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
+        k_sort_count<T><<<2 * sms, threads, smem, st>>>(dd, nd, sp, ng_max);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            k_sort_scan<T><<<nd, threads, (size_t)ng_max * 4, st>>>(dd, sp);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            k_sort_scatter<T><<<2 * sms, threads, smem, st>>>(dd, nd, sp, ng_max);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            k_sort_copy<T><<<4 * sms, threads, (size_t)(nd + 1) * 4, st>>>(dd, nd, sp);
+            e = cudaGetLastError();
+        }
+    }
+    return e;
+}
+
+template <typename T>
 cudaError_t Launch<T>::wait_expiry(unsigned long long limit_ns, int *err, cudaStream_t st)
 {
     k_wait_expiry<<<1, 32, 0, st>>>(limit_ns, err);

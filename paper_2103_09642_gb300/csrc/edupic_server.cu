@@ -208,6 +208,10 @@ int open_slot(edupic_server *V, uint64_t ticket, int d)
     if (rc == EDUPIC_OK) {
         fill_desc(S, d);
         S->desc[d].stop_step = r.target;
+        if (r.p.sort_every > 0 && !S->sort_any) {
+            S->sort_any = 1;  // from now on every ion subcycle ends with the sort launches
+            S->drop_graphs();
+        }
         update_null_any(S);
         rc = upload_desc_one(S, d);
     }

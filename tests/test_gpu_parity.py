@@ -696,9 +696,11 @@ def test_fp32_collision_selection_bit_exact():
 
 
 # --------------------------------------------------------------- periodic cell sort
-def _cells_of(x, d):
-    dx = d.gap_m / (d.n_grid - 1)
-    return np.minimum(np.floor(x / dx).astype(np.int64), d.n_grid - 2)
+def _cells_of(x, d, precision=ed.FP64):
+    # the kernels' cell: x * (1 / dx), rounded in the particle precision
+    inv_dx = 1.0 / (d.gap_m / (d.n_grid - 1))
+    c0 = x * inv_dx if precision == ed.FP64 else np.float32(x) * np.float32(inv_dx)
+    return np.minimum(np.floor(c0).astype(np.int64), d.n_grid - 2)
 
 
 def test_cell_sort_fp64_per_step():
@@ -744,4 +746,4 @@ def test_cell_sort_batched_equals_alone(precision):
         if ds[k].sort_every > 0:
             # step 80 is a multiple of both sort periods: the run ends sorted
             for sp in (0, 1):
-                assert (np.diff(_cells_of(together[0][k][sp][0], ds[k])) >= 0).all(), (k, sp)
+                assert (np.diff(_cells_of(together[0][k][sp][0], ds[k], precision)) >= 0).all(), (k, sp)

@@ -940,9 +940,10 @@ def test_table_index_is_the_nearest_entry_ions_by_com_energy():
 
 # ------------------------------------------------------------------ periodic cell sort (slot order)
 def _cells(x, d):
-    # the cell of the deposition (Algorithm 2): floor(x / dx), the last cell taking x = L
-    dx = d.gap_m / (d.n_grid - 1)
-    return np.minimum(np.floor(x / dx).astype(np.int64), d.n_grid - 2)
+    # the cell of the deposition (Algorithm 2): floor(x / dx) formed as
+    # x * (1 / dx), the last cell taking x = L
+    inv_dx = 1.0 / (d.gap_m / (d.n_grid - 1))
+    return np.minimum(np.floor(x * inv_dx).astype(np.int64), d.n_grid - 2)
 
 
 def _sort_pair(sort_every, steps):

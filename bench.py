@@ -210,13 +210,78 @@ def _run_oracle(sims, steps):
     return ps, dt
 
 
-def cpu_baseline(mix) -> dict:
-    """The oracle (FP64, one thread) on a bounded sample of the same batch."""
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_one_discharge(args):
+    """One discharge of the batch in the oracle for `steps` time steps
+    (a worker of the all-core baseline; CPU only)."""
+    k, steps = args
+    import numpy as np
+
+    import oracle
+    from paper_2103_09642_gb300 import workloads as wl
+
+    d, e, i = wl.draw_discharge(np.random.default_rng(1000 + k), 1000 + k)  # discharge k of the batch
+    se, si = wl.standin_cross_sections()
+    s = oracle.Sim(d, se, si, wl.CS_DE_EV, e, i)
+    c0 = s.counters()
+    t0 = time.perf_counter()
+    s.step(steps, measure=True)
+    dt = time.perf_counter() - t0
+    c = s.counters()
+    return (c["push_e"] - c0["push_e"]) + (c["push_i"] - c0["push_i"]), dt
+
+
+def cpu_baseline_all_cores(mix, pool, cores: int) -> dict:
+    """The oracle on every host core at once: discharge k of the batch in
+    worker k (independent discharges, as the batch is), each for a number of
+    time steps sized to about CPU_SAMPLE_WORK / 4 particle-steps."""
+    jobs = []
+    for k in range(cores):
+        d, e, i = mix[k % len(mix)]
+        n = e.n + i.n / 20.0
+        jobs.append((k % len(mix), int(max(20, min(2000, CPU_SAMPLE_WORK / 4 / max(n, 1.0))) // 20 * 20)))
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_one_discharge, jobs)
+    wall = time.perf_counter() - t0
+    ps = sum(r[0] for r in res)
+    return {"value": ps / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"discharges 0-{cores - 1} of the 64-discharge batch, one per process on {cores} cores "
+                      f"({', '.join(str(j[1]) for j in jobs[:4])}... time steps each), FP64 "
+                      f"({ps} particle-steps in {wall:.1f} s of wall time)"}
+
+
+def cpu_baseline(mix, pool=None, cores: int = 1) -> dict:
+    """The oracle (FP64) on a bounded sample of the same batch: one host
+    thread on discharges 0-3, and, with a worker pool, all host cores."""
     sims, steps = _oracle_sample(mix, CPU_SAMPLE_WORK)
     ps, dt = _run_oracle(sims, steps)
-    return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"discharges 0-{CPU_SAMPLE_DISCHARGES - 1} of the 64-discharge batch, {steps} time steps each, "
-                      f"FP64, one host thread ({ps} particle-steps in {dt:.1f} s)"}
+    one = {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"discharges 0-{CPU_SAMPLE_DISCHARGES - 1} of the 64-discharge batch, {steps} time steps each, "
+                     f"FP64, one host thread ({ps} particle-steps in {dt:.1f} s)"}
+    if pool is None:
+        one["cpu_model"] = _cpu_model()
+        return one
+    out = cpu_baseline_all_cores(mix, pool, cores)
+    out["one_core"] = one
+    out["cpu_model"] = _cpu_model()
+    out["nproc"] = os.cpu_count()
+    return out
 
 
 def run_reference(args):
@@ -476,6 +541,13 @@ def run_ours(args):
     from paper_2103_09642_gb300 import edupic as ed
     from paper_2103_09642_gb300 import workloads as wl
 
+    # the all-core oracle baseline's workers, started (spawn) before any GPU work
+    pool, cores = None, 1
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import multiprocessing as mp
+
+        cores = max(1, min(os.cpu_count() or 1, BATCH_DISCHARGES))
+        pool = mp.get_context("spawn").Pool(cores)
     ed.load_library()
     peak, peak_kind = _peak_hbm()
     _log("generating the 64-discharge batch")
@@ -576,7 +648,10 @@ def run_ours(args):
         extra["served"] = leg_served(args)
     if rank == 0 and ws == 1 and not args.no_cpu:
         _log("cpu baseline")
-    cpu = cpu_baseline(mix) if (rank == 0 and ws == 1 and not args.no_cpu) else None
+    cpu = cpu_baseline(mix, pool, cores) if (rank == 0 and ws == 1 and not args.no_cpu) else None
+    if pool is not None:
+        pool.close()
+        pool.join()
     _log("done")
 
     if rank == 0:

@@ -166,29 +166,29 @@ __device__ __forceinline__ unsigned long long split_q2(float c2)
 
 // Per-block deposition accumulator in shared memory.  A particle in cell p
 // adds q1 = 2^32 - q2 to point p and q2 to point p+1; the block keeps, per
-// cell, one 64-bit word with the deposit count in bits 48-63 and the sum S_p
-// of q2 in bits 0-47 (one 64-bit shared atomic per deposit), and forms
-// Q_p = 2^32 cnt_p - S_p + S_{p-1} when it flushes.  Neither field can
-// overflow while a cell takes fewer than 2^16 deposits between flushes: the
-// kernel flushes every kDepFlush particles, and a flush interval holds at
-// most kDepFlush + one tile particles plus one ionisation product each and
-// the products of the colliders still queued (< 2^16 deposits, so
-// S_p < 2^16 * 2^32 = 2^48).
+// cell, the count and the sum S_p of q2 in two 16-bit halves (three 32-bit
+// shared atomics per deposit; measured faster on sm_103a than one packed
+// 64-bit shared atomic), and forms Q_p = 2^32 cnt_p - S_p + S_{p-1} when it
+// flushes.  The halves cannot overflow while a cell takes fewer than 2^16
+// deposits between flushes: the kernel flushes every kDepFlush particles,
+// and a flush interval holds at most kDepFlush + one tile particles plus one
+// ionisation product each and the products of the colliders still queued.
 struct DepAcc {
-    unsigned long long *w;
+    unsigned int *cnt, *lo, *hi;
 };
 constexpr int kDepFlush = 28000;
-constexpr unsigned long long kDepCount = 1ull << 48;
 
 __device__ __forceinline__ void dep_add(const DepAcc &a, int p, unsigned long long q2)
 {
-    atomicAdd(a.w + p, kDepCount + q2);
+    atomicAdd(a.cnt + p, 1u);
+    atomicAdd(a.lo + p, (unsigned int)(q2 & 0xFFFFull));
+    atomicAdd(a.hi + p, (unsigned int)(q2 >> 16));
 }
 
-__device__ __forceinline__ unsigned long long dep_cnt(const DepAcc &a, int p) { return a.w[p] >> 48; }
+__device__ __forceinline__ unsigned long long dep_cnt(const DepAcc &a, int p) { return a.cnt[p]; }
 __device__ __forceinline__ unsigned long long dep_sum(const DepAcc &a, int p)  // S_p
 {
-    return a.w[p] & (kDepCount - 1);
+    return (unsigned long long)a.lo[p] + ((unsigned long long)a.hi[p] << 16);
 }
 
 // Nearest cross-section bin (Algorithm 6).
@@ -776,14 +776,14 @@ __host__ __device__ constexpr PushShape shape_of()
 }
 
 // Dynamic shared memory: [tile ring: stages x 4 arrays x TILE T][coarse
-// sigma_max: kCoarse T][E pairs: ng_max T2][deposition: ng_max u64]
+// sigma_max: kCoarse T][E pairs: ng_max T2][deposition: 3 x ng_max u32]
 // [tile prefix: nd+1 int][xt variant, from the next 16-byte boundary: sum
 // w v_c,x and sum w eps_c, ng_max T each].
 template <typename T, bool XT, int SH>
 __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eepf_max)
 {
     return (size_t)shape_of<T, XT, SH>().stages * 4 * shape_of<T, XT, SH>().threads * VecOf<T>::n * sizeof(T) +
-           (size_t)kCoarse * sizeof(T) + (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 8 + (size_t)(nd + 1) * 4 +
+           (size_t)kCoarse * sizeof(T) + (size_t)ng_max * 2 * sizeof(T) + (size_t)ng_max * 12 + (size_t)(nd + 1) * 4 +
            (XT ? 16 + (size_t)ng_max * 2 * sizeof(T) : 0) + 0 * (size_t)eepf_max;
 }
 
@@ -810,8 +810,10 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
     T *sC = sRing + S * 4 * TILE;
     T2 *sE2 = reinterpret_cast<T2 *>(sC + kCoarse);
     DepAcc acc;
-    acc.w = reinterpret_cast<unsigned long long *>(sE2 + ng_max);
-    int *sPre = reinterpret_cast<int *>(acc.w + ng_max);
+    acc.cnt = reinterpret_cast<unsigned int *>(sE2 + ng_max);
+    acc.lo = acc.cnt + ng_max;
+    acc.hi = acc.lo + ng_max;
+    int *sPre = reinterpret_cast<int *>(acc.hi + ng_max);
     // xt variant: sum w v_c,x and sum w eps_c of the block, per grid point, on a
     // 16-byte boundary after the prefix (whose end is 4-byte aligned only)
     T *sXv = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(sPre + nd + 1) + 15) & ~(uintptr_t)15);
@@ -931,7 +933,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
         if (!clear) return;
         __syncthreads();
         for (int p = tid; p < ng; p += blockDim.x) {
-            acc.w[p] = 0ull;
+            acc.cnt[p] = acc.lo[p] = acc.hi[p] = 0u;
             if constexpr (XT) sXv[p] = sXe[p] = (T)0;
         }
         __syncthreads();
@@ -1057,7 +1059,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
             const T *ef = reinterpret_cast<const T *>(D->ef_t);
             for (int p = tid; p < ng; p += blockDim.x) {
                 sE2[p] = T2{ef[p], p + 1 < ng ? ef[p + 1] : (T)0};
-                acc.w[p] = 0ull;
+                acc.cnt[p] = acc.lo[p] = acc.hi[p] = 0u;
                 if constexpr (XT) sXv[p] = sXe[p] = (T)0;
             }
             since_flush = 0;
@@ -1067,13 +1069,15 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
         if (tid == 0) atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_PUSH_E : EDUPIC_C_PUSH_I), (unsigned)min(TILE, n - tbase));
         const int base = tbase + tid * VEC;
         // this tile's particles from the ring; each warp then marks the stage read
-        const bool aborted = sAbort != 0;
-        if (!aborted) {
-            if (mbar_wait_bounded(sFull + st, (uint32_t)((it / S) & 1))) {
-                if (tid == 0) seen0 = it + 1;
-            } else {
+        // (after an expired wait anywhere in the block, the tile is skipped)
+        bool ok = sAbort == 0;
+        if (ok) {
+            ok = mbar_wait_bounded(sFull + st, (uint32_t)((it / S) & 1));
+            if (!ok) {
                 atomicOr(&D->ctrl->error, kErrTimeout);
                 sAbort = 1;
+            } else if (tid == 0) {
+                seen0 = it + 1;
             }
         }
         {
@@ -1105,7 +1109,9 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
         since_flush += TILE;
         // a tile adds at most 32 * VEC colliders to this warp's queue
         if (sQn[warp] > kWarpQueue - 32 * VEC) drain();
-        if (base >= n || sAbort) continue;  // after an expired wait the stage contents are not used
+        // lanes with particles in this tile (every lane of the warp reaches this ballot)
+        const unsigned int live_lanes = __ballot_sync(0xffffffffu, base < n && ok);
+        if (base >= n || !ok) continue;  // after an expired wait the stage contents are not used
 
         // phase 1: gather (Sec. 2.1.3), leapfrog push (Sec. 2.1.4), absorption
         // test (Sec. 2.1.5), energy and table index
@@ -1162,6 +1168,13 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 ut[2] = u24(w.c);
                 ut[3] = u24(w.d);
             }
+        }
+        int dcell[VEC];                // cell of each deposit (-1: none)
+        unsigned long long dq2[VEC];  // its fixed-point weight of point cell + 1
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            dcell[e] = -1;
+            dq2[e] = 0ull;
         }
         // phase 3: collision test (Algorithm 6), absorption records, deposition.
         // With x = n sigma_tot v dt, P_coll = 1 - exp(-x) <= x, and the coarse
@@ -1236,10 +1249,61 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                     if (ut[e] < pc) sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;  // executed after the stores below
                 }
             }
-            // deposition of the new position for the next step (Sec. 2.1.1)
+            // deposition of the new position for the next step (Sec. 2.1.1),
+            // gathered below
             T d0;
-            const int pp = cell<T>(xa[e], inv_dx, ng, d0);
-            dep_add(acc, pp, split_q2(d0 - (T)pp));
+            dcell[e] = cell<T>(xa[e], inv_dx, ng, d0);
+            dq2[e] = split_q2(d0 - (T)dcell[e]);
+        }
+        // Deposition through warp-level reductions where deposits share a
+        // cell (particles in cell order, after the periodic sort): all 32 x
+        // VEC deposits of the warp in one cell -> one set of shared atomics
+        // for the warp; a thread's VEC deposits in one cell -> one set for
+        // the thread; otherwise one set per deposit.  The sums are the same
+        // integers in every case.
+        {
+            bool same = dcell[0] >= 0;
+#pragma unroll
+            for (int e = 1; e < VEC; ++e) same = same && dcell[e] == dcell[0];
+            // the warp path only with all 32 lanes here (a warp-uniform branch)
+            int c0w = -1;
+            bool warp_same = false;
+            if (live_lanes == 0xffffffffu) {
+                c0w = __shfl_sync(0xffffffffu, dcell[0], 0);
+                warp_same = __all_sync(0xffffffffu, same && dcell[0] == c0w);
+            }
+            if (warp_same) {
+                unsigned int lo = 0u, hi = 0u;
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    lo += (unsigned int)(dq2[e] & 0xFFFFull);
+                    hi += (unsigned int)(dq2[e] >> 16);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo += __shfl_xor_sync(0xffffffffu, lo, o);
+                    hi += __shfl_xor_sync(0xffffffffu, hi, o);
+                }
+                if (lane == 0) {
+                    atomicAdd(acc.cnt + c0w, 32u * VEC);
+                    atomicAdd(acc.lo + c0w, lo);
+                    atomicAdd(acc.hi + c0w, hi);
+                }
+            } else if (same) {
+                unsigned int lo = 0u, hi = 0u;
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    lo += (unsigned int)(dq2[e] & 0xFFFFull);
+                    hi += (unsigned int)(dq2[e] >> 16);
+                }
+                atomicAdd(acc.cnt + dcell[0], (unsigned int)VEC);
+                atomicAdd(acc.lo + dcell[0], lo);
+                atomicAdd(acc.hi + dcell[0], hi);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e)
+                    if (dcell[e] >= 0) dep_add(acc, dcell[e], dq2[e]);
+            }
         }
         *reinterpret_cast<V *>(X + base) = pack(xa, V{});
         *reinterpret_cast<V *>(VX + base) = pack(vxa, V{});

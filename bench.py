@@ -54,11 +54,13 @@ BATCH_STEPS = 400             # time steps per bench step (20 ion subcycles)
 N_STEADY = 500_000            # plain leg: particles per species of the steady-shape state
 DF_N = 2_000_000              # dual-frequency particles per species
 DF_SWEEP_N = 100_000  # particles per species in each Table 3 discharge
-SERVED_REQUESTS = 32
-SERVED_CYCLES = (2, 10)
-# 0.8 x (batched capacity ~1e11 particle-steps/s) / mean request work
-# (mean 3.8e5 particles per species x 1.05 x 4000 steps x 6 cycles)
-SERVED_RATE_HZ = 8.0
+# served leg: the C5 stream shape (200 Poisson requests of 20-200 RF cycles,
+# parameters as the batch) with the particle counts scaled by SERVED_SCALE so
+# that the stream fits the bench's time budget (--served-scale 1 for full size)
+SERVED_REQUESTS = 200
+SERVED_CYCLES = (20, 200)
+SERVED_SCALE = 0.15
+SERVED_LOAD = 0.8  # arrival rate as a fraction of the main line's measured throughput
 CPU_SAMPLE_DISCHARGES = 4     # oracle sample: the first discharges of the batch
 CPU_SAMPLE_WORK = 4e8         # particle-steps of the oracle sample (~15 s on one core)
 _T0 = time.time()
@@ -80,6 +82,11 @@ def _args():
     ap.add_argument("--no-extra", action="store_true", help="skip the plain, dual-frequency and served legs")
     ap.add_argument("--reference-sample", type=int, default=20,
                     help="time steps of the oracle per bench step in --impl reference")
+    ap.add_argument("--served-requests", type=int, default=SERVED_REQUESTS)
+    ap.add_argument("--served-cycles", type=int, nargs=2, default=SERVED_CYCLES)
+    ap.add_argument("--served-scale", type=float, default=SERVED_SCALE,
+                    help="particle counts of the served requests relative to the batch's (1 = config size)")
+    ap.add_argument("--served-max-wall", type=float, default=300.0)
     return ap.parse_args()
 
 
@@ -501,28 +508,38 @@ def leg_df_sweep(args, peak, peak_kind, flush) -> dict:
             "roofline": roof}
 
 
-def leg_served(args) -> dict:
-    """A bounded Poisson stream through the request server: 32 requests
-    drawn like the 64-discharge batch, 2-10 RF cycles each (the full stream,
-    200 requests of 20-200 cycles, is run by paper_2103_09642_gb300.serving),
-    arrival rate about 0.8 x the batched capacity."""
+def leg_served(args, capacity_ps: float) -> dict:
+    """The served configuration: a Poisson stream of requests through the
+    request server (continuous batching), drawn like the 64-discharge batch
+    (particle counts scaled by --served-scale), each asking for a number of RF
+    cycles drawn from --served-cycles; arrivals at SERVED_LOAD x the main
+    line's throughput divided by the mean request work."""
+    import math
+
     import torch
 
     from paper_2103_09642_gb300 import edupic as ed
     from paper_2103_09642_gb300 import serving
     from paper_2103_09642_gb300 import workloads as wl
 
-    specs = serving.poisson_stream(SERVED_REQUESTS, rate_hz=SERVED_RATE_HZ, seed=7, cycles=SERVED_CYCLES)
+    lo, hi = args.served_cycles
+    mean_n = (2e6 - 1e4) / math.log(2e6 / 1e4) * args.served_scale  # log-uniform mean per species
+    mean_ps = mean_n * (1.0 + 1.0 / 20.0) * 4000 * 0.5 * (lo + hi)
+    rate = SERVED_LOAD * capacity_ps / mean_ps
+    specs = serving.poisson_stream(args.served_requests, rate_hz=rate, seed=7, cycles=(lo, hi),
+                                   scale=args.served_scale)
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.5 * free) // 256 * 256
     se, si = wl.standin_cross_sections()
     srv = ed.Server(budget, max_slots=96, max_grid=800, max_eepf_bins=2000, precision=ed.FP32)
     srv.set_cross_sections(ed.ELECTRONS, se, wl.CS_DE_EV)
     srv.set_cross_sections(ed.IONS, si, wl.CS_DE_EV)
-    rep = serving.run_stream(srv, specs, chunk_subcycles=5, max_wall_s=180.0)
+    rep = serving.run_stream(srv, specs, chunk_subcycles=5, max_wall_s=args.served_max_wall)
     srv.close()
-    return {"workload": f"{SERVED_REQUESTS} Poisson-arrival requests (rate {SERVED_RATE_HZ}/s), parameters as the "
-                        f"64-discharge batch, {SERVED_CYCLES[0]}-{SERVED_CYCLES[1]} RF cycles each",
+    return {"workload": f"{args.served_requests} Poisson-arrival requests (rate {rate:.3g}/s = {SERVED_LOAD} x the "
+                        f"main line's throughput / mean request work), parameters as the 64-discharge batch with "
+                        f"particle counts x{args.served_scale:g}, {lo}-{hi} RF cycles each",
+            "particle_scale": args.served_scale, "rate_hz": rate,
             "value": rep["particle_steps_per_s"], "unit": UNIT,
             "p50_time_to_result_s": rep["p50_time_to_result_s"], "p99_time_to_result_s": rep["p99_time_to_result_s"],
             "makespan_s": rep["makespan_s"], "requests": rep["requests"], "failed": rep["failed"],
@@ -645,7 +662,7 @@ def run_ours(args):
         _log("null-collision leg")
         extra["null_collision_ions"] = leg_null_collision(args, mix, flush)
         _log("served leg")
-        extra["served"] = leg_served(args)
+        extra["served"] = leg_served(args, value)
     if rank == 0 and ws == 1 and not args.no_cpu:
         _log("cpu baseline")
     cpu = cpu_baseline(mix, pool, cores) if (rank == 0 and ws == 1 and not args.no_cpu) else None

@@ -622,6 +622,43 @@ __device__ __noinline__ bool null_pick(const DischargeDev *Dp, const RngKey key,
     return null_real<T, SP>(D, k, q2, u, sCnt);
 }
 
+// The direct collision test of Algorithm 6 for a particle that the short
+// cut could not settle (a few per cent): for Ar+ the thermal partner drawn
+// before the probability; the table index of the (relative) energy; an exact
+// coarse bound, then the fine entry.  Out of line, so the unrolled particle
+// loop stays small.
+template <typename T, int SP>
+__device__ __noinline__ bool direct_test(const DischargeDev *Dp, const RngKey key, int slot, T vx, T vy, T vz,
+                                         T v2, T u, T idx_scale, int cs_n, int cs_shift, const T *sC, T ndt, T dt)
+{
+    const DischargeDev &D = *Dp;
+    T q2 = v2;
+    if constexpr (SP == 1) {
+        T vax, vay, vaz;
+        ion_partner<T>(D, key, (uint32_t)slot, vax, vay, vaz);
+        q2 = sq3(vx - vax, vy - vay, vz - vaz);
+    }
+    int k;
+    if constexpr (is_f64<T>())
+        k = cs_index((SP == 0 ? D.half_me : D.half_mu_arar) * q2 / EDUPIC_QE, idx_scale, cs_n);
+    else
+        k = cs_index_f(madd(q2, idx_scale, 0.5f), cs_n);
+    const T speed = sqrt(q2);
+    T xu;
+    if constexpr (is_f64<T>())
+        xu = sC[k >> cs_shift] * ndt * speed * dt * 1.000001 + 1e-15;
+    else
+        xu = madd(sC[k >> cs_shift] * ndt * speed, 1.00001f, 1e-6f);
+    if (!(u < xu)) return false;
+    const T sg = __ldg(reinterpret_cast<const T *>(D.cs_sig[SP]) + k);
+    T pc;
+    if constexpr (is_f64<T>())
+        pc = p_coll(sg * ndt * speed * dt);
+    else
+        pc = p_coll(sg * ndt * speed);
+    return u < pc;
+}
+
 // Ar+ + Ar collision of the ion in `slot` with its thermal partner.
 template <typename T>
 __device__ __forceinline__ void ion_collision(const DischargeDev &D, int slot, const RngKey &key, T idx_scale, int cs_n,
@@ -892,6 +929,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
     bool nullc = false;  // null-collision method for the current discharge
     T pstar = 0;         // its P*
     T tbound = 0, v2lim = 0;  // short cut of the direct collision test
+    bool sorted = false;      // the discharge keeps its particles in cell order (warp-level deposition)
     int xcol = -1;       // xt time bin of this step for the current discharge (-1: none)
     T e_of_v2 = 0;       // energy in eV of v^2 (xt variant)
 
@@ -1042,6 +1080,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 nullc = ((D->null_coll >> SP) & 1) != 0;
                 pstar = is_f64<T>() ? (T)D->p_star[SP] : (T)D->p_starf[SP];
             }
+            sorted = D->sort_every > 0;
             if constexpr (is_f64<T>()) {
                 tbound = D->tbound[SP];
                 v2lim = D->v2lim[SP];
@@ -1219,49 +1258,30 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
             } else if (ut[e] < tbound || w2[e] > v2lim) {
                 // R >= tbound with v^2 <= v2lim: P_coll < R for every table
                 // entry (and partner), so only the other particles are tested
-                T q2 = w2[e];
-                if constexpr (SP == 1) {
-                    // thermal partner drawn before the collision probability
-                    T vax, vay, vaz;
-                    const RngKey key{s_lo, s_hi, k0, k1};
-                    ion_partner<T>(*D, key, (uint32_t)slot, vax, vay, vaz);
-                    const T gx = vxa[e] - vax, gy = vya[e] - vay, gz = vza[e] - vaz;
-                    q2 = sq3(gx, gy, gz);
-                }
-                int k;
-                if constexpr (is_f64<T>())
-                    k = cs_index((SP == 0 ? D->half_me : D->half_mu_arar) * q2 / EDUPIC_QE, idx_scale, cs_n);
-                else
-                    k = cs_index_f(madd(q2, idx_scale, 0.5f), cs_n);
-                const T speed = sqrt(q2);
-                T xu;
-                if constexpr (is_f64<T>())
-                    xu = sC[k >> cs_shift] * ndt * speed * dt * 1.000001 + 1e-15;
-                else
-                    xu = madd(sC[k >> cs_shift] * ndt * speed, 1.00001f, 1e-6f);
-                if (ut[e] < xu) {
-                    const T sg = __ldg(sig + k);
-                    T pc;
-                    if constexpr (is_f64<T>())
-                        pc = p_coll(sg * ndt * speed * dt);
-                    else
-                        pc = p_coll(sg * ndt * speed);
-                    if (ut[e] < pc) sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;  // executed after the stores below
-                }
+                const RngKey key{s_lo, s_hi, k0, k1};
+                if (direct_test<T, SP>(D, key, slot, vxa[e], vya[e], vza[e], w2[e], ut[e], idx_scale, cs_n, cs_shift,
+                                       sC, ndt, dt))
+                    sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;  // executed after the stores below
             }
-            // deposition of the new position for the next step (Sec. 2.1.1),
-            // gathered below
+            // deposition of the new position for the next step (Sec. 2.1.1);
+            // gathered below when the discharge keeps its particles in cell order
             T d0;
-            dcell[e] = cell<T>(xa[e], inv_dx, ng, d0);
-            dq2[e] = split_q2(d0 - (T)dcell[e]);
+            const int pp = cell<T>(xa[e], inv_dx, ng, d0);
+            const unsigned long long q2 = split_q2(d0 - (T)pp);
+            if (sorted) {
+                dcell[e] = pp;
+                dq2[e] = q2;
+            } else {
+                dep_add(acc, pp, q2);
+            }
         }
-        // Deposition through warp-level reductions where deposits share a
-        // cell (particles in cell order, after the periodic sort): all 32 x
-        // VEC deposits of the warp in one cell -> one set of shared atomics
-        // for the warp; a thread's VEC deposits in one cell -> one set for
-        // the thread; otherwise one set per deposit.  The sums are the same
-        // integers in every case.
-        {
+        // Deposition through warp-level reductions for a discharge that
+        // keeps its particles in cell order (the periodic sort), whose
+        // neighbouring slots share cells: all 32 x VEC deposits of the warp
+        // in one cell -> one set of shared atomics for the warp; a thread's
+        // VEC deposits in one cell -> one set for the thread; otherwise one
+        // set per deposit.  The sums are the same integers in every case.
+        if (sorted) {
             bool same = dcell[0] >= 0;
 #pragma unroll
             for (int e = 1; e < VEC; ++e) same = same && dcell[e] == dcell[0];

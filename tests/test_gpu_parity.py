@@ -10,7 +10,9 @@ Tolerances (derived in the design notes):
   (the field difference above plus last-bit differences of libm functions
   in colliding particles).
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -50,11 +52,15 @@ def _compare_states(sim, ref, d, tol_x=1e-12, tol_v=1e-10):
         assert g[0].size == o[0].size, f"species {sp}: count {g[0].size} vs {o[0].size}"
         if not o[0].size:
             continue
-        assert np.abs(g[0] - o[0]).max() <= tol_x * d.gap_m, f"species {sp}: positions"
-        for c in (1, 2, 3):
-            vs = _vscale(o[c])
-            err = np.abs(g[c] - o[c]).max()
-            assert err <= tol_v * vs, f"species {sp} component {c}: {err} vs scale {vs}"
+        ex = np.abs(g[0] - o[0]).max() / d.gap_m
+        ev = max(np.abs(g[c] - o[c]).max() / _vscale(o[c]) for c in (1, 2, 3))
+        log = os.environ.get("EDUPIC_PARITY_LOG")
+        if log:  # observed deviations, for the tolerance statement
+            with open(log, "a") as f:
+                f.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", "?"), "species": sp,
+                                    "dx_over_L": float(ex), "dv_over_vscale": float(ev)}) + "\n")
+        assert ex <= tol_x, f"species {sp}: positions {ex} of L"
+        assert ev <= tol_v, f"species {sp}: velocities {ev} of the RMS speed"
 
 
 # --------------------------------------------------------------- deposition

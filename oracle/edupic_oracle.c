@@ -17,8 +17,8 @@
  *
  * Each function follows the paper's equations and algorithms in the paper's
  * order, one particle at a time, with no blocking, fusion or reordering beyond
- * what is noted.  Readings of points the paper leaves open are marked
- * "Reading:" and are listed with their reasons in the design notes.
+ * what is noted.  Each point the paper leaves open is marked "Reading:" with
+ * the choice made and its reason.
  *
  * Parity pins: every function here is pinned by a CPU test against a closed
  * form, an invariant, a textbook result, brute force or a published

@@ -1108,8 +1108,9 @@ int edupic_profile_steps(edupic_sim *S, int64_t n_steps, int measure, double out
 int edupic_set_push_grid(edupic_sim *S, int species, int blocks)
 {
     if (!S || (species != 0 && species != 1) || blocks < 0) return EDUPIC_EINVAL;
-    // only the resident limit: a persistent grid below it stalled on large
-    // batches (see the design notes), so such grids are refused
+    // only the resident limit: persistent grids below it (with kernel
+    // versions since withdrawn) stalled on a 64-discharge batch without a
+    // cause found, so such grids are refused
     if (blocks != 0 && blocks != S->grid_max[species]) return EDUPIC_EINVAL;
     const int g = S->grid_max[species];
     if (g != S->grid[species]) {

@@ -1,6 +1,6 @@
 """Parity of the CUDA particle loop with the CPU oracle, through the C ABI.
 
-Tolerances (derived in the design notes):
+Tolerances:
 * integer work (cell indices, fixed-point deposition, collision counts,
   particle counts, histograms) is compared exactly;
 * the field solve: the GPU sums the exact integer form of the tridiagonal

@@ -459,10 +459,10 @@ template <typename T>
 int launch_step(edupic_sim *S, bool ion, int measure)
 {
     cudaError_t e = Launch<T>::push(S->d_desc, S->nd, 0, measure, push_grid(S, 0, measure), S->ng_max,
-                                    S->eepf_max, S->null_any[0], xt_on(S, measure), S->shape[0], S->stream);
+                                    S->eepf_max, S->null_any[0], xt_on(S, measure), S->shape[0], S->sort_any, S->stream);
     if (e == cudaSuccess && ion)
         e = Launch<T>::push(S->d_desc, S->nd, 1, measure, push_grid(S, 1, measure), S->ng_max,
-                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->shape[1], S->stream);
+                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->shape[1], S->sort_any, S->stream);
     if (e == cudaSuccess) e = Launch<T>::finalize(S->d_desc, S->nd, ion ? 1 : 0, measure, S->stream);
     return cuda_status(e);
 }
@@ -1062,21 +1062,21 @@ int edupic_profile_steps(edupic_sim *S, int64_t n_steps, int measure, double out
             if (S->precision == EDUPIC_FP32) {
                 if (e == cudaSuccess)
                     e = Launch<float>::push(S->d_desc, S->nd, 0, measure, push_grid(S, 0, measure), S->ng_max,
-                                            S->eepf_max, S->null_any[0], xt_on(S, measure), S->shape[0], S->stream);
+                                            S->eepf_max, S->null_any[0], xt_on(S, measure), S->shape[0], S->sort_any, S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[1], S->stream);
                 if (e == cudaSuccess && ion[i])
                     e = Launch<float>::push(S->d_desc, S->nd, 1, measure, push_grid(S, 1, measure), S->ng_max,
-                                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->shape[1], S->stream);
+                                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->shape[1], S->sort_any, S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[2], S->stream);
                 if (e == cudaSuccess) e = Launch<float>::finalize(S->d_desc, S->nd, ion[i], measure, S->stream);
             } else {
                 if (e == cudaSuccess)
                     e = Launch<double>::push(S->d_desc, S->nd, 0, measure, push_grid(S, 0, measure), S->ng_max,
-                                            S->eepf_max, S->null_any[0], xt_on(S, measure), S->shape[0], S->stream);
+                                            S->eepf_max, S->null_any[0], xt_on(S, measure), S->shape[0], S->sort_any, S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[1], S->stream);
                 if (e == cudaSuccess && ion[i])
                     e = Launch<double>::push(S->d_desc, S->nd, 1, measure, push_grid(S, 1, measure), S->ng_max,
-                                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->shape[1], S->stream);
+                                            S->eepf_max, S->null_any[1], xt_on(S, measure), S->shape[1], S->sort_any, S->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(E[2], S->stream);
                 if (e == cudaSuccess) e = Launch<double>::finalize(S->d_desc, S->nd, ion[i], measure, S->stream);
             }

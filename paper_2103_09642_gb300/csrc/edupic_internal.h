@@ -154,8 +154,9 @@ struct Launch {
     static cudaError_t averages(const DischargeDev *dd, int nd, int d, cudaStream_t st);
     // xt: the instantiation that accumulates the xt diagnostics (measured steps);
     // shape: launch shape of the others (0..kPushShapes-1, see push_shape)
+    // sorted: some launched discharge keeps cell order (the warp-level deposition variant)
     static cudaError_t push(const DischargeDev *dd, int nd, int species, int measure, int grid, int ng_max,
-                            int eepf_max, int null_any, int xt, int shape, cudaStream_t st);
+                            int eepf_max, int null_any, int xt, int shape, int sorted, cudaStream_t st);
     static cudaError_t finalize(const DischargeDev *dd, int nd, int ion_step, int measure, cudaStream_t st);
     // one block waiting on a barrier that is never armed, for limit_ns (sets kErrTimeout in *err)
     static cudaError_t wait_expiry(unsigned long long limit_ns, int *err, cudaStream_t st);

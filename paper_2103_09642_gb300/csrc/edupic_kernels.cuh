@@ -628,8 +628,9 @@ __device__ __noinline__ bool null_pick(const DischargeDev *Dp, const RngKey key,
 // coarse bound, then the fine entry.  Out of line, so the unrolled particle
 // loop stays small.
 template <typename T, int SP>
-__device__ __noinline__ bool direct_test(const DischargeDev *Dp, const RngKey key, int slot, T vx, T vy, T vz,
-                                         T v2, T u, T idx_scale, int cs_n, int cs_shift, const T *sC, T ndt, T dt)
+__device__ __forceinline__ bool direct_test_body(const DischargeDev *Dp, const RngKey key, int slot, T vx, T vy,
+                                                 T vz, T v2, T u, T idx_scale, int cs_n, int cs_shift, const T *sC,
+                                                 T ndt, T dt)
 {
     const DischargeDev &D = *Dp;
     T q2 = v2;
@@ -657,6 +658,28 @@ __device__ __noinline__ bool direct_test(const DischargeDev *Dp, const RngKey ke
     else
         pc = p_coll(sg * ndt * speed);
     return u < pc;
+}
+
+// Electrons take the test in line (measured faster); ions out of line, whose
+// partner draw (two Philox blocks, two Box-Muller pairs) in the unrolled loop
+// overflowed the instruction cache (measured: 5 warps per issue stalled on
+// instruction fetch in line, 0.5 out of line).
+template <typename T, int SP>
+__device__ __noinline__ bool direct_test_ool(const DischargeDev *Dp, const RngKey key, int slot, T vx, T vy, T vz,
+                                             T v2, T u, T idx_scale, int cs_n, int cs_shift, const T *sC, T ndt,
+                                             T dt)
+{
+    return direct_test_body<T, SP>(Dp, key, slot, vx, vy, vz, v2, u, idx_scale, cs_n, cs_shift, sC, ndt, dt);
+}
+
+template <typename T, int SP>
+__device__ __forceinline__ bool direct_test(const DischargeDev *Dp, const RngKey key, int slot, T vx, T vy, T vz,
+                                            T v2, T u, T idx_scale, int cs_n, int cs_shift, const T *sC, T ndt, T dt)
+{
+    if constexpr (SP == 0)
+        return direct_test_body<T, SP>(Dp, key, slot, vx, vy, vz, v2, u, idx_scale, cs_n, cs_shift, sC, ndt, dt);
+    else
+        return direct_test_ool<T, SP>(Dp, key, slot, vx, vy, vz, v2, u, idx_scale, cs_n, cs_shift, sC, ndt, dt);
 }
 
 // Ar+ + Ar collision of the ion in `slot` with its thermal partner.
@@ -829,7 +852,10 @@ __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eep
 // variant carries none of its code).
 // XT: the variant that also accumulates the xt diagnostics of the measured
 // steps (launched only for measured steps of a simulation that keeps them).
-template <typename T, int SP, bool NC, bool XT, int SH>
+// AGG: the variant for discharges that keep their particles in cell order
+// (the periodic sort), whose deposits go through warp-level reductions
+// (launched only when one does: the others carry none of its code).
+template <typename T, int SP, bool NC, bool XT, int SH, bool AGG = false>
 __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT, SH>().min_blocks)
     k_push(const DischargeDev *__restrict__ DD, int nd, int ng_max, int eepf_max, int measure)
 {
@@ -929,7 +955,6 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
     bool nullc = false;  // null-collision method for the current discharge
     T pstar = 0;         // its P*
     T tbound = 0, v2lim = 0;  // short cut of the direct collision test
-    bool sorted = false;      // the discharge keeps its particles in cell order (warp-level deposition)
     int xcol = -1;       // xt time bin of this step for the current discharge (-1: none)
     T e_of_v2 = 0;       // energy in eV of v^2 (xt variant)
 
@@ -1080,7 +1105,6 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 nullc = ((D->null_coll >> SP) & 1) != 0;
                 pstar = is_f64<T>() ? (T)D->p_star[SP] : (T)D->p_starf[SP];
             }
-            sorted = D->sort_every > 0;
             if constexpr (is_f64<T>()) {
                 tbound = D->tbound[SP];
                 v2lim = D->v2lim[SP];
@@ -1268,7 +1292,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
             T d0;
             const int pp = cell<T>(xa[e], inv_dx, ng, d0);
             const unsigned long long q2 = split_q2(d0 - (T)pp);
-            if (sorted) {
+            if constexpr (AGG) {
                 dcell[e] = pp;
                 dq2[e] = q2;
             } else {
@@ -1281,7 +1305,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
         // in one cell -> one set of shared atomics for the warp; a thread's
         // VEC deposits in one cell -> one set for the thread; otherwise one
         // set per deposit.  The sums are the same integers in every case.
-        if (sorted) {
+        if constexpr (AGG) {
             bool same = dcell[0] >= 0;
 #pragma unroll
             for (int e = 1; e < VEC; ++e) same = same && dcell[e] == dcell[0];

@@ -40,7 +40,15 @@ int blocks_per_sm(size_t smem)
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_push<T, SP, false, XT, SH>, nthr, smem);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_push<T, SP, true, XT, SH>, nthr, smem);
-    return e == cudaSuccess ? (a < b ? a : b) : -1;
+    int c = a;
+    if constexpr (!XT) {
+        cudaFuncSetAttribute(k_push<T, SP, false, false, SH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_push<T, SP, false, false, SH, true>, nthr, smem);
+    }
+    const int m = a < b ? a : b;
+    return e == cudaSuccess ? (m < c ? m : c) : -1;
 }
 
 template <typename T>
@@ -110,30 +118,38 @@ static cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cuda
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// null_any: the null-collision instantiation; sorted: the warp-level
+// deposition instantiation for discharges in cell order (direct test and no
+// xt accumulation only; a sorting discharge with null collisions or xt maps
+// runs the plain deposition, which is exact too)
 template <typename T, int SP, bool XT, int SH>
 cudaError_t push_variant(const DischargeDev *dd, int nd, int measure, int grid, int ng_max, int eb, int null_any,
-                         size_t smem, cudaStream_t st)
+                         int sorted, size_t smem, cudaStream_t st)
 {
     constexpr int nthr = shape_of<T, XT, SH>().threads;
-    return null_any ? launch_pdl(k_push<T, SP, true, XT, SH>, dim3(grid), dim3(nthr), smem, st, dd, nd, ng_max, eb,
-                                 measure)
-                    : launch_pdl(k_push<T, SP, false, XT, SH>, dim3(grid), dim3(nthr), smem, st, dd, nd, ng_max, eb,
-                                 measure);
+    if (null_any)
+        return launch_pdl(k_push<T, SP, true, XT, SH>, dim3(grid), dim3(nthr), smem, st, dd, nd, ng_max, eb, measure);
+    if constexpr (!XT)
+        if (sorted)
+            return launch_pdl(k_push<T, SP, false, false, SH, true>, dim3(grid), dim3(nthr), smem, st, dd, nd, ng_max,
+                              eb, measure);
+    return launch_pdl(k_push<T, SP, false, XT, SH>, dim3(grid), dim3(nthr), smem, st, dd, nd, ng_max, eb, measure);
 }
 
 template <typename T>
 cudaError_t Launch<T>::push(const DischargeDev *dd, int nd, int species, int measure, int grid, int ng_max,
-                            int eepf_max, int null_any, int xt, int shape, cudaStream_t st)
+                            int eepf_max, int null_any, int xt, int shape, int sorted, cudaStream_t st)
 {
     const int eb = species == 0 && measure ? eepf_max : 0;
     const size_t smem = push_smem(nd, ng_max, eb, xt, shape);
     if (xt)
-        return species == 0 ? push_variant<T, 0, true, 0>(dd, nd, measure, grid, ng_max, eb, null_any, smem, st)
-                            : push_variant<T, 1, true, 0>(dd, nd, measure, grid, ng_max, 0, null_any, smem, st);
+        return species == 0 ? push_variant<T, 0, true, 0>(dd, nd, measure, grid, ng_max, eb, null_any, 0, smem, st)
+                            : push_variant<T, 1, true, 0>(dd, nd, measure, grid, ng_max, 0, null_any, 0, smem, st);
     return with_shape(shape, [&](auto sh) {
         constexpr int SH = decltype(sh)::value;
-        return species == 0 ? push_variant<T, 0, false, SH>(dd, nd, measure, grid, ng_max, eb, null_any, smem, st)
-                            : push_variant<T, 1, false, SH>(dd, nd, measure, grid, ng_max, 0, null_any, smem, st);
+        return species == 0
+                   ? push_variant<T, 0, false, SH>(dd, nd, measure, grid, ng_max, eb, null_any, sorted, smem, st)
+                   : push_variant<T, 1, false, SH>(dd, nd, measure, grid, ng_max, 0, null_any, sorted, smem, st);
     });
 }
 

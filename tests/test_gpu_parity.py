@@ -6,9 +6,10 @@ Tolerances:
 * the field solve: the GPU sums the exact integer form of the tridiagonal
   system, the oracle runs the Thomas algorithm in FP64, so phi agrees to
   1e-12 of max|phi| and E to 1e-9 of max|E|;
-* FP64 particle states after k steps: |dx| <= 1e-12 L, |dv| <= 1e-10 v_scale
-  (the field difference above plus last-bit differences of libm functions
-  in colliding particles).
+* FP64 particle states per slot: |dx| <= 1e-12 L, |dv| <= 5e-11 v_scale (the
+  field difference above, accumulated over the steps, plus last-bit
+  differences of libm functions in colliding particles; the largest values
+  observed over every test here are 9e-14 L and 1.5e-11 v_scale).
 """
 import json
 import math
@@ -45,7 +46,7 @@ def _vscale(v):
     return max(float(np.sqrt(np.mean(v * v))) if v.size else 1.0, 1.0)
 
 
-def _compare_states(sim, ref, d, tol_x=1e-12, tol_v=1e-10):
+def _compare_states(sim, ref, d, tol_x=1e-12, tol_v=5e-11):
     for sp in (0, 1):
         g = sim.particles(0, sp)
         o = ref.particles(sp)

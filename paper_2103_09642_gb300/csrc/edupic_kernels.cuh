@@ -622,11 +622,10 @@ __device__ __noinline__ bool null_pick(const DischargeDev *Dp, const RngKey key,
     return null_real<T, SP>(D, k, q2, u, sCnt);
 }
 
-// The direct collision test of Algorithm 6 for a particle that the short
-// cut could not settle (a few per cent): for Ar+ the thermal partner drawn
-// before the probability; the table index of the (relative) energy; an exact
-// coarse bound, then the fine entry.  Out of line, so the unrolled particle
-// loop stays small.
+// The direct collision test of Algorithm 6 for an Ar+ that the short cut
+// could not settle (a few per cent): the thermal partner drawn before the
+// probability; the table index of the relative energy; an exact coarse
+// bound, then the fine entry.
 template <typename T, int SP>
 __device__ __forceinline__ bool direct_test_body(const DischargeDev *Dp, const RngKey key, int slot, T vx, T vy,
                                                  T vz, T v2, T u, T idx_scale, int cs_n, int cs_shift, const T *sC,
@@ -660,26 +659,15 @@ __device__ __forceinline__ bool direct_test_body(const DischargeDev *Dp, const R
     return u < pc;
 }
 
-// Electrons take the test in line (measured faster); ions out of line, whose
-// partner draw (two Philox blocks, two Box-Muller pairs) in the unrolled loop
-// overflowed the instruction cache (measured: 5 warps per issue stalled on
-// instruction fetch in line, 0.5 out of line).
+// Out of line: the partner draw (two Philox blocks, two Box-Muller pairs)
+// in the unrolled particle loop overflowed the instruction cache (measured:
+// 5 warps per issue stalled on instruction fetch in line, 0.5 out of line).
 template <typename T, int SP>
 __device__ __noinline__ bool direct_test_ool(const DischargeDev *Dp, const RngKey key, int slot, T vx, T vy, T vz,
                                              T v2, T u, T idx_scale, int cs_n, int cs_shift, const T *sC, T ndt,
                                              T dt)
 {
     return direct_test_body<T, SP>(Dp, key, slot, vx, vy, vz, v2, u, idx_scale, cs_n, cs_shift, sC, ndt, dt);
-}
-
-template <typename T, int SP>
-__device__ __forceinline__ bool direct_test(const DischargeDev *Dp, const RngKey key, int slot, T vx, T vy, T vz,
-                                            T v2, T u, T idx_scale, int cs_n, int cs_shift, const T *sC, T ndt, T dt)
-{
-    if constexpr (SP == 0)
-        return direct_test_body<T, SP>(Dp, key, slot, vx, vy, vz, v2, u, idx_scale, cs_n, cs_shift, sC, ndt, dt);
-    else
-        return direct_test_ool<T, SP>(Dp, key, slot, vx, vy, vz, v2, u, idx_scale, cs_n, cs_shift, sC, ndt, dt);
 }
 
 // Ar+ + Ar collision of the ion in `slot` with its thermal partner.
@@ -955,6 +943,8 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
     bool nullc = false;  // null-collision method for the current discharge
     T pstar = 0;         // its P*
     T tbound = 0, v2lim = 0;  // short cut of the direct collision test
+    float eepf_k = 0.f, eepf_nbf = 0.f;
+    unsigned long long *eepf_row = nullptr;
     int xcol = -1;       // xt time bin of this step for the current discharge (-1: none)
     T e_of_v2 = 0;       // energy in eV of v^2 (xt variant)
 
@@ -1105,6 +1095,9 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 nullc = ((D->null_coll >> SP) & 1) != 0;
                 pstar = is_f64<T>() ? (T)D->p_star[SP] : (T)D->p_starf[SP];
             }
+            eepf_k = D->e_of_v2_ef * D->inv_eepf_def;
+            eepf_nbf = (float)D->eepf_bins;
+            eepf_row = D->eepf + (blockIdx.x & (kEepfStripes - 1)) * D->eepf_bins;
             if constexpr (is_f64<T>()) {
                 tbound = D->tbound[SP];
                 v2lim = D->v2lim[SP];
@@ -1197,8 +1190,19 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
             }
             const T vxn = SP == 0 ? madd(-e_x, factor, vx) : madd(e_x, factor, vx);
             if (measure && live) pw = madd(e_x, vx + vxn, pw);
-            if (SP == 0 && eepf_on && live && x >= lo && x <= hi)
+            if constexpr (SP == 0 && !is_f64<T>()) {
+                // EEPF sample (Sec. 3.5): every lane forms the bin and only the
+                // atomic is predicated (a tenth of the electrons sample, so a
+                // branch would be taken by some lane of almost every warp)
+                const bool take = eepf_on && live && x >= lo && x <= hi;
+                const T vxc = (T)0.5 * (vx + vxn);
+                const float r = eepf_k * sq3(vxc, vya[e], vza[e]);
+                const bool ok = take && r < eepf_nbf;
+                const int b = ok ? (int)r : 0;
+                if (ok) atomicAdd(eepf_row + b, 1ull);
+            } else if (SP == 0 && eepf_on && live && x >= lo && x <= hi) {
                 eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e]);
+            }
             if constexpr (XT) {
                 // xt sums at x(t) with the time-centred velocity, weighted like the deposition
                 if (xcol >= 0 && live) {
@@ -1279,12 +1283,39 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                     }
                     if (real) sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;
                 }
+            } else if (SP == 0) {
+                // electrons: the exact coarse bound of Algorithm 6's test for
+                // every particle (all lanes together), the fine entry and
+                // P_coll only below it (~0.3 % of the electrons); measured
+                // faster than settling them against P* and testing the P*
+                // share (2.6 %, some lane of almost every warp) in full
+                int k;
+                if constexpr (is_f64<T>())
+                    k = cs_index(D->half_me * w2[e] / EDUPIC_QE, idx_scale, cs_n);
+                else
+                    k = cs_index_f(madd(w2[e], idx_scale, 0.5f), cs_n);
+                const T speed = sqrt(w2[e]);
+                T xu;
+                if constexpr (is_f64<T>())
+                    xu = sC[k >> cs_shift] * ndt * speed * dt * 1.000001 + 1e-15;
+                else
+                    xu = madd(sC[k >> cs_shift] * ndt * speed, 1.00001f, 1e-6f);
+                if (ut[e] < xu) {
+                    const T sg = __ldg(sig + k);
+                    T pc;
+                    if constexpr (is_f64<T>())
+                        pc = p_coll(sg * ndt * speed * dt);
+                    else
+                        pc = p_coll(sg * ndt * speed);
+                    if (ut[e] < pc) sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;
+                }
             } else if (ut[e] < tbound || w2[e] > v2lim) {
-                // R >= tbound with v^2 <= v2lim: P_coll < R for every table
-                // entry (and partner), so only the other particles are tested
+                // Ar+: R >= tbound with v^2 <= v2lim means P_coll < R for every
+                // table entry and partner; only the rest draw the partner and
+                // take the full test (out of line)
                 const RngKey key{s_lo, s_hi, k0, k1};
-                if (direct_test<T, SP>(D, key, slot, vxa[e], vya[e], vza[e], w2[e], ut[e], idx_scale, cs_n, cs_shift,
-                                       sC, ndt, dt))
+                if (direct_test_ool<T, SP>(D, key, slot, vxa[e], vya[e], vza[e], w2[e], ut[e], idx_scale, cs_n,
+                                           cs_shift, sC, ndt, dt))
                     sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;  // executed after the stores below
             }
             // deposition of the new position for the next step (Sec. 2.1.1);

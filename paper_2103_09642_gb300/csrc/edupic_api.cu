@@ -157,6 +157,7 @@ size_t shared_bytes(int nd, size_t elem, int cs_entries)
     o += 2 * align_up((size_t)cs_entries * elem, kAlign);      // sigsum
     o += 2 * align_up((size_t)cs_entries * 2 * elem, kAlign);  // thr1, thr2
     o += 2 * align_up((size_t)kCoarse * elem, kAlign);         // coarse maxima
+    o += 2 * align_up((size_t)kCoarse * elem, kAlign);         // prefix maxima of sigma_tot * v
     return o;
 }
 
@@ -308,6 +309,7 @@ void fill_desc(edupic_sim *S, int d)
         D.cs_sig[sp] = S->cs_sig[sp];
         D.cs_thr[sp] = S->cs_thr[sp];
         D.cs_max[sp] = S->cs_max[sp];
+        D.cs_pm[sp] = S->cs_pm[sp];
         D.cs_shift[sp] = S->desc.size() > (size_t)d ? S->desc[d].cs_shift[sp] : 0;
     }
     D.vdrive = reinterpret_cast<const double *>(b + L.vdrive);
@@ -342,27 +344,23 @@ void update_null_any(edupic_sim *S)
 void null_bounds(edupic_sim *S, int d)
 {
     DischargeDev &D = S->desc[d];
-    // Short cut of the direct test (Algorithm 6).  An energy rounds to the
-    // nearest entry k, so it lies below (k + 1/2) DE and its speed below v_k
-    // at that energy: n sigma_tot,k v <= n max_k(sigma_tot,k v_k) = nu_b, and
-    // P_coll <= 1 - exp(-nu_b dt), for every speed up to that of the last
-    // entry.  The bound is widened far beyond the rounding of either
-    // precision's test.  An Ar+ collides at its relative speed to a partner
-    // drawn by Box-Muller, whose speed is at most about 12.1 sigma_th (the
-    // largest normal the uniforms can give), so the ion's own speed must stay
-    // below the last entry's by 12.2 sigma_th.
+    // Bound of the Ar+ direct test (Algorithm 6).  An energy rounds to the
+    // nearest entry k, so it lies below (k + 1/2) DE and the relative speed g
+    // below v_k at that energy: n sigma_tot,k g <= n max_{k' <= k}(sigma_tot,k'
+    // v_k'), the prefix maximum the kernel reads for the largest entry the ion
+    // can reach.  The partner is drawn by Box-Muller, so its speed is at most
+    // about 12.1 sigma_th (the largest normal the uniforms can give): g <=
+    // |v| + 12.2 sigma_th.  Valid while that bound stays below the last
+    // entry's speed (v2top); beyond it the full test is taken.
     for (int sp = 0; sp < 2; ++sp) {
         const double m = sp == 0 ? kME : kArMassU * kAMU / 2.0;
         const int n = S->sigsum_host[sp].empty() ? 0 : (int)S->sigsum_host[sp].size();
-        const double dt = sp == 0 ? D.dt_e : D.dt_i;
-        const double pb = 1.0 - std::exp(-D.n_gas * S->sigv_top[sp] * (1.0 + 1e-9) * dt);
-        double vtop = n ? std::sqrt(2.0 * ((n - 0.5) * S->cs_de_host[sp]) * kQE / m) : 0.0;
-        if (sp == 1) vtop -= 12.2 * D.sig_th;
-        D.tbound[sp] = n ? pb * (1.0 + 1e-9) + 1e-300 : 0.0;
-        D.tboundf[sp] = n ? (float)(pb * (1.0 + 2e-5) + 1e-6) : 0.0f;
-        D.v2lim[sp] = vtop > 0.0 ? vtop * vtop * (1.0 - 1e-9) : -1.0;
-        D.v2limf[sp] = vtop > 0.0 ? (float)(vtop * vtop * (1.0 - 1e-5)) : -1.0f;
+        const double vtop = n ? std::sqrt(2.0 * ((n - 0.5) * S->cs_de_host[sp]) * kQE / m) : 0.0;
+        D.v2top[sp] = vtop * vtop * (1.0 - 1e-9);
+        D.v2topf[sp] = (float)(vtop * vtop * (1.0 - 1e-5));
     }
+    D.gcap = 12.2 * D.sig_th;
+    D.gcapf = (float)(D.gcap * (1.0 + 1e-5));
     if (!D.null_coll) return;
     for (int sp = 0; sp < 2; ++sp) {
         const std::vector<double> &st = S->sigsum_host[sp];
@@ -416,6 +414,10 @@ void carve_shared(edupic_sim *S, int cs_entries)
     }
     for (int sp = 0; sp < 2; ++sp) {
         S->cs_max[sp] = S->arena + o;
+        o += align_up((size_t)kCoarse * S->elem, kAlign);
+    }
+    for (int sp = 0; sp < 2; ++sp) {
+        S->cs_pm[sp] = S->arena + o;
         o += align_up((size_t)kCoarse * S->elem, kAlign);
     }
 }
@@ -518,7 +520,7 @@ int error_of(const Ctrl &c)
 }
 
 template <typename T>
-int upload_tables(edupic_sim *S, int species, int n_proc, int n_entries, const double *sig)
+int upload_tables(edupic_sim *S, int species, int n_proc, int n_entries, double de_ev, const double *sig)
 {
     std::vector<T> sum((size_t)n_entries);
     std::vector<T> thr(2 * (size_t)n_entries);
@@ -543,9 +545,28 @@ int upload_tables(edupic_sim *S, int species, int n_proc, int n_entries, const d
         if ((double)t < v) t = std::nextafter(t, (T)INFINITY);
         if (t > cmax[j]) cmax[j] = t;
     }
+    // prefix maxima of sigma_tot,k * v_k (v_k the lab / relative speed at the
+    // top of entry k's energy bin) up to the end of each coarse block: a bound
+    // of sigma_tot * g over every energy up to that block (rounded up)
+    std::vector<T> pmax(kCoarse, (T)0);
+    {
+        const double m = species == 0 ? kME : 0.5 * kArMassU * kAMU;
+        double run = 0.0;
+        for (int k = 0; k < n_entries; ++k) {
+            run = std::max(run, (double)sum[k] * std::sqrt(2.0 * ((k + 0.5) * de_ev) * kQE / m));
+            const int j = k >> shift;
+            const double v = run * (1.0 + 1e-6);
+            T t = (T)v;
+            if ((double)t < v) t = std::nextafter(t, (T)INFINITY);
+            pmax[j] = t;  // the last entry of block j leaves the block's prefix maximum
+        }
+        for (int j = ((n_entries - 1) >> shift) + 1; j < kCoarse; ++j) pmax[j] = pmax[j - 1];
+    }
     S->cs_shift_pending[species] = shift;
     cudaError_t e = cudaMemcpyAsync(S->cs_max[species], cmax.data(), sizeof(T) * kCoarse, cudaMemcpyHostToDevice,
                                     S->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->cs_pm[species], pmax.data(), sizeof(T) * kCoarse, cudaMemcpyHostToDevice, S->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(S->cs_sig[species], sum.data(), sizeof(T) * sum.size(), cudaMemcpyHostToDevice,
                             S->stream);
@@ -904,8 +925,8 @@ int edupic_set_cross_sections(edupic_sim *S, int species, int n_proc, int n_entr
     if (n_entries < 1 || n_entries > S->params[0].cs_entries) return EDUPIC_EINVAL;
     for (size_t k = 0; k < (size_t)n_proc * n_entries; ++k)
         if (!(sigma_m2[k] >= 0) || !std::isfinite(sigma_m2[k])) return EDUPIC_EINVAL;
-    int rc = S->precision == EDUPIC_FP32 ? upload_tables<float>(S, species, n_proc, n_entries, sigma_m2)
-                                         : upload_tables<double>(S, species, n_proc, n_entries, sigma_m2);
+    int rc = S->precision == EDUPIC_FP32 ? upload_tables<float>(S, species, n_proc, n_entries, de_ev, sigma_m2)
+                                         : upload_tables<double>(S, species, n_proc, n_entries, de_ev, sigma_m2);
     if (rc) return rc;
     for (int d = 0; d < S->nd; ++d) {
         S->desc[d].cs_shift[species] = S->cs_shift_pending[species];

@@ -51,6 +51,7 @@ struct edupic_sim {
     void *cs_sig[2] = {nullptr, nullptr};
     void *cs_thr[2] = {nullptr, nullptr};
     void *cs_max[2] = {nullptr, nullptr};
+    void *cs_pm[2] = {nullptr, nullptr};  // prefix maxima of sigma_tot * v per coarse block
     bool cs_set[2] = {false, false};
     cudaStream_t stream = nullptr;
     int ng_max = 0, eepf_max = 0, nsub = 1, nt_common = -1;

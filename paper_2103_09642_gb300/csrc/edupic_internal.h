@@ -90,12 +90,10 @@ struct DischargeDev {
     float refl_etaf[2], see_gammaf[2], see_sthf;
     float p_starf[2];   // P* in FP32
     float null_ratf[2]; // n_gas / nu*: nu / nu* = sigsum v null_ratf
-    // exact short cut of the direct collision test, per species: with R the
-    // test uniform and v2 the particle's own squared speed, R >= tbound and
-    // v2 <= v2lim imply P_coll < R for every table entry and (Ar+) every
-    // partner the generator can draw, so the particle does not collide
-    double tbound[2], v2lim[2];
-    float tboundf[2], v2limf[2];
+    // bound of the Ar+ direct collision test: the partner's largest speed
+    // (gcap) and the squared speed at the top of the table's last entry
+    double v2top[2], gcap;
+    float v2topf[2], gcapf;
     double inv_2dx;
     double edge_c;     // e FACTOR_W * 2 / 2^32 * dx / (2 eps0): edge term of E from Q_i - Q_e
     int ng, nt, nsub, n_harm, eepf_bins, ifed_bins, cs_n_e, cs_n_i;
@@ -137,6 +135,7 @@ struct DischargeDev {
     const void *cs_sig[2];     // T[cs_n]
     const void *cs_thr[2];     // T2[cs_n]
     const void *cs_max[2];     // T[kCoarse]: max of cs_sig over 2^cs_shift consecutive entries, rounded up
+    const void *cs_pm[2];      // T[kCoarse]: max of cs_sig_k v_k over every entry up to the end of each block
     int cs_shift[2];
     const double *vdrive;      // V(t) at the N_T steps of one cycle
     // periodic cell sort (sort_every > 0): [chunk][ng] counts, then first

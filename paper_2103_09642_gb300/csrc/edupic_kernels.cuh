@@ -942,7 +942,8 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
     bool eepf_on = false;
     bool nullc = false;  // null-collision method for the current discharge
     T pstar = 0;         // its P*
-    T tbound = 0, v2lim = 0;  // short cut of the direct collision test
+    T v2top = 0, gcap = 0;     // bound of the Ar+ direct test
+    const T *pm = nullptr;    // prefix maxima of sigma_tot * v (Ar+ bound)
     float eepf_k = 0.f, eepf_nbf = 0.f;
     unsigned long long *eepf_row = nullptr;
     int xcol = -1;       // xt time bin of this step for the current discharge (-1: none)
@@ -1098,12 +1099,13 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
             eepf_k = D->e_of_v2_ef * D->inv_eepf_def;
             eepf_nbf = (float)D->eepf_bins;
             eepf_row = D->eepf + (blockIdx.x & (kEepfStripes - 1)) * D->eepf_bins;
+            pm = reinterpret_cast<const T *>(D->cs_pm[SP]);
             if constexpr (is_f64<T>()) {
-                tbound = D->tbound[SP];
-                v2lim = D->v2lim[SP];
+                v2top = D->v2top[SP];
+                gcap = D->gcap;
             } else {
-                tbound = D->tboundf[SP];
-                v2lim = D->v2limf[SP];
+                v2top = D->v2topf[SP];
+                gcap = D->gcapf;
             }
             if constexpr (XT) {
                 xcol = (measure && D->nxt > 0) ? (int)((long long)(s % (unsigned long long)D->nt) / D->nbin) : -1;
@@ -1309,13 +1311,32 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                         pc = p_coll(sg * ndt * speed);
                     if (ut[e] < pc) sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;
                 }
-            } else if (ut[e] < tbound || w2[e] > v2lim) {
-                // Ar+: R >= tbound with v^2 <= v2lim means P_coll < R for every
-                // table entry and partner; only the rest draw the partner and
-                // take the full test (out of line)
+            } else {
+                // Ar+: the relative speed to any partner the generator can draw
+                // is at most gm = |v| + gcap, so P_coll <= n dt max(sigma_tot v)
+                // over the entries up to gm's (the prefix maximum): above that
+                // bound the ion does not collide, whatever its partner.  Only
+                // the rest draw the partner and take the full test (out of line).
+                const T gm = (sqrt(w2[e]) + gcap) * (T)(1.0 + 1e-6);
+                const T gm2 = gm * gm;
+                bool full = gm2 > v2top;  // past the table: no bound
+                if (!full) {
+                    int k;
+                    if constexpr (is_f64<T>())
+                        k = cs_index(D->half_mu_arar * gm2 / EDUPIC_QE, idx_scale, cs_n);
+                    else
+                        k = cs_index_f(madd(gm2, idx_scale, 0.5f), cs_n);
+                    const T pmx = __ldg(pm + (k >> cs_shift));
+                    T xb;
+                    if constexpr (is_f64<T>())
+                        xb = pmx * ndt * dt * 1.000001 + 1e-15;
+                    else
+                        xb = madd(pmx * ndt, 1.00001f, 1e-6f);
+                    full = ut[e] < xb;
+                }
                 const RngKey key{s_lo, s_hi, k0, k1};
-                if (direct_test_ool<T, SP>(D, key, slot, vxa[e], vya[e], vza[e], w2[e], ut[e], idx_scale, cs_n,
-                                           cs_shift, sC, ndt, dt))
+                if (full && direct_test_ool<T, SP>(D, key, slot, vxa[e], vya[e], vza[e], w2[e], ut[e], idx_scale,
+                                                   cs_n, cs_shift, sC, ndt, dt))
                     sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;  // executed after the stores below
             }
             // deposition of the new position for the next step (Sec. 2.1.1);

@@ -161,6 +161,7 @@ DischargeDev idle_desc(edupic_sim *S, int d)
         D.cs_sig[sp] = S->cs_sig[sp];
         D.cs_thr[sp] = S->cs_thr[sp];
         D.cs_max[sp] = S->cs_max[sp];
+        D.cs_pm[sp] = S->cs_pm[sp];
     }
     // keep the table scalars set by edupic_server_set_cross_sections
     if ((size_t)d < S->desc.size()) {

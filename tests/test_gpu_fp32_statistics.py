@@ -148,9 +148,8 @@ def test_config_c2_at_size_fp32_against_the_fp64_oracle():
     energy at each electrode, all within 2 %.  The IFED's share in four
     energy bins per electrode is within 2 % plus four standard deviations of
     its counts (one cycle puts ~1e4 ions on an electrode per seed, so these
-    shares carry ~1 % of Monte Carlo noise on each side).  Measured (design
-    notes, statistical tier): at most 0.4 % on every figure except the IFED
-    bins."""
+    shares carry ~1 % of Monte Carlo noise on each side).  Measured on a
+    GB300: at most 0.4 % on every figure except the IFED bins."""
     ctx = mp.get_context("spawn")
     with ctx.Pool(len(SEEDS)) as pool:
         ref_async = pool.starmap_async(oracle_workers.run_statistics, [(s, N_C2, 0, 1) for s in SEEDS])

@@ -312,6 +312,8 @@ void fill_desc(edupic_sim *S, int d)
         D.cs_pm[sp] = S->cs_pm[sp];
         D.cs_shift[sp] = S->desc.size() > (size_t)d ? S->desc[d].cs_shift[sp] : 0;
     }
+    D.lv_base = S->desc.size() > (size_t)d ? S->desc[d].lv_base : 0;
+    D.lv_n = S->desc.size() > (size_t)d ? S->desc[d].lv_n : 1;
     D.vdrive = reinterpret_cast<const double *>(b + L.vdrive);
     D.sort_every = p.sort_every;
     if (p.sort_every > 0) {
@@ -519,6 +521,75 @@ int error_of(const Ctrl &c)
     return EDUPIC_OK;
 }
 
+// Bucket of v^2 as the particle kernel forms it (lv_bucket): exponent and top
+// five mantissa bits of the particle-precision value, and the smallest v^2 of
+// a bucket.
+static uint64_t lv_bits(float w2)
+{
+    uint32_t b;
+    std::memcpy(&b, &w2, 4);
+    return b >> 18;
+}
+static uint64_t lv_bits(double w2)
+{
+    uint64_t b;
+    std::memcpy(&b, &w2, 8);
+    return b >> 47;
+}
+template <typename T>
+static T lv_lower(uint64_t j)
+{
+    T w;
+    if constexpr (sizeof(T) == 4) {
+        const uint32_t b = (uint32_t)(j << 18);
+        std::memcpy(&w, &b, 4);
+    } else {
+        const uint64_t b = j << 47;
+        std::memcpy(&w, &b, 8);
+    }
+    return w;
+}
+
+// The electrons' collision bound per v^2 bucket (replaces the coarse table of
+// species 0): for each bucket, the largest sigma_tot,k over every entry k the
+// kernel's nearest-entry index can take for a v^2 in the bucket (one entry of
+// margin on each side for the rounding of the index arithmetic) times the
+// speed at the bucket's top, widened by 1e-6 and rounded up.  The kernel
+// multiplies by n dt: P_coll = 1 - exp(-n sigma_tot v dt) of any particle in
+// the bucket lies below it.  Buckets above the table's last entry (where the
+// clamped entry meets unbounded speeds) and the last bucket are +inf.
+template <typename T>
+void lv_table(edupic_sim *S, const std::vector<T> &sum, double de_ev, std::vector<T> &out)
+{
+    const int n = (int)sum.size();
+    // the entry index of v^2 as the kernel forms it (FP32: v^2 * s + 0.5 with
+    // s rounded to float; FP64: (m/2) v^2 / e / de + 0.5), before the clamp
+    const double sf = (double)(float)(0.5 * kME / kQE / de_ev);
+    auto kidx = [&](double w2) -> long long {
+        const double r = sizeof(T) == 4 ? w2 * sf + 0.5 : 0.5 * kME * w2 / kQE / de_ev + 0.5;
+        return r >= 4e18 ? (long long)4e18 : (long long)std::floor(r);
+    };
+    // top: a v^2 whose entry is past the last one
+    const double w2_top = (sizeof(T) == 4 ? (n + 1.0) / sf : (n + 1.0) * de_ev * kQE / (0.5 * kME));
+    const uint64_t jt = lv_bits((T)w2_top) + 1;          // unbounded from this bucket on
+    const uint64_t j0 = jt >= (uint64_t)(kCoarse - 1) ? jt - (kCoarse - 1) : 0;
+    const int nb = (int)(jt - j0 + 1);
+    out.assign(kCoarse, (T)INFINITY);
+    for (int j = 0; j + 1 < nb; ++j) {
+        const double lo = j == 0 ? 0.0 : (double)lv_lower<T>(j0 + j);
+        const double hi = (double)lv_lower<T>(j0 + j + 1);
+        const long long a = std::max(0ll, kidx(lo) - 1), b = std::min((long long)n - 1, kidx(hi) + 1);
+        double m = 0.0;
+        for (long long k = a; k <= b; ++k) m = std::max(m, (double)sum[(size_t)k]);
+        const double v = m * std::sqrt(hi) * (1.0 + 1e-6);
+        T t = (T)v;
+        if ((double)t < v) t = std::nextafter(t, (T)INFINITY);
+        out[(size_t)j] = t;
+    }
+    S->lv_base_pending = (int)j0;
+    S->lv_n_pending = nb;
+}
+
 template <typename T>
 int upload_tables(edupic_sim *S, int species, int n_proc, int n_entries, double de_ev, const double *sig)
 {
@@ -563,6 +634,7 @@ int upload_tables(edupic_sim *S, int species, int n_proc, int n_entries, double 
         for (int j = ((n_entries - 1) >> shift) + 1; j < kCoarse; ++j) pmax[j] = pmax[j - 1];
     }
     S->cs_shift_pending[species] = shift;
+    if (species == 0) lv_table<T>(S, sum, de_ev, cmax);
     cudaError_t e = cudaMemcpyAsync(S->cs_max[species], cmax.data(), sizeof(T) * kCoarse, cudaMemcpyHostToDevice,
                                     S->stream);
     if (e == cudaSuccess)
@@ -931,6 +1003,8 @@ int edupic_set_cross_sections(edupic_sim *S, int species, int n_proc, int n_entr
     for (int d = 0; d < S->nd; ++d) {
         S->desc[d].cs_shift[species] = S->cs_shift_pending[species];
         if (species == 0) {
+            S->desc[d].lv_base = S->lv_base_pending;
+            S->desc[d].lv_n = S->lv_n_pending;
             S->desc[d].cs_n_e = n_entries;
             S->desc[d].cs_de_e = de_ev;
             S->desc[d].inv_cs_de_ef = (float)(1.0 / de_ev);

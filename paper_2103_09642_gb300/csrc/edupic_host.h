@@ -57,6 +57,7 @@ struct edupic_sim {
     int ng_max = 0, eepf_max = 0, nsub = 1, nt_common = -1;
     int phase = 0;  // common step index modulo N_SUB
     int cs_shift_pending[2] = {0, 0};
+    int lv_base_pending = 0, lv_n_pending = 1;  // e- bound table: first v^2 bucket, buckets
     int grid[2] = {0, 0};      // persistent grid of the particle kernel per species (its shape's resident limit)
     int grid_max[2] = {0, 0};  // resident limit (blocks per SM x SMs) of the shape in use
     int shape[2] = {0, 0};     // launch shape of the particle kernel per species (edupic_autotune)

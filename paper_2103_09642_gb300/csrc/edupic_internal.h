@@ -134,9 +134,13 @@ struct DischargeDev {
     void *prod_x, *prod_ve[3], *prod_vi[3];
     const void *cs_sig[2];     // T[cs_n]
     const void *cs_thr[2];     // T2[cs_n]
-    const void *cs_max[2];     // T[kCoarse]: max of cs_sig over 2^cs_shift consecutive entries, rounded up
+    // T[kCoarse]: Ar+: max of cs_sig over 2^cs_shift consecutive entries, rounded up;
+    // e-: max of cs_sig_k times the bucket's top speed over the entries a v^2 of
+    // each bucket (lv_bucket) can index, rounded up (the last bucket: +inf)
+    const void *cs_max[2];
     const void *cs_pm[2];      // T[kCoarse]: max of cs_sig_k v_k over every entry up to the end of each block
     int cs_shift[2];
+    int lv_base, lv_n;         // e-: first v^2 bucket of cs_max[0] and the number of buckets
     const double *vdrive;      // V(t) at the N_T steps of one cycle
     // periodic cell sort (sort_every > 0): [chunk][ng] counts, then first
     // slots, of kSortChunk-particle chunks; scratch copy of one species (T)

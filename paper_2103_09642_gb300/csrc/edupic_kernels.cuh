@@ -83,13 +83,22 @@ struct Words {
     uint32_t a, b, c, d;
 };
 
+// 32 x 32 -> 64-bit product as its (lo, hi) words, one wide multiply.
+__device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t &lo, uint32_t &hi)
+{
+    asm("{\n\t.reg .u64 t;\n\tmul.wide.u32 t, %2, %3;\n\tmov.b64 {%0, %1}, t;\n\t}"
+        : "=r"(lo), "=r"(hi)
+        : "r"(a), "r"(b));
+}
+
 __device__ __forceinline__ Words philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                                         uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        uint32_t lo0, hi0, lo1, hi1;
+        mul_wide(0xD2511F53u, c0, lo0, hi0);
+        mul_wide(0xCD9E8D57u, c2, lo1, hi1);
         const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
         c0 = n0;
         c1 = lo1;
@@ -171,24 +180,49 @@ __device__ __forceinline__ unsigned long long split_q2(float c2)
 // 64-bit shared atomic), and forms Q_p = 2^32 cnt_p - S_p + S_{p-1} when it
 // flushes.  The halves cannot overflow while a cell takes fewer than 2^16
 // deposits between flushes: the kernel flushes every kDepFlush particles,
-// and a flush interval holds at most kDepFlush + one tile particles plus one
-// ionisation product each and the products of the colliders still queued.
+// a flush interval holds at most kDepFlush + one tile particles, and each
+// takes one deposit (ionisation products and emitted electrons deposit
+// straight into the discharge's global accumulators).
 struct DepAcc {
     unsigned int *cnt, *lo, *hi;
+    uint32_t s_cnt, s_lo, s_hi;  // the same arrays as shared-memory addresses
 };
-constexpr int kDepFlush = 28000;
+constexpr int kDepFlush = 64000;
+static_assert(kDepFlush + 1024 < 65536, "a flush interval stays below 2^16 deposits per cell");
+
+// Reduction into shared memory in the shared state space (no generic
+// address resolution, and no ordering against global accesses).
+__device__ __forceinline__ void red_shared_u32(uint32_t addr, uint32_t v)
+{
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
 
 __device__ __forceinline__ void dep_add(const DepAcc &a, int p, unsigned long long q2)
 {
-    atomicAdd(a.cnt + p, 1u);
-    atomicAdd(a.lo + p, (unsigned int)(q2 & 0xFFFFull));
-    atomicAdd(a.hi + p, (unsigned int)(q2 >> 16));
+    red_shared_u32(a.s_cnt + 4u * (uint32_t)p, 1u);
+    red_shared_u32(a.s_lo + 4u * (uint32_t)p, (unsigned int)(q2 & 0xFFFFull));
+    red_shared_u32(a.s_hi + 4u * (uint32_t)p, (unsigned int)(q2 >> 16));
 }
 
 __device__ __forceinline__ unsigned long long dep_cnt(const DepAcc &a, int p) { return a.cnt[p]; }
 __device__ __forceinline__ unsigned long long dep_sum(const DepAcc &a, int p)  // S_p
 {
     return (unsigned long long)a.lo[p] + ((unsigned long long)a.hi[p] << 16);
+}
+
+// Bucket of a squared speed for the electrons' collision bound: the
+// exponent and the top five mantissa bits of its floating-point form (32
+// buckets per octave, monotonic in v^2 >= 0), clamped into the table's
+// [base, base + n - 1]; the last bucket is unbounded.
+__device__ __forceinline__ int lv_bucket(float w2, int base, int n)
+{
+    const int b = (int)(__float_as_uint(w2) >> 18);
+    return min(max(b, base), base + n - 1) - base;
+}
+__device__ __forceinline__ int lv_bucket(double w2, int base, int n)
+{
+    const int b = (int)((unsigned long long)__double_as_longlong(w2) >> 47);
+    return min(max(b, base), base + n - 1) - base;
 }
 
 // Nearest cross-section bin (Algorithm 6).
@@ -416,6 +450,21 @@ static __global__ void k_wait_expiry(unsigned long long limit_ns, int *err)
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Per-thread asynchronous copies global -> shared of 16 bytes (cp.async,
+// bypassing L1), grouped per tile: a thread waits only for its own groups.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <typename V>
 __device__ __forceinline__ V warp_incl_scan(V v)
 {
@@ -505,12 +554,79 @@ __device__ __forceinline__ bool null_real(const DischargeDev &D, int k, T q2, T 
     return real;
 }
 
+// The same decision with sigma_tot of the entry already fetched (sg).
+template <typename T, int SP>
+__device__ __forceinline__ bool null_real_sg(const DischargeDev &D, T sg, T q2, T u, unsigned int *sCnt)
+{
+    bool over, real;
+    if constexpr (is_f64<T>()) {
+        const double nu = sg * D.n_gas * sqrt(q2);
+        over = nu > D.nu_star[SP];
+        real = u / D.p_star[SP] < nu / D.nu_star[SP];
+    } else {
+        const float r = sg * sqrtf(q2) * D.null_ratf[SP];
+        over = r > 1.0f;
+        real = u < r * D.p_starf[SP];
+    }
+    if (over) atomicAdd(sCnt + EDUPIC_C_NULL_OVER, 1u);
+    return real;
+}
+
+// *p += 1 (64-bit, global memory) when c holds: a predicated reduction in
+// the global state space, so that the compiler may keep shared-memory
+// accesses of neighbouring particles on either side of it.
+__device__ __forceinline__ void red_add1_global_if(unsigned long long *p, bool c)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t@q red.relaxed.gpu.global.add.u64 [%0], %2;\n\t}" ::"l"(
+                     __cvta_generic_to_global(p)),
+                 "r"((unsigned)c), "l"(1ull));
+}
+
+// Read-only load of *p when c holds (a predicated load: the address is not
+// touched otherwise), else 0.  Issued early so that its latency overlaps
+// the work before its use.
+__device__ __forceinline__ float ldg_if(const float *p, bool c)
+{
+    float v = 0.0f;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.f32 %0, [%1];\n\t}"
+        : "+f"(v)
+        : "l"(p), "r"((unsigned)c));
+    return v;
+}
+__device__ __forceinline__ double ldg_if(const double *p, bool c)
+{
+    double v = 0.0;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.f64 %0, [%1];\n\t}"
+        : "+d"(v)
+        : "l"(p), "r"((unsigned)c));
+    return v;
+}
+
+// Collision-test uniform of `slot` for species SP: word slot % VEC of the
+// block-0 Philox draw of its group of VEC slots (the draw of the particle loop).
+template <typename T, int SP>
+__device__ __forceinline__ T test_uniform(const RngKey &key, uint32_t slot)
+{
+    constexpr uint32_t VEC = VecOf<T>::n;
+    const Words w = philox(slot / VEC, key.s_lo, key.s_hi, (uint32_t)SP << 8, key.k0, key.k1);
+    if constexpr (is_f64<T>()) {
+        return (slot & 1u) ? u53(w.c, w.d) : u53(w.a, w.b);
+    } else {
+        const uint32_t q = slot & 3u;
+        return u24(q == 0 ? w.a : q == 1 ? w.b : q == 2 ? w.c : w.d);
+    }
+}
+
 // e- + Ar collision of the particle in `slot` (post-push state in memory),
 // including the append record and the deposition of an ionisation pair.
+// With `test`, the slot is a candidate that the particle loop's bound could
+// not settle: the direct test of Algorithm 6 (P_coll of its fine table
+// entry against its test uniform) is taken first, and the particle
+// collides only if it passes.
 template <typename T>
 __device__ __forceinline__ void electron_collision(const DischargeDev &D, int slot, const RngKey &key, T idx_scale,
-                                                   int cs_n, T inv_dx, const DepAcc &acc, int xcol,
-                                                   unsigned int *sCnt)
+                                                   int cs_n, T inv_dx, int xcol,
+                                                   unsigned int *sCnt, bool test, T ndt, T dt)
 {
     using T2 = typename VecOf<T>::pair;
     T *X = reinterpret_cast<T *>(D.x[0]);
@@ -525,6 +641,16 @@ __device__ __forceinline__ void electron_collision(const DischargeDev &D, int sl
         k = cs_index(D.half_me * v2 / EDUPIC_QE, idx_scale, cs_n);
     else
         k = cs_index_f(madd(v2, idx_scale, 0.5f), cs_n);
+    if (test) {
+        const T sg = __ldg(reinterpret_cast<const T *>(D.cs_sig[0]) + k);
+        const T speed = sqrt(v2);
+        T pc;
+        if constexpr (is_f64<T>())
+            pc = p_coll(sg * ndt * speed * dt);
+        else
+            pc = p_coll(sg * ndt * speed);
+        if (!(test_uniform<T, 0>(key, (uint32_t)slot) < pc)) return;
+    }
     const T2 thr = reinterpret_cast<const T2 *>(D.cs_thr[0])[k];
     T u_proc, u_chi, u_eta, u_opal, vej[3];
     draw<T>(key, (uint32_t)slot, 0, 1, u_proc, u_chi);
@@ -560,7 +686,10 @@ __device__ __forceinline__ void electron_collision(const DischargeDev &D, int sl
     T d0;
     const int pp = cell<T>(xn, inv_dx, D.ng, d0);
     const unsigned long long q2 = split_q2(d0 - (T)pp);
-    dep_add(acc, pp, q2);
+    // straight into the discharge's accumulators (products are rare), so the
+    // block's shared counters take one deposit per particle pushed
+    atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_e + pp), 4294967296ull - q2);
+    atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_e + pp + 1), q2);
     atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp), 4294967296ull - q2);
     atomicAdd(reinterpret_cast<unsigned long long *>(D.acc_i + pp + 1), q2);
     if (xcol >= 0) {
@@ -864,6 +993,9 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
     acc.cnt = reinterpret_cast<unsigned int *>(sE2 + ng_max);
     acc.lo = acc.cnt + ng_max;
     acc.hi = acc.lo + ng_max;
+    acc.s_cnt = (uint32_t)__cvta_generic_to_shared(acc.cnt);
+    acc.s_lo = (uint32_t)__cvta_generic_to_shared(acc.lo);
+    acc.s_hi = (uint32_t)__cvta_generic_to_shared(acc.hi);
     int *sPre = reinterpret_cast<int *>(acc.hi + ng_max);
     // xt variant: sum w v_c,x and sum w eps_c of the block, per grid point, on a
     // 16-byte boundary after the prefix (whose end is 4-byte aligned only)
@@ -875,35 +1007,23 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
     __shared__ int sQueue[kWarps][kWarpQueue];  // colliders queued by each warp
     __shared__ int sQn[kWarps];
     __shared__ DischargeDev sD;  // descriptor of the discharge being processed
-    __shared__ __align__(8) uint64_t sFull[S];   // stage holds its tile (bulk-copy transactions)
-    __shared__ __align__(8) uint64_t sEmpty[S];  // every warp has read the stage
-    // set when a bounded wait expired: no further copies are issued and the
-    // remaining tiles are skipped (the error bit is set), so the block still
-    // reaches all its barriers and ends
-    __shared__ volatile int sAbort;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     // set-up data that does not depend on the preceding kernel, fetched
     // before waiting for it: the coarse table (shared by all discharges) and
     // the descriptor of discharge 0
-    {
+    if constexpr (SP == 1) {
         const float4 *cm = reinterpret_cast<const float4 *>(DD[0].cs_max[SP]);
         float4 *dst = reinterpret_cast<float4 *>(sC);
         for (int j = tid; j < (int)(kCoarse * sizeof(T) / 16); j += blockDim.x) dst[j] = cm[j];
+    }
+    {
         const int *src = reinterpret_cast<const int *>(DD);
         int *dd = reinterpret_cast<int *>(&sD);
         for (int i = tid; i < (int)(sizeof(DischargeDev) / 4); i += blockDim.x) dd[i] = src[i];
     }
     if (tid < kWarps) sQn[tid] = 0;
-    if (tid == 0) {
-        sAbort = 0;
-        for (int k = 0; k < S; ++k) {
-            mbar_init(sFull + k, 1);
-            mbar_init(sEmpty + k, kWarps);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
     if (tid < EDUPIC_N_COUNTERS) sCnt[tid] = 0;
     __syncthreads();
     const int cs_shift = sD.cs_shift[SP];
@@ -948,6 +1068,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
     unsigned long long *eepf_row = nullptr;
     int xcol = -1;       // xt time bin of this step for the current discharge (-1: none)
     T e_of_v2 = 0;       // energy in eV of v^2 (xt variant)
+    int lv_base = 0, lv_n = 1;  // electrons: v^2 buckets of the bound table
 
     // execute the collisions queued by this warp (the 32 lanes of the warp;
     // the particles were stored by lanes of the same warp, ordered by the
@@ -959,7 +1080,8 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
         const RngKey key{s_lo, s_hi, k0, k1};
         for (int i = lane; i < qn; i += 32) {
             if (SP == 0)
-                electron_collision<T>(*D, sQueue[warp][i], key, idx_scale, cs_n, inv_dx, acc, XT ? xcol : -1, sCnt);
+                electron_collision<T>(*D, sQueue[warp][i], key, idx_scale, cs_n, inv_dx, XT ? xcol : -1, sCnt,
+                                      !(NC && nullc), ndt, dt);
             else
                 ion_collision<T>(*D, sQueue[warp][i], key, idx_scale, cs_n, sCnt);
         }
@@ -1028,23 +1150,30 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
 
     // Producer (thread 0): bulk-copy tile `pt` (x, vx, vy, vz; a whole TILE,
     // inside the padded capacity) into ring stage `st`.
+    // Tile ring: every thread copies its own VEC particles (16 bytes per array)
+    // of tile `pt` into stage `st` and reads back only those, so no thread
+    // waits for another; each tile is one commit group, S - 1 tiles ahead.
     int pt = t0, pcur = 0;
-    int seen0 = 0;  // tiles whose arrival thread 0 has observed (its own waits)
+    const uint32_t ring_me = (uint32_t)__cvta_generic_to_shared(sRing + tid * VEC);
     auto issue = [&](int st) {
-        while (pt >= sPre[pcur + 1]) ++pcur;
-        const DischargeDev *Dq = DD + pcur;
-        const size_t off = (size_t)(pt - sPre[pcur]) * TILE;
-        uint64_t *bar = sFull + st;
-        T *dst = sRing + (size_t)st * 4 * TILE;
-        mbar_expect_tx(bar, 4u * TILE * (uint32_t)sizeof(T));
-        bulk_load(dst, reinterpret_cast<const T *>(Dq->x[SP]) + off, TILE * sizeof(T), bar);
-        bulk_load(dst + TILE, reinterpret_cast<const T *>(Dq->vx[SP]) + off, TILE * sizeof(T), bar);
-        bulk_load(dst + 2 * TILE, reinterpret_cast<const T *>(Dq->vy[SP]) + off, TILE * sizeof(T), bar);
-        bulk_load(dst + 3 * TILE, reinterpret_cast<const T *>(Dq->vz[SP]) + off, TILE * sizeof(T), bar);
-        ++pt;
+        if (pt < t1) {
+            while (pt >= sPre[pcur + 1]) ++pcur;
+            const DischargeDev *Dq = DD + pcur;
+            const size_t off = (size_t)(pt - sPre[pcur]) * TILE + (size_t)tid * VEC;
+            const uint32_t dst = ring_me + (uint32_t)(st * 4 * TILE * (int)sizeof(T));
+            cp_async16(dst, reinterpret_cast<const T *>(__ldg(reinterpret_cast<const unsigned long long *>(&Dq->x[SP]))) + off);
+            cp_async16(dst + TILE * sizeof(T),
+                       reinterpret_cast<const T *>(__ldg(reinterpret_cast<const unsigned long long *>(&Dq->vx[SP]))) + off);
+            cp_async16(dst + 2 * TILE * sizeof(T),
+                       reinterpret_cast<const T *>(__ldg(reinterpret_cast<const unsigned long long *>(&Dq->vy[SP]))) + off);
+            cp_async16(dst + 3 * TILE * sizeof(T),
+                       reinterpret_cast<const T *>(__ldg(reinterpret_cast<const unsigned long long *>(&Dq->vz[SP]))) + off);
+            ++pt;
+        }
+        cp_async_commit();  // one group per tile, empty past the block's last tile
     };
-    if (tid == 0)
-        for (int k = 0; k < S && pt < t1; ++k) issue(k);
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) issue(k);
 
     for (int t = t0, it = 0; t < t1; ++t, ++it) {
         const int st = it % S;
@@ -1114,6 +1243,24 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 else
                     e_of_v2 = SP == 0 ? D->e_of_v2_ef : D->e_of_v2_if;
             }
+            if constexpr (SP == 0) {
+                // electrons' collision bound per v^2 bucket: n dt max(sigma_tot v)
+                // over the bucket (the table holds max sigma_tot v, rounded up),
+                // widened past the rounding of the test's own arithmetic
+                lv_base = D->lv_base;
+                lv_n = D->lv_n;
+                const T *mt = reinterpret_cast<const T *>(D->cs_max[0]);
+                for (int j = tid; j < lv_n; j += blockDim.x) {
+                    if constexpr (is_f64<T>()) {
+                        sC[j] = mt[j] * ndt * dt * 1.000001 + 1e-15;
+                    } else {
+                        // FP32: the bound B as the integer threshold of the test
+                        // word, u = (w >> 8) 2^-24 < B  <=>  (w >> 8) < ceil(B 2^24)
+                        const float b = madd(mt[j] * ndt, 1.00001f, 1e-6f) * 16777216.0f;
+                        reinterpret_cast<uint32_t *>(sC)[j] = b >= 16777216.0f ? 16777216u : (uint32_t)ceilf(b);
+                    }
+                }
+            }
             const T *ef = reinterpret_cast<const T *>(D->ef_t);
             for (int p = tid; p < ng; p += blockDim.x) {
                 sE2[p] = T2{ef[p], p + 1 < ng ? ef[p + 1] : (T)0};
@@ -1126,40 +1273,6 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
         const int tbase = (t - sPre[cur]) * TILE;
         if (tid == 0) atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_PUSH_E : EDUPIC_C_PUSH_I), (unsigned)min(TILE, n - tbase));
         const int base = tbase + tid * VEC;
-        // this tile's particles from the ring; each warp then marks the stage read
-        // (after an expired wait anywhere in the block, the tile is skipped)
-        bool ok = sAbort == 0;
-        if (ok) {
-            ok = mbar_wait_bounded(sFull + st, (uint32_t)((it / S) & 1));
-            if (!ok) {
-                atomicOr(&D->ctrl->error, kErrTimeout);
-                sAbort = 1;
-            } else if (tid == 0) {
-                seen0 = it + 1;
-            }
-        }
-        {
-            const T *rs = sRing + (size_t)st * 4 * TILE + tid * VEC;
-            unpack(*reinterpret_cast<const V *>(rs), xa);
-            unpack(*reinterpret_cast<const V *>(rs + TILE), vxa);
-            unpack(*reinterpret_cast<const V *>(rs + 2 * TILE), vya);
-            unpack(*reinterpret_cast<const V *>(rs + 3 * TILE), vza);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(sEmpty + st);
-        // the producer refills the stage read in the previous iteration (every
-        // warp marked it then, so this wait rarely blocks) with the tile S - 1
-        // ahead
-        if (tid == 0 && it > 0 && pt < t1 && !sAbort) {
-            const int ps = (it - 1) % S;
-            if (mbar_wait_bounded(sEmpty + ps, (uint32_t)(((it - 1) / S) & 1))) {
-                fence_proxy_async();
-                issue(ps);
-            } else {
-                atomicOr(&D->ctrl->error, kErrTimeout);
-                sAbort = 1;
-            }
-        }
         if (since_flush >= kDepFlush) {
             flush_dep(true);
             since_flush = 0;
@@ -1167,14 +1280,54 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
         since_flush += TILE;
         // a tile adds at most 32 * VEC colliders to this warp's queue
         if (sQn[warp] > kWarpQueue - 32 * VEC) drain();
+        // the tile S - 1 ahead into the stage this thread read in the previous
+        // iteration; then this tile's own copies (allowing S - 1 newer groups)
+        issue((it + S - 1) % S);
+        cp_async_wait<S - 1>();
+        {
+            const T *rs = sRing + (size_t)st * 4 * TILE + tid * VEC;
+            unpack(*reinterpret_cast<const V *>(rs), xa);
+            unpack(*reinterpret_cast<const V *>(rs + TILE), vxa);
+            unpack(*reinterpret_cast<const V *>(rs + 2 * TILE), vya);
+            unpack(*reinterpret_cast<const V *>(rs + 3 * TILE), vza);
+        }
         // lanes with particles in this tile (every lane of the warp reaches this ballot)
-        const unsigned int live_lanes = __ballot_sync(0xffffffffu, base < n && ok);
-        if (base >= n || !ok) continue;  // after an expired wait the stage contents are not used
+        const unsigned int live_lanes = __ballot_sync(0xffffffffu, base < n);
+        if (base >= n) continue;
 
+        // collision-test draw (one Philox block per thread, Sec. 3.3): it
+        // depends on the slots only, and its arithmetic interleaves with the
+        // particles' own below.  tw: the raw words (FP32: u = (word >> 8) 2^-24)
+        T ut[VEC];
+        uint32_t tw[4];
+        {
+            const Words w = philox((uint32_t)base / VEC, s_lo, s_hi, (uint32_t)SP << 8, k0, k1);
+            tw[0] = w.a;
+            tw[1] = w.b;
+            tw[2] = w.c;
+            tw[3] = w.d;
+            if constexpr (is_f64<T>()) {
+                uniforms(w, ut[0], ut[1]);
+            } else {
+                ut[0] = u24(w.a);
+                ut[1] = u24(w.b);
+                ut[2] = u24(w.c);
+                ut[3] = u24(w.d);
+            }
+        }
         // phase 1: gather (Sec. 2.1.3), leapfrog push (Sec. 2.1.4), absorption
-        // test (Sec. 2.1.5), energy and table index
+        // test (Sec. 2.1.5), and the first part of the collision test
+        // (Algorithm 6): the particle's table entry and the bound that settles
+        // most particles without it.  With x = n sigma_tot v dt, P_coll =
+        // 1 - exp(-x) <= x, and the coarse maximum of sigma_tot bounds x from
+        // above: R01 at or above that bound (plus a rounding margin) decides
+        // "no collision".  The fine entry of the particles below it (and of
+        // the null-collision picks) is fetched here, predicated, and used
+        // after the deposition.
         bool in[VEC];
-        T w2[VEC];  // v^2 after the push
+        bool cand[VEC];  // a candidate for a collision: the full test follows
+        T sgp[VEC];      // e-: sigma_tot of the fine entry (candidates); Ar+: the bound's table value
+        bool far[VEC];   // Ar+: relative speed bound past the table (always a candidate)
         T pw = (T)0;  // E_x (v_old + v_new) of the measured pushes of this tile
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
@@ -1199,9 +1352,9 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 const bool take = eepf_on && live && x >= lo && x <= hi;
                 const T vxc = (T)0.5 * (vx + vxn);
                 const float r = eepf_k * sq3(vxc, vya[e], vza[e]);
-                const bool ok = take && r < eepf_nbf;
-                const int b = ok ? (int)r : 0;
-                if (ok) atomicAdd(eepf_row + b, 1ull);
+                const bool okb = take && r < eepf_nbf;
+                const int b = okb ? (int)r : 0;
+                red_add1_global_if(eepf_row + b, okb);
             } else if (SP == 0 && eepf_on && live && x >= lo && x <= hi) {
                 eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e]);
             }
@@ -1221,134 +1374,132 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
             xa[e] = live ? xn : x;
             vxa[e] = live ? vxn : vx;
             in[e] = live && (xn >= (T)0.0) && (xn <= L);
-            // own squared speed after the push (the direct test's short cut)
-            w2[e] = sq3(vxn, vya[e], vza[e]);
-        }
-        if (measure) pw_acc += (double)pw;
-        // phase 2: collision-test uniforms (one Philox block per thread)
-        T ut[VEC];
-        {
-            const Words w = philox((uint32_t)base / VEC, s_lo, s_hi, (uint32_t)SP << 8, k0, k1);
-            if constexpr (is_f64<T>()) {
-                uniforms(w, ut[0], ut[1]);
-            } else {
-                ut[0] = u24(w.a);
-                ut[1] = u24(w.b);
-                ut[2] = u24(w.c);
-                ut[3] = u24(w.d);
-            }
-        }
-        int dcell[VEC];                // cell of each deposit (-1: none)
-        unsigned long long dq2[VEC];  // its fixed-point weight of point cell + 1
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-            dcell[e] = -1;
-            dq2[e] = 0ull;
-        }
-        // phase 3: collision test (Algorithm 6), absorption records, deposition.
-        // With x = n sigma_tot v dt, P_coll = 1 - exp(-x) <= x, and the coarse
-        // maximum of sigma_tot bounds x from above: R01 at or above that bound
-        // (plus a rounding margin) decides "no collision" without the fine
-        // table; otherwise the test of Algorithm 6 is taken with the fine
-        // entry.  Colliding slots are queued.
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-            const int slot = base + e;
-            if (slot >= n) break;
-            if (!in[e]) {
-                const RngKey key{s_lo, s_hi, k0, k1};
-                const T xr = absorbed<T, SP>(D, key, slot, xa[e], vxa[e], vya[e], vza[e], measure, sCnt);
-                if (SP == 1 || xr < (T)0.0) continue;
-                // reflected electron: continues in the gap (v^2 and the table index are unchanged)
-                xa[e] = xr;
-                vxa[e] = -vxa[e];
-            }
-            if (NC && nullc) {
-                // null-collision method: picked with P*, tested in place; only
-                // real collisions are queued
-                if (ut[e] < pstar) {
-                    ++picks;
-                    bool real;
-                    if constexpr (SP == 0) {
-                        // e-: the energy's table entry, in line
-                        const T q2 = sq3(vxa[e], vya[e], vza[e]);
-                        int k;
-                        if constexpr (is_f64<T>())
-                            k = cs_index(D->half_me * q2 / EDUPIC_QE, idx_scale, cs_n);
-                        else
-                            k = cs_index_f(madd(q2, idx_scale, 0.5f), cs_n);
-                        real = null_real<T, 0>(*D, k, q2, ut[e], sCnt);
-                    } else {
-                        // Ar+: the thermal partner is drawn out of line
-                        const RngKey key{s_lo, s_hi, k0, k1};
-                        real = null_pick<T, SP>(D, key, slot, vxa[e], vya[e], vza[e], ut[e], idx_scale, cs_n, sCnt);
-                    }
-                    if (real) sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;
-                }
-            } else if (SP == 0) {
-                // electrons: the exact coarse bound of Algorithm 6's test for
-                // every particle (all lanes together), the fine entry and
-                // P_coll only below it (~0.3 % of the electrons); measured
-                // faster than settling them against P* and testing the P*
-                // share (2.6 %, some lane of almost every warp) in full
-                int k;
-                if constexpr (is_f64<T>())
-                    k = cs_index(D->half_me * w2[e] / EDUPIC_QE, idx_scale, cs_n);
-                else
-                    k = cs_index_f(madd(w2[e], idx_scale, 0.5f), cs_n);
-                const T speed = sqrt(w2[e]);
-                T xu;
-                if constexpr (is_f64<T>())
-                    xu = sC[k >> cs_shift] * ndt * speed * dt * 1.000001 + 1e-15;
-                else
-                    xu = madd(sC[k >> cs_shift] * ndt * speed, 1.00001f, 1e-6f);
-                if (ut[e] < xu) {
-                    const T sg = __ldg(sig + k);
-                    T pc;
+            // own squared speed after the push
+            const T w2 = sq3(vxn, vya[e], vza[e]);
+            far[e] = false;
+            if constexpr (SP == 0) {
+                if (NC && nullc) {
+                    // the null-collision pick, tested in place below with its fine entry
+                    int k;
                     if constexpr (is_f64<T>())
-                        pc = p_coll(sg * ndt * speed * dt);
+                        k = cs_index(D->half_me * w2 / EDUPIC_QE, idx_scale, cs_n);
                     else
-                        pc = p_coll(sg * ndt * speed);
-                    if (ut[e] < pc) sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;
+                        k = cs_index_f(madd(w2, idx_scale, 0.5f), cs_n);
+                    cand[e] = live && ut[e] < pstar;
+                    sgp[e] = ldg_if(sig + k, cand[e]);
+                } else {
+                    // the bound of the particle's v^2 bucket; candidates are
+                    // tested against their fine entry in the collider
+                    const int j = lv_bucket(w2, lv_base, lv_n);
+                    if constexpr (is_f64<T>())
+                        cand[e] = live && ut[e] < sC[j];
+                    else
+                        cand[e] = live && (tw[e] >> 8) < reinterpret_cast<const uint32_t *>(sC)[j];
+                    sgp[e] = (T)0;
                 }
             } else {
                 // Ar+: the relative speed to any partner the generator can draw
                 // is at most gm = |v| + gcap, so P_coll <= n dt max(sigma_tot v)
-                // over the entries up to gm's (the prefix maximum): above that
-                // bound the ion does not collide, whatever its partner.  Only
-                // the rest draw the partner and take the full test (out of line).
-                const T gm = (sqrt(w2[e]) + gcap) * (T)(1.0 + 1e-6);
+                // over the entries up to gm's (the prefix maximum); its table
+                // value is fetched here and compared below
+                const T gm = (sqrt(w2) + gcap) * (T)(1.0 + 1e-6);
                 const T gm2 = gm * gm;
-                bool full = gm2 > v2top;  // past the table: no bound
-                if (!full) {
-                    int k;
-                    if constexpr (is_f64<T>())
-                        k = cs_index(D->half_mu_arar * gm2 / EDUPIC_QE, idx_scale, cs_n);
-                    else
-                        k = cs_index_f(madd(gm2, idx_scale, 0.5f), cs_n);
-                    const T pmx = __ldg(pm + (k >> cs_shift));
-                    T xb;
-                    if constexpr (is_f64<T>())
-                        xb = pmx * ndt * dt * 1.000001 + 1e-15;
-                    else
-                        xb = madd(pmx * ndt, 1.00001f, 1e-6f);
-                    full = ut[e] < xb;
-                }
-                const RngKey key{s_lo, s_hi, k0, k1};
-                if (full && direct_test_ool<T, SP>(D, key, slot, vxa[e], vya[e], vza[e], w2[e], ut[e], idx_scale,
-                                                   cs_n, cs_shift, sC, ndt, dt))
-                    sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;  // executed after the stores below
+                far[e] = gm2 > v2top;  // past the table: no bound
+                int k;
+                if constexpr (is_f64<T>())
+                    k = cs_index(D->half_mu_arar * gm2 / EDUPIC_QE, idx_scale, cs_n);
+                else
+                    k = cs_index_f(madd(gm2, idx_scale, 0.5f), cs_n);
+                cand[e] = live;
+                sgp[e] = ldg_if(pm + (k >> cs_shift), live && !far[e] && !(NC && nullc));
             }
-            // deposition of the new position for the next step (Sec. 2.1.1);
-            // gathered below when the discharge keeps its particles in cell order
+        }
+        if (measure) pw_acc += (double)pw;
+        // deposition of the new position for the next step (Sec. 2.1.1) of the
+        // particles that stay in the gap (a reflected electron deposits below);
+        // gathered below when the discharge keeps its particles in cell order
+        int dcell[VEC];                // cell of each deposit (-1: none)
+        unsigned long long dq2[VEC];  // its fixed-point weight of point cell + 1
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
             T d0;
             const int pp = cell<T>(xa[e], inv_dx, ng, d0);
             const unsigned long long q2 = split_q2(d0 - (T)pp);
             if constexpr (AGG) {
-                dcell[e] = pp;
+                dcell[e] = in[e] ? pp : -1;
                 dq2[e] = q2;
             } else {
-                dep_add(acc, pp, q2);
+                if (in[e]) dep_add(acc, pp, q2);
+            }
+        }
+        if constexpr (SP == 1) {
+            // Ar+: the bound decides (null-collision method: the pick)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                if (NC && nullc) {
+                    cand[e] = cand[e] && ut[e] < pstar;
+                } else {
+                    T xb;
+                    if constexpr (is_f64<T>())
+                        xb = sgp[e] * ndt * dt * 1.000001 + 1e-15;
+                    else
+                        xb = madd(sgp[e] * ndt, 1.00001f, 1e-6f);
+                    cand[e] = cand[e] && (far[e] || ut[e] < xb);
+                }
+            }
+        }
+        // the rare part, per lane: particles that left the gap (absorption,
+        // reflection, emission) and the full collision test of the candidates;
+        // colliding slots are queued (executed after the stores below)
+        bool rare = false;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) rare = rare || cand[e] || (base + e < n && !in[e]);
+        if (rare) {
+            const RngKey key{s_lo, s_hi, k0, k1};
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const int slot = base + e;
+                bool go = cand[e];
+                if (slot < n && !in[e]) {
+                    const T xr = absorbed<T, SP>(D, key, slot, xa[e], vxa[e], vya[e], vza[e], measure, sCnt);
+                    if (SP == 1 || xr < (T)0.0) {
+                        go = false;
+                    } else {
+                        // reflected electron: continues in the gap (v^2 and the
+                        // table index are unchanged) and deposits at its mirror image
+                        xa[e] = xr;
+                        vxa[e] = -vxa[e];
+                        T d0;
+                        const int pp = cell<T>(xr, inv_dx, ng, d0);
+                        const unsigned long long q2 = split_q2(d0 - (T)pp);
+                        if constexpr (AGG) {
+                            dcell[e] = pp;
+                            dq2[e] = q2;
+                        } else {
+                            dep_add(acc, pp, q2);
+                        }
+                    }
+                }
+                if (!go) continue;
+                bool real;
+                if constexpr (SP == 0) {
+                    if (NC && nullc) {
+                        ++picks;
+                        real = null_real_sg<T, 0>(*D, sgp[e], sq3(vxa[e], vya[e], vza[e]), ut[e], sCnt);
+                    } else {
+                        real = true;  // a candidate: the collider takes the direct test
+                    }
+                } else {
+                    if (NC && nullc) {
+                        ++picks;
+                        real = null_pick<T, SP>(D, key, slot, vxa[e], vya[e], vza[e], ut[e], idx_scale, cs_n, sCnt);
+                    } else {
+                        real = direct_test_ool<T, SP>(D, key, slot, vxa[e], vya[e], vza[e],
+                                                      sq3(vxa[e], vya[e], vza[e]), ut[e], idx_scale, cs_n,
+                                                      cs_shift, sC, ndt, dt);
+                    }
+                }
+                if (real) sQueue[warp][atomicAdd(sQn + warp, 1)] = slot;
             }
         }
         // Deposition through warp-level reductions for a discharge that
@@ -1405,10 +1556,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
         *reinterpret_cast<V *>(VX + base) = pack(vxa, V{});
     }
     if (cur >= 0) flush(true);
-    // after an expired wait: wait (bounded) for the copies issued but never
-    // observed, so that none is still writing shared memory when the block ends
-    if (tid == 0 && sAbort)
-        for (int j = seen0; j < pt - t0; ++j) (void)mbar_wait_bounded(sFull + j % S, (uint32_t)((j / S) & 1));
+    cp_async_wait_all();  // the groups issued past the block's last tile are empty; none is left writing
 }
 
 // ---------------------------------------------------------------- field solve

@@ -176,6 +176,8 @@ DischargeDev idle_desc(edupic_sim *S, int d)
         D.g_idx_if = o.g_idx_if;
         D.cs_shift[0] = o.cs_shift[0];
         D.cs_shift[1] = o.cs_shift[1];
+        D.lv_base = o.lv_base;
+        D.lv_n = o.lv_n;
     }
     return D;
 }

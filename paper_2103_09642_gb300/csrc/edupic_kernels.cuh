@@ -157,9 +157,9 @@ template <typename T>
 __device__ __forceinline__ int cell(T x, T inv_dx, int ng, T &c0)
 {
     c0 = x * inv_dx;
-    int p = (int)c0;
-    p = p < 0 ? 0 : (p > ng - 2 ? ng - 2 : p);
-    return p;
+    // one unsigned minimum: c0 in (-1, 0] truncates to 0, anything below -1
+    // (no particle inside the gap) wraps above ng - 2 and clamps there
+    return (int)min((unsigned)(int)c0, (unsigned)(ng - 2));
 }
 
 // Fixed-point weight of point p+1: round-to-nearest-even(c2 * 2^32).
@@ -1371,8 +1371,10 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 }
             }
             const T xn = madd(vxn, dt, x);
-            xa[e] = live ? xn : x;
-            vxa[e] = live ? vxn : vx;
+            // slots past the count (the last tile's padding) are pushed too and
+            // written back to the padding, which holds no particle
+            xa[e] = xn;
+            vxa[e] = vxn;
             in[e] = live && (xn >= (T)0.0) && (xn <= L);
             // own squared speed after the push
             const T w2 = sq3(vxn, vya[e], vza[e]);

@@ -597,6 +597,8 @@ def run_ours(args):
     tot = lambda: sum(split())
     s0 = split()
     c0 = sum(s0)
+    ne0 = sum(sim.counts(k)[0] for k in range(nd))
+    ni0 = sum(sim.counts(k)[1] for k in range(nd))
     _log("timed steps")
     clocks = Clocks(local)
     barrier()
@@ -684,7 +686,11 @@ def run_ours(args):
                        "l2": "256 MB buffer written between timed steps (outside the timed events); "
                              "particle state 0.7 GB > L2",
                        "parallelism": f"replicas x{ws}", "cross_sections": "stand-in set",
-                       "push_grid": list(grids), "push_shape": _shapes_desc(shapes), "graph_replay": graphs},
+                       "push_grid": list(grids), "push_shape": _shapes_desc(shapes), "graph_replay": graphs,
+                       # the steady-shape states still relax during the timed steps; `value` counts the
+                       # pushes actually made, so it is exact for the population of the timed region
+                       "population_timed": {"e_start": int(ne0), "e_end": int(n_e), "i_start": int(ni0),
+                                            "i_end": int(n_i)}},
             "roofline": roof,
             "pushes": pushes,
             "gpu_launches": int(args.steps * (2 * BATCH_STEPS + BATCH_STEPS // ds[0].ion_subcycle)),

@@ -1,7 +1,7 @@
 """A short, fixed run of the particle loop for profiler captures.
 
   python -m paper_2103_09642_gb300.profile_case --n 5000000 --steps 3 [--fp64] [--discharges K]
-  python -m paper_2103_09642_gb300.profile_case --mix 64 --steps 3
+  python -m paper_2103_09642_gb300.profile_case --mix 64 --steps 3 [--shape S]
 
 Runs the reference discharge in a steady-shape state with n particles per
 species (split over K independent discharges), or with --mix K the batch of
@@ -24,6 +24,7 @@ def main():
     ap.add_argument("--discharges", type=int, default=1)
     ap.add_argument("--measure", action="store_true")
     ap.add_argument("--mix", type=int, default=0, help="the batch of this many seed-drawn discharges")
+    ap.add_argument("--shape", type=int, default=-1, help="launch shape of the particle kernel (both species)")
     a = ap.parse_args()
 
     import torch
@@ -47,6 +48,9 @@ def main():
     sim = ed.simulation_for(ds, ed.FP64 if a.fp64 else ed.FP32, sigma=(se, si), de_ev=wl.CS_DE_EV,
                             particles=parts)
     sim.set_graphs(False)
+    if a.shape >= 0:
+        sim.set_push_shape(ed.ELECTRONS, a.shape)
+        sim.set_push_shape(ed.IONS, a.shape)
     sim.step(a.warmup, measure=a.measure)
     sim.synchronize()
     sim.step(a.steps, measure=a.measure)

@@ -110,6 +110,28 @@ __device__ __forceinline__ Words philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     return Words{c0, c1, c2, c3};
 }
 
+// The same block with the ten round keys (k0, k1 of rounds 2j and 2j + 1 in
+// rk[j]) read from shared memory, where they are formed once per discharge.
+__device__ __forceinline__ Words philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const uint4 *rk)
+{
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const uint4 k = rk[j];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t lo0, hi0, lo1, hi1;
+            mul_wide(0xD2511F53u, c0, lo0, hi0);
+            mul_wide(0xCD9E8D57u, c2, lo1, hi1);
+            const uint32_t n0 = hi1 ^ c1 ^ (h ? k.z : k.x), n2 = hi0 ^ c3 ^ (h ? k.w : k.y);
+            c0 = n0;
+            c1 = lo1;
+            c2 = n2;
+            c3 = lo0;
+        }
+    }
+    return Words{c0, c1, c2, c3};
+}
+
 struct RngKey {
     uint32_t s_lo, s_hi, k0, k1;
 };
@@ -202,6 +224,18 @@ __device__ __forceinline__ void dep_add(const DepAcc &a, int p, unsigned long lo
     red_shared_u32(a.s_cnt + 4u * (uint32_t)p, 1u);
     red_shared_u32(a.s_lo + 4u * (uint32_t)p, (unsigned int)(q2 & 0xFFFFull));
     red_shared_u32(a.s_hi + 4u * (uint32_t)p, (unsigned int)(q2 >> 16));
+}
+
+// The same deposit when c holds: one predicate for the three reductions, so
+// no branch is taken around them.
+__device__ __forceinline__ void dep_add_if(const DepAcc &a, int p, unsigned long long q2, bool c)
+{
+    const uint32_t o = 4u * (uint32_t)p;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %6, 0;\n\t@q red.shared.add.u32 [%0], %3;\n\t"
+        "@q red.shared.add.u32 [%1], %4;\n\t@q red.shared.add.u32 [%2], %5;\n\t}" ::"r"(a.s_cnt + o),
+        "r"(a.s_lo + o), "r"(a.s_hi + o), "r"(1u), "r"((unsigned int)(q2 & 0xFFFFull)), "r"((unsigned int)(q2 >> 16)),
+        "r"((unsigned)c));
 }
 
 __device__ __forceinline__ unsigned long long dep_cnt(const DepAcc &a, int p) { return a.cnt[p]; }
@@ -1006,6 +1040,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
     __shared__ int sW[33];
     __shared__ int sQueue[kWarps][kWarpQueue];  // colliders queued by each warp
     __shared__ int sQn[kWarps];
+    __shared__ uint4 sRK[5];  // Philox round keys of the current discharge (philox_rk)
     __shared__ DischargeDev sD;  // descriptor of the discharge being processed
 
     const int tid = threadIdx.x;
@@ -1221,6 +1256,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
             VZ = reinterpret_cast<T *>(D->vz[SP]);
             cs_n = SP == 0 ? D->cs_n_e : D->cs_n_i;
             eepf_on = SP == 0 && measure;
+            if (!eepf_on) lo = (T)INFINITY;  // an empty sampling window: no position is at or above it
             if constexpr (NC) {
                 nullc = ((D->null_coll >> SP) & 1) != 0;
                 pstar = is_f64<T>() ? (T)D->p_star[SP] : (T)D->p_starf[SP];
@@ -1242,6 +1278,12 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                     e_of_v2 = (SP == 0 ? D->half_me : D->half_mar) / EDUPIC_QE;
                 else
                     e_of_v2 = SP == 0 ? D->e_of_v2_ef : D->e_of_v2_if;
+            }
+            if (tid < 5) {
+                // round keys of the test draws: k0 + r 0x9E3779B9, k1 + r 0xBB67AE85 (rounds 2 tid, 2 tid + 1)
+                const uint32_t r = 2u * (uint32_t)tid;
+                sRK[tid] = make_uint4(k0 + r * 0x9E3779B9u, k1 + r * 0xBB67AE85u, k0 + (r + 1u) * 0x9E3779B9u,
+                                      k1 + (r + 1u) * 0xBB67AE85u);
             }
             if constexpr (SP == 0) {
                 // electrons' collision bound per v^2 bucket: n dt max(sigma_tot v)
@@ -1301,7 +1343,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
         T ut[VEC];
         uint32_t tw[4];
         {
-            const Words w = philox((uint32_t)base / VEC, s_lo, s_hi, (uint32_t)SP << 8, k0, k1);
+            const Words w = philox_rk((uint32_t)base / VEC, s_lo, s_hi, (uint32_t)SP << 8, sRK);
             tw[0] = w.a;
             tw[1] = w.b;
             tw[2] = w.c;
@@ -1349,12 +1391,13 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 // EEPF sample (Sec. 3.5): every lane forms the bin and only the
                 // atomic is predicated (a tenth of the electrons sample, so a
                 // branch would be taken by some lane of almost every warp)
-                const bool take = eepf_on && live && x >= lo && x <= hi;
+                // (the window is empty when not measuring; the bin's address is
+                // formed by every lane and used only by those that sample)
+                const bool take = live && x >= lo && x <= hi;
                 const T vxc = (T)0.5 * (vx + vxn);
                 const float r = eepf_k * sq3(vxc, vya[e], vza[e]);
                 const bool okb = take && r < eepf_nbf;
-                const int b = okb ? (int)r : 0;
-                red_add1_global_if(eepf_row + b, okb);
+                red_add1_global_if(eepf_row + (int)r, okb);
             } else if (SP == 0 && eepf_on && live && x >= lo && x <= hi) {
                 eepf_sample<T>(D, (T)0.5 * (vx + vxn), vya[e], vza[e]);
             }
@@ -1431,7 +1474,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 dcell[e] = in[e] ? pp : -1;
                 dq2[e] = q2;
             } else {
-                if (in[e]) dep_add(acc, pp, q2);
+                dep_add_if(acc, pp, q2, in[e]);
             }
         }
         if constexpr (SP == 1) {

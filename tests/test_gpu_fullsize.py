@@ -1,12 +1,13 @@
 """Parity on the paths the particle kernel takes only at large sizes.
 
 * The block-local deposition counters are flushed to the discharge's int64
-  accumulator every 30 000 particles a block processes.  With the persistent
-  grid of two blocks per SM, a launch needs about 10^7 particles of one
-  species before every block passes that point, so these tests step 1.2e7
-  electrons and 1.2e7 ions once (ion subcycle 1, so both densities are
-  re-deposited in that step) and require the fused deposition to equal the
-  fixed-point definition (Algorithm 2) of the stored positions exactly.
+  accumulator every 64 000 particles a block processes.  With the persistent
+  grid of two blocks per SM, a launch needs about 2*10^7 particles of one
+  species before every block passes that point, so these tests step that
+  many electrons and ions once (66 000 per block of the grid; ion subcycle
+  1, so both densities are re-deposited in that step) and require the fused
+  deposition to equal the fixed-point definition (Algorithm 2) of the
+  stored positions exactly.
   In FP64 the whole step is also compared with the oracle.
 * Event lists above 8192 entries per step are sorted in global memory
   instead of shared memory before the canonical hole fill (Algorithm 5):
@@ -43,7 +44,8 @@ def _deposit_of_positions(x, d, inv_dx, precision):
 
 @pytest.mark.parametrize("precision", [ed.FP64, ed.FP32])
 def test_one_step_at_full_size_fused_deposition_is_exact(precision):
-    n = 12_000_000
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 2 * sms * 66_000  # every block of the two-per-SM grid takes more than the 64 000-particle flush interval
     # no space charge and no drive (E = 0): the step is push, absorption,
     # collisions (stand-in cross sections) and the fused deposition
     d = wl.reference_discharge(weight=0.0, harmonics=((13.56e6, 0.0),), ion_subcycle=1,
@@ -52,6 +54,8 @@ def test_one_step_at_full_size_fused_deposition_is_exact(precision):
     e = wl.maxwellian(n, d.gap_m, 3.0 * QE, ME, rng)
     i = wl.maxwellian(n, d.gap_m, 0.05 * QE, MAR, rng)
     sim = ed.simulation_for([d], precision, sigma=(SE, SI), de_ev=DE, particles=[(e, i)])
+    grid = sim.push_grid()
+    assert max(grid) * 65_000 < n, grid  # each block passes the flush point
     sim.step(1)
     f = sim.fields(0)
     ne, ni, step = sim.counts(0)

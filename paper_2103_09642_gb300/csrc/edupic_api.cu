@@ -255,6 +255,8 @@ void fill_desc(edupic_sim *S, int d)
         D.vx[s] = b + L.vx[s];
         D.vy[s] = b + L.vy[s];
         D.vz[s] = b + L.vz[s];
+        // layout_of takes the four arrays one after another with the same padded size
+        D.pstride[s] = (long long)(L.vx[s] - L.x[s]);
         D.holes[s] = reinterpret_cast<int *>(b + L.holes[s]);
     }
     D.q_e = reinterpret_cast<long long *>(b + L.q_e);

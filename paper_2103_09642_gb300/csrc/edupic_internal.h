@@ -107,6 +107,7 @@ struct DischargeDev {
     unsigned long long seed;
     // particle SoA (T = float or double)
     void *x[2], *vx[2], *vy[2], *vz[2];
+    long long pstride[2];  // bytes from x to vx, vx to vy and vy to vz (the arena spaces them equally)
     // grid (FP64 unless noted)
     long long *q_e, *q_i;      // deposition sums used by the current step
     long long *acc_e, *acc_i;  // deposition of the next step (ions: next ion step)

@@ -1188,21 +1188,32 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
     // Tile ring: every thread copies its own VEC particles (16 bytes per array)
     // of tile `pt` into stage `st` and reads back only those, so no thread
     // waits for another; each tile is one commit group, S - 1 tiles ahead.
-    int pt = t0, pcur = 0;
+    // The discharge of the tile being fetched (pcur) is cached with its tile
+    // range and this thread's source address in its x array; v_x, v_y, v_z
+    // follow at equal strides.
+    int pt = t0, pcur = -1, la_base = 0, la_end = 0;
+    const char *la_src = nullptr;
+    long long la_stride = 0;
     const uint32_t ring_me = (uint32_t)__cvta_generic_to_shared(sRing + tid * VEC);
     auto issue = [&](int st) {
         if (pt < t1) {
-            while (pt >= sPre[pcur + 1]) ++pcur;
-            const DischargeDev *Dq = DD + pcur;
-            const size_t off = (size_t)(pt - sPre[pcur]) * TILE + (size_t)tid * VEC;
+            if (pt >= la_end) {
+                do {
+                    ++pcur;
+                } while (pt >= sPre[pcur + 1]);
+                la_base = sPre[pcur];
+                la_end = sPre[pcur + 1];
+                const DischargeDev *Dq = DD + pcur;
+                la_src = reinterpret_cast<const char *>(__ldg(reinterpret_cast<const unsigned long long *>(&Dq->x[SP]))) +
+                         (size_t)tid * VEC * sizeof(T);
+                la_stride = __ldg(&Dq->pstride[SP]);
+            }
+            const char *src = la_src + (size_t)(pt - la_base) * (TILE * sizeof(T));
             const uint32_t dst = ring_me + (uint32_t)(st * 4 * TILE * (int)sizeof(T));
-            cp_async16(dst, reinterpret_cast<const T *>(__ldg(reinterpret_cast<const unsigned long long *>(&Dq->x[SP]))) + off);
-            cp_async16(dst + TILE * sizeof(T),
-                       reinterpret_cast<const T *>(__ldg(reinterpret_cast<const unsigned long long *>(&Dq->vx[SP]))) + off);
-            cp_async16(dst + 2 * TILE * sizeof(T),
-                       reinterpret_cast<const T *>(__ldg(reinterpret_cast<const unsigned long long *>(&Dq->vy[SP]))) + off);
-            cp_async16(dst + 3 * TILE * sizeof(T),
-                       reinterpret_cast<const T *>(__ldg(reinterpret_cast<const unsigned long long *>(&Dq->vz[SP]))) + off);
+            cp_async16(dst, src);
+            cp_async16(dst + TILE * sizeof(T), src + la_stride);
+            cp_async16(dst + 2 * TILE * sizeof(T), src + 2 * la_stride);
+            cp_async16(dst + 3 * TILE * sizeof(T), src + 3 * la_stride);
             ++pt;
         }
         cp_async_commit();  // one group per tile, empty past the block's last tile
@@ -1210,12 +1221,14 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
 #pragma unroll
     for (int k = 0; k < S - 1; ++k) issue(k);
 
-    for (int t = t0, it = 0; t < t1; ++t, ++it) {
-        const int st = it % S;
-        if (cur < 0 || t >= sPre[cur + 1]) {
+    int cur_base = 0, cur_end = 0;  // tile range of the current discharge
+    for (int t = t0, st = 0; t < t1; ++t, st = st + 1 == S ? 0 : st + 1) {
+        if (t >= cur_end) {
             if (cur >= 0) flush(false);
             ++cur;
             while (sPre[cur + 1] <= t) ++cur;
+            cur_base = sPre[cur];
+            cur_end = sPre[cur + 1];
             if (cur != staged) {
                 const int *src = reinterpret_cast<const int *>(DD + cur);
                 int *dd = reinterpret_cast<int *>(&sD);
@@ -1312,7 +1325,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
             since_flush = 0;
             __syncthreads();
         }
-        const int tbase = (t - sPre[cur]) * TILE;
+        const int tbase = (t - cur_base) * TILE;
         if (tid == 0) atomicAdd(sCnt + (SP == 0 ? EDUPIC_C_PUSH_E : EDUPIC_C_PUSH_I), (unsigned)min(TILE, n - tbase));
         const int base = tbase + tid * VEC;
         if (since_flush >= kDepFlush) {
@@ -1324,7 +1337,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
         if (sQn[warp] > kWarpQueue - 32 * VEC) drain();
         // the tile S - 1 ahead into the stage this thread read in the previous
         // iteration; then this tile's own copies (allowing S - 1 newer groups)
-        issue((it + S - 1) % S);
+        issue(st ? st - 1 : S - 1);
         cp_async_wait<S - 1>();
         {
             const T *rs = sRing + (size_t)st * 4 * TILE + tid * VEC;
@@ -1627,9 +1640,16 @@ struct FieldScratch {
 
 // Load (Q_e, Q_i) of the owned points; swap in the accumulated deposition
 // when `swap` (and add the current field to the time sums when `measure`).
+// The arrays are distinct (one discharge's grid blocks); the restrict
+// qualifiers let every load be issued before the stores instead of one
+// round trip per array.
 template <int PMAX>
-__device__ __forceinline__ void load_q(const DischargeDev &D, int first, int last, bool swap, bool next_ion,
-                                       bool measure, long long *Qe, long long *Qi)
+__device__ __forceinline__ void load_q_arrays(long long *__restrict__ q_e, long long *__restrict__ q_i,
+                                              long long *__restrict__ acc_e, long long *__restrict__ acc_i,
+                                              const long long *__restrict__ f_cur, double *__restrict__ sum_qe,
+                                              double *__restrict__ sum_qi, double *__restrict__ sum_f, int first,
+                                              int last, bool swap, bool next_ion, bool measure, long long *Qe,
+                                              long long *Qi)
 {
 #pragma unroll
     for (int j = 0; j < PMAX; ++j) {
@@ -1638,26 +1658,34 @@ __device__ __forceinline__ void load_q(const DischargeDev &D, int first, int las
         Qi[j] = 0;
         if (p >= last) continue;
         if (swap && measure) {
-            D.sum_qe[p] += (double)D.q_e[p];
-            D.sum_qi[p] += (double)D.q_i[p];
-            D.sum_f[p] += (double)D.f_cur[p];
+            sum_qe[p] += (double)q_e[p];
+            sum_qi[p] += (double)q_i[p];
+            sum_f[p] += (double)f_cur[p];
         }
         if (swap) {
-            Qe[j] = D.acc_e[p];
-            D.acc_e[p] = 0;
-            D.q_e[p] = Qe[j];
+            Qe[j] = acc_e[p];
+            acc_e[p] = 0;
+            q_e[p] = Qe[j];
             if (next_ion) {
-                Qi[j] = D.acc_i[p];
-                D.acc_i[p] = 0;
-                D.q_i[p] = Qi[j];
+                Qi[j] = acc_i[p];
+                acc_i[p] = 0;
+                q_i[p] = Qi[j];
             } else {
-                Qi[j] = D.q_i[p];
+                Qi[j] = q_i[p];
             }
         } else {
-            Qe[j] = D.q_e[p];
-            Qi[j] = D.q_i[p];
+            Qe[j] = q_e[p];
+            Qi[j] = q_i[p];
         }
     }
+}
+
+template <int PMAX>
+__device__ __forceinline__ void load_q(const DischargeDev &D, int first, int last, bool swap, bool next_ion,
+                                       bool measure, long long *Qe, long long *Qi)
+{
+    load_q_arrays<PMAX>(D.q_e, D.q_i, D.acc_e, D.acc_i, D.f_cur, D.sum_qe, D.sum_qi, D.sum_f, first, last, swap,
+                        next_ion, measure, Qe, Qi);
 }
 
 // Field of within-cycle step tc.  full: also densities n_e, n_i and phi.
@@ -1673,6 +1701,7 @@ __device__ void solve_field(const DischargeDev &D, long long tc, bool swap, bool
         D.fs->sum_V += D.fs->V;
         D.fs->sum_d0 += D.fs->d0;
     }
+    const double V = D.vdrive[tc];  // read before the stores below
     long long Qe[PMAX], Qi[PMAX], F[PMAX];
     load_q<PMAX>(D, first, last, swap, next_ion, measure, Qe, Qi);
     // F: inclusive scan of D_p over p = 0..M (D_p = 0 at the electrodes)
@@ -1698,7 +1727,6 @@ __device__ void solve_field(const DischargeDev &D, long long tc, bool swap, bool
         }
     }
     const __int128 gtot = group_sum128(gpart, sm.w128, gtid, G, bar);
-    const double V = D.vdrive[tc];
     const double c = D.poisson_c;
     if (gtid == 0) {
         const double d0 = (c * (double)gtot - V) / (double)M;

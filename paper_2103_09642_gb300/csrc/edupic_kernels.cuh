@@ -66,6 +66,41 @@ __host__ __device__ constexpr bool is_f64() { return std::is_same<T, double>::va
 __device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double madd(double a, double b, double c) { return a * b + c; }
 
+// Paired FP32 arithmetic (sm_100+ f32x2 instructions): two independent
+// lanes in one instruction, each rounded exactly as the scalar operation
+// (round to nearest, denormals flushed, as the FP32 unit is compiled).
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.ftz.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.ftz.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c)  // a * b + c, one rounding
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.ftz.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_sq3(float2 x, float2 y, float2 z)  // sq3 of two lanes
+{
+    return f2_fma(z, z, f2_fma(y, y, f2_mul(x, x)));
+}
+
 // v_x^2 + v_y^2 + v_z^2, summed left to right
 template <typename T>
 __device__ __forceinline__ T sq3(T x, T y, T z)
@@ -1384,22 +1419,80 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
         T sgp[VEC];      // e-: sigma_tot of the fine entry (candidates); Ar+: the bound's table value
         bool far[VEC];   // Ar+: relative speed bound past the table (always a candidate)
         T pw = (T)0;  // E_x (v_old + v_new) of the measured pushes of this tile
+        // FP32: two particles per step of the loop through paired FP32
+        // instructions (each lane rounds as the scalar operation); their
+        // measured E_x (v_old + v_new) summed per lane
+        constexpr int PR = is_f64<T>() ? 1 : 2;
+        float2 pw2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) {
+        for (int h = 0; h < VEC; h += PR) {
+            T c0v[PR], exv[PR], vxnv[PR], xnv[PR], w2v[PR], rv[PR];
+            int pv[PR];
+            if constexpr (PR == 2) {
+                const float2 xp = make_float2(xa[h], xa[h + 1]);
+                const float2 vxp = make_float2(vxa[h], vxa[h + 1]);
+                const float2 vyp = make_float2(vya[h], vya[h + 1]);
+                const float2 vzp = make_float2(vza[h], vza[h + 1]);
+                const float2 c0 = f2_mul(xp, make_float2(inv_dx, inv_dx));
+                pv[0] = (int)min((unsigned)(int)c0.x, (unsigned)(ng - 2));
+                pv[1] = (int)min((unsigned)(int)c0.y, (unsigned)(ng - 2));
+                const T2 ep0 = sE2[pv[0]], ep1 = sE2[pv[1]];
+                // c0 - p (one rounding, as the subtraction), then the linear weights
+                const float2 fr = f2_fma(make_float2((float)pv[0], (float)pv[1]), make_float2(-1.0f, -1.0f), c0);
+                const float2 ex = make_float2(madd(fr.x, ep0.y - ep0.x, ep0.x), madd(fr.y, ep1.y - ep1.x, ep1.x));
+                // electrons: -e_x factor is e_x (-factor), the same product
+                const float fs = SP == 0 ? -factor : factor;
+                const float2 vxn = f2_fma(ex, make_float2(fs, fs), vxp);
+                const float2 sv = f2_add(vxp, vxn);
+                if (measure) {
+                    const float2 t = f2_fma(ex, sv, pw2);
+                    pw2.x = base + h < n ? t.x : pw2.x;
+                    pw2.y = base + h + 1 < n ? t.y : pw2.y;
+                }
+                if constexpr (SP == 0) {
+                    const float2 vxc = f2_mul(make_float2(0.5f, 0.5f), sv);
+                    const float2 r = f2_mul(make_float2(eepf_k, eepf_k), f2_sq3(vxc, vyp, vzp));
+                    rv[0] = r.x;
+                    rv[1] = r.y;
+                }
+                const float2 xn = f2_fma(vxn, make_float2(dt, dt), xp);
+                const float2 w2 = f2_sq3(vxn, vyp, vzp);
+                c0v[0] = c0.x;
+                c0v[1] = c0.y;
+                exv[0] = ex.x;
+                exv[1] = ex.y;
+                vxnv[0] = vxn.x;
+                vxnv[1] = vxn.y;
+                xnv[0] = xn.x;
+                xnv[1] = xn.y;
+                w2v[0] = w2.x;
+                w2v[1] = w2.y;
+            } else {
+                const T x = xa[h], vx = vxa[h];
+                T c0;
+                const int p = cell<T>(x, inv_dx, ng, c0);
+                const T2 ep = sE2[p];
+                const T c1 = (T)(p + 1) - c0, c2 = c0 - (T)p;
+                const T e_x = c1 * ep.x + c2 * ep.y;
+                const T vxn = SP == 0 ? madd(-e_x, factor, vx) : madd(e_x, factor, vx);
+                if (measure && base + h < n) pw = madd(e_x, vx + vxn, pw);
+                c0v[0] = c0;
+                pv[0] = p;
+                exv[0] = e_x;
+                vxnv[0] = vxn;
+                xnv[0] = madd(vxn, dt, x);
+                w2v[0] = sq3(vxn, vya[h], vza[h]);
+                rv[0] = (T)0;
+            }
+#pragma unroll
+        for (int q = 0; q < PR; ++q) {
+            const int e = h + q;
             const bool live = base + e < n;
             const T x = xa[e], vx = vxa[e];
-            T c0;
-            const int p = cell<T>(x, inv_dx, ng, c0);
-            const T2 ep = sE2[p];
-            T e_x;
-            if constexpr (is_f64<T>()) {
-                const T c1 = (T)(p + 1) - c0, c2 = c0 - (T)p;
-                e_x = c1 * ep.x + c2 * ep.y;
-            } else {
-                e_x = madd(c0 - (T)p, ep.y - ep.x, ep.x);  // same linear weights
-            }
-            const T vxn = SP == 0 ? madd(-e_x, factor, vx) : madd(e_x, factor, vx);
-            if (measure && live) pw = madd(e_x, vx + vxn, pw);
+            const T c0 = c0v[q], vxn = vxnv[q];
+            const int p = pv[q];
+            (void)exv;
+            (void)vx;
             if constexpr (SP == 0 && !is_f64<T>()) {
                 // EEPF sample (Sec. 3.5): every lane forms the bin and only the
                 // atomic is predicated (a tenth of the electrons sample, so a
@@ -1407,8 +1500,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 // (the window is empty when not measuring; the bin's address is
                 // formed by every lane and used only by those that sample)
                 const bool take = live && x >= lo && x <= hi;
-                const T vxc = (T)0.5 * (vx + vxn);
-                const float r = eepf_k * sq3(vxc, vya[e], vza[e]);
+                const float r = rv[q];  // eepf_k sq3(v_c) of the time-centred velocity
                 const bool okb = take && r < eepf_nbf;
                 red_add1_global_if(eepf_row + (int)r, okb);
             } else if (SP == 0 && eepf_on && live && x >= lo && x <= hi) {
@@ -1426,14 +1518,14 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                     atomicAdd(sXe + p + 1, w2 * en);
                 }
             }
-            const T xn = madd(vxn, dt, x);
+            const T xn = xnv[q];
             // slots past the count (the last tile's padding) are pushed too and
             // written back to the padding, which holds no particle
             xa[e] = xn;
             vxa[e] = vxn;
             in[e] = live && (xn >= (T)0.0) && (xn <= L);
             // own squared speed after the push
-            const T w2 = sq3(vxn, vya[e], vza[e]);
+            const T w2 = w2v[q];
             far[e] = false;
             if constexpr (SP == 0) {
                 if (NC && nullc) {
@@ -1472,22 +1564,41 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 sgp[e] = ldg_if(pm + (k >> cs_shift), live && !far[e] && !(NC && nullc));
             }
         }
-        if (measure) pw_acc += (double)pw;
+        }
+        if (measure) pw_acc += (double)pw + (double)(pw2.x + pw2.y);
         // deposition of the new position for the next step (Sec. 2.1.1) of the
         // particles that stay in the gap (a reflected electron deposits below);
         // gathered below when the discharge keeps its particles in cell order
         int dcell[VEC];                // cell of each deposit (-1: none)
         unsigned long long dq2[VEC];  // its fixed-point weight of point cell + 1
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-            T d0;
-            const int pp = cell<T>(xa[e], inv_dx, ng, d0);
-            const unsigned long long q2 = split_q2(d0 - (T)pp);
-            if constexpr (AGG) {
-                dcell[e] = in[e] ? pp : -1;
-                dq2[e] = q2;
+        for (int h = 0; h < VEC; h += PR) {
+            int ppv[PR];
+            unsigned long long q2v[PR];
+            if constexpr (PR == 2) {
+                // the cell and weight of cell (x) and split_q2, two lanes per instruction
+                const float2 c0 = f2_mul(make_float2(xa[h], xa[h + 1]), make_float2(inv_dx, inv_dx));
+                ppv[0] = (int)min((unsigned)(int)c0.x, (unsigned)(ng - 2));
+                ppv[1] = (int)min((unsigned)(int)c0.y, (unsigned)(ng - 2));
+                const float2 c2 =
+                    f2_fma(make_float2((float)ppv[0], (float)ppv[1]), make_float2(-1.0f, -1.0f), c0);
+                const float2 sc = f2_mul(c2, make_float2(4294967296.0f, 4294967296.0f));
+                q2v[0] = c2.x < 1.0f ? (unsigned long long)__float2uint_rn(sc.x) : 4294967296ull;
+                q2v[1] = c2.y < 1.0f ? (unsigned long long)__float2uint_rn(sc.y) : 4294967296ull;
             } else {
-                dep_add_if(acc, pp, q2, in[e]);
+                T d0;
+                ppv[0] = cell<T>(xa[h], inv_dx, ng, d0);
+                q2v[0] = split_q2(d0 - (T)ppv[0]);
+            }
+#pragma unroll
+            for (int q = 0; q < PR; ++q) {
+                const int e = h + q;
+                if constexpr (AGG) {
+                    dcell[e] = in[e] ? ppv[q] : -1;
+                    dq2[e] = q2v[q];
+                } else {
+                    dep_add_if(acc, ppv[q], q2v[q], in[e]);
+                }
             }
         }
         if constexpr (SP == 1) {

@@ -1353,7 +1353,10 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
             }
             const T *ef = reinterpret_cast<const T *>(D->ef_t);
             for (int p = tid; p < ng; p += blockDim.x) {
-                sE2[p] = T2{ef[p], p + 1 < ng ? ef[p + 1] : (T)0};
+                // FP64: (E_p, E_p+1); FP32: (E_p, E_p+1 - E_p), the slope the
+                // linear weights take (the same FP32 difference the push formed)
+                const T e1 = p + 1 < ng ? ef[p + 1] : (T)0;
+                sE2[p] = is_f64<T>() ? T2{ef[p], e1} : T2{ef[p], e1 - ef[p]};
                 acc.cnt[p] = acc.lo[p] = acc.hi[p] = 0u;
                 if constexpr (XT) sXv[p] = sXe[p] = (T)0;
             }
@@ -1439,7 +1442,7 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
                 const T2 ep0 = sE2[pv[0]], ep1 = sE2[pv[1]];
                 // c0 - p (one rounding, as the subtraction), then the linear weights
                 const float2 fr = f2_fma(make_float2((float)pv[0], (float)pv[1]), make_float2(-1.0f, -1.0f), c0);
-                const float2 ex = make_float2(madd(fr.x, ep0.y - ep0.x, ep0.x), madd(fr.y, ep1.y - ep1.x, ep1.x));
+                const float2 ex = make_float2(madd(fr.x, ep0.y, ep0.x), madd(fr.y, ep1.y, ep1.x));
                 // electrons: -e_x factor is e_x (-factor), the same product
                 const float fs = SP == 0 ? -factor : factor;
                 const float2 vxn = f2_fma(ex, make_float2(fs, fs), vxp);

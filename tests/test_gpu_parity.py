@@ -308,6 +308,74 @@ def test_direct_test_short_cut_at_the_edge_of_its_bound():
     assert c["coll_e_ela"] > 0 and c["coll_i_iso"] + c["coll_i_back"] > 0
 
 
+def _bucket_edge_case(precision):
+    """Electrons with v^2 a few ulps either side of the boundaries of the
+    kernel's v^2 buckets (exponent and top five mantissa bits of the
+    particle-precision value) between 8 and 12 eV, no field, and an elastic
+    cross section rising as E^12, so that the collision bound of neighbouring
+    buckets differs by a third: a bound taken from the wrong side of a
+    boundary would miss colliders."""
+    nent = 40_000
+    e_ev = (np.arange(nent) * DE).astype(np.float64)
+    se = np.zeros((3, nent))
+    se[0] = 3e-18 * (e_ev / 10.0) ** 12
+    _, si = wl.standin_cross_sections(nent)
+    d = wl.reference_discharge(weight=0.0, harmonics=((13.56e6, 0.0),), capacity=1 << 18, seed=21)
+    me = 9.1093837015e-31
+    if precision == ed.FP64:
+        shift, ftype, itype, ulp = 47, np.float64, np.uint64, 2.0 ** -52
+    else:
+        shift, ftype, itype, ulp = 18, np.float32, np.uint32, 2.0 ** -23
+    w_lo = np.array(2 * 8.0 * 1.602176634e-19 / me, dtype=ftype)
+    w_hi = np.array(2 * 12.0 * 1.602176634e-19 / me, dtype=ftype)
+    j0 = int(w_lo.view(itype)) >> shift
+    j1 = int(w_hi.view(itype)) >> shift
+    bounds = np.array([(j << shift) for j in range(j0 + 1, j1 + 1)], dtype=itype).view(ftype).astype(np.float64)
+    vs = np.concatenate([np.sqrt(bounds) * (1.0 + m * ulp) for m in range(-3, 4)])
+    rep = 1000
+    vx = np.repeat(vs, rep)
+    rng = np.random.default_rng(21)
+    e = wl.Particles(rng.uniform(0.0, d.gap_m, vx.size), vx.copy(), np.zeros(vx.size), np.zeros(vx.size))
+    i = wl.maxwellian(1000, d.gap_m, 0.0, 39.948 * 1.66053906660e-27, rng)
+    return d, e, i, (se, si), bounds.size
+
+
+def test_electron_bound_at_bucket_edges_fp64():
+    """FP64: counters bit-exact against the oracle (which tests every
+    electron in full) over three steps, states per slot."""
+    d, e, i, sigma, nb = _bucket_edge_case(ed.FP64)
+    assert nb >= 15
+    sim, ref = _pair(d, e, i, sigma=sigma)
+    for _ in range(3):
+        sim.step(1)
+        ref.step(1)
+        assert sim.counters(0) == ref.counters()
+        _compare_states(sim, ref, d)
+    c = ref.counters()
+    assert 0.1 * e.n < c["coll_e_ela"] < 0.9 * 3 * e.n
+    sim.close()
+
+
+def test_electron_bound_at_bucket_edges_fp32():
+    """FP32: one step's elastic collisions equal the expected sum of P_coll =
+    1 - exp(-n sigma(E) v dt) over the electrons (nearest table entry), within
+    five binomial standard deviations plus 0.5 %: a bound from the neighbouring
+    bucket would remove ~10 % of them."""
+    d, e, i, sigma, nb = _bucket_edge_case(ed.FP32)
+    assert nb >= 15
+    sim = ed.simulation_for([d], ed.FP32, sigma=sigma, de_ev=DE, particles=[(e, i)])
+    sim.step(1)
+    c = sim.counters(0)
+    sim.close()
+    drv = oracle.Sim(d, sigma[0], sigma[1], DE, e, i).derived()
+    v = np.abs(e.vx.astype(np.float32).astype(np.float64))
+    en = 0.5 * 9.1093837015e-31 * v * v / 1.602176634e-19
+    k = np.minimum(np.floor(en / DE + 0.5).astype(np.int64), sigma[0].shape[1] - 1)
+    p = 1.0 - np.exp(-drv["n_gas"] * sigma[0][0][k] * v * drv["dt_e"])
+    mean, sd = p.sum(), math.sqrt((p * (1 - p)).sum())
+    assert abs(c["coll_e_ela"] - mean) <= 5 * sd + 0.005 * mean, (c["coll_e_ela"], mean, sd)
+
+
 def test_null_collision_fp32_pick_rate():
     """FP32: the share of in-gap electrons picked per step is P* (binomial)."""
     d, e, i = wl.reference_steady(seed=10, n=40_000)

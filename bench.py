@@ -46,11 +46,11 @@ HBM_PEAK_FALLBACK = 6800.0   # GB/s: the profiling recipe's fallback, used only 
 BYTES_PER_PUSH_FP32 = 24     # read x, vx, vy, vz (16 B) + write x, vx (8 B)
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the electron
 # particle kernel on the 64-discharge batch, from one ncu capture
-# (profiles/k_push_electron_batch64.md: 336.497 + 125.479 MB for 19 973 477
+# (profiles/k_push_electron_batch64.md: 336.512 + 125.846 MB for 19 973 477
 # electrons), valid for the kernel source whose hash is given (null
 # otherwise); scaled to a launch of the bench by its electron count (traffic
 # grows in proportion: the particle streams dominate it).
-TRAFFIC = {"sha": "33ad48e284d80b57", "bytes": 336496640 + 125479424, "particles": 19973477}
+TRAFFIC = {"sha": "47f25bf9b1035364", "bytes": 336512256 + 125845504, "particles": 19973477}
 BATCH_DISCHARGES = 64
 BATCH_STEPS = 400             # time steps per bench step (20 ion subcycles)
 N_STEADY = 500_000            # plain leg: particles per species of the steady-shape state

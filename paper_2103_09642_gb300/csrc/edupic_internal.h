@@ -43,7 +43,7 @@ enum : int {
     kErrProducts = 2,  // more ionisations in a step than kEvents
     kErrCapacity = 4,  // created pairs dropped at particle capacity
     kErrNan = 8,       // non-finite position
-    kErrTimeout = 16,  // a bounded wait for an asynchronous copy expired
+    kErrTimeout = 16,  // a bounded device wait expired (the wait self-test)
 };
 
 // Per-discharge counters and counts, written by the kernels.

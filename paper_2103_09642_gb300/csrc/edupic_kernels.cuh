@@ -442,35 +442,14 @@ __device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// ---------------------------------------------------------------- bulk copies
-// One-dimensional bulk copies global -> shared (cp.async.bulk), completed on
-// an mbarrier through its transaction count.  Addresses and sizes are
-// multiples of 16 bytes (particle arrays are 256-byte aligned and tiles are
-// whole multiples of 4 KB).
+// ---------------------------------------------------------------- mbarrier wait
+// A bounded wait on an mbarrier phase (used by the self-test of the expiry
+// path; the particle kernel itself waits only for its own copies).
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
@@ -516,8 +495,6 @@ static __global__ void k_wait_expiry(unsigned long long limit_ns, int *err)
     __syncthreads();
     if (!mbar_wait_bounded(&bar, 0, limit_ns)) atomicOr(err, kErrTimeout);
 }
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Per-thread asynchronous copies global -> shared of 16 bytes (cp.async,
 // bypassing L1), grouped per tile: a thread waits only for its own groups.
@@ -1021,10 +998,11 @@ __host__ __device__ constexpr PushShape shape_of()
     return XT ? push_shape_xt<T>() : push_shape<T>(SH);
 }
 
-// Dynamic shared memory: [tile ring: stages x 4 arrays x TILE T][coarse
-// sigma_max: kCoarse T][E pairs: ng_max T2][deposition: 3 x ng_max u32]
-// [tile prefix: nd+1 int][xt variant, from the next 16-byte boundary: sum
-// w v_c,x and sum w eps_c, ng_max T each].
+// Dynamic shared memory: [tile ring: stages x 4 arrays x TILE T][bound
+// table: kCoarse T (e-: the threshold of each v^2 bucket; Ar+: the coarse
+// sigma_max)][field: ng_max T2 (FP64: E_p, E_p+1; FP32: E_p, E_p+1 - E_p)]
+// [deposition: 3 x ng_max u32][tile prefix: nd+1 int][xt variant, from the
+// next 16-byte boundary: sum w v_c,x and sum w eps_c, ng_max T each].
 template <typename T, bool XT, int SH>
 __host__ __device__ constexpr size_t push_smem_bytes(int nd, int ng_max, int eepf_max)
 {
@@ -1218,10 +1196,9 @@ __global__ void __launch_bounds__(shape_of<T, XT, SH>().threads, shape_of<T, XT,
     int since_flush = 0;
     T xa[VEC], vxa[VEC], vya[VEC], vza[VEC];  // particles of this thread in the current tile
 
-    // Producer (thread 0): bulk-copy tile `pt` (x, vx, vy, vz; a whole TILE,
-    // inside the padded capacity) into ring stage `st`.
-    // Tile ring: every thread copies its own VEC particles (16 bytes per array)
-    // of tile `pt` into stage `st` and reads back only those, so no thread
+    // Tile ring: every thread copies its own VEC particles (16 bytes per array;
+    // whole tiles stay inside the padded capacity) of tile `pt` into stage
+    // `st` and reads back only those, so no thread
     // waits for another; each tile is one commit group, S - 1 tiles ahead.
     // The discharge of the tile being fetched (pcur) is cached with its tile
     // range and this thread's source address in its x array; v_x, v_y, v_z

@@ -181,6 +181,24 @@ int edupic_destroy(edupic_sim *sim);
 int edupic_set_cross_sections(edupic_sim *sim, int species, int n_proc, int n_entries, double de_ev,
                               const double *sigma_m2);
 
+/* The electrons' collision-test bound that edupic_set_cross_sections forms
+ * (host computation only, no device; for inspection).  The direct test of
+ * Algorithm 6 compares the test uniform with P_coll = 1 - exp(-n sigma_tot v
+ * dt); the particle kernel first compares it with a bound per v^2 bucket:
+ * the bucket of a squared speed w is the exponent and top five mantissa bits
+ * of w in the particle precision (FP32: bits >> 18; FP64: bits >> 47),
+ * clamped to [*base_out, *base_out + *n_out - 1].  Entry j - *base_out of
+ * table_out holds the largest sigma_tot,k times the speed at the bucket's
+ * top over every entry k a w of the bucket can index (nearest entry, one
+ * entry of margin each side), widened by 1e-6 and rounded up in the
+ * particle precision; the kernel multiplies it by n dt.  The last bucket is
+ * +inf.  sigma_sum: host, n_entries values of the summed electron cross
+ * sections (m^2) at energies k*de_ev; table_out: host, EDUPIC_BOUND_BUCKETS
+ * doubles (entries past *n_out are +inf).  EDUPIC_EINVAL on a bad argument. */
+#define EDUPIC_BOUND_BUCKETS 2048
+int edupic_electron_bound_table(int precision, int n_entries, double de_ev, const double *sigma_sum,
+                                double *table_out, int *base_out, int *n_out);
+
 /* Replace the particles of one species of discharge d (host FP64 arrays of n
  * entries; stored as FP32 in EDUPIC_FP32 mode).  The densities of that species
  * and the field of the current step are recomputed (Algorithms 2-3), as the

@@ -561,7 +561,7 @@ static T lv_lower(uint64_t j)
 // the bucket lies below it.  Buckets above the table's last entry (where the
 // clamped entry meets unbounded speeds) and the last bucket are +inf.
 template <typename T>
-void lv_table(edupic_sim *S, const std::vector<T> &sum, double de_ev, std::vector<T> &out)
+void lv_table(const std::vector<T> &sum, double de_ev, std::vector<T> &out, int &base, int &nbuckets)
 {
     const int n = (int)sum.size();
     // the entry index of v^2 as the kernel forms it (FP32: v^2 * s + 0.5 with
@@ -588,8 +588,8 @@ void lv_table(edupic_sim *S, const std::vector<T> &sum, double de_ev, std::vecto
         if ((double)t < v) t = std::nextafter(t, (T)INFINITY);
         out[(size_t)j] = t;
     }
-    S->lv_base_pending = (int)j0;
-    S->lv_n_pending = nb;
+    base = (int)j0;
+    nbuckets = nb;
 }
 
 template <typename T>
@@ -600,7 +600,7 @@ int upload_tables(edupic_sim *S, int species, int n_proc, int n_entries, double 
     for (int k = 0; k < n_entries; ++k) {
         const double s0 = sig[k], s1 = sig[(size_t)n_entries + k];
         const double s2 = n_proc == 3 ? sig[2 * (size_t)n_entries + k] : 0.0;
-        // processes summed in order, as calc_total_cross_sections() does
+        // the processes summed in their order (elastic, excitation, ionisation)
         const double stot = n_proc == 3 ? s0 + s1 + s2 : s0 + s1;
         sum[k] = (T)stot;
         thr[2 * (size_t)k] = (T)(s0 / stot);
@@ -636,7 +636,7 @@ int upload_tables(edupic_sim *S, int species, int n_proc, int n_entries, double 
         for (int j = ((n_entries - 1) >> shift) + 1; j < kCoarse; ++j) pmax[j] = pmax[j - 1];
     }
     S->cs_shift_pending[species] = shift;
-    if (species == 0) lv_table<T>(S, sum, de_ev, cmax);
+    if (species == 0) lv_table<T>(sum, de_ev, cmax, S->lv_base_pending, S->lv_n_pending);
     cudaError_t e = cudaMemcpyAsync(S->cs_max[species], cmax.data(), sizeof(T) * kCoarse, cudaMemcpyHostToDevice,
                                     S->stream);
     if (e == cudaSuccess)
@@ -988,6 +988,29 @@ int edupic_destroy(edupic_sim *S)
     if (!S) return EDUPIC_EINVAL;
     if (S->stream) cudaStreamSynchronize(S->stream);
     delete S;
+    return EDUPIC_OK;
+}
+
+int edupic_electron_bound_table(int precision, int n_entries, double de_ev, const double *sigma_sum,
+                                double *table_out, int *base_out, int *n_out)
+{
+    if (!sigma_sum || !table_out || !base_out || !n_out || n_entries < 1 || !(de_ev > 0) ||
+        (precision != EDUPIC_FP32 && precision != EDUPIC_FP64))
+        return EDUPIC_EINVAL;
+    static_assert(EDUPIC_BOUND_BUCKETS == kCoarse, "the header states the table's length");
+    for (int k = 0; k < n_entries; ++k)
+        if (!(sigma_sum[k] >= 0) || !std::isfinite(sigma_sum[k])) return EDUPIC_EINVAL;
+    auto run = [&](auto zero) {
+        using T = decltype(zero);
+        std::vector<T> sum((size_t)n_entries), out;
+        for (int k = 0; k < n_entries; ++k) sum[(size_t)k] = (T)sigma_sum[k];
+        lv_table<T>(sum, de_ev, out, *base_out, *n_out);
+        for (int j = 0; j < kCoarse; ++j) table_out[j] = (double)out[(size_t)j];
+    };
+    if (precision == EDUPIC_FP32)
+        run(0.0f);
+    else
+        run(0.0);
     return EDUPIC_OK;
 }
 

@@ -24,6 +24,7 @@ MAX_HARMONICS = 4
 N_COUNTERS = 19
 XT_NAMES = ("pot", "efield", "ne", "ni", "je", "ji", "powere", "poweri", "meanee", "meanei", "ioniz")
 STEP_EVENTS = 65536
+BOUND_BUCKETS = 2048
 COUNTER_NAMES = ("abs_e_pow", "abs_e_gnd", "abs_i_pow", "abs_i_gnd", "coll_e_ela", "coll_e_exc",
                  "coll_e_ion", "coll_i_iso", "coll_i_back", "subthreshold", "created", "dropped",
                  "push_e", "push_i", "reflected", "emitted_pow", "emitted_gnd",
@@ -136,6 +137,8 @@ def load_library(path: str = LIB_PATH):
         "edupic_get_push_grid": ([_VP, ctypes.POINTER(ctypes.c_int)]),
         "edupic_set_push_shape": ([_VP, ctypes.c_int, ctypes.c_int]),
         "edupic_get_push_shape": ([_VP, ctypes.POINTER(ctypes.c_int)]),
+        "edupic_electron_bound_table": ([ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "edupic_describe_push_shape": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "edupic_autotune": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]),
@@ -436,6 +439,18 @@ def describe_push_shape(precision: int, shape: int) -> dict:
     _ck(L.edupic_describe_push_shape(precision, shape, ctypes.byref(t), ctypes.byref(s), ctypes.byref(m)),
         "describe_push_shape")
     return dict(threads=t.value, stages=s.value, min_blocks=m.value)
+
+
+def electron_bound_table(precision: int, sigma_sum, de_ev: float):
+    """The electrons' collision bound per v^2 bucket (edupic_electron_bound_table):
+    (table of BOUND_BUCKETS values, first bucket, number of buckets)."""
+    L = load_library()
+    sig = np.ascontiguousarray(sigma_sum, dtype=np.float64)
+    out = np.zeros(BOUND_BUCKETS)
+    base, nb = ctypes.c_int(), ctypes.c_int()
+    _ck(L.edupic_electron_bound_table(precision, int(sig.size), float(de_ev), _ptr(sig), _ptr(out),
+                                      ctypes.byref(base), ctypes.byref(nb)), "electron_bound_table")
+    return out, base.value, nb.value
 
 
 def simulation_for(discharges: Iterable, precision: int = FP64, sigma=None, de_ev: float = 1e-3,
